@@ -1,0 +1,193 @@
+"""FP64 CPU oracle of batched HMC for the SPS posterior (TEST INFRASTRUCTURE ONLY).
+
+Restates the sampler of Sec. 4 and App. D.2: Hamiltonian Monte Carlo with a
+leapfrog integrator, a fixed number of leapfrog steps per trajectory drawn
+per iteration, a Metropolis accept on the energy difference, and step-size
+adaptation during a warm-up phase.  The paper runs Blackjax HMC; it does not
+print the adaptation constants or the trajectory-length rule, so the
+declared readings are:
+
+* identity mass matrix; trajectory length L ~ U{L_min .. L_max} per iteration;
+* step size adapted per chain by the dual-averaging scheme of Hoffman &
+  Gelman (2014, Sec. 3.2.1) with target 0.8, gamma 0.05, t0 10, kappa 0.75,
+  mu = log(10 eps0); warm-up uses eps_m, sampling uses the averaged eps-bar;
+* random numbers from Philox-4x32-10 (Salmon et al. 2011), keyed by the
+  64-bit seed, counter (iteration, block, chain, 0): blocks 0-2 give twelve
+  uniforms -> six Box-Muller pairs of momenta, block 3 gives the accept
+  uniform (word 0) and L (word 1, L = L_min + (word * n) >> 32 with
+  n = L_max - L_min + 1, an exact integer rule).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import sps as O
+
+PHILOX_M0 = 0xD2511F53
+PHILOX_M1 = 0xCD9E8D57
+PHILOX_W0 = 0x9E3779B9
+PHILOX_W1 = 0xBB67AE85
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11).
+
+    ctr: [..., 4] integers < 2^32, key: [..., 2].  Each round multiplies
+    words 0 and 2 by M0, M1 (64-bit products), mixes the high halves with
+    words 1, 3 and the key, and the key is bumped by the Weyl constants
+    between rounds.  Returns [..., 4] uint64 holding 32-bit words."""
+    c = [np.asarray(ctr[..., i], dtype=np.uint64) & _MASK32 for i in range(4)]
+    k0 = np.asarray(key[..., 0], dtype=np.uint64) & _MASK32
+    k1 = np.asarray(key[..., 1], dtype=np.uint64) & _MASK32
+    for _ in range(10):
+        p0 = np.uint64(PHILOX_M0) * c[0]
+        p1 = np.uint64(PHILOX_M1) * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK32
+        c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+        k0 = (k0 + np.uint64(PHILOX_W0)) & _MASK32
+        k1 = (k1 + np.uint64(PHILOX_W1)) & _MASK32
+    return np.stack(c, axis=-1)
+
+
+def uniform01(words):
+    """32-bit word -> (word + 1/2) / 2^32 in (0, 1), exact in float64."""
+    return (np.asarray(words, dtype=np.float64) + 0.5) * 2.0 ** -32
+
+
+def draws(seed: int, chains: np.ndarray, it: int, L_min: int, L_max: int):
+    """Momenta [C, 12], accept uniforms [C] and trajectory lengths [C] of
+    iteration `it` for the given chain ids (the counter layout above)."""
+    chains = np.asarray(chains, dtype=np.uint64)
+    n = chains.shape[0]
+    key = np.zeros((n, 2), np.uint64)
+    key[:, 0] = np.uint64(seed & 0xFFFFFFFF)
+    key[:, 1] = np.uint64((seed >> 32) & 0xFFFFFFFF)
+    words = []
+    for blk in range(4):
+        ctr = np.zeros((n, 4), np.uint64)
+        ctr[:, 0] = np.uint64(it)
+        ctr[:, 1] = np.uint64(blk)
+        ctr[:, 2] = chains & _MASK32
+        words.append(philox4x32_10(ctr, key))
+    u = uniform01(np.concatenate(words[:3], axis=1))               # [n, 12]
+    u1, u2 = u[:, 0::2], u[:, 1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    p = np.empty((n, 12))
+    p[:, 0::2] = r * np.cos(2.0 * math.pi * u2)
+    p[:, 1::2] = r * np.sin(2.0 * math.pi * u2)
+    u_acc = uniform01(words[3][:, 0])
+    span = np.uint64(L_max - L_min + 1)
+    L = (L_min + ((words[3][:, 1] * span) >> np.uint64(32))).astype(np.int64)
+    return p, u_acc, L
+
+
+class ApproxTarget:
+    """log posterior in unbounded space, approximate photometry, with the
+    per-galaxy redshift-dependent pieces (c_SSP, lambda_eff, N_b, distance
+    factor) computed once, as Sec. 3 allows when z is known."""
+
+    def __init__(self, tables, z, mag_obs, sigma, mask, lo, hi):
+        z = O._t(z)
+        self.tables = tables
+        self.cssp = O.c_ssp(tables, z)                      # [G, B, K]
+        self.lam_eff = O.lambda_eff(tables, z)              # [G, B]
+        _, self.nb, _ = O.band_weights(tables, z)
+        dl_cm = O.lum_dist_mpc(z.numpy()) * O.MPC_CM
+        self.fac = (1.0 + z) * O.L_SUN_ERG_S / (4.0 * math.pi * dl_cm ** 2 * O.AB_ZP_CGS)
+        self.t_obs = O.t_obs_gyr(z)
+        self.mag_obs, self.sigma = O._t(mag_obs), O._t(sigma)
+        self.mask = np.asarray(mask)
+        self.lo, self.hi = O._t(lo), O._t(hi)
+
+    def mags(self, theta, rows):
+        W, _, _, _ = O.ssp_weights(theta, self.tables, self.t_obs[rows])
+        F = O.attenuation(self.lam_eff[rows], theta[:, 9:10], theta[:, 10:11], theta[:, 11:12])
+        c = F * torch.einsum("nbk,nk->nb", self.cssp[rows], W.reshape(W.shape[0], -1))
+        return -2.5 * torch.log10(self.fac[rows, None] * c / self.nb[rows])
+
+    def __call__(self, x, rows):
+        x = O._t(x).clone().requires_grad_(True)
+        th = O.bound(x, self.lo, self.hi)
+        mag = self.mags(th, rows)
+        lp = O.loglike(mag, self.mag_obs[rows], self.sigma[rows], self.mask[rows]) \
+            + O.log_prior_unbounded(x)
+        (g,) = torch.autograd.grad(lp.sum(), x)
+        return lp.detach().numpy(), g.detach().numpy()
+
+
+def leapfrog(target, rows, x, p, g, eps, L):
+    """L leapfrog steps (half kick, drift, gradient, half kick), per chain
+    lengths L; returns the end point, its momentum, log p and gradient."""
+    x, p, g = x.copy(), p.copy(), g.copy()
+    lp = np.full(x.shape[0], np.nan)
+    Lmax = int(np.max(L)) if len(L) else 0
+    for step in range(Lmax):
+        act = step < L
+        if not act.any():
+            break
+        e = eps[act, None]
+        p[act] += 0.5 * e * g[act]
+        x[act] += e * p[act]
+        lpa, ga = target(x[act], rows[act])
+        g[act] = ga
+        lp[act] = lpa
+        p[act] += 0.5 * e * g[act]
+    return x, p, g, lp
+
+
+def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
+            eps0=0.1, target_accept=0.8, gamma=0.05, t0=10.0, kappa=0.75,
+            chain_ids=None):
+    """Batched HMC over independent chains (Sec. 4, App. D.2).
+
+    Returns dict with samples [C, n_samp, 12] (bounded parameters),
+    accept_prob [C] (mean over sampling), eps [C], divergences [C],
+    grad_evals [C]."""
+    x = np.array(x0, dtype=np.float64)
+    C = x.shape[0]
+    rows = np.asarray(gal_of_chain)
+    ids = np.arange(C) if chain_ids is None else np.asarray(chain_ids)
+    lp, g = target(x, rows)
+    eps = np.full(C, eps0)
+    mu = math.log(10.0 * eps0)
+    hbar = np.zeros(C)
+    log_eps_bar = np.zeros(C)
+    samples = np.zeros((C, n_samp, x.shape[1]))
+    acc_sum = np.zeros(C)
+    warm_acc = np.zeros(C)
+    div = np.zeros(C, np.int64)
+    nevals = np.zeros(C, np.int64)
+    for it in range(n_warm + n_samp):
+        p, u, L = draws(seed, ids, it, L_min, L_max)
+        x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L)
+        nevals += L
+        h0 = -lp + 0.5 * (p * p).sum(1)
+        h1 = -lp1 + 0.5 * (p1 * p1).sum(1)
+        dh = h1 - h0
+        finite = np.isfinite(dh)
+        a = np.where(finite, np.minimum(1.0, np.exp(-np.where(finite, dh, 0.0))), 0.0)
+        div += (~finite) | (np.where(finite, dh, 0.0) > 1000.0)
+        take = finite & (np.log(u) < -np.where(finite, dh, np.inf))
+        x[take], g[take], lp[take] = x1[take], g1[take], lp1[take]
+        if it < n_warm:
+            if it >= n_warm // 2:
+                warm_acc += a
+            m = it + 1
+            hbar = (1.0 - 1.0 / (m + t0)) * hbar + (target_accept - a) / (m + t0)
+            log_eps = mu - math.sqrt(m) / gamma * hbar
+            w = m ** -kappa
+            log_eps_bar = w * log_eps + (1.0 - w) * log_eps_bar
+            eps = np.exp(log_eps) if it < n_warm - 1 else np.exp(log_eps_bar)
+        else:
+            s = it - n_warm
+            th = O.bound(torch.as_tensor(x), target.lo, target.hi).numpy()
+            samples[:, s] = th
+            acc_sum += a
+    return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps,
+                warm_accept=warm_acc / max(n_warm - n_warm // 2, 1),
+                divergences=div, grad_evals=nevals)

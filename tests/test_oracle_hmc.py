@@ -1,0 +1,125 @@
+"""Pins of the HMC and diagnostics oracle (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import sps_workloads as W
+from oracle import diagnostics as D
+from oracle import hmc as H
+
+
+def test_philox_words_are_uniform_and_decorrelated():
+    n = 50_000
+    ctr = np.zeros((n, 4), np.uint64)
+    ctr[:, 0] = np.arange(n)
+    key = np.tile(np.array([12345, 678], np.uint64), (n, 1))
+    w = H.philox4x32_10(ctr, key)
+    assert w.max() < 2 ** 32
+    u = H.uniform01(w).ravel()
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # neighbouring counters give uncorrelated outputs
+    a = H.uniform01(w[:-1, 0])
+    b = H.uniform01(w[1:, 0])
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.02
+    # one flipped counter bit changes about half of the 128 output bits
+    ctr2 = ctr.copy()
+    ctr2[:, 1] ^= np.uint64(1)
+    w2 = H.philox4x32_10(ctr2, key)
+    flips = np.unpackbits((w ^ w2).astype(">u4").view(np.uint8)).reshape(n, -1).sum(1)
+    assert abs(flips.mean() - 64.0) < 0.5
+
+
+def test_momentum_and_length_draws():
+    p, u, L = H.draws(99, np.arange(4000), 3, 8, 64)
+    assert p.shape == (4000, 12)
+    assert stats.kstest(p.ravel(), "norm").pvalue > 1e-3
+    assert (u > 0).all() and (u < 1).all()
+    assert L.min() == 8 and L.max() == 64
+    counts = np.bincount(L - 8, minlength=57)
+    assert stats.chisquare(counts).pvalue > 1e-3
+    # counter-based: a chain's draws do not depend on which other chains run
+    p1, _, L1 = H.draws(99, np.array([17]), 3, 8, 64)
+    np.testing.assert_array_equal(p1[0], p[17])
+    assert L1[0] == L[17]
+
+
+class _Uniform:
+    """Prior-only target: uniform in theta on [0, 1] => logistic in the
+    unbounded coordinate (Eq. BoundingFunction with k = 1, x0 = 0)."""
+    lo = torch.zeros(12, dtype=torch.float64)
+    hi = torch.ones(12, dtype=torch.float64)
+
+    def __call__(self, x, rows):
+        x = np.asarray(x)
+        lp = -(np.abs(x) + 2 * np.log1p(np.exp(-np.abs(x)))).sum(1)
+        g = 1.0 - 2.0 / (1.0 + np.exp(-x))
+        return lp, g
+
+
+def test_hmc_samples_the_prior_when_no_band_is_observed():
+    """With no data the posterior is the prior, uniform in each bounded
+    parameter: checks detailed balance and the adaptation, independently
+    of the oracle's photometry."""
+    C = 64
+    x0 = np.random.default_rng(0).normal(0, 2, size=(C, 12))
+    out = H.run_hmc(_Uniform(), x0, np.zeros(C, int), seed=7, n_warm=150, n_samp=150,
+                    L_min=4, L_max=12)
+    s = out["samples"].reshape(-1, 12)
+    for k in range(12):
+        assert stats.kstest(s[::7, k], "uniform").pvalue > 1e-4
+    assert abs(s.mean() - 0.5) < 0.01
+    assert abs(s.var() - 1 / 12) < 0.004
+    # dual averaging drives the warm-up mean acceptance to its target; the
+    # averaged step size used afterwards is smaller, so acceptance rises
+    assert abs(out["warm_accept"].mean() - 0.8) < 0.03
+    assert out["accept_prob"].mean() > out["warm_accept"].mean()
+
+
+def _sps_target(n_gal=2):
+    wl = W.config(3, n_gal=n_gal)
+    from oracle import sps as O
+    th = torch.as_tensor(wl.theta_true, dtype=torch.float64)
+    mobs = O.photometry(th, wl.z, wl.tables, "approx").numpy() + wl.noise
+    t = H.ApproxTarget(wl.tables, wl.z, mobs, wl.sigma, wl.mask, W.PRIOR_LO, W.PRIOR_HI)
+    x0 = W.unbounded_of(wl.theta_true)
+    return t, x0
+
+
+def test_leapfrog_is_reversible_and_second_order():
+    t, x0 = _sps_target()
+    rows = np.arange(2)
+    lp0, g0 = t(x0, rows)
+    p0 = np.random.default_rng(1).normal(size=x0.shape)
+    L = np.array([10, 10])
+    x1, p1, g1, lp1 = H.leapfrog(t, rows, x0, p0, g0, np.full(2, 1e-3), L)
+    x2, p2, _, _ = H.leapfrog(t, rows, x1, -p1, g1, np.full(2, 1e-3), L)
+    np.testing.assert_allclose(x2, x0, atol=1e-9)
+    np.testing.assert_allclose(-p2, p0, atol=1e-7)
+    # energy error shrinks ~ eps^2 at fixed trajectory length
+    dh = []
+    for eps, n in ((4e-4, 10), (2e-4, 20)):
+        x1, p1, _, lp1 = H.leapfrog(t, rows, x0, p0, g0, np.full(2, eps), np.array([n, n]))
+        dh.append(np.abs((-lp1 + 0.5 * (p1 * p1).sum(1)) - (-lp0 + 0.5 * (p0 * p0).sum(1))))
+    ratio = dh[0] / dh[1]
+    assert ((ratio > 3.0) & (ratio < 5.0)).all()
+
+
+def test_ess_and_rhat_pins():
+    rng = np.random.default_rng(3)
+    iid = rng.normal(size=(4, 2000))
+    assert D.ess(iid) == pytest.approx(8000, rel=0.1)
+    assert D.split_rhat(iid) < 1.01
+    rho = 0.9
+    ar = np.zeros((4, 4000))
+    e = rng.normal(size=(4, 4000))
+    for t in range(1, 4000):
+        ar[:, t] = rho * ar[:, t - 1] + math.sqrt(1 - rho ** 2) * e[:, t]
+    assert D.ess(ar) == pytest.approx(16000 * (1 - rho) / (1 + rho), rel=0.25)
+    shifted = iid + np.arange(4)[:, None]
+    assert D.split_rhat(shifted) > 1.2
+    tot, per = D.posteriors_at_ess(np.stack([iid.T, iid.T[::-1]], 0).reshape(2, 2000, 4)
+                                   .transpose(0, 1, 2), chains_per_gal=1)
+    assert tot == pytest.approx(2.0)
