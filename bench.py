@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: batched HMC posteriors per minute at fixed ESS on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+4,096 galaxies x 4 chains, production SSP grid (107 ages x 12 metallicities x
+5,994 wavelengths), 12 Gaussian bands 300-2400 nm with 3-12 observed per
+galaxy, trajectory lengths U(8, 64), 500 warm-up + 500 sampling iterations,
+per-chain dual-averaged step size, approximate photometry, one persistent
+graph-captured launch.  Inputs are synthetic and seeded (sps_workloads);
+observed magnitudes are the model at a seeded truth plus N(0, 0.05) noise.
+
+value = sum_g min(1, ESS_g / 100) / (minutes per step), ESS_g the minimum over
+the 12 parameters of the multi-chain ESS of galaxy g.
+
+Also reported: log-likelihood + gradient evaluations per second on 100,000
+(galaxy, chain) pairs (approximate FP32, exact FP32, exact BF16), the
+roofline of the dominant kernel, the clocks seen during the timed region,
+an end-to-end number through the C ABI with host buffers, and the FP64
+oracle timed on a bounded sample on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sps_workloads as W  # noqa: E402
+
+ESS_TARGET = 100.0
+METRIC = "posteriors/min at fixed ESS"
+UNIT = "posteriors/min"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SPS_BENCH_GLOO") is None else "gloo")
+    return ws, rank
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _hmc_workload(rank: int, n_gal: int | None = None):
+    wl = W.config(3, n_gal=n_gal, seed_offset=rank)
+    return wl
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    from paper_2506_19919_gb300 import _lib
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = _hmc_workload(rank)
+    G, C = wl.n_gal, wl.chains
+    n_warm, n_samp = wl.extra["n_warm"], wl.extra["n_samp"]
+    ctx = pkg.Context(wl.tables, device=local)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    # data: the model at the seeded truth plus seeded noise
+    mtrue = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev),
+                           mode="approx")
+    mobs = (mtrue + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)).contiguous()
+    sigma = torch.as_tensor(wl.sigma, dtype=torch.float32, device=dev)
+    mask = torch.as_tensor(wl.mask.view(np.int32), device=dev)
+    x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
+    NC = G * C
+    samples = torch.empty((NC, n_samp, 12), dtype=torch.float32, device=dev)
+    stats = {k: torch.empty(NC, dtype=t, device=dev) for k, t in
+             (("accept_prob", torch.float32), ("step_size", torch.float32),
+              ("divergences", torch.int32), ("grad_evals", torch.int64), ("status", torch.int32))}
+    cfg = _lib.sps_hmc_config()
+    lib = _lib.load()
+    lib.sps_hmc_config_default(__import__("ctypes").byref(cfg))
+    cfg.chains_per_gal, cfg.n_warm, cfg.n_samp = C, n_warm, n_samp
+    cfg.L_min, cfg.L_max = wl.extra["L_min"], wl.extra["L_max"]
+    cfg.seed = 2506199190 + rank
+    cfg.use_graph, cfg.autotune = 1, 1
+    import ctypes as Ct
+    st = _lib.sps_hmc_stats(*(Ct.c_void_p(stats[k].data_ptr()) for k in
+                              ("accept_prob", "step_size", "divergences", "grad_evals", "status")))
+    stream = torch.cuda.current_stream(dev)
+    sp = Ct.c_void_p(stream.cuda_stream)
+    vp = lambda t: Ct.c_void_p(t.data_ptr())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        _lib.check(lib.sps_hmc_run(ctx.h, Ct.byref(cfg), vp(x0), vp(mobs), vp(sigma), vp(mask),
+                                   vp(samples), Ct.byref(st), sp), "sps_hmc_run")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                    # L2 flush between timed steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = _max_over_ranks(float(np.mean(kern_ms)), ws)
+
+    # ESS from the last step's draws (host diagnostics, outside the timed region)
+    ess, rhat = pkg.diagnostics(samples, G, C)
+    ess_g = ess.min(1)
+    post = float(np.minimum(1.0, ess_g / ESS_TARGET).sum())
+    value = post * ws / (ms_step / 60000.0)
+    nev = stats["grad_evals"].cpu().numpy()
+    nb = np.array([bin(int(m)).count("1") for m in wl.mask])
+    K = wl.tables.n_age * wl.tables.n_met
+    flop = float(((4 * nb * K)[:, None] * nev.reshape(G, C)).sum())
+    peaks, src = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s, FMA pipe
+    achieved = flop / (ms_step / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": W.CONFIG_NAMES[3], "galaxies": G, "chains_per_gal": C,
+                   "n_warm": n_warm, "n_samp": n_samp, "L": [cfg.L_min, cfg.L_max],
+                   "ssp_grid": [wl.tables.n_age, wl.tables.n_met, wl.tables.n_lam],
+                   "bands": wl.tables.n_band, "photometry": "approx",
+                   "l2": "flushed (256 MB write) between timed steps; working set > L2",
+                   "parallelism": f"replicas{ws}"},
+        "ess": {"target": ESS_TARGET, "galaxies_at_target": int((ess_g >= ESS_TARGET).sum()),
+                "median_ess": float(np.median(ess_g)), "median_rhat_max": float(np.median(rhat.max(1))),
+                "frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean()),
+                "accept_mean": float(stats["accept_prob"].mean()),
+                "divergences": int(stats["divergences"].sum())},
+        "grad_evals_per_s": float(nev.sum()) * ws / (ms_step / 1e3),
+        "roofline": {"kernel": "k_hmc_approx", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived)",
+                     "algorithmic": "4 * n_obs_bands * K FLOP per gradient evaluation"},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+        "wall_s": wall,
+    }
+    if rank == 0 and not args.skip_extra:
+        out["loglike_grad"] = _loglike_grad_rates(ctx, dev)
+    if rank == 0 and not args.skip_e2e:
+        out["e2e"] = _e2e(ctx, cfg, lib, wl, mobs, x0, post, ws)
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        out["cpu_baseline"] = _cpu_baseline(wl, mobs.cpu().numpy(), post / G, budget_s=args.cpu_budget)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
+    """Same metric through the C ABI with host buffers: the call stages the
+    inputs to the device and copies the draws back inside the timed region."""
+    import ctypes as Ct
+
+    from paper_2506_19919_gb300 import _lib
+    G, C = wl.n_gal, wl.chains
+    NC = G * C
+    x0 = np.ascontiguousarray(x0_dev.cpu().numpy())
+    mobs = np.ascontiguousarray(mobs_dev.cpu().numpy())
+    sigma = np.ascontiguousarray(wl.sigma.astype(np.float32))
+    mask = np.ascontiguousarray(wl.mask)
+    samples = np.empty((NC, cfg.n_samp, 12), np.float32)
+    acc = np.empty(NC, np.float32)
+    st = _lib.sps_hmc_stats(acc.ctypes.data, None, None, None, None)
+    vp = lambda a: Ct.c_void_p(a.ctypes.data)
+    times = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        _lib.check(lib.sps_hmc_run(ctx.h, Ct.byref(cfg), vp(x0), vp(mobs), vp(sigma), vp(mask),
+                                   vp(samples), Ct.byref(st), None), "sps_hmc_run (host)")
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    h2d = x0.nbytes + mobs.nbytes + sigma.nbytes + mask.nbytes + 4 * G
+    d2h = samples.nbytes + acc.nbytes
+    return {"value": post * ws / (t / 60.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "s_per_step": t}
+
+
+def _loglike_grad_rates(ctx_hmc, dev):
+    """loglike + gradient evaluations per second on 100,000 pairs."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    wl = W.config(2)
+    ctx = pkg.Context(wl.tables, device=dev.index)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    th = torch.as_tensor(wl.theta, dtype=torch.float32, device=dev)
+    mobs = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev),
+                          mode="approx") + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)
+    res = {"pairs": wl.n_gal, "workload": W.CONFIG_NAMES[2]}
+    for mode, prec, reps in (("approx", "fp32", 10), ("exact", "fp32", 2), ("exact", "bf16", 2)):
+        ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[f"{mode}_{prec}"] = {"evals_per_s": wl.n_gal / (ms / 1e3), "ms": ms}
+    ctx.close()
+    return res
+
+
+def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
+    """The FP64 oracle's HMC, as it stands, on a bounded sample of the same
+    workload (2 galaxies x 4 chains, a few iterations), extrapolated to the
+    full 1,000-iteration run per galaxy; the ESS fraction per galaxy is taken
+    from the GPU run of the same sampler."""
+    import torch
+
+    from oracle import hmc as OH
+    n = 2
+    tgt = OH.ApproxTarget(wl.tables, wl.z[:n], mobs[:n], wl.sigma[:n], wl.mask[:n],
+                          W.PRIOR_LO, W.PRIOR_HI)
+    x0 = wl.extra["theta0_unb"][: n * wl.chains]
+    it_total = wl.extra["n_warm"] + wl.extra["n_samp"]
+    t0 = time.perf_counter()
+    iters = 0
+    while True:
+        OH.run_hmc(tgt, x0, np.repeat(np.arange(n), wl.chains), seed=1, n_warm=1, n_samp=0,
+                   L_min=wl.extra["L_min"], L_max=wl.extra["L_max"])
+        iters += 1
+        if time.perf_counter() - t0 > budget_s or iters >= 50:
+            break
+    dt = (time.perf_counter() - t0) / iters          # s per iteration for n galaxies
+    s_per_gal = dt * it_total / n
+    value = post_frac * 60.0 / s_per_gal
+    return {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n} galaxies x {wl.chains} chains x {iters} iterations of the FP64 "
+                      f"oracle HMC ({dt:.2f} s/iteration), extrapolated to {it_total} iterations "
+                      f"per galaxy; ESS fraction per galaxy from the GPU run"}
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores (rank 0 only)."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    wl = _hmc_workload(0, n_gal=2)
+    from oracle import sps as O
+    mobs = O.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float64), wl.z, wl.tables,
+                        "approx").numpy() + wl.noise
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        cb = _cpu_baseline(wl, mobs, 1.0, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+        steps.append(cb)
+    vals = [s["value"] for s in steps[args.warmup:]]
+    v = float(np.mean(vals))
+    cb = dict(steps[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": W.CONFIG_NAMES[3], "photometry": "approx",
+                      "note": "ESS fraction assumed 1 per galaxy (upper bound for the oracle)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * sps.h - C ABI of the GB300 (sm_103a) SPS photometry / likelihood / HMC library.
+ *
+ * The library evaluates, for every (galaxy, chain) row, the stellar population
+ * synthesis model of arXiv 2506.19919 and its Gaussian photometric likelihood:
+ *
+ *   L_gal(lambda) = M_star sum_ij L_SSP(lambda | tau_i, Z_j) F_att(lambda) P_SFH(tau_i) P_met(Z_j)
+ *                                                      (Eq. galSEDdef, Eq. galSED_decomposed)
+ *   c_b = int dlambda T_b(lambda | z) L_gal(lambda)     (Eq. photo_integral_exact)
+ *   c_b ~ F_att(lambda_eff,b) sum_ij P_ij c_SSP,b,ij(z) (Eq. lambda_eff, Eq. photo_integral_approx)
+ *   log L = -1/2 sum_b ((m_b - m_obs,b) / sigma_b)^2    (App. D.1)
+ *
+ * and runs batched Hamiltonian Monte Carlo over it (Sec. 4, App. D.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Parameters: 12 physical columns per row, in this order (App. A.1-A.3):
+ *      0 lgM       log10 SFR amplitude M_formed [M_sun/yr] (Eq. SFRsmooth)
+ *      1 tau       double-power-law turnover time [Gyr]
+ *      2 alpha     falling slope          3 beta   rising slope
+ *      4 F_burst   burst mass fraction (Eq. composite_age_weights)
+ *      5 lgT_peak  log10 burst peak age [yr] (Eq. triweight)
+ *      6 dlgT      log10 T_max - log10 T_peak [dex] (sigma_burst = dlgT / 3)
+ *      7 lgZ       mean of the Gaussian in log10 Z/Z_sun (App. A.2)
+ *      8 sigma_lgZ width of that Gaussian [dex]
+ *      9 A_V       10 delta   11 F_floor   (Eq. DustAtt and the F_floor equation)
+ *    The redshift is per galaxy and fixed (it is data, not a parameter).
+ *  - Rows are (galaxy, chain) pairs.  A row refers to a galaxy of the set given
+ *    to sps_set_galaxies, either by gal_idx[row] or, when gal_idx is NULL, by
+ *    row == galaxy (then n must equal the galaxy count).
+ *  - Every array argument may be a host pointer or a device pointer of the
+ *    context's device; the library detects which (cudaPointerGetAttributes)
+ *    and stages host arrays through its own device buffers.  With device
+ *    pointers the call is asynchronous on `stream` (a cudaStream_t, NULL =
+ *    legacy default stream); with any host pointer it synchronises `stream`
+ *    before returning.  The caller keeps ownership of every array.
+ *  - Row-major, C-contiguous layouts; float32 unless stated.
+ *  - Errors are returned as sps_status; nothing is thrown across the ABI.
+ *    Shapes and arguments are checked on the host before any launch.  After
+ *    SPS_E_CUDA the context should be destroyed.  sps_last_error_message()
+ *    gives a human-readable reason for the last failure of this thread.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef SPS_GB300_H
+#define SPS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPS_NPARAM 12
+#define SPS_MAX_BANDS 32
+#define SPS_MAX_AGES 128
+#define SPS_MAX_METS 32
+
+typedef struct sps_ctx sps_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    SPS_OK = 0,
+    SPS_E_INVALID_ARG = 1, /* NULL pointer, bad enum, non-increasing grid, bad band */
+    SPS_E_SHAPE = 2,       /* sizes out of range or inconsistent                   */
+    SPS_E_NONFINITE = 3,   /* some output rows are NaN because inputs were         */
+    SPS_E_CUDA = 4,        /* a CUDA runtime call failed                          */
+    SPS_E_TIMEOUT = 5,     /* a bounded device wait gave up (HMC work queue)       */
+    SPS_E_UNSUPPORTED = 6, /* mode / precision / device not supported              */
+    SPS_E_STATE = 7,       /* call order: e.g. no galaxy set, or no approx tables */
+    SPS_E_NOMEM = 8        /* device allocation failed                             */
+} sps_status;
+
+typedef enum { SPS_EXACT = 0, SPS_APPROX = 1 } sps_mode;
+typedef enum { SPS_FP32 = 0, SPS_BF16 = 1 } sps_prec;
+typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1 } sps_band_kind;
+
+/* Model grids, SSP table and filters (host memory, float64; copied in).
+ *  age_yr[n_age]  strictly increasing SSP ages [yr]
+ *  lgZ[n_met]     strictly increasing log10(Z/Z_sun) grid
+ *  lam_ang[n_lam] strictly increasing rest-frame wavelengths [Angstrom]
+ *  ssp[n_age*n_met*n_lam] L_SSP[i][j][n] in L_sun/Hz per solar mass formed
+ *  band_kind[n_band], band_p0, band_p1: observed-frame filters;
+ *    TOPHAT: transmission 1 on [p0, p1) Angstrom;
+ *    GAUSS:  transmission exp(-(l - p0)^2 / (2 s^2)), s = p1 / (2 sqrt(2 ln 2)) (p1 = FWHM). */
+typedef struct {
+    int32_t n_age, n_met, n_lam, n_band;
+    const double* age_yr;
+    const double* lgZ;
+    const double* lam_ang;
+    const double* ssp;
+    const int32_t* band_kind;
+    const double* band_p0;
+    const double* band_p1;
+} sps_tables;
+
+/* Context configuration.  sps_config_default() fills the declared defaults:
+ * flat LambdaCDM with H0 = 70 km/s/Mpc, Omega_m = 0.3 (the paper states none),
+ * the package's prior bounds, device 0, Gauss-Legendre order 6 and panel width
+ * 0.25 in ln t for the SFH bin integrals. */
+typedef struct {
+    double h0_kms_mpc;
+    double omega_m;
+    double prior_lo[SPS_NPARAM];
+    double prior_hi[SPS_NPARAM];
+    int32_t device;
+    int32_t sfh_gl_order; /* 2..16 */
+    double sfh_panel;     /* max panel width in ln t, (0, 2] */
+} sps_config;
+
+sps_status sps_config_default(sps_config* cfg);
+
+/* Create a context on cfg->device: validates and uploads the tables (FP32,
+ * BF16 row-scaled and per-wavelength dust constants).  On success *out owns
+ * device memory until sps_destroy.  Sec. 2 (fixed SSP library), App. A.3. */
+sps_status sps_create(sps_ctx** out, const sps_tables* tables, const sps_config* cfg);
+sps_status sps_destroy(sps_ctx* ctx);
+
+/* Set the galaxies (their redshifts z[n_gal], float32) that later rows refer to.
+ * Computes per galaxy, in FP64: t_obs(z), d_L(z), the age bins in cosmic time
+ * (Eq. smoothPsfh), band supports, band normalisations and AB zero points, and,
+ * if build_approx != 0, lambda_eff (Eq. lambda_eff) and the per-galaxy table
+ * c_SSP[g][b][ij] (the c_SSP definition of Sec. 3, "at a fixed z if the
+ * redshift is known").  Replaces any previous set.  Synchronous. */
+sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t build_approx,
+                            void* stream);
+
+/* AB magnitudes of n rows: theta[n][12] -> mag_out[n][n_band].
+ * mode EXACT: Eq. photo_integral_exact (SSP contraction over the full
+ * wavelength grid, dust and filters applied per wavelength); prec selects the
+ * contraction arithmetic (FP32, or BF16 operands with per-age-row power-of-two
+ * scaling and FP32 accumulation).  mode APPROX: Eq. photo_integral_approx
+ * (FP32; prec must be SPS_FP32).  Rows whose theta is non-finite give NaN
+ * magnitudes and SPS_E_NONFINITE (the other rows are still valid). */
+sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                          sps_mode mode, sps_prec prec, float* mag_out, void* stream);
+
+/* Gaussian log-likelihood (App. D.1) of n rows and its gradient with respect
+ * to the 12 physical parameters, by a hand-written adjoint that recomputes the
+ * per-SSP products instead of storing them.
+ *  mag_obs[n_gal][n_band], sigma[n_gal][n_band]: per-galaxy data;
+ *  mask[n_gal]: bit b set <=> band b enters the likelihood;
+ *  loglike_out[n]; grad_out[n][12] or NULL (value only). */
+sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                            const float* mag_obs, const float* sigma, const uint32_t* mask,
+                            sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
+                            void* stream);
+
+/* Batched HMC configuration (Sec. 4, App. D.2). */
+typedef struct {
+    int32_t chains_per_gal; /* C >= 1; chain c of galaxy g is row g*C + c          */
+    int32_t n_warm;         /* adaptation iterations (dual-averaged step size)      */
+    int32_t n_samp;         /* sampling iterations                                 */
+    int32_t L_min, L_max;   /* leapfrog steps per trajectory ~ U{L_min..L_max}      */
+    float target_accept;    /* dual-averaging target (0.8)                        */
+    float eps0;             /* initial step size (0.1)                            */
+    uint64_t seed;          /* Philox-4x32-10 key                                 */
+    int32_t mode;           /* sps_mode (APPROX runs the persistent fused kernel)  */
+    int32_t prec;           /* sps_prec (EXACT only)                              */
+    int32_t use_graph;      /* capture the device work in a CUDA graph             */
+    int32_t autotune;       /* pick the launch shape by timing candidates          */
+} sps_hmc_config;
+
+sps_status sps_hmc_config_default(sps_hmc_config* cfg);
+
+/* Per-chain statistics (each pointer may be NULL; host or device). */
+typedef struct {
+    float* accept_prob;   /* [G*C] mean Metropolis acceptance probability, sampling phase */
+    float* step_size;     /* [G*C] step size used for sampling                           */
+    int32_t* divergences; /* [G*C] trajectories with non-finite or > 1000 energy error    */
+    int64_t* grad_evals;  /* [G*C] log-posterior gradient evaluations                     */
+    int32_t* status;      /* [G*C] 0 finished, 1 not finished (timeout)                   */
+} sps_hmc_stats;
+
+/* Run batched HMC for every chain of every galaxy of the current set.
+ * The target is log L (App. D.1) plus the log-Jacobian of the bounding map
+ * theta = lo + (hi - lo) / (1 + exp(-x)) (Eq. BoundingFunction, k = 1, x0 = 0),
+ * i.e. a prior uniform in each bounded parameter; sampling is in x.
+ *  theta0_unb[G*C][12]: start points in unbounded space;
+ *  samples_out[G*C][n_samp][12]: bounded (physical) draws, or NULL.
+ * Random numbers: Philox-4x32-10 keyed by seed, counter (iteration, block,
+ * chain, 0); a run is a pure function of its inputs. */
+sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
+                       const float* mag_obs, const float* sigma, const uint32_t* mask,
+                       float* samples_out, sps_hmc_stats* stats, void* stream);
+
+/* Deterministic leapfrog trajectories (the HMC integrator of App. D.2 without
+ * the random draws): for each row, L[row] steps of size eps[row] from
+ * (x0, p0) in unbounded space; writes the end point, its momentum and log
+ * posterior.  Uses the same device code as sps_hmc_run (APPROX mode). */
+sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const float* eps,
+                        const int32_t* L, const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                        const float* sigma, const uint32_t* mask, float* x_out, float* p_out,
+                        double* logp_out, void* stream);
+
+/* The device Philox-4x32-10 generator: out[n][4] = philox(ctr[n][4], key).
+ * (Salmon et al. 2011; the generator behind every HMC draw.) */
+sps_status sps_philox(sps_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out,
+                      void* stream);
+
+/* SSP weights of n rows: W[n][n_age*n_met] = M_star P_SFH,i P_met,j (Eq.
+ * galSED_decomposed with Eq. composite_age_weights) and M_star[n] in M_sun. */
+sps_status sps_weights(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                       float* W_out, double* mstar_out, void* stream);
+
+/* Host-side diagnostics (FP64): multi-chain effective sample size with Geyer's
+ * initial monotone sequence and split R-hat (Gelman-Rubin, Sec. 4), per galaxy
+ * and parameter, of samples[G*C][N][P] (host memory).  ess_out, rhat_out:
+ * [G][P] (either may be NULL). */
+sps_status sps_diagnostics(const float* samples, int64_t n_gal, int32_t chains_per_gal,
+                           int32_t n_draws, int32_t n_param, double* ess_out, double* rhat_out);
+
+/* Sizes and a few derived quantities of a context (host integers). */
+typedef struct {
+    int32_t n_age, n_met, n_lam, n_band, k_pad;
+    int64_t n_gal;
+    int32_t has_approx;
+    int32_t device;
+    int32_t sfh_gl_order;
+    int32_t max_panels;
+} sps_info;
+sps_status sps_get_info(const sps_ctx* ctx, sps_info* out);
+
+/* Gauss-Legendre rule the library built for the SFH integrals (host copy):
+ * nodes[order], weights[order] on [-1, 1]. */
+sps_status sps_gl_rule(const sps_ctx* ctx, double* nodes, double* weights);
+
+const char* sps_error_string(sps_status status);
+const char* sps_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPS_GB300_H */

@@ -1,0 +1,222 @@
+"""GB300 (sm_103a) implementation of the SPS photometry likelihood and batched
+HMC of arXiv 2506.19919, behind the C ABI declared in include/sps.h.
+
+The Python layer marshals arguments only: torch tensors provide device memory
+and streams, every step of the computation runs in the CUDA library.  Loading
+fails loudly when the library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (SPS_APPROX, SPS_BF16, SPS_EXACT, SPS_FP32, SpsError, check, load, sps_config,
+                   sps_hmc_config, sps_hmc_stats, sps_info, sps_tables)
+
+__all__ = ["Context", "diagnostics", "SpsError", "load", "MODES", "PRECS"]
+
+MODES = {"exact": SPS_EXACT, "approx": SPS_APPROX}
+PRECS = {"fp32": SPS_FP32, "bf16": SPS_BF16}
+
+
+def _vp(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(t):
+    if isinstance(t, torch.Tensor) and t.is_cuda:
+        return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return None
+
+
+def _f32(x, device):
+    t = torch.as_tensor(x)
+    return t.to(device=device, dtype=torch.float32).contiguous()
+
+
+class Context:
+    """One library context: tables on one device plus the current galaxy set."""
+
+    def __init__(self, tables, device: int = 0, h0: float = 70.0, omega_m: float = 0.3,
+                 prior_lo=None, prior_hi=None, gl_order: int = 6, panel: float = 0.25):
+        lib = load()
+        self._lib = lib
+        cfg = sps_config()
+        check(lib.sps_config_default(C.byref(cfg)), "sps_config_default")
+        cfg.h0_kms_mpc = h0
+        cfg.omega_m = omega_m
+        cfg.device = device
+        cfg.sfh_gl_order = gl_order
+        cfg.sfh_panel = panel
+        if prior_lo is not None:
+            for k in range(_lib.NPARAM):
+                cfg.prior_lo[k] = float(prior_lo[k])
+                cfg.prior_hi[k] = float(prior_hi[k])
+        self._keep = [np.ascontiguousarray(tables.age_yr, dtype=np.float64),
+                      np.ascontiguousarray(tables.lgZ, dtype=np.float64),
+                      np.ascontiguousarray(tables.lam_ang, dtype=np.float64),
+                      np.ascontiguousarray(tables.ssp, dtype=np.float64),
+                      np.ascontiguousarray(tables.band_kind, dtype=np.int32),
+                      np.ascontiguousarray(tables.band_p0, dtype=np.float64),
+                      np.ascontiguousarray(tables.band_p1, dtype=np.float64)]
+        a, z, l, s, k, p0, p1 = self._keep
+        t = sps_tables(len(a), len(z), len(l), len(k), a.ctypes.data, z.ctypes.data,
+                       l.ctypes.data, s.ctypes.data, k.ctypes.data, p0.ctypes.data,
+                       p1.ctypes.data)
+        h = C.c_void_p()
+        check(lib.sps_create(C.byref(h), C.byref(t), C.byref(cfg)), "sps_create")
+        self.h = h
+        self.device = torch.device("cuda", device)
+        self.n_band = len(k)
+        self.n_gal = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ set-up
+    def set_galaxies(self, z, build_approx: bool = True):
+        zt = _f32(z, "cpu").numpy()
+        check(self._lib.sps_set_galaxies(self.h, _vp(zt), len(zt), int(build_approx), None),
+              "sps_set_galaxies")
+        self.n_gal = len(zt)
+
+    def info(self) -> dict:
+        i = sps_info()
+        check(self._lib.sps_get_info(self.h, C.byref(i)), "sps_get_info")
+        return {f: getattr(i, f) for f, _ in sps_info._fields_}
+
+    def gl_rule(self):
+        n = self.info()["sfh_gl_order"]
+        x = np.zeros(n)
+        w = np.zeros(n)
+        check(self._lib.sps_gl_rule(self.h, _vp(x), _vp(w)), "sps_gl_rule")
+        return x, w
+
+    # ------------------------------------------------------------------ compute
+    def photometry(self, theta, gal_idx=None, mode="exact", prec="fp32", out=None):
+        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        n = th.shape[0]
+        if out is None:
+            out = torch.empty((n, self.n_band), dtype=torch.float32, device=th.device)
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=th.device).contiguous()
+        check(self._lib.sps_photometry(self.h, _vp(th), _vp(gi), n, MODES[mode], PRECS[prec],
+                                       _vp(out), _stream(th)), "sps_photometry")
+        return out
+
+    def loglike_grad(self, theta, mag_obs, sigma, mask, gal_idx=None, mode="approx",
+                     prec="fp32", grad=True):
+        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        dev = th.device
+        n = th.shape[0]
+        mo = _f32(mag_obs, dev)
+        sg = _f32(sigma, dev)
+        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
+            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=dev).contiguous()
+        ll = torch.empty(n, dtype=torch.float32, device=dev)
+        g = torch.empty((n, _lib.NPARAM), dtype=torch.float32, device=dev) if grad else None
+        check(self._lib.sps_loglike_grad(self.h, _vp(th), _vp(gi), n, _vp(mo), _vp(sg), _vp(mk),
+                                         MODES[mode], PRECS[prec], _vp(ll), _vp(g), _stream(th)),
+              "sps_loglike_grad")
+        return ll, g
+
+    def hmc_run(self, theta0_unb, mag_obs, sigma, mask, chains_per_gal=4, n_warm=500,
+                n_samp=500, L_min=8, L_max=64, target_accept=0.8, eps0=0.1, seed=2506199190,
+                use_graph=True, autotune=True, samples=True, mode="approx"):
+        x0 = theta0_unb if isinstance(theta0_unb, torch.Tensor) else _f32(theta0_unb, self.device)
+        dev = x0.device
+        mo = _f32(mag_obs, dev)
+        sg = _f32(sigma, dev)
+        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
+            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        nc = x0.shape[0]
+        cfg = sps_hmc_config()
+        check(self._lib.sps_hmc_config_default(C.byref(cfg)), "sps_hmc_config_default")
+        cfg.chains_per_gal, cfg.n_warm, cfg.n_samp = chains_per_gal, n_warm, n_samp
+        cfg.L_min, cfg.L_max = L_min, L_max
+        cfg.target_accept, cfg.eps0, cfg.seed = target_accept, eps0, seed
+        cfg.mode = MODES[mode]
+        cfg.use_graph, cfg.autotune = int(use_graph), int(autotune)
+        out = {
+            "samples": torch.empty((nc, n_samp, _lib.NPARAM), dtype=torch.float32, device=dev)
+            if samples else None,
+            "accept_prob": torch.empty(nc, dtype=torch.float32, device=dev),
+            "step_size": torch.empty(nc, dtype=torch.float32, device=dev),
+            "divergences": torch.empty(nc, dtype=torch.int32, device=dev),
+            "grad_evals": torch.empty(nc, dtype=torch.int64, device=dev),
+            "status": torch.empty(nc, dtype=torch.int32, device=dev),
+        }
+        st = sps_hmc_stats(*(C.c_void_p(out[k].data_ptr()) for k in
+                             ("accept_prob", "step_size", "divergences", "grad_evals", "status")))
+        check(self._lib.sps_hmc_run(self.h, C.byref(cfg), _vp(x0), _vp(mo), _vp(sg), _vp(mk),
+                                    _vp(out["samples"]), C.byref(st), _stream(x0)), "sps_hmc_run")
+        return out
+
+    def leapfrog(self, x0, p0, eps, L, mag_obs, sigma, mask, gal_idx=None):
+        x = _f32(x0, self.device)
+        dev = x.device
+        n = x.shape[0]
+        p = _f32(p0, dev)
+        e = _f32(eps, dev)
+        l = torch.as_tensor(L, dtype=torch.int32).to(dev).contiguous()
+        mo, sg = _f32(mag_obs, dev), _f32(sigma, dev)
+        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous()
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=dev).contiguous()
+        xo = torch.empty_like(x)
+        po = torch.empty_like(x)
+        lo = torch.empty(n, dtype=torch.float64, device=dev)
+        check(self._lib.sps_leapfrog(self.h, _vp(x), _vp(p), _vp(e), _vp(l), _vp(gi), n, _vp(mo),
+                                     _vp(sg), _vp(mk), _vp(xo), _vp(po), _vp(lo), _stream(x)),
+              "sps_leapfrog")
+        return xo, po, lo
+
+    def philox(self, ctr, key: int):
+        c = torch.as_tensor(np.asarray(ctr, dtype=np.uint32).view(np.int32)).to(self.device).contiguous()
+        n = c.shape[0]
+        o = torch.empty_like(c)
+        check(self._lib.sps_philox(self.h, _vp(c), n, C.c_uint64(key), _vp(o), _stream(c)),
+              "sps_philox")
+        return o.cpu().numpy().view(np.uint32)
+
+    def weights(self, theta, gal_idx=None):
+        th = _f32(theta, self.device)
+        n = th.shape[0]
+        info = self.info()
+        W = torch.empty((n, info["n_age"] * info["n_met"]), dtype=torch.float32, device=th.device)
+        M = torch.empty(n, dtype=torch.float64, device=th.device)
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=th.device).contiguous()
+        check(self._lib.sps_weights(self.h, _vp(th), _vp(gi), n, _vp(W), _vp(M), _stream(th)),
+              "sps_weights")
+        return W, M
+
+
+def diagnostics(samples, n_gal: int, chains_per_gal: int):
+    """Multi-chain ESS and split R-hat per galaxy and parameter (host, FP64)."""
+    lib = load()
+    s = np.ascontiguousarray(samples.detach().cpu().numpy() if isinstance(samples, torch.Tensor)
+                             else samples, dtype=np.float32)
+    nd, npar = s.shape[1], s.shape[2]
+    ess = np.zeros((n_gal, npar))
+    rh = np.zeros((n_gal, npar))
+    check(lib.sps_diagnostics(_vp(s), n_gal, chains_per_gal, nd, npar, _vp(ess), _vp(rh)),
+          "sps_diagnostics")
+    return ess, rh

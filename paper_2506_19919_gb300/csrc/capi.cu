@@ -1,0 +1,866 @@
+// Host runtime behind the C ABI of include/sps.h: context and table upload,
+// argument checks, host/device pointer detection and staging, chunked
+// dispatch of the exact path, the HMC launch (graph capture, autotuned launch
+// shape) and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sps_internal.h"
+
+namespace sps {
+size_t hmc_warp_smem_bytes();
+cudaError_t hmc_set_smem(size_t bytes);
+cudaError_t hmc_occupancy(int warps, size_t smem, int* blocks_per_sm);
+}  // namespace sps
+
+using namespace sps;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sps_status fail(sps_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+sps_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(SPS_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+uint16_t bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+}  // namespace
+
+struct sps_ctx {
+    int device = 0;
+    Consts c{};
+    double h0 = 70.0, om = 0.3;
+    double gl_x[kMaxGL], gl_w[kMaxGL];
+    std::vector<double> band_p0, band_p1;
+    // tables
+    DevBuf lam64, lam32, lamc, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, age_edges, bp0, bp1;
+    // galaxies
+    int64_t n_gal = 0;
+    bool has_approx = false;
+    DevBuf gz, glnT, glT10, gbins, gzp, gsup, ggauss, gcssp, gdust;
+    // scratch
+    DevBuf nonfinite, queue, err;
+    DevBuf W, V, Wbar, cJ, gbar, rowinfo;
+    DevBuf stage[12];
+    // HMC graph cache
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
+    std::map<std::string, std::pair<int, int>> tuned;  // key -> (warps, blocks)
+
+    Grid grid() const {
+        Grid g;
+        g.lam = lam32.as<float>();
+        g.lamc = lamc.as<float4>();
+        g.lam64 = lam64.as<double>();
+        g.ssp = ssp.as<float>();
+        g.ssp_t = ssp_t.as<float>();
+        g.ssp_bf = ssp_bf.as<uint16_t>();
+        g.ssp_t_bf = ssp_t_bf.as<uint16_t>();
+        g.row_scale = row_scale.as<float>();
+        return g;
+    }
+    Galaxies gal() const {
+        Galaxies g;
+        g.n = n_gal;
+        g.z = gz.as<float>();
+        g.lnT = glnT.as<float>();
+        g.lT10 = glT10.as<float>();
+        g.bins = gbins.as<float2>();
+        g.zp = gzp.as<double>();
+        g.support = gsup.as<int2>();
+        g.gauss = ggauss.as<float2>();
+        g.cssp = has_approx ? gcssp.as<float>() : nullptr;
+        g.dust_eff = gdust.as<float4>();
+        return g;
+    }
+    ~sps_ctx() {
+        cudaSetDevice(device);
+        if (graph) cudaGraphExecDestroy(graph);
+        DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
+                         &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
+                         &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
+                         &rowinfo};
+        for (DevBuf* b : all) b->release();
+        for (auto& b : stage) b.release();
+    }
+};
+
+namespace {
+
+// Staging of host arrays: in() returns a device pointer holding the data,
+// out() a device pointer whose contents are copied back by finish().
+struct Stager {
+    sps_ctx* ctx;
+    cudaStream_t s;
+    int slot = 0;
+    bool any_host = false;
+    struct Back {
+        void* host;
+        const void* dev;
+        size_t bytes;
+    };
+    std::vector<Back> back;
+    cudaError_t err = cudaSuccess;
+
+    template <typename T>
+    const T* in(const T* p, size_t count) {
+        if (!p || count == 0 || is_device_ptr(p)) return p;
+        any_host = true;
+        DevBuf& b = ctx->stage[slot++];
+        if ((err = b.reserve(count * sizeof(T))) != cudaSuccess) return nullptr;
+        if ((err = cudaMemcpyAsync(b.p, p, count * sizeof(T), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return nullptr;
+        return b.as<T>();
+    }
+    template <typename T>
+    T* out(T* p, size_t count) {
+        if (!p || count == 0 || is_device_ptr(p)) return p;
+        any_host = true;
+        DevBuf& b = ctx->stage[slot++];
+        if ((err = b.reserve(count * sizeof(T))) != cudaSuccess) return nullptr;
+        back.push_back({p, b.p, count * sizeof(T)});
+        return b.as<T>();
+    }
+    cudaError_t finish() {
+        for (auto& bk : back) {
+            cudaError_t e = cudaMemcpyAsync(bk.host, bk.dev, bk.bytes, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (any_host) return cudaStreamSynchronize(s);
+        return cudaSuccess;
+    }
+};
+
+sps_status check_rows(const sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n) {
+    if (!ctx) return fail(SPS_E_INVALID_ARG, "null context");
+    if (ctx->n_gal <= 0) return fail(SPS_E_STATE, "no galaxy set: call sps_set_galaxies first");
+    if (n < 0) return fail(SPS_E_SHAPE, "negative row count");
+    if (n == 0) return SPS_OK;
+    if (!theta) return fail(SPS_E_INVALID_ARG, "theta is NULL");
+    if (!gal_idx && n != ctx->n_gal)
+        return fail(SPS_E_SHAPE, "gal_idx is NULL but n differs from the galaxy count");
+    if (gal_idx && n > 0 && !is_device_ptr(gal_idx)) {
+        for (int64_t i = 0; i < n; ++i)
+            if (gal_idx[i] < 0 || gal_idx[i] >= ctx->n_gal)
+                return fail(SPS_E_SHAPE, "gal_idx out of range at row " + std::to_string(i));
+    }
+    return SPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sps_error_string(sps_status s) {
+    switch (s) {
+        case SPS_OK: return "ok";
+        case SPS_E_INVALID_ARG: return "invalid argument";
+        case SPS_E_SHAPE: return "shape or size out of range";
+        case SPS_E_NONFINITE: return "non-finite inputs gave NaN rows";
+        case SPS_E_CUDA: return "CUDA error";
+        case SPS_E_TIMEOUT: return "bounded device wait timed out";
+        case SPS_E_UNSUPPORTED: return "unsupported mode, precision or device";
+        case SPS_E_STATE: return "call order (state) error";
+        case SPS_E_NOMEM: return "device allocation failed";
+    }
+    return "unknown status";
+}
+
+const char* sps_last_error_message(void) { return g_last_error.c_str(); }
+
+sps_status sps_config_default(sps_config* cfg) {
+    if (!cfg) return fail(SPS_E_INVALID_ARG, "null config");
+    static const double lo[SPS_NPARAM] = {-1.5, 0.5, 0.1, 0.1, 0.0, 6.0, 0.05, -2.0, 0.05, 0.0, -1.0, 0.0};
+    static const double hi[SPS_NPARAM] = {2.5, 12.0, 5.0, 5.0, 0.2, 8.5, 1.5, 0.2, 0.5, 3.0, 0.4, 0.5};
+    cfg->h0_kms_mpc = 70.0;
+    cfg->omega_m = 0.3;
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        cfg->prior_lo[k] = lo[k];
+        cfg->prior_hi[k] = hi[k];
+    }
+    cfg->device = 0;
+    cfg->sfh_gl_order = 6;
+    cfg->sfh_panel = 0.25;
+    return SPS_OK;
+}
+
+sps_status sps_hmc_config_default(sps_hmc_config* cfg) {
+    if (!cfg) return fail(SPS_E_INVALID_ARG, "null config");
+    cfg->chains_per_gal = 4;
+    cfg->n_warm = 500;
+    cfg->n_samp = 500;
+    cfg->L_min = 8;
+    cfg->L_max = 64;
+    cfg->target_accept = 0.8f;
+    cfg->eps0 = 0.1f;
+    cfg->seed = 2506199190ull;
+    cfg->mode = SPS_APPROX;
+    cfg->prec = SPS_FP32;
+    cfg->use_graph = 1;
+    cfg->autotune = 1;
+    return SPS_OK;
+}
+
+sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_in) {
+    if (!out || !t) return fail(SPS_E_INVALID_ARG, "null argument");
+    *out = nullptr;
+    sps_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else sps_config_default(&cfg);
+    const int A = t->n_age, Zn = t->n_met, L = t->n_lam, B = t->n_band;
+    if (A < 2 || A > SPS_MAX_AGES) return fail(SPS_E_SHAPE, "n_age must be in [2, 128]");
+    if (Zn < 1 || Zn > SPS_MAX_METS) return fail(SPS_E_SHAPE, "n_met must be in [1, 32]");
+    if (L < 2) return fail(SPS_E_SHAPE, "n_lam must be >= 2");
+    if (B < 1 || B > SPS_MAX_BANDS) return fail(SPS_E_SHAPE, "n_band must be in [1, 32]");
+    if (A * Zn > kKTileMax * 32) return fail(SPS_E_SHAPE, "n_age * n_met must be <= 1312");
+    if (!t->age_yr || !t->lgZ || !t->lam_ang || !t->ssp || !t->band_kind || !t->band_p0 || !t->band_p1)
+        return fail(SPS_E_INVALID_ARG, "null table pointer");
+    for (int i = 0; i < A; ++i)
+        if (!(t->age_yr[i] > 0) || (i && !(t->age_yr[i] > t->age_yr[i - 1])))
+            return fail(SPS_E_INVALID_ARG, "age grid must be positive and increasing");
+    for (int j = 1; j < Zn; ++j)
+        if (!(t->lgZ[j] > t->lgZ[j - 1])) return fail(SPS_E_INVALID_ARG, "lgZ grid must increase");
+    for (int n = 0; n < L; ++n)
+        if (!(t->lam_ang[n] > 0) || (n && !(t->lam_ang[n] > t->lam_ang[n - 1])))
+            return fail(SPS_E_INVALID_ARG, "wavelength grid must be positive and increasing");
+    for (int b = 0; b < B; ++b) {
+        int k = t->band_kind[b];
+        if (k != SPS_BAND_TOPHAT && k != SPS_BAND_GAUSS) return fail(SPS_E_INVALID_ARG, "bad band kind");
+        if (k == SPS_BAND_TOPHAT && !(t->band_p1[b] > t->band_p0[b] && t->band_p0[b] > 0))
+            return fail(SPS_E_INVALID_ARG, "top-hat band needs 0 < p0 < p1");
+        if (k == SPS_BAND_GAUSS && !(t->band_p1[b] > 0 && t->band_p0[b] > 0))
+            return fail(SPS_E_INVALID_ARG, "Gaussian band needs positive centre and FWHM");
+    }
+    const size_t K = (size_t)A * Zn;
+    for (size_t e = 0; e < K * L; ++e)
+        if (!std::isfinite(t->ssp[e]) || t->ssp[e] < 0) return fail(SPS_E_INVALID_ARG, "SSP table must be finite and >= 0");
+    if (cfg.sfh_gl_order < 2 || cfg.sfh_gl_order > kMaxGL) return fail(SPS_E_INVALID_ARG, "sfh_gl_order in [2, 16]");
+    if (!(cfg.sfh_panel > 0 && cfg.sfh_panel <= 2.0)) return fail(SPS_E_INVALID_ARG, "sfh_panel in (0, 2]");
+    if (!(cfg.h0_kms_mpc > 0) || !(cfg.omega_m > 0 && cfg.omega_m < 1))
+        return fail(SPS_E_INVALID_ARG, "cosmology out of range");
+    for (int k = 0; k < SPS_NPARAM; ++k)
+        if (!(cfg.prior_hi[k] > cfg.prior_lo[k])) return fail(SPS_E_INVALID_ARG, "prior_hi must exceed prior_lo");
+    // Worst-case SFH panel count per row: every bin one panel plus the log-time
+    // range down to the truncation point (at most ~45 in ln t) in panels.
+    const int max_panels = A + (int)std::ceil(48.0 / cfg.sfh_panel) + 2;
+    if (max_panels > kMaxPanels) return fail(SPS_E_INVALID_ARG, "sfh_panel too small for the panel budget");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SPS_E_UNSUPPORTED, "no CUDA device");
+    }
+    if (cfg.device < 0 || cfg.device >= ndev) return fail(SPS_E_INVALID_ARG, "bad device ordinal");
+    CK(cudaSetDevice(cfg.device));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, cfg.device));
+    if (prop.major < 10) return fail(SPS_E_UNSUPPORTED, "needs a Blackwell (sm_100+) device");
+
+    sps_ctx* ctx = new sps_ctx();
+    ctx->device = cfg.device;
+    ctx->h0 = cfg.h0_kms_mpc;
+    ctx->om = cfg.omega_m;
+    Consts& c = ctx->c;
+    c.n_age = A;
+    c.n_met = Zn;
+    c.n_lam = L;
+    c.n_band = B;
+    c.K = (int)K;
+    c.k_pad = (int)((K + 31) / 32 * 32);
+    c.lam_pad = (L + 31) / 32 * 32;
+    c.gl_order = cfg.sfh_gl_order;
+    c.panel = (float)cfg.sfh_panel;
+    gauss_legendre(c.gl_order, ctx->gl_x, ctx->gl_w);
+    for (int i = 0; i < c.gl_order; ++i) {
+        c.gl_x[i] = (float)ctx->gl_x[i];
+        c.gl_w[i] = (float)ctx->gl_w[i];
+    }
+    std::vector<double> edges(A + 1);
+    edges[0] = 0.0;
+    for (int i = 1; i < A; ++i) edges[i] = std::sqrt(t->age_yr[i - 1] * t->age_yr[i]);
+    edges[A] = INFINITY;
+    c.log_age_edge[0] = -100.0f;
+    for (int i = 1; i < A; ++i) c.log_age_edge[i] = (float)std::log10(edges[i]);
+    c.log_age_edge[A] = 100.0f;
+    c.lgz_edge[0] = -INFINITY;
+    for (int j = 1; j < Zn; ++j) c.lgz_edge[j] = (float)(0.5 * (t->lgZ[j - 1] + t->lgZ[j]));
+    c.lgz_edge[Zn] = INFINITY;
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        c.prior_lo[k] = (float)cfg.prior_lo[k];
+        c.prior_span[k] = (float)(cfg.prior_hi[k] - cfg.prior_lo[k]);
+    }
+    for (int b = 0; b < B; ++b) c.band_kind[b] = t->band_kind[b];
+    ctx->band_p0.assign(t->band_p0, t->band_p0 + B);
+    ctx->band_p1.assign(t->band_p1, t->band_p1 + B);
+
+    // tables: FP32 [k_pad][lam_pad], transposed, BF16 row-scaled versions
+    const int kp = c.k_pad, lp = c.lam_pad;
+    std::vector<float> s32((size_t)kp * lp, 0.f), st32((size_t)lp * kp, 0.f);
+    std::vector<uint16_t> sbf((size_t)kp * lp, 0), stbf((size_t)lp * kp, 0);
+    std::vector<float> rscale(A);
+    for (int i = 0; i < A; ++i) {
+        double mx = 0.0;
+        for (int j = 0; j < Zn; ++j)
+            for (int n = 0; n < L; ++n) mx = std::max(mx, t->ssp[((size_t)i * Zn + j) * L + n]);
+        int e = (mx > 0) ? (int)std::lround(std::log2(mx)) : 0;
+        rscale[i] = std::ldexp(1.0f, e);
+        for (int j = 0; j < Zn; ++j) {
+            size_t k = (size_t)i * Zn + j;
+            for (int n = 0; n < L; ++n) {
+                double v = t->ssp[k * L + n];
+                float f = (float)v;
+                s32[k * lp + n] = f;
+                st32[(size_t)n * kp + k] = f;
+                uint16_t h = bf16_rne((float)std::ldexp(v, -e));
+                sbf[k * lp + n] = h;
+                stbf[(size_t)n * kp + k] = h;
+            }
+        }
+    }
+    auto upload = [&](DevBuf& b, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t e = b.reserve(bytes);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = upload(ctx->lam64, t->lam_ang, sizeof(double) * L)) != cudaSuccess ||
+        (e = upload(ctx->ssp, s32.data(), s32.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->ssp_t, st32.data(), st32.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->ssp_bf, sbf.data(), sbf.size() * 2)) != cudaSuccess ||
+        (e = upload(ctx->ssp_t_bf, stbf.data(), stbf.size() * 2)) != cudaSuccess ||
+        (e = upload(ctx->row_scale, rscale.data(), rscale.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->age_edges, edges.data(), edges.size() * 8)) != cudaSuccess ||
+        (e = upload(ctx->bp0, t->band_p0, sizeof(double) * B)) != cudaSuccess ||
+        (e = upload(ctx->bp1, t->band_p1, sizeof(double) * B)) != cudaSuccess ||
+        (e = ctx->lam32.reserve(sizeof(float) * L)) != cudaSuccess ||
+        (e = ctx->lamc.reserve(sizeof(float4) * L)) != cudaSuccess ||
+        (e = ctx->nonfinite.reserve(64)) != cudaSuccess || (e = ctx->queue.reserve(64)) != cudaSuccess ||
+        (e = ctx->err.reserve(64)) != cudaSuccess) {
+        delete ctx;
+        return (e == cudaErrorMemoryAllocation) ? fail(SPS_E_NOMEM, "table upload: out of memory")
+                                                : cuda_fail(e, "table upload");
+    }
+    if ((e = launch_lambda_consts(ctx->lam64.as<double>(), L, ctx->lamc.as<float4>(),
+                                  ctx->lam32.as<float>(), 0)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(e, "lambda constants");
+    }
+    *out = ctx;
+    return SPS_OK;
+}
+
+sps_status sps_destroy(sps_ctx* ctx) {
+    delete ctx;
+    return SPS_OK;
+}
+
+sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t build_approx,
+                            void* stream) {
+    if (!ctx || (!z && n_gal > 0)) return fail(SPS_E_INVALID_ARG, "null argument");
+    if (n_gal <= 0 || n_gal > (int64_t)1 << 31) return fail(SPS_E_SHAPE, "n_gal out of range");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<float> zh((size_t)n_gal);
+    if (is_device_ptr(z)) CK(cudaMemcpy(zh.data(), z, n_gal * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(zh.data(), z, n_gal * 4);
+    for (int64_t i = 0; i < n_gal; ++i)
+        if (!(zh[i] > 0.0f && zh[i] < 20.0f)) return fail(SPS_E_INVALID_ARG, "redshift must be in (0, 20)");
+    const Consts& c = ctx->c;
+    const size_t G = (size_t)n_gal, B = c.n_band;
+    CK(ctx->gz.reserve(G * 4));
+    CK(ctx->glnT.reserve(G * 4));
+    CK(ctx->glT10.reserve(G * 4));
+    CK(ctx->gbins.reserve(G * c.n_age * sizeof(float2)));
+    CK(ctx->gzp.reserve(G * B * 8));
+    CK(ctx->gsup.reserve(G * B * sizeof(int2)));
+    CK(ctx->ggauss.reserve(G * B * sizeof(float2)));
+    CK(ctx->gdust.reserve(G * B * sizeof(float4)));
+    CK(cudaMemcpyAsync(ctx->gz.p, zh.data(), G * 4, cudaMemcpyHostToDevice, s));
+    ctx->n_gal = n_gal;
+    ctx->has_approx = false;
+    CK(launch_prepare_galaxies(c, ctx->grid(), ctx->lam64.as<double>(), ctx->bp0.as<double>(),
+                               ctx->bp1.as<double>(), ctx->age_edges.as<double>(), ctx->gz.as<float>(),
+                               n_gal, ctx->h0, ctx->om, ctx->glnT.as<float>(), ctx->glT10.as<float>(),
+                               ctx->gbins.as<float2>(), ctx->gzp.as<double>(), ctx->gsup.as<int2>(),
+                               ctx->ggauss.as<float2>(), ctx->gdust.as<float4>(), s));
+    if (build_approx) {
+        cudaError_t e = ctx->gcssp.reserve(G * B * c.K * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPS_E_NOMEM, "c_SSP table does not fit in device memory");
+        }
+        ctx->has_approx = true;
+        CK(launch_cssp(c, ctx->grid(), ctx->gal(), ctx->bp0.as<double>(), ctx->gcssp.as<float>(), s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return SPS_OK;
+}
+
+static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gidx, int64_t n,
+                            const float* mobs, const float* sigma, const uint32_t* mask, int bf16,
+                            float* mag_out, float* ll_out, float* grad_out, cudaStream_t s) {
+    const Consts& c = ctx->c;
+    const int64_t chunk = 32768;
+    const int64_t rows = std::min<int64_t>(n, chunk);
+    CK(ctx->W.reserve((size_t)rows * c.k_pad * 4));
+    CK(ctx->cJ.reserve((size_t)rows * c.n_band * 4 * 4));
+    CK(ctx->rowinfo.reserve((size_t)rows * 4 * 4));
+    CK(ctx->gbar.reserve((size_t)rows * c.n_band * 4));
+    if (grad_out) {
+        CK(ctx->V.reserve((size_t)rows * c.lam_pad * 4));
+        CK(ctx->Wbar.reserve((size_t)rows * c.k_pad * 4));
+    }
+    const Grid grid = ctx->grid();
+    const Galaxies gal = ctx->gal();
+    int* nf = ctx->nonfinite.as<int>();
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t m = std::min(chunk, n - r0);
+        const float* th = theta + r0 * SPS_NPARAM;
+        const int32_t* gi = gidx ? gidx + r0 : nullptr;
+        // rows of a chunk without gal_idx map to galaxies r0 + row: pass an
+        // offset view of the galaxy tables instead of an index array
+        Galaxies gv = gal;
+        const float* mo = mobs;
+        const float* sg = sigma;
+        const uint32_t* mk = mask;
+        if (!gidx) {
+            if (mo) mo += r0 * c.n_band;
+            if (sg) sg += r0 * c.n_band;
+            if (mk) mk += r0;
+            gv.z += r0; gv.lnT += r0; gv.lT10 += r0;
+            gv.bins += r0 * c.n_age; gv.zp += r0 * c.n_band; gv.support += r0 * c.n_band;
+            gv.gauss += r0 * c.n_band; gv.dust_eff += r0 * c.n_band;
+            if (gv.cssp) gv.cssp += r0 * c.n_band * c.K;
+            gv.n = m;
+        }
+        CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s));
+        CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
+                            ctx->cJ.as<float>(), s));
+        CK(launch_exact_like(c, gv, th, gi, m, ctx->cJ.as<float>(), ctx->rowinfo.as<float>(), mo, sg,
+                             mk, mag_out ? mag_out + r0 * c.n_band : nullptr,
+                             ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s));
+        if (grad_out) {
+            CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), ctx->V.as<float>(), s));
+            CK(launch_exact_adj(c, grid, m, bf16, ctx->V.as<float>(), ctx->Wbar.as<float>(), s));
+            CK(launch_exact_grad(c, gv, th, gi, m, ctx->rowinfo.as<float>(), ctx->Wbar.as<float>(),
+                                 grad_out + r0 * SPS_NPARAM, s));
+        }
+    }
+    return SPS_OK;
+}
+
+static sps_status finish_call(sps_ctx* ctx, Stager& st, cudaStream_t s) {
+    int nf = 0;
+    CK(st.finish());
+    CK(cudaMemcpyAsync(&nf, ctx->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nf) return fail(SPS_E_NONFINITE, "some rows are NaN (non-finite inputs or results)");
+    return SPS_OK;
+}
+
+sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                          sps_mode mode, sps_prec prec, float* mag_out, void* stream) {
+    sps_status st0 = check_rows(ctx, theta, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (mode != SPS_EXACT && mode != SPS_APPROX) return fail(SPS_E_INVALID_ARG, "bad mode");
+    if (prec != SPS_FP32 && prec != SPS_BF16) return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (mode == SPS_APPROX && prec != SPS_FP32) return fail(SPS_E_UNSUPPORTED, "approximate path is FP32");
+    if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (n > 0 && !mag_out) return fail(SPS_E_INVALID_ARG, "mag_out is NULL");
+    if (n == 0) return SPS_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Stager st{ctx, s};
+    const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    float* mo = st.out(mag_out, (size_t)n * ctx->c.n_band);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, sizeof(int), s));
+    if (mode == SPS_APPROX) {
+        CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, nullptr, nullptr, nullptr, mo, nullptr,
+                              nullptr, nullptr, ctx->nonfinite.as<int>(), s));
+    } else {
+        sps_status r = run_exact(ctx, th, gi, n, nullptr, nullptr, nullptr, prec == SPS_BF16, mo,
+                                 nullptr, nullptr, s);
+        if (r != SPS_OK) return r;
+    }
+    return finish_call(ctx, st, s);
+}
+
+sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                            const float* mag_obs, const float* sigma, const uint32_t* mask,
+                            sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
+                            void* stream) {
+    sps_status st0 = check_rows(ctx, theta, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (mode != SPS_EXACT && mode != SPS_APPROX) return fail(SPS_E_INVALID_ARG, "bad mode");
+    if (prec != SPS_FP32 && prec != SPS_BF16) return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (mode == SPS_APPROX && prec != SPS_FP32) return fail(SPS_E_UNSUPPORTED, "approximate path is FP32");
+    if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
+        return fail(SPS_E_INVALID_ARG, "null data or output pointer");
+    if (n == 0) return SPS_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t GB = (size_t)ctx->n_gal * ctx->c.n_band;
+    Stager st{ctx, s};
+    const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
+    float* llo = st.out(loglike_out, (size_t)n);
+    float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, sizeof(int), s));
+    if (mode == SPS_APPROX) {
+        CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, mo, sg, mk, nullptr, llo, gro, nullptr,
+                              ctx->nonfinite.as<int>(), s));
+    } else {
+        sps_status r = run_exact(ctx, th, gi, n, mo, sg, mk, prec == SPS_BF16, nullptr, llo, gro, s);
+        if (r != SPS_OK) return r;
+    }
+    return finish_call(ctx, st, s);
+}
+
+sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const float* eps,
+                        const int32_t* L, const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                        const float* sigma, const uint32_t* mask, float* x_out, float* p_out,
+                        double* logp_out, void* stream) {
+    sps_status st0 = check_rows(ctx, x0, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (n > 0 && (!p0 || !eps || !L || !mag_obs || !sigma || !mask || !x_out || !p_out || !logp_out))
+        return fail(SPS_E_INVALID_ARG, "null argument");
+    if (n == 0) return SPS_OK;
+    if (!is_device_ptr(L))
+        for (int64_t i = 0; i < n; ++i)
+            if (L[i] < 0 || L[i] > 100000) return fail(SPS_E_SHAPE, "L out of range");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t GB = (size_t)ctx->n_gal * ctx->c.n_band;
+    Stager st{ctx, s};
+    const float* x = st.in(x0, (size_t)n * SPS_NPARAM);
+    const float* p = st.in(p0, (size_t)n * SPS_NPARAM);
+    const float* e = st.in(eps, (size_t)n);
+    const int32_t* l = st.in(L, (size_t)n);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
+    float* xo = st.out(x_out, (size_t)n * SPS_NPARAM);
+    float* po = st.out(p_out, (size_t)n * SPS_NPARAM);
+    double* lo = st.out(logp_out, (size_t)n);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(launch_leapfrog(ctx->c, ctx->gal(), x, p, e, l, gi, n, mo, sg, mk, xo, po, lo, s));
+    CK(st.finish());
+    return SPS_OK;
+}
+
+sps_status sps_philox(sps_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out,
+                      void* stream) {
+    if (!ctx || (n > 0 && (!ctr || !out))) return fail(SPS_E_INVALID_ARG, "null argument");
+    if (n <= 0) return SPS_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Stager st{ctx, s};
+    const uint32_t* c = st.in(ctr, (size_t)n * 4);
+    uint32_t* o = st.out(out, (size_t)n * 4);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(launch_philox(c, n, key, o, s));
+    CK(st.finish());
+    return SPS_OK;
+}
+
+sps_status sps_weights(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                       float* W_out, double* mstar_out, void* stream) {
+    sps_status st0 = check_rows(ctx, theta, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (n == 0) return SPS_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Stager st{ctx, s};
+    const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    float* w = st.out(W_out, (size_t)n * ctx->c.K);
+    double* m = st.out(mstar_out, (size_t)n);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(launch_weights_rows(ctx->c, ctx->gal(), th, gi, n, w, m, s));
+    CK(st.finish());
+    return SPS_OK;
+}
+
+sps_status sps_get_info(const sps_ctx* ctx, sps_info* out) {
+    if (!ctx || !out) return fail(SPS_E_INVALID_ARG, "null argument");
+    out->n_age = ctx->c.n_age;
+    out->n_met = ctx->c.n_met;
+    out->n_lam = ctx->c.n_lam;
+    out->n_band = ctx->c.n_band;
+    out->k_pad = ctx->c.k_pad;
+    out->n_gal = ctx->n_gal;
+    out->has_approx = ctx->has_approx ? 1 : 0;
+    out->device = ctx->device;
+    out->sfh_gl_order = ctx->c.gl_order;
+    out->max_panels = kMaxPanels;
+    return SPS_OK;
+}
+
+sps_status sps_gl_rule(const sps_ctx* ctx, double* nodes, double* weights) {
+    if (!ctx || !nodes || !weights) return fail(SPS_E_INVALID_ARG, "null argument");
+    for (int i = 0; i < ctx->c.gl_order; ++i) {
+        nodes[i] = ctx->gl_x[i];
+        weights[i] = ctx->gl_w[i];
+    }
+    return SPS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- HMC
+namespace {
+
+struct HmcLaunch {
+    int warps, blocks;
+    size_t table_bytes;
+};
+
+}  // namespace
+
+extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
+                                  const float* mag_obs, const float* sigma, const uint32_t* mask,
+                                  float* samples_out, sps_hmc_stats* stats, void* stream) {
+    if (!ctx || !cfg) return fail(SPS_E_INVALID_ARG, "null argument");
+    if (ctx->n_gal <= 0) return fail(SPS_E_STATE, "no galaxy set");
+    if (cfg->mode != SPS_APPROX) return fail(SPS_E_UNSUPPORTED, "HMC runs on the approximate path");
+    if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
+    if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
+        return fail(SPS_E_SHAPE, "iteration counts");
+    if (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096) return fail(SPS_E_SHAPE, "L range");
+    if (!(cfg->eps0 > 0) || !(cfg->target_accept > 0 && cfg->target_accept < 1))
+        return fail(SPS_E_INVALID_ARG, "eps0 / target_accept");
+    if (!theta0_unb || !mag_obs || !sigma || !mask) return fail(SPS_E_INVALID_ARG, "null input");
+    const int64_t G = ctx->n_gal;
+    const int C = cfg->chains_per_gal;
+    const int64_t NC = G * C;
+    if (NC > ((int64_t)1 << 31)) return fail(SPS_E_SHAPE, "too many chains");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const Consts& c = ctx->c;
+    const size_t GB = (size_t)G * c.n_band;
+    // maximum observed band count decides the shared table size
+    std::vector<uint32_t> mh((size_t)G);
+    if (is_device_ptr(mask)) CK(cudaMemcpy(mh.data(), mask, G * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(mh.data(), mask, G * 4);
+    const uint32_t all = (c.n_band >= 32) ? 0xffffffffu : ((1u << c.n_band) - 1u);
+    int nb_max = 0;
+    std::vector<int32_t> order((size_t)G);
+    std::vector<int> nbs((size_t)G);
+    for (int64_t g = 0; g < G; ++g) {
+        nbs[g] = __builtin_popcount(mh[g] & all);
+        nb_max = std::max(nb_max, nbs[g]);
+        order[g] = (int32_t)g;
+    }
+    // longest work first (more observed bands = more work per gradient)
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return nbs[a] > nbs[b]; });
+    Stager st{ctx, s};
+    const float* x0 = st.in(theta0_unb, (size_t)NC * SPS_NPARAM);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)G);
+    const int32_t* ord = st.in(order.data(), (size_t)G);
+    float* so = st.out(samples_out, (size_t)NC * cfg->n_samp * SPS_NPARAM);
+    float* acc = stats ? st.out(stats->accept_prob, (size_t)NC) : nullptr;
+    float* epo = stats ? st.out(stats->step_size, (size_t)NC) : nullptr;
+    int32_t* dv = stats ? st.out(stats->divergences, (size_t)NC) : nullptr;
+    int64_t* nev = stats ? st.out(stats->grad_evals, (size_t)NC) : nullptr;
+    int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+
+    HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
+                 cfg->seed, 0};
+    const size_t table_bytes = (size_t)nb_max * c.K * sizeof(float);
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, ctx->device));
+    const int sms = prop.multiProcessorCount;
+    // launch shape: warps per block from {C, 2C (>= 2 warps)}, blocks = occupancy x SMs
+    std::vector<int> cand_w = {C};
+    if (2 * C <= 16) cand_w.push_back(2 * C);
+    if (C < 4 && 4 <= 16) cand_w.push_back(4);
+    const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max);
+    auto shape_for = [&](int warps, int& blocks) -> cudaError_t {
+        size_t smem = hmc_warp_smem_bytes() * warps + table_bytes;
+        cudaError_t e = hmc_set_smem(smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = hmc_occupancy(warps, smem, &per_sm);
+        if (e != cudaSuccess) return e;
+        blocks = std::max(1, per_sm) * sms;
+        return cudaSuccess;
+    };
+    int warps = C, blocks = sms;
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        warps = it->second.first;
+        blocks = it->second.second;
+        CK(hmc_set_smem(hmc_warp_smem_bytes() * warps + table_bytes));
+    } else if (cfg->autotune && cand_w.size() > 1 && G >= 64) {
+        // time each candidate on a short run over a slice of the galaxies
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        HmcParams tp = hp;
+        tp.n_warm = 2;
+        tp.n_samp = 0;
+        Galaxies gsub = ctx->gal();
+        for (int w : cand_w) {
+            int b = 0;
+            CK(shape_for(w, b));
+            gsub.n = std::min<int64_t>(G, (int64_t)b * std::max(1, w / C) * 2);
+            CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s));
+            CK(cudaEventRecord(e0, s));
+            CK(launch_hmc_approx(c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, ctx->queue.as<int>(), ctx->err.as<int>(), b, w,
+                                 table_bytes, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            float per = ms / (float)gsub.n;
+            if (per < best) {
+                best = per;
+                warps = w;
+                blocks = b;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->tuned[key] = {warps, blocks};
+        CK(hmc_set_smem(hmc_warp_smem_bytes() * warps + table_bytes));
+    } else {
+        CK(shape_for(warps, blocks));
+    }
+
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        return launch_hmc_approx(c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+                                 ctx->queue.as<int>(), ctx->err.as<int>(), blocks, warps, table_bytes, s);
+    };
+    if (cfg->use_graph) {
+        char kb[512];
+        std::snprintf(kb, sizeof(kb), "%p%p%p%p%p%p%p%p%p%p%p%lld%d%d%d%d%d%d%llu%g%g", (const void*)x0,
+                      (const void*)mo, (const void*)sg, (const void*)mk, (const void*)ord, (void*)so,
+                      (void*)acc, (void*)epo, (void*)dv, (void*)nev, (void*)sto, (long long)G, C,
+                      hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, (unsigned long long)hp.seed,
+                      (double)hp.eps0, (double)hp.target_accept);
+        std::string gk = std::string(kb) + ":" + std::to_string(blocks);
+        if (!ctx->graph || gk != ctx->graph_key) {
+            if (ctx->graph) {
+                cudaGraphExecDestroy(ctx->graph);
+                ctx->graph = nullptr;
+            }
+            cudaStream_t cs;
+            CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            cudaStream_t saved = s;
+            s = cs;
+            cudaError_t e = enqueue();
+            s = saved;
+            cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) return cuda_fail(e, "capture");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+            CK(cudaGraphInstantiate(&ctx->graph, gr, 0));
+            cudaGraphDestroy(gr);
+            ctx->graph_key = gk;
+        }
+        CK(cudaGraphLaunch(ctx->graph, s));
+    } else {
+        CK(enqueue());
+    }
+    CK(st.finish());
+    return SPS_OK;
+}

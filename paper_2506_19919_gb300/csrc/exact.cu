@@ -1,0 +1,482 @@
+// Exact photometry (Eq. photo_integral_exact) and its adjoint, as a chain of
+// kernels over a block of rows:
+//   weights : W[r][ij] = w_i q_j (FP32, or BF16 scaled by 2^{e_i})
+//   fwd     : S = W L over the wavelength grid, reduced in the epilogue with
+//             the dust curve and the redshifted band weights into
+//             A[r][b][0..3] = sum_n wb S (1, E, E base, E dterm)   (10^-0.4A = E)
+//   like    : magnitudes, log L, gamma_b / c_b, dust and lgM gradients
+//   vgen    : v[r][n] = F_att(n) sum_b (gamma_b / c_b) wb(n)
+//   adj     : Wbar = v L^T (the second contraction: recomputed, not stored)
+//   grad    : Wbar -> d logL / d theta through the SFH, burst and MDF weights
+// This file holds the SIMT contraction kernels.
+#include <cuda_bf16.h>
+
+#include "sps_device.cuh"
+
+namespace sps {
+
+namespace {
+
+constexpr int kBM = 64, kBN = 128, kBK = 16, kThreads = 256;
+
+__device__ __forceinline__ float bf16_to_f(uint16_t h) { return __uint_as_float(((uint32_t)h) << 16); }
+__device__ __forceinline__ uint16_t f_to_bf16(float f) {
+    __nv_bfloat16 b = __float2bfloat16_rn(f);
+    return *reinterpret_cast<uint16_t*>(&b);
+}
+template <typename T>
+__device__ __forceinline__ float ld_elem(const T* p);
+template <>
+__device__ __forceinline__ float ld_elem<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld_elem<uint16_t>(const uint16_t* p) { return bf16_to_f(__ldg(p)); }
+
+// ---------------------------------------------------------------- weights
+__global__ void __launch_bounds__(32 * kWarpsApprox)
+k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
+          const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
+          int bf16, float* __restrict__ W32, uint16_t* __restrict__ Wbf) {
+    __shared__ RowScratch scratch[kWarpsApprox];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    RowScratch& s = scratch[warp];
+    for (int64_t row = (int64_t)blockIdx.x * kWarpsApprox + warp; row < n;
+         row += (int64_t)gridDim.x * kWarpsApprox) {
+        const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+        RowParams p;
+        load_params(c, theta + row * SPS_NPARAM, false, p);
+        if (gi < 0 || gi >= g.n) p.finite = false;
+        if (p.finite) {
+            age_met_weights(c, s, g.bins + (size_t)gi * c.n_age, g.lnT[gi], g.lT10[gi], p, false);
+        } else {
+            for (int i = lane; i < c.n_age; i += 32) s.w[i] = __int_as_float(0x7fc00000);
+            if (lane < c.n_met) s.q[lane] = 1.0f;
+            __syncwarp();
+        }
+        for (int k = lane; k < c.k_pad; k += 32) {
+            float v = 0.0f;
+            int i = 0;
+            if (k < c.K) {
+                i = k / c.n_met;
+                v = s.w[i] * s.q[k % c.n_met];
+            }
+            if (bf16) Wbf[row * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
+            else W32[row * c.k_pad + k] = v;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- SIMT NN tile
+// acc[4][8] of thread (ty, tx) = rows m0 + 4 ty + i, columns n0 + 8 tx + j of
+// A[m][0:red] * B[0:red][n]; A rows red-contiguous (lda), B rows n-contiguous (ldb).
+template <typename TA, typename TB>
+__device__ __forceinline__ void tile_contract(const TA* __restrict__ A, int64_t lda, int64_t m0,
+                                              int64_t M, const TB* __restrict__ Bm, int64_t ldb,
+                                              int n0, int N, int red, float (&As)[kBK][kBM + 4],
+                                              float (&Bs)[kBK][kBN], float (&acc)[4][8]) {
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < red; k0 += kBK) {
+        for (int e = tid; e < kBM * kBK; e += kThreads) {
+            int mm = e / kBK, kk = e % kBK;
+            int64_t m = m0 + mm;
+            int k = k0 + kk;
+            As[kk][mm] = (m < M && k < red) ? ld_elem<TA>(A + m * lda + k) : 0.0f;
+        }
+        for (int e = tid; e < kBK * kBN; e += kThreads) {
+            int kk = e / kBN, nn = e % kBN;
+            int k = k0 + kk, nidx = n0 + nn;
+            Bs[kk][nn] = (k < red && nidx < N) ? ld_elem<TB>(Bm + (int64_t)k * ldb + nidx) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            float a[4], b[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx * 8 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- forward + epilogue
+// One block per 64 rows, looping over every wavelength tile; the epilogue
+// folds each tile into A[r][b][4] in shared memory (fixed order).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
+            const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
+            const T* __restrict__ W, const T* __restrict__ Ltab, float* __restrict__ cJ) {
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN];
+    __shared__ float4 lc[kBN];
+    __shared__ float lamt[kBN];
+    __shared__ float4 rdust[kBM];  // A_V/4.05, delta, F_floor, E_b
+    extern __shared__ float dyn[];
+    const int B = c.n_band;
+    float* accsm = dyn;                                              // [kBM][B][4]
+    int2* sup = reinterpret_cast<int2*>(dyn + kBM * B * 4);          // [kBM][B]
+    float2* ga = reinterpret_cast<float2*>(sup + kBM * B);           // [kBM][B]
+    const int64_t m0 = (int64_t)blockIdx.x * kBM;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int e = tid; e < kBM * B * 4; e += kThreads) accsm[e] = 0.0f;
+    for (int e = tid; e < kBM * B; e += kThreads) {
+        int r = e / B, b = e % B;
+        int64_t row = m0 + r;
+        int64_t gi = (row < n) ? (gal_idx ? (int64_t)gal_idx[row] : row) : -1;
+        if (gi >= 0 && gi < g.n) {
+            sup[e] = g.support[gi * B + b];
+            ga[e] = g.gauss[gi * B + b];
+        } else {
+            sup[e] = make_int2(0, 0);
+            ga[e] = make_float2(0.f, 0.f);
+        }
+    }
+    for (int r = tid; r < kBM; r += kThreads) {
+        int64_t row = m0 + r;
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < n) {
+            const float* t = theta + row * SPS_NPARAM;
+            d = make_float4(t[9] * (1.0f / 4.05f), t[10], t[11], fmaxf(0.85f - 1.9f * t[10], 0.0f));
+        }
+        rdust[r] = d;
+    }
+    __syncthreads();
+    float acc[4][8];
+    for (int n0 = 0; n0 < c.n_lam; n0 += kBN) {
+        tile_contract<T, T>(W, c.k_pad, m0, n, Ltab, c.lam_pad, n0, c.n_lam, c.K, As, Bs, acc);
+        for (int t = tid; t < kBN; t += kThreads) {
+            int nn = n0 + t;
+            lc[t] = (nn < c.n_lam) ? grid.lamc[nn] : make_float4(0.f, 0.f, 0.f, 0.f);
+            lamt[t] = (nn < c.n_lam) ? grid.lam[nn] : 0.0f;
+        }
+        __syncthreads();
+        for (int b = 0; b < B; ++b) {
+            const bool top = c.band_kind[b] == 0;
+            float v[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.0f;
+                const int r = ty * 4 + i;
+                const int2 sp = sup[r * B + b];
+                const float2 gg = ga[r * B + b];
+                const float4 rd = rdust[r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int nl = tx * 8 + j, nn = n0 + nl;
+                    if (nn >= sp.x && nn < sp.y) {
+                        const float4 L4 = lc[nl];
+                        float wb = L4.x;
+                        if (!top) {
+                            float u = (lamt[nl] - gg.x) * gg.y;
+                            wb *= __expf(-0.5f * u * u);
+                        }
+                        float pw = __expf(rd.y * L4.z);
+                        float base = L4.y * pw + rd.w * L4.w;
+                        float E = exp2f(-0.4f * kLog2_10f * rd.x * base);
+                        float dterm = L4.y * pw * L4.z - (rd.w > 0.0f ? 1.9f * L4.w : 0.0f);
+                        float S = acc[i][j] * wb;
+                        float es = S * E;
+                        v[i][0] += S;
+                        v[i][1] += es;
+                        v[i][2] += es * base;
+                        v[i][3] += es * dterm;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float x = v[i][q];
+                    x += __shfl_xor_sync(kFull, x, 8);
+                    x += __shfl_xor_sync(kFull, x, 4);
+                    x += __shfl_xor_sync(kFull, x, 2);
+                    x += __shfl_xor_sync(kFull, x, 1);
+                    v[i][q] = x;
+                }
+            if (tx == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) accsm[((ty * 4 + i) * B + b) * 4 + q] += v[i][q];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kBM * B * 4; e += kThreads) {
+        int64_t row = m0 + e / (B * 4);
+        if (row < n) cJ[m0 * B * 4 + e] = accsm[e];
+    }
+}
+
+// ---------------------------------------------------------------- likelihood
+// One thread per row.  cJ -> magnitudes, log L, gbar[r][b] = gamma_b / c_b
+// and rowinfo[r] = (dlogL/dlgM, dA_V, ddelta, dF_floor).
+__global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
+                             const float* __restrict__ theta, const int32_t* __restrict__ gal_idx,
+                             int64_t n, const float* __restrict__ cJ,
+                             const float* __restrict__ mag_obs, const float* __restrict__ sigma,
+                             const uint32_t* __restrict__ mask, float* __restrict__ mag_out,
+                             float* __restrict__ ll_out, float* __restrict__ gbar,
+                             float* __restrict__ rowinfo, int* __restrict__ nonfinite) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int B = c.n_band;
+    const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+    if (gi < 0 || gi >= g.n) {
+        atomicOr(nonfinite, 1);
+        if (ll_out) ll_out[row] = __int_as_float(0x7fc00000);
+        for (int b = 0; b < B; ++b) {
+            if (mag_out) mag_out[row * B + b] = __int_as_float(0x7fc00000);
+            if (gbar) gbar[row * B + b] = 0.0f;
+        }
+        if (rowinfo)
+            for (int q = 0; q < 4; ++q) rowinfo[row * 4 + q] = 0.0f;
+        return;
+    }
+    const float* t = theta + row * SPS_NPARAM;
+    const float lgM = t[0], AV = t[9], ff = t[11];
+    const uint32_t bits = mask ? mask[gi] : 0u;
+    double ll = 0.0;
+    float g0 = 0.f, gAV = 0.f, gdl = 0.f, gff = 0.f;
+    bool bad = false;
+    for (int b = 0; b < B; ++b) {
+        const float* a = cJ + (row * B + b) * 4;
+        float cprime = ff * a[0] + (1.0f - ff) * a[1];
+        double m = g.zp[gi * B + b] - 2.5 * (log10((double)cprime) + (double)lgM + 9.0);
+        bad = bad || !isfinite(m);
+        if (mag_out) mag_out[row * B + b] = (float)m;
+        float gb = 0.0f;
+        if ((bits >> b) & 1u) {
+            double is2 = 1.0 / ((double)sigma[gi * B + b] * (double)sigma[gi * B + b]);
+            double r = m - (double)mag_obs[gi * B + b];
+            ll += -0.5 * r * r * is2;
+            float gam = (float)(2.5 * r * is2 / 2.302585092994046);
+            gb = gam / cprime;
+            g0 += gam * kLn10f;
+            gAV += gb * (1.0f - ff) * (-0.4f * kLn10f / 4.05f) * a[2];
+            gdl += gb * (1.0f - ff) * (-0.4f * kLn10f) * (AV / 4.05f) * a[3];
+            gff += gb * (a[0] - a[1]);
+        }
+        if (gbar) gbar[row * B + b] = gb;
+    }
+    if (ll_out) ll_out[row] = (float)ll;
+    if (rowinfo) {
+        rowinfo[row * 4 + 0] = g0;
+        rowinfo[row * 4 + 1] = gAV;
+        rowinfo[row * 4 + 2] = gdl;
+        rowinfo[row * 4 + 3] = gff;
+    }
+    if (bad || (mask && !isfinite(ll))) atomicOr(nonfinite, 1);
+}
+
+// ---------------------------------------------------------------- adjoint source
+// One block per row: v[n] = F_att(n) sum_b gbar_b wb(n), zero beyond the grid.
+__global__ void __launch_bounds__(256)
+k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
+             const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
+             const float* __restrict__ gbar, float* __restrict__ V) {
+    __shared__ float gb[kMaxBands];
+    __shared__ int2 sp[kMaxBands];
+    __shared__ float2 gg[kMaxBands];
+    const int64_t row = blockIdx.x;
+    if (row >= n) return;
+    const int B = c.n_band;
+    int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+    if (gi < 0 || gi >= g.n) gi = 0;          // row already flagged; gbar is zero
+    if (threadIdx.x < B) {
+        gb[threadIdx.x] = gbar[row * B + threadIdx.x];
+        sp[threadIdx.x] = g.support[gi * B + threadIdx.x];
+        gg[threadIdx.x] = g.gauss[gi * B + threadIdx.x];
+    }
+    __syncthreads();
+    const float* t = theta + row * SPS_NPARAM;
+    const float AV = t[9], dl = t[10], ff = t[11];
+    for (int nn = threadIdx.x; nn < c.lam_pad; nn += blockDim.x) {
+        float v = 0.0f;
+        if (nn < c.n_lam) {
+            const float4 L4 = grid.lamc[nn];
+            const float lam = grid.lam[nn];
+            float sum = 0.0f;
+            for (int b = 0; b < B; ++b) {
+                if (gb[b] != 0.0f && nn >= sp[b].x && nn < sp[b].y) {
+                    float wb = L4.x;
+                    if (c.band_kind[b] != 0) {
+                        float u = (lam - gg[b].x) * gg[b].y;
+                        wb *= __expf(-0.5f * u * u);
+                    }
+                    sum = fmaf(gb[b], wb, sum);
+                }
+            }
+            if (sum != 0.0f) v = dust_eval(L4.y, L4.z, L4.w, AV, dl, ff).F * sum;
+        }
+        V[row * c.lam_pad + nn] = v;
+    }
+}
+
+// ---------------------------------------------------------------- adjoint contraction
+// Wbar[m][k] = sum_n V[m][n] Lt[n][k] (x 2^{e_i} for the scaled BF16 table).
+template <typename TB>
+__global__ void __launch_bounds__(kThreads)
+k_exact_adj(const __grid_constant__ Consts c, const Grid grid, int64_t n,
+            const float* __restrict__ V, const TB* __restrict__ Lt, int scaled,
+            float* __restrict__ Wbar) {
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN];
+    const int64_t m0 = (int64_t)blockIdx.x * kBM;
+    const int n0 = blockIdx.y * kBN;
+    float acc[4][8];
+    tile_contract<float, TB>(V, c.lam_pad, m0, n, Lt, c.k_pad, n0, c.K, c.n_lam, As, Bs, acc);
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t row = m0 + ty * 4 + i;
+        if (row >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            int k = n0 + tx * 8 + j;
+            if (k < c.K) {
+                float v = acc[i][j];
+                if (scaled) v *= grid.row_scale[k / c.n_met];
+                Wbar[row * c.k_pad + k] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- gradient assembly
+__global__ void __launch_bounds__(32 * kWarpsApprox)
+k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
+             const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ rowinfo,
+             const float* __restrict__ Wbar, float* __restrict__ grad_out) {
+    __shared__ RowScratch scratch[kWarpsApprox];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    RowScratch& s = scratch[warp];
+    const int A = c.n_age, Zn = c.n_met, K = c.K;
+    for (int64_t row = (int64_t)blockIdx.x * kWarpsApprox + warp; row < n;
+         row += (int64_t)gridDim.x * kWarpsApprox) {
+        const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+        RowParams p;
+        load_params(c, theta + row * SPS_NPARAM, false, p);
+        if (gi < 0 || gi >= g.n) p.finite = false;
+        if (!p.finite) {
+            if (lane < SPS_NPARAM) grad_out[row * SPS_NPARAM + lane] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const double M = age_met_weights(c, s, g.bins + (size_t)gi * A, g.lnT[gi], g.lT10[gi], p, true);
+        for (int k = lane; k < K; k += 32) s.u.kbuf[k] = Wbar[row * c.k_pad + k];
+        __syncwarp();
+        for (int i = lane; i < A; i += 32) {
+            float a = 0.0f;
+            for (int j = 0; j < Zn; ++j) a = fmaf(s.u.kbuf[i * Zn + j], s.q[j], a);
+            s.wb[i] = a;
+        }
+        if (lane < Zn) {
+            float a = 0.0f;
+            for (int i = 0; i < A; ++i) a = fmaf(s.u.kbuf[i * Zn + lane], s.w[i], a);
+            s.qb[lane] = a;
+        }
+        __syncwarp();
+        float gr[SPS_NPARAM];
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) gr[k] = 0.0f;
+        gr[0] = rowinfo[row * 4 + 0];
+        gr[9] = rowinfo[row * 4 + 1];
+        gr[10] = rowinfo[row * 4 + 2];
+        gr[11] = rowinfo[row * 4 + 3];
+        age_met_adjoint(c, s, g.lT10[gi], M, p, gr);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < SPS_NPARAM; ++k) grad_out[row * SPS_NPARAM + k] = gr[k];
+        }
+        __syncwarp();
+    }
+}
+
+int blocks_rows(int64_t rows, int per_block) {
+    int64_t b = (rows + per_block - 1) / per_block;
+    if (b > 152LL * 64) b = 152LL * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
+                                 const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
+                                 float* W32, uint16_t* Wbf, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_weights<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, grid, g, theta, gal_idx,
+                                                                         n, bf16, W32, Wbf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
+                             const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
+                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t dyn = (size_t)kBM * c.n_band * (4 * sizeof(float) + sizeof(int2) + sizeof(float2));
+    const unsigned grid_m = (unsigned)((n + kBM - 1) / kBM);
+    if (bf16) {
+        cudaFuncSetAttribute(k_exact_fwd<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_exact_fwd<uint16_t><<<grid_m, kThreads, dyn, s>>>(c, grid, g, theta, gal_idx, n, Wbf,
+                                                            grid.ssp_bf, cJ);
+    } else {
+        cudaFuncSetAttribute(k_exact_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        k_exact_fwd<float><<<grid_m, kThreads, dyn, s>>>(c, grid, g, theta, gal_idx, n, W32,
+                                                         grid.ssp, cJ);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* theta,
+                              const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
+                              const float* mag_obs, const float* sigma, const uint32_t* mask,
+                              float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_exact_like<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, g, theta, gal_idx, n, cJ, mag_obs,
+                                                             sigma, mask, mag_out, loglike_out, gbar,
+                                                             rowinfo, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
+                              const float* theta, const int32_t* gal_idx, int64_t n,
+                              const float* gbar, float* V32, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int bf16,
+                             const float* V32, float* Wbar, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    dim3 grd((unsigned)((n + kBM - 1) / kBM), (unsigned)((c.K + kBN - 1) / kBN));
+    if (bf16)
+        k_exact_adj<uint16_t><<<grd, kThreads, 0, s>>>(c, grid, n, V32, grid.ssp_t_bf, 1, Wbar);
+    else
+        k_exact_adj<float><<<grd, kThreads, 0, s>>>(c, grid, n, V32, grid.ssp_t, 0, Wbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
+                              const int32_t* gal_idx, int64_t n, const float* rowinfo,
+                              const float* Wbar, float* grad_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_exact_grad<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, g, theta, gal_idx, n,
+                                                                            rowinfo, Wbar, grad_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sps

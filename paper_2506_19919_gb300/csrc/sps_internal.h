@@ -1,0 +1,125 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sps.h"
+
+namespace sps {
+
+constexpr int kMaxAges = SPS_MAX_AGES;   // bins per row held in shared memory
+constexpr int kMaxMets = SPS_MAX_METS;
+constexpr int kMaxBands = SPS_MAX_BANDS;
+constexpr int kMaxGL = 16;
+constexpr int kMaxPanels = 512;          // SFH panels per row (checked on the host)
+constexpr int kKTileMax = 41;            // ceil(K / 32) held in registers: K <= 1312
+constexpr int kWarpsApprox = 4;          // warps per block of the fused approximate kernel
+
+// Tables-wide constants handed to every kernel by value.
+struct Consts {
+    int n_age, n_met, n_lam, n_band, K, k_pad;
+    int lam_pad;                          // wavelength stride of the padded tables
+    int gl_order;
+    float panel;                          // max panel width in ln t
+    float gl_x[kMaxGL], gl_w[kMaxGL];     // Gauss-Legendre rule on [-1, 1]
+    float log_age_edge[kMaxAges + 1];     // log10 age-bin edges [yr]; [0] = -100 stand-in
+    float lgz_edge[kMaxMets + 1];         // metallicity-bin edges; outer +-inf
+    float prior_lo[SPS_NPARAM], prior_span[SPS_NPARAM];
+    int band_kind[kMaxBands];
+};
+
+// Per-galaxy tables built by sps_set_galaxies (device, structure of arrays).
+struct Galaxies {
+    int64_t n;
+    const float* z;          // [G]
+    const float* lnT;        // [G] ln(t_obs / Gyr)
+    const float* lT10;       // [G] log10(t_obs / yr)
+    const float2* bins;      // [G][A] (centre, half-width) in ln(t/Gyr); Big-Bang bin: (ln t_hi, -1)
+    const double* zp;        // [G][B] AB zero point: m = zp - 2.5 log10(c)
+    const int2* support;     // [G][B] wavelength index range [lo, hi) of the redshifted band
+    const float2* gauss;     // [G][B] (rest centre, (1+z)/s) of a Gaussian band
+    const float* cssp;       // [G][B][K] per-galaxy c_SSP (approximate path) or nullptr
+    const float4* dust_eff;  // [G][B] (k0, ln(l/lV), Drude, lambda_eff) at lambda_eff
+};
+
+// Per-wavelength constants of the rest grid (device).
+struct Grid {
+    const float* lam;        // [L] Angstrom
+    const float4* lamc;      // [L] (q_n / lambda_n, k0, ln(lambda/lambda_V), Drude shape)
+    const double* lam64;     // [L] Angstrom, FP64
+    const float* ssp_t;      // [lam_pad][k_pad] SSP table transposed, FP32 (zero padded)
+    const float* ssp;        // [k_pad][lam_pad] SSP table, FP32 (zero padded)
+    const uint16_t* ssp_bf;  // [k_pad][lam_pad] SSP table, BF16 bits, row-scaled by 2^-e_i
+    const uint16_t* ssp_t_bf;// [lam_pad][k_pad] transposed BF16 row-scaled
+    const float* row_scale;  // [A] 2^e_i
+};
+
+// Launchers (defined in the .cu files); all return cudaError_t of the launch.
+cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const double* lam64,
+                                    const double* band_p0, const double* band_p1,
+                                    const double* age_edges_yr, const float* z, int64_t n_gal,
+                                    double h0, double om, float* lnT, float* lT10, float2* bins,
+                                    double* zp, int2* support, float2* gauss, float4* dust_eff,
+                                    cudaStream_t s);
+cudaError_t launch_cssp(const Consts& c, const Grid& grid, const Galaxies& g,
+                        const double* band_p0, float* cssp, cudaStream_t s);
+
+// Row evaluation of the approximate path (photometry / log-likelihood + gradient).
+cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* theta,
+                               int theta_unbounded, const int32_t* gal_idx, int64_t n,
+                               const float* mag_obs, const float* sigma, const uint32_t* mask,
+                               float* mag_out, float* loglike_out, float* grad_out,
+                               double* logp_out, int* nonfinite, cudaStream_t s);
+
+// Exact path pieces.
+cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
+                                 const float* theta, const int32_t* gal_idx, int64_t n,
+                                 int bf16, float* W32, uint16_t* Wbf, cudaStream_t s);
+cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
+                             const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
+                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s);
+cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32,
+                                 cudaStream_t s);
+cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* theta,
+                              const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
+                              const float* mag_obs, const float* sigma, const uint32_t* mask,
+                              float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
+                              cudaStream_t s);
+cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
+                              const float* theta, const int32_t* gal_idx, int64_t n,
+                              const float* gbar, float* V32, cudaStream_t s);
+cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int bf16,
+                             const float* V32, float* Wbar, cudaStream_t s);
+cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
+                              const int32_t* gal_idx, int64_t n, const float* rowinfo,
+                              const float* Wbar, float* grad_out, cudaStream_t s);
+
+cudaError_t launch_weights_rows(const Consts& c, const Galaxies& g, const float* theta,
+                                const int32_t* gal_idx, int64_t n, float* W_out,
+                                double* mstar_out, cudaStream_t s);
+
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out,
+                          cudaStream_t s);
+
+// HMC.
+struct HmcParams {
+    int chains_per_gal, n_warm, n_samp, L_min, L_max;
+    float target_accept, eps0;
+    uint64_t seed;
+    long long spin_limit;   // bound on the work-queue wait
+};
+struct HmcState;            // per-chain state, device
+cudaError_t launch_hmc_approx(const Consts& c, const Galaxies& g, const HmcParams& hp,
+                              const float* theta0, const float* mag_obs, const float* sigma,
+                              const uint32_t* mask, const int32_t* gal_order, float* samples,
+                              float* acc, float* eps_out, int32_t* div, int64_t* nevals,
+                              int32_t* status, int* queue, int* err, int grid_blocks,
+                              int warps_per_block, size_t smem_cssp_bytes, cudaStream_t s);
+cudaError_t launch_leapfrog(const Consts& c, const Galaxies& g, const float* x0,
+                            const float* p0, const float* eps, const int32_t* L,
+                            const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                            const float* sigma, const uint32_t* mask, float* x_out,
+                            float* p_out, double* logp_out, cudaStream_t s);
+
+}  // namespace sps

@@ -1,0 +1,240 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (stated by the target accuracy of the method):
+  magnitudes: 1e-3 mag for FP32 paths, 5e-3 mag for the BF16 contraction;
+  gradients:  max_k |g_k - g_ref,k| / max_k |g_ref,k| <= 1e-4 per row (FP32);
+  SSP weights and masses: 1e-5 relative (FP32 arithmetic, FP64 mass sum).
+"""
+import numpy as np
+import pytest
+import torch
+
+import sps_workloads as W
+from oracle import hmc as OH
+from oracle import sps as O
+
+pytestmark = pytest.mark.gpu
+
+MAG_TOL = 1e-3
+MAG_TOL_BF16 = 5e-3
+GRAD_TOL = 1e-4
+
+
+def _ctx(tables, z, approx=True):
+    import paper_2506_19919_gb300 as pkg
+    ctx = pkg.Context(tables, device=0)
+    ctx.set_galaxies(z, build_approx=approx)
+    return ctx
+
+
+def _grad_rel(g, ref):
+    g, ref = np.asarray(g, np.float64), np.asarray(ref, np.float64)
+    return (np.abs(g - ref).max(1) / np.abs(ref).max(1)).max()
+
+
+@pytest.fixture(scope="module")
+def parity64():
+    """64 galaxies, 50 ages x 6 Z x 2000 lambda, 6 top-hats, z ~ U(0.05, 1)."""
+    wl = W.config(0)
+    return wl, _ctx(wl.tables, wl.z)
+
+
+@pytest.fixture(scope="module")
+def prod96():
+    """96 galaxies (one full 64-row tile plus a ragged one) on the production
+    grid (107 x 12 x 5994), 6 Gaussian bands, z ~ U(0.05, 3)."""
+    wl = W.config(1, n_gal=96)
+    return wl, _ctx(wl.tables, wl.z)
+
+
+def test_weights_and_mass(parity64):
+    wl, ctx = parity64
+    Wg, Mg = ctx.weights(wl.theta)
+    th = torch.as_tensor(wl.theta, dtype=torch.float64)
+    Wr, Mr, _, _ = O.ssp_weights(th, wl.tables, O.t_obs_gyr(wl.z))
+    np.testing.assert_allclose(Mg.cpu().numpy(), Mr.numpy(), rtol=1e-6)
+    Wr = Wr.reshape(64, -1).numpy()
+    err = np.abs(Wg.cpu().numpy() - Wr).max(1) / Wr.max(1)
+    assert err.max() < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", MAG_TOL), ("bf16", MAG_TOL_BF16)])
+def test_exact_photometry_parity64(parity64, prec, tol):
+    wl, ctx = parity64
+    m = ctx.photometry(wl.theta, mode="exact", prec=prec).cpu().numpy()
+    ref = O.photometry(wl.theta, wl.z, wl.tables, "exact").numpy()
+    assert np.abs(m - ref).max() < tol
+
+
+@pytest.mark.parametrize("mode,prec,tol", [("exact", "fp32", MAG_TOL), ("exact", "bf16", MAG_TOL_BF16),
+                                           ("approx", "fp32", MAG_TOL)])
+def test_photometry_production_grid(prod96, mode, prec, tol):
+    wl, ctx = prod96
+    m = ctx.photometry(wl.theta, mode=mode, prec=prec).cpu().numpy()
+    ref = O.photometry(wl.theta, wl.z, wl.tables, mode).numpy()
+    assert np.abs(m - ref).max() < tol
+
+
+@pytest.mark.parametrize("mode", ["approx", "exact"])
+def test_loglike_grad_production_grid(prod96, mode):
+    wl, ctx = prod96
+    th_true = torch.as_tensor(wl.theta_true, dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z, wl.tables, mode).numpy() + wl.noise
+    ev = W.prior_draw(np.random.default_rng(17), wl.n_gal)      # independent evaluation point
+    ll, g = ctx.loglike_grad(ev, mobs, wl.sigma, wl.mask, mode=mode)
+    llr, gr, _ = O.loglike_and_grad(ev, wl.z, wl.tables, mobs, wl.sigma, wl.mask, mode)
+    np.testing.assert_allclose(ll.cpu().numpy(), llr.numpy(), rtol=2e-4)
+    assert _grad_rel(g.cpu().numpy(), gr.numpy()) < GRAD_TOL
+
+
+@pytest.mark.parametrize("mode", ["approx", "exact"])
+def test_loglike_grad_near_truth(prod96, mode):
+    """Near the data the residuals are ~ sigma and the gradient is most
+    sensitive to magnitude rounding."""
+    wl, ctx = prod96
+    th_true = torch.as_tensor(wl.theta_true, dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z, wl.tables, mode).numpy() + wl.noise
+    ll, g = ctx.loglike_grad(wl.theta_true, mobs, wl.sigma, wl.mask, mode=mode)
+    llr, gr, _ = O.loglike_and_grad(wl.theta_true, wl.z, wl.tables, mobs, wl.sigma, wl.mask, mode)
+    np.testing.assert_allclose(ll.cpu().numpy(), llr.numpy(), rtol=1e-3, atol=1e-3)
+    assert _grad_rel(g.cpu().numpy(), gr.numpy()) < GRAD_TOL
+
+
+def test_masks_gal_idx_and_host_pointers(prod96):
+    """Uneven band masks, rows that repeat galaxies (chains), and host
+    buffers through the same C ABI give the same numbers."""
+    wl, ctx = prod96
+    rng = np.random.default_rng(3)
+    mask = rng.integers(1, 64, size=wl.n_gal).astype(np.uint32)
+    gidx = rng.integers(0, wl.n_gal, size=40).astype(np.int32)
+    ev = W.prior_draw(rng, 40)
+    mobs = np.full((wl.n_gal, 6), 22.0) + wl.noise
+    ll_d, g_d = ctx.loglike_grad(ev, mobs, wl.sigma, mask, gal_idx=gidx, mode="approx")
+    llr, gr, _ = O.loglike_and_grad(ev, wl.z[gidx], wl.tables, mobs[gidx], wl.sigma[gidx],
+                                    mask[gidx], "approx")
+    np.testing.assert_allclose(ll_d.cpu().numpy(), llr.numpy(), rtol=2e-4)
+    assert _grad_rel(g_d.cpu().numpy(), gr.numpy()) < GRAD_TOL
+    ll_h, g_h = ctx.loglike_grad(torch.as_tensor(ev, dtype=torch.float32), mobs, wl.sigma, mask,
+                                 gal_idx=gidx, mode="approx")
+    torch.testing.assert_close(ll_h.cpu(), ll_d.cpu(), rtol=0, atol=0)
+
+
+def test_nonfinite_rows_flagged(parity64):
+    import paper_2506_19919_gb300 as pkg
+    wl, ctx = parity64
+    th = wl.theta.copy()
+    th[5, 3] = np.nan
+    with pytest.raises(pkg.SpsError) as e:
+        ctx.photometry(th, mode="approx")
+    assert e.value.status == 3
+    m = torch.empty((64, 6), dtype=torch.float32, device="cuda")
+    try:
+        ctx.photometry(th, mode="approx", out=m)
+    except pkg.SpsError:
+        pass
+    m = m.cpu().numpy()
+    assert np.isnan(m[5]).all() and np.isfinite(np.delete(m, 5, 0)).all()
+
+
+def test_philox_matches_oracle_bit_exact(parity64):
+    _, ctx = parity64
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = 0x1234_5678_9ABC_DEF0
+    out = ctx.philox(ctr, key)
+    ref = OH.philox4x32_10(ctr.astype(np.uint64), np.tile(
+        np.array([key & 0xFFFFFFFF, key >> 32], np.uint64), (4096, 1)))
+    np.testing.assert_array_equal(out.astype(np.uint64), ref)
+
+
+def test_leapfrog_trajectories_match_oracle(prod96):
+    wl, ctx = prod96
+    n = 12
+    th_true = torch.as_tensor(wl.theta_true[:n], dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z[:n], wl.tables, "approx").numpy() + wl.noise[:n]
+    x0 = W.unbounded_of(wl.theta_true[:n])
+    p0 = np.random.default_rng(4).normal(size=(n, 12)).astype(np.float32).astype(np.float64)
+    eps = np.full(n, 2e-3, np.float32)
+    L = np.full(n, 8, np.int32)
+    xg, pg, lg = ctx.leapfrog(x0, p0, eps, L, mobs, wl.sigma[:n], wl.mask[:n],
+                              gal_idx=np.arange(n, dtype=np.int32))
+    tgt = OH.ApproxTarget(wl.tables, wl.z[:n], mobs, wl.sigma[:n], wl.mask[:n], W.PRIOR_LO,
+                          W.PRIOR_HI)
+    rows = np.arange(n)
+    _, g0 = tgt(x0, rows)
+    xr, pr, _, lr = OH.leapfrog(tgt, rows, x0, p0, g0, eps.astype(np.float64), L)
+    np.testing.assert_allclose(xg.cpu().numpy(), xr, rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(pg.cpu().numpy(), pr, rtol=1e-3, atol=1e-3 * np.abs(pr).max())
+    np.testing.assert_allclose(lg.cpu().numpy(), lr, rtol=1e-5, atol=1e-3)
+
+
+def test_hmc_prior_only_matches_oracle_draws(parity64):
+    """No observed band: the target is the bounding-map prior alone, so the
+    GPU chains must reproduce the oracle's chains draw by draw (same Philox
+    stream, same dual averaging), up to FP32 rounding."""
+    wl, ctx = parity64
+    C = 2
+    x0 = np.random.default_rng(1).normal(0, 1.5, size=(64 * C, 12)).astype(np.float32)
+    mask = np.zeros(64, np.uint32)
+    out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), mask, chains_per_gal=C, n_warm=20,
+                      n_samp=10, L_min=4, L_max=12, seed=99)
+    s = out["samples"].cpu().numpy()
+
+    class Prior:
+        lo = torch.as_tensor(W.PRIOR_LO)
+        hi = torch.as_tensor(W.PRIOR_HI)
+
+        def __call__(self, x, rows):
+            x = np.asarray(x)
+            lp = -(np.abs(x) + 2 * np.log1p(np.exp(-np.abs(x)))).sum(1)
+            return lp, 1.0 - 2.0 / (1.0 + np.exp(-x))
+
+    ref = OH.run_hmc(Prior(), x0.astype(np.float64), np.zeros(64 * C, int), seed=99, n_warm=20,
+                     n_samp=10, L_min=4, L_max=12)
+    np.testing.assert_allclose(s, ref["samples"], rtol=1e-4, atol=1e-4 * (W.PRIOR_HI - W.PRIOR_LO))
+    np.testing.assert_allclose(out["step_size"].cpu().numpy(), ref["eps"], rtol=1e-4)
+    assert (out["grad_evals"].cpu().numpy() == ref["grad_evals"] + 1).all()
+
+
+def test_hmc_prior_only_is_uniform(parity64):
+    from scipy import stats
+    wl, ctx = parity64
+    C = 4
+    x0 = np.zeros((64 * C, 12), np.float32)
+    out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32),
+                      chains_per_gal=C, n_warm=100, n_samp=100, L_min=4, L_max=12, seed=5)
+    s = out["samples"].cpu().numpy().reshape(-1, 12)
+    u = (s - W.PRIOR_LO) / (W.PRIOR_HI - W.PRIOR_LO)
+    for k in range(12):
+        assert stats.kstest(u[::13, k], "uniform").pvalue > 1e-4
+
+
+@pytest.mark.parametrize("mode", ["approx", "exact"])
+def test_full_size_sampled_rows(mode):
+    """100,000 galaxies on the production grid in one call (the benchmark's
+    launch configuration); 24 sampled rows checked against the oracle."""
+    wl = W.config(2)
+    ctx = _ctx(wl.tables, wl.z, approx=(mode == "approx"))
+    G = wl.n_gal
+    pick = np.unique(np.concatenate([[0, 1, 63, 64, G - 2, G - 1],
+                                     np.random.default_rng(8).integers(0, G, 18)]))
+    mobs = np.full((G, 6), 23.0, np.float64) + wl.noise
+    th = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
+    ll, g = ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode)
+    llr, gr, _ = O.loglike_and_grad(wl.theta[pick], wl.z[pick], wl.tables, mobs[pick],
+                                    wl.sigma[pick], wl.mask[pick], mode)
+    np.testing.assert_allclose(ll.cpu().numpy()[pick], llr.numpy(), rtol=2e-4)
+    assert _grad_rel(g.cpu().numpy()[pick], gr.numpy()) < GRAD_TOL
+    m = ctx.photometry(th, mode=mode).cpu().numpy()[pick]
+    ref = O.photometry(wl.theta[pick], wl.z[pick], wl.tables, mode).numpy()
+    assert np.abs(m - ref).max() < MAG_TOL
+    ctx.close()
+
+
+def test_empty_and_single_row(parity64):
+    wl, ctx = parity64
+    out = ctx.photometry(np.zeros((0, 12), np.float32), gal_idx=np.zeros(0, np.int32), mode="approx")
+    assert out.shape == (0, 6)
+    m = ctx.photometry(wl.theta[7:8], gal_idx=np.array([7], np.int32), mode="exact").cpu().numpy()
+    ref = O.photometry(wl.theta[7:8], wl.z[7:8], wl.tables, "exact").numpy()
+    assert np.abs(m - ref).max() < MAG_TOL
