@@ -130,8 +130,10 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _hmc_workload(rank: int, n_gal: int | None = None):
+def _hmc_workload(rank: int, n_gal: int | None = None, iters=None):
     wl = W.config(3, n_gal=n_gal, seed_offset=rank)
+    if iters is not None:                      # reduced run for profiling captures only
+        wl.extra["n_warm"], wl.extra["n_samp"] = iters
     return wl
 
 
@@ -145,7 +147,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = _hmc_workload(rank)
+    wl = _hmc_workload(rank, args.gal, (args.warm, args.samp) if args.warm is not None else None)
     G, C = wl.n_gal, wl.chains
     n_warm, n_samp = wl.extra["n_warm"], wl.extra["n_samp"]
     ctx = pkg.Context(wl.tables, device=local)
@@ -341,6 +343,36 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
                       f"per galaxy; ESS fraction per galaxy from the GPU run"}
 
 
+def run_loglike_only(args):
+    """loglike + gradient throughput on the 100,000-pair workload only (or a
+    smaller galaxy count for profiling captures)."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    wl = W.config(2, n_gal=args.gal)
+    dev = torch.device("cuda", 0)
+    ctx = pkg.Context(wl.tables, device=0)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    th = torch.as_tensor(wl.theta, dtype=torch.float32, device=dev)
+    mobs = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev),
+                          mode="approx") + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)
+    out = {"pairs": wl.n_gal}
+    for spec in args.loglike_only.split(","):
+        mode, prec = spec.split("_")
+        for _ in range(args.warmup):
+            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[spec] = {"ms": ms, "evals_per_s": wl.n_gal / (ms / 1e3)}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     """The FP64 oracle timed on the host cores (rank 0 only)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,11 +412,21 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    # profiling captures only (not bench values): smaller galaxy count / iterations
+    ap.add_argument("--gal", type=int, default=None)
+    ap.add_argument("--warm", type=int, default=None)
+    ap.add_argument("--samp", type=int, default=None)
+    ap.add_argument("--loglike-only", default=None,
+                    help="comma list of mode_prec (e.g. exact_bf16,approx_fp32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.warm is not None and args.samp is None:
+        args.samp = args.warm
     if args.impl == "reference":
         run_reference(args)
+    elif args.loglike_only:
+        run_loglike_only(args)
     else:
         run_ours(args)
 

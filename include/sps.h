@@ -156,6 +156,7 @@ typedef struct {
     int32_t prec;           /* sps_prec (EXACT only)                              */
     int32_t use_graph;      /* capture the device work in a CUDA graph             */
     int32_t autotune;       /* pick the launch shape by timing candidates          */
+    int32_t adapt_mass;     /* adapt a diagonal inverse metric in the warm-up       */
 } sps_hmc_config;
 
 sps_status sps_hmc_config_default(sps_hmc_config* cfg);
@@ -170,6 +171,10 @@ typedef struct {
 } sps_hmc_stats;
 
 /* Run batched HMC for every chain of every galaxy of the current set.
+ * Warm-up adapts, per chain, the step size by dual averaging (Hoffman & Gelman
+ * 2014) and, if adapt_mass, a diagonal inverse metric in windows (75-iteration
+ * initial buffer, slow windows of 25, 50, 100, ..., 50-iteration terminal
+ * buffer; regularised variances of each window's positions).
  * The target is log L (App. D.1) plus the log-Jacobian of the bounding map
  * theta = lo + (hi - lo) / (1 + exp(-x)) (Eq. BoundingFunction, k = 1, x0 = 0),
  * i.e. a prior uniform in each bounded parameter; sampling is in x.

@@ -7,10 +7,21 @@ adaptation during a warm-up phase.  The paper runs Blackjax HMC; it does not
 print the adaptation constants or the trajectory-length rule, so the
 declared readings are:
 
-* identity mass matrix; trajectory length L ~ U{L_min .. L_max} per iteration;
+* trajectory length L ~ U{L_min .. L_max} per iteration;
 * step size adapted per chain by the dual-averaging scheme of Hoffman &
   Gelman (2014, Sec. 3.2.1) with target 0.8, gamma 0.05, t0 10, kappa 0.75,
   mu = log(10 eps0); warm-up uses eps_m, sampling uses the averaged eps-bar;
+* a diagonal inverse metric (mass matrix) adapted per chain in the windowed
+  scheme of the Stan reference manual (the paper's Blackjax window
+  adaptation is of this family): an initial buffer of 75 iterations, slow
+  windows of 25, 50, 100, ... iterations (the last one stretched to the
+  terminal buffer), a terminal buffer of 50 (15% / 75% / 10% of the warm-up
+  when it is shorter than 150).  At the end of each slow window the inverse
+  metric becomes the regularised variance n/(n+5) var + 1e-3 * 5/(n+5) of the
+  window's positions (Welford, FP64) and dual averaging restarts with
+  mu = log(10 eps).  Momenta p = z / sqrt(minv), kinetic energy
+  sum minv p^2 / 2, drift x += eps minv p.  With adapt_mass False the metric
+  stays the identity;
 * random numbers from Philox-4x32-10 (Salmon et al. 2011), keyed by the
   64-bit seed, counter (iteration, block, chain, 0): blocks 0-2 give twelve
   uniforms -> six Box-Muller pairs of momenta, block 3 gives the accept
@@ -120,10 +131,30 @@ class ApproxTarget:
         return lp.detach().numpy(), g.detach().numpy()
 
 
-def leapfrog(target, rows, x, p, g, eps, L):
+def warmup_windows(n_warm):
+    """(end of the initial buffer, slow windows [(start, end)], start of the
+    terminal buffer) of the windowed metric adaptation."""
+    if n_warm >= 150:
+        init, term, w = 75, 50, 25
+    else:
+        init, term = int(0.15 * n_warm), int(0.1 * n_warm)
+        w = n_warm - init - term
+    wins = []
+    start, stop = init, n_warm - term
+    while start < stop and w > 0:
+        end = start + w
+        if end + 2 * w > stop:
+            end = stop
+        wins.append((start, end))
+        start, w = end, 2 * w
+    return init, wins, stop
+
+
+def leapfrog(target, rows, x, p, g, eps, L, minv=None):
     """L leapfrog steps (half kick, drift, gradient, half kick), per chain
     lengths L; returns the end point, its momentum, log p and gradient."""
     x, p, g = x.copy(), p.copy(), g.copy()
+    minv = np.ones_like(x) if minv is None else minv
     lp = np.full(x.shape[0], np.nan)
     Lmax = int(np.max(L)) if len(L) else 0
     for step in range(Lmax):
@@ -132,7 +163,7 @@ def leapfrog(target, rows, x, p, g, eps, L):
             break
         e = eps[act, None]
         p[act] += 0.5 * e * g[act]
-        x[act] += e * p[act]
+        x[act] += e * minv[act] * p[act]
         lpa, ga = target(x[act], rows[act])
         g[act] = ga
         lp[act] = lpa
@@ -142,7 +173,7 @@ def leapfrog(target, rows, x, p, g, eps, L):
 
 def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
             eps0=0.1, target_accept=0.8, gamma=0.05, t0=10.0, kappa=0.75,
-            chain_ids=None):
+            chain_ids=None, adapt_mass=True):
     """Batched HMC over independent chains (Sec. 4, App. D.2).
 
     Returns dict with samples [C, n_samp, 12] (bounded parameters),
@@ -154,20 +185,25 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
     ids = np.arange(C) if chain_ids is None else np.asarray(chain_ids)
     lp, g = target(x, rows)
     eps = np.full(C, eps0)
-    mu = math.log(10.0 * eps0)
+    mu = np.full(C, math.log(10.0 * eps0))
     hbar = np.zeros(C)
     log_eps_bar = np.zeros(C)
+    m_da = 0                                   # iterations since the last restart
+    minv = np.ones_like(x)
+    _, wins, _ = warmup_windows(n_warm) if adapt_mass else (0, [], 0)
+    w_n, w_mean, w_m2 = 0, np.zeros_like(x), np.zeros_like(x)
     samples = np.zeros((C, n_samp, x.shape[1]))
     acc_sum = np.zeros(C)
     warm_acc = np.zeros(C)
     div = np.zeros(C, np.int64)
     nevals = np.zeros(C, np.int64)
     for it in range(n_warm + n_samp):
-        p, u, L = draws(seed, ids, it, L_min, L_max)
-        x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L)
+        z, u, L = draws(seed, ids, it, L_min, L_max)
+        p = z / np.sqrt(minv)
+        x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L, minv)
         nevals += L
-        h0 = -lp + 0.5 * (p * p).sum(1)
-        h1 = -lp1 + 0.5 * (p1 * p1).sum(1)
+        h0 = -lp + 0.5 * (minv * p * p).sum(1)
+        h1 = -lp1 + 0.5 * (minv * p1 * p1).sum(1)
         dh = h1 - h0
         finite = np.isfinite(dh)
         a = np.where(finite, np.minimum(1.0, np.exp(-np.where(finite, dh, 0.0))), 0.0)
@@ -177,17 +213,32 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
         if it < n_warm:
             if it >= n_warm // 2:
                 warm_acc += a
-            m = it + 1
+            m_da += 1
+            m = m_da
             hbar = (1.0 - 1.0 / (m + t0)) * hbar + (target_accept - a) / (m + t0)
             log_eps = mu - math.sqrt(m) / gamma * hbar
             w = m ** -kappa
             log_eps_bar = w * log_eps + (1.0 - w) * log_eps_bar
             eps = np.exp(log_eps) if it < n_warm - 1 else np.exp(log_eps_bar)
+            for (ws_, we_) in wins:
+                if ws_ <= it < we_:
+                    w_n += 1                     # Welford over the window's positions
+                    d = x - w_mean
+                    w_mean = w_mean + d / w_n
+                    w_m2 = w_m2 + d * (x - w_mean)
+                    if it == we_ - 1:
+                        var = w_m2 / (w_n - 1.0)
+                        minv = (w_n / (w_n + 5.0)) * var + 1e-3 * (5.0 / (w_n + 5.0))
+                        w_n, w_mean, w_m2 = 0, np.zeros_like(x), np.zeros_like(x)
+                        mu = np.log(10.0 * eps)
+                        hbar = np.zeros(C)
+                        log_eps_bar = np.zeros(C)
+                        m_da = 0
         else:
             s = it - n_warm
             th = O.bound(torch.as_tensor(x), target.lo, target.hi).numpy()
             samples[:, s] = th
             acc_sum += a
-    return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps,
+    return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps, minv=minv,
                 warm_accept=warm_acc / max(n_warm - n_warm // 2, 1),
                 divergences=div, grad_evals=nevals)

@@ -139,7 +139,7 @@ class Context:
 
     def hmc_run(self, theta0_unb, mag_obs, sigma, mask, chains_per_gal=4, n_warm=500,
                 n_samp=500, L_min=8, L_max=64, target_accept=0.8, eps0=0.1, seed=2506199190,
-                use_graph=True, autotune=True, samples=True, mode="approx"):
+                use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=True):
         x0 = theta0_unb if isinstance(theta0_unb, torch.Tensor) else _f32(theta0_unb, self.device)
         dev = x0.device
         mo = _f32(mag_obs, dev)
@@ -154,6 +154,7 @@ class Context:
         cfg.target_accept, cfg.eps0, cfg.seed = target_accept, eps0, seed
         cfg.mode = MODES[mode]
         cfg.use_graph, cfg.autotune = int(use_graph), int(autotune)
+        cfg.adapt_mass = int(adapt_mass)
         out = {
             "samples": torch.empty((nc, n_samp, _lib.NPARAM), dtype=torch.float32, device=dev)
             if samples else None,

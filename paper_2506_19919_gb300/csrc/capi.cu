@@ -8,10 +8,13 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "sps_internal.h"
 
@@ -103,6 +106,34 @@ uint16_t bf16_rne(float f) {
     return (uint16_t)(u >> 16);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D BF16 tensor [rows][inner] (row stride `ld` elements), box {64, box_rows},
+// 128-byte swizzle, zero fill outside the tensor.
+bool make_tmap_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
+                    uint32_t box_rows) {
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct sps_ctx {
@@ -119,7 +150,8 @@ struct sps_ctx {
     DevBuf gz, glnT, glT10, gbins, gzp, gsup, ggauss, gcssp, gdust;
     // scratch
     DevBuf nonfinite, queue, err;
-    DevBuf W, V, Wbar, cJ, gbar, rowinfo;
+    DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr;
+    bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
     cudaGraphExec_t graph = nullptr;
@@ -158,7 +190,7 @@ struct sps_ctx {
         DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
-                         &rowinfo};
+                         &rowinfo, &tcerr};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }
@@ -277,6 +309,7 @@ sps_status sps_hmc_config_default(sps_hmc_config* cfg) {
     cfg->prec = SPS_FP32;
     cfg->use_graph = 1;
     cfg->autotune = 1;
+    cfg->adapt_mass = 1;
     return SPS_OK;
 }
 
@@ -345,7 +378,7 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
     c.n_lam = L;
     c.n_band = B;
     c.K = (int)K;
-    c.k_pad = (int)((K + 31) / 32 * 32);
+    c.k_pad = (int)((K + 63) / 64 * 64);   // k-blocks of 64 BF16 (128-byte TMA rows)
     c.lam_pad = (L + 31) / 32 * 32;
     c.gl_order = cfg.sfh_gl_order;
     c.panel = (float)cfg.sfh_panel;
@@ -425,6 +458,7 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         delete ctx;
         return cuda_fail(e, "lambda constants");
     }
+    if (const char* v = std::getenv("SPS_NO_TCGEN05")) ctx->use_tc = (v[0] == '0');
     *out = ctx;
     return SPS_OK;
 }
@@ -480,7 +514,8 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                             const float* mobs, const float* sigma, const uint32_t* mask, int bf16,
                             float* mag_out, float* ll_out, float* grad_out, cudaStream_t s) {
     const Consts& c = ctx->c;
-    const int64_t chunk = 32768;
+    const bool tc = bf16 && ctx->use_tc;
+    const int64_t chunk = tc ? 131072 : 32768;
     const int64_t rows = std::min<int64_t>(n, chunk);
     CK(ctx->W.reserve((size_t)rows * c.k_pad * 4));
     CK(ctx->cJ.reserve((size_t)rows * c.n_band * 4 * 4));
@@ -493,6 +528,7 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
     const Grid grid = ctx->grid();
     const Galaxies gal = ctx->gal();
     int* nf = ctx->nonfinite.as<int>();
+    int* terr = ctx->nonfinite.as<int>() + 1;
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t m = std::min(chunk, n - r0);
         const float* th = theta + r0 * SPS_NPARAM;
@@ -514,14 +550,33 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
             gv.n = m;
         }
         CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s));
-        CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
-                            ctx->cJ.as<float>(), s));
+        if (tc) {
+            CUtensorMap ta, tb;
+            if (!make_tmap_bf16(&ta, ctx->W.p, c.k_pad, m, c.k_pad, 128) ||
+                !make_tmap_bf16(&tb, ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256))
+                return fail(SPS_E_CUDA, "tensor map encoding failed");
+            CK(launch_fwd_tc(ta, tb, c, grid, gv, th, gi, m, ctx->cJ.as<float>(), terr, s));
+        } else {
+            CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
+                                ctx->cJ.as<float>(), s));
+        }
         CK(launch_exact_like(c, gv, th, gi, m, ctx->cJ.as<float>(), ctx->rowinfo.as<float>(), mo, sg,
                              mk, mag_out ? mag_out + r0 * c.n_band : nullptr,
                              ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s));
         if (grad_out) {
-            CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), ctx->V.as<float>(), s));
-            CK(launch_exact_adj(c, grid, m, bf16, ctx->V.as<float>(), ctx->Wbar.as<float>(), s));
+            if (tc) {
+                CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), nullptr,
+                                     ctx->V.as<uint16_t>(), s));
+                CUtensorMap ta, tb;
+                if (!make_tmap_bf16(&ta, ctx->V.p, c.lam_pad, m, c.lam_pad, 128) ||
+                    !make_tmap_bf16(&tb, ctx->ssp_bf.p, c.lam_pad, c.K, c.lam_pad, 192))
+                    return fail(SPS_E_CUDA, "tensor map encoding failed");
+                CK(launch_adj_tc(ta, tb, c, grid, m, ctx->Wbar.as<float>(), terr, s));
+            } else {
+                CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), ctx->V.as<float>(),
+                                     nullptr, s));
+                CK(launch_exact_adj(c, grid, m, bf16, ctx->V.as<float>(), ctx->Wbar.as<float>(), s));
+            }
             CK(launch_exact_grad(c, gv, th, gi, m, ctx->rowinfo.as<float>(), ctx->Wbar.as<float>(),
                                  grad_out + r0 * SPS_NPARAM, s));
         }
@@ -530,11 +585,12 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
 }
 
 static sps_status finish_call(sps_ctx* ctx, Stager& st, cudaStream_t s) {
-    int nf = 0;
+    int fl[2] = {0, 0};
     CK(st.finish());
-    CK(cudaMemcpyAsync(&nf, ctx->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(fl, ctx->nonfinite.p, sizeof(fl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (nf) return fail(SPS_E_NONFINITE, "some rows are NaN (non-finite inputs or results)");
+    if (fl[1]) return fail(SPS_E_TIMEOUT, "a tensor-core pipeline wait timed out");
+    if (fl[0]) return fail(SPS_E_NONFINITE, "some rows are NaN (non-finite inputs or results)");
     return SPS_OK;
 }
 
@@ -555,7 +611,7 @@ sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_i
     const int32_t* gi = st.in(gal_idx, (size_t)n);
     float* mo = st.out(mag_out, (size_t)n * ctx->c.n_band);
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
-    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, nullptr, nullptr, nullptr, mo, nullptr,
                               nullptr, nullptr, ctx->nonfinite.as<int>(), s));
@@ -592,7 +648,7 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     float* llo = st.out(loglike_out, (size_t)n);
     float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
-    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, mo, sg, mk, nullptr, llo, gro, nullptr,
                               ctx->nonfinite.as<int>(), s));
@@ -758,7 +814,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
 
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
-                 cfg->seed, 0};
+                 cfg->seed, cfg->adapt_mass ? 1 : 0};
     const size_t table_bytes = (size_t)nb_max * c.K * sizeof(float);
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, ctx->device));
@@ -830,10 +886,10 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     };
     if (cfg->use_graph) {
         char kb[512];
-        std::snprintf(kb, sizeof(kb), "%p%p%p%p%p%p%p%p%p%p%p%lld%d%d%d%d%d%d%llu%g%g", (const void*)x0,
+        std::snprintf(kb, sizeof(kb), "%p%p%p%p%p%p%p%p%p%p%p%lld%d%d%d%d%d%d%d%llu%g%g", (const void*)x0,
                       (const void*)mo, (const void*)sg, (const void*)mk, (const void*)ord, (void*)so,
                       (void*)acc, (void*)epo, (void*)dv, (void*)nev, (void*)sto, (long long)G, C,
-                      hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, (unsigned long long)hp.seed,
+                      hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, hp.adapt_mass, (unsigned long long)hp.seed,
                       (double)hp.eps0, (double)hp.target_accept);
         std::string gk = std::string(kb) + ":" + std::to_string(blocks);
         if (!ctx->graph || gk != ctx->graph_key) {

@@ -286,7 +286,7 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
 __global__ void __launch_bounds__(256)
 k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
              const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
-             const float* __restrict__ gbar, float* __restrict__ V) {
+             const float* __restrict__ gbar, float* __restrict__ V, uint16_t* __restrict__ Vbf) {
     __shared__ float gb[kMaxBands];
     __shared__ int2 sp[kMaxBands];
     __shared__ float2 gg[kMaxBands];
@@ -321,7 +321,8 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
             }
             if (sum != 0.0f) v = dust_eval(L4.y, L4.z, L4.w, AV, dl, ff).F * sum;
         }
-        V[row * c.lam_pad + nn] = v;
+        if (Vbf) Vbf[row * c.lam_pad + nn] = f_to_bf16(v);
+        else V[row * c.lam_pad + nn] = v;
     }
 }
 
@@ -453,9 +454,9 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
 
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
-                              const float* gbar, float* V32, cudaStream_t s) {
+                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32);
+    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32, Vbf);
     return cudaGetLastError();
 }
 

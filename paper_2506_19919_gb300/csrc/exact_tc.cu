@@ -1,0 +1,374 @@
+// Tensor-core (tcgen05) contractions of the exact path (Eq. photo_integral_exact)
+// for sm_103a, BF16 operands with per-age-row power-of-two scaling and FP32
+// accumulation in TMEM.
+//
+// Forward: S[r][n] = sum_k W[r][k] L[k][n] for a 128-row tile and 256-wide
+// wavelength tiles, with the dust x filter reduction over n fused into the
+// epilogue (the SED never reaches HBM).  Adjoint: Wbar[r][k] = sum_n v[r][n]
+// L[k][n] for 128 x 192 tiles.
+//
+// Block of 6 warps, one block per SM: warp 0 issues TMA loads of A and B
+// k-blocks (128-byte rows, 128-byte swizzle) into a ring of stages; one lane
+// of warp 1 issues tcgen05.mma into one of two TMEM accumulators and commits
+// to mbarriers; warps 2-5 drain the other accumulator with tcgen05.ld.  Every
+// wait is bounded: a timeout sets the block's abort flag and the global error
+// word, the roles unwind, in-flight copies are waited for (bounded) and TMEM
+// is released.
+#include <cuda.h>
+
+#include "sps_device.cuh"
+#include "tc_ptx.cuh"
+
+namespace sps {
+
+namespace {
+
+constexpr int kTM = 128;       // rows per tile (MMA M)
+constexpr int kBK = 64;        // bf16 per k-block row (128 bytes)
+constexpr int kThreadsTC = 192;
+constexpr int kFwdBN = 256;
+constexpr int kFwdStages = 4;
+constexpr int kAdjBN = 192;
+constexpr int kAdjStages = 5;
+constexpr uint32_t kTmemCols = 512;
+
+template <int BN, int STAGES>
+struct Ring {
+    static constexpr int kA = kTM * kBK * 2;
+    static constexpr int kB = BN * kBK * 2;
+    static constexpr int kBytes = STAGES * (kA + kB);
+};
+
+struct Ctl {
+    uint64_t full[8], empty[8];
+    uint64_t tfull[2], tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort;
+    int issued;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err);
+
+// Warp-uniform wait: lane 0 polls, the outcome is broadcast.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, ctl, err) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
+    for (uint32_t i = 0; i < tc::kSpinLimit; ++i) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023) == 1023 && ctl->abort) return false;
+    }
+    ctl->abort = 1;
+    atomicOr(err, 2);
+    return false;
+}
+
+// Shared prologue: barriers and TMEM allocation.  Returns the ring base.
+template <int STAGES>
+__device__ __forceinline__ void tc_setup(Ctl* ctl, int warp) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&ctl->tfull[b], 1);
+            tc::mbar_init(&ctl->tempty[b], 4 * 32);
+        }
+        tc::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        ctl->issued = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem_base, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+}
+
+// Producer (one lane): k-blocks of A (rows m0..) and B (rows of the n tile).
+template <int BN, int STAGES>
+__device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtensorMap* tA,
+                                           const CUtensorMap* tB, int m0, int n_tiles, int n_kb,
+                                           int* err) {
+    using R = Ring<BN, STAGES>;
+    int it = 0;
+    for (int nt = 0; nt < n_tiles && !ctl->abort; ++nt) {
+        for (int kb = 0; kb < n_kb; ++kb, ++it) {
+            const int s = it % STAGES;
+            const uint32_t round = (uint32_t)(it / STAGES);
+            if (!wait_or_abort(&ctl->empty[s], (round & 1u) ^ 1u, ctl, err)) return;
+            uint8_t* a = ring + s * (R::kA + R::kB);
+            uint8_t* b = a + R::kA;
+            tc::mbar_expect_tx(&ctl->full[s], R::kA + R::kB);
+            tc::tma_load_2d(a, tA, kb * kBK, m0, &ctl->full[s]);
+            tc::tma_load_2d(b, tB, kb * kBK, nt * BN, &ctl->full[s]);
+            ctl->issued = it + 1;
+        }
+    }
+}
+
+// MMA issuer (one lane).
+template <int BN, int STAGES>
+__device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int n_kb, int* err) {
+    using R = Ring<BN, STAGES>;
+    constexpr uint32_t idesc = tc::idesc_bf16(kTM, BN);
+    int it = 0;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+        const int buf = nt & 1;
+        const uint32_t use = (uint32_t)(nt >> 1);
+        if (!wait_or_abort(&ctl->tempty[buf], (use & 1u) ^ 1u, ctl, err)) break;
+        tc::tc_fence_after();
+        const uint32_t d = ctl->tmem_base + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int kb = 0; kb < n_kb; ++kb, ++it) {
+            const int s = it % STAGES;
+            const uint32_t round = (uint32_t)(it / STAGES);
+            if (!wait_or_abort(&ctl->full[s], round & 1u, ctl, err)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            uint8_t* a = ring + s * (R::kA + R::kB);
+            uint8_t* b = a + R::kA;
+            const uint64_t da = tc::sw128_desc(a), db = tc::sw128_desc(b);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+                tc::mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+            tc::mma_commit(&ctl->empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&ctl->tfull[buf]);
+    }
+    // all issued MMAs complete before TMEM is released
+    tc::mma_commit(&ctl->drain);
+    for (uint32_t i = 0; i < tc::kSpinLimit; ++i)
+        if (tc::mbar_try_wait(&ctl->drain, 0)) break;
+}
+
+// Teardown: wait (bounded) for the producer's copies still in flight, then
+// free TMEM from the allocating warp.
+template <int BN, int STAGES>
+__device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int issued = ctl->issued;
+        for (int it = max(0, issued - STAGES); it < issued; ++it) {
+            const int s = it % STAGES;
+            const uint32_t round = (uint32_t)(it / STAGES);
+            for (uint32_t i = 0; i < tc::kSpinLimit; ++i)
+                if (tc::mbar_try_wait(&ctl->full[s], round & 1u)) break;
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(ctl->tmem_base, kTmemCols);
+    }
+}
+
+template <int BN, int STAGES>
+__device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
+    uintptr_t p = reinterpret_cast<uintptr_t>(raw);
+    p = (p + 1023) & ~uintptr_t(1023);
+    uint8_t* ring = reinterpret_cast<uint8_t*>(p);
+    ctl = reinterpret_cast<Ctl*>(ring + Ring<BN, STAGES>::kBytes);
+    return ring;
+}
+
+// ---------------------------------------------------------------- forward
+template <int NB>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+         const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
+         const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
+         float* __restrict__ cJ, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    Ctl* ctl;
+    uint8_t* ring = carve<kFwdBN, kFwdStages>(smem_raw, ctl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTM;
+    const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
+    const int n_kb = c.k_pad / kBK;
+    tc_setup<kFwdStages>(ctl, warp);
+    if (warp == 0) {
+        if (lane == 0) tc_produce<kFwdBN, kFwdStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
+    } else if (warp == 1) {
+        if (lane == 0) tc_mma<kFwdBN, kFwdStages>(ctl, ring, n_tiles, n_kb, err);
+    } else {
+        const int q = warp & 3;                    // TMEM lane quarter of this warp
+        const int rl = 32 * q + lane;
+        const int64_t row = (int64_t)m0 + rl;
+        const bool live = row < n;
+        const int B = c.n_band;
+        int64_t gi = live ? (gal_idx ? (int64_t)gal_idx[row] : row) : 0;
+        const bool valid = live && gi >= 0 && gi < g.n;
+        if (!valid) gi = 0;
+        float cA = 0.f, dl = 0.f, eb = 0.f;
+        if (valid) {
+            const float* t = theta + row * SPS_NPARAM;
+            cA = -0.4f * kLog2_10f * t[9] * (1.0f / 4.05f);
+            dl = t[10];
+            eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
+        }
+        int sx[NB], sy[NB];
+        float gc[NB], gs[NB];
+        float acc[NB][4];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            int2 sp = make_int2(0, 0);
+            float2 ga = make_float2(0.f, 0.f);
+            if (b < B && valid) {
+                sp = g.support[gi * B + b];
+                ga = g.gauss[gi * B + b];
+            }
+            sx[b] = sp.x;
+            sy[b] = sp.y;
+            gc[b] = ga.x;
+            gs[b] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 marks a top-hat
+            acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0f;
+        }
+        for (int nt = 0; nt < n_tiles; ++nt) {
+            const int buf = nt & 1;
+            const uint32_t use = (uint32_t)(nt >> 1);
+            if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
+            tc::tc_fence_after();
+            for (int cc = 0; cc < kFwdBN / 32; ++cc) {
+                float S[32];
+                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kFwdBN + cc * 32), S);
+                const int nb0 = nt * kFwdBN + cc * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int nn = min(nb0 + j, c.n_lam - 1);   // columns past the grid hold S = 0
+                    const float4 L4 = __ldg(grid.lamc + nn);
+                    const float lam = __ldg(grid.lam + nn);
+                    const float pw = __expf(dl * L4.z);
+                    const float base = L4.y * pw + eb * L4.w;
+                    const float E = exp2f(cA * base);
+                    const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (nn >= sx[b] && nn < sy[b]) {
+                            float w = L4.x;
+                            if (gs[b] != 0.0f) {
+                                const float u = (lam - gc[b]) * gs[b];
+                                w *= __expf(-0.5f * u * u);
+                            }
+                            const float Sw = S[j] * w;
+                            const float es = Sw * E;
+                            acc[b][0] += Sw;
+                            acc[b][1] += es;
+                            acc[b][2] += es * base;
+                            acc[b][3] += es * dterm;
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&ctl->tempty[buf]);
+        }
+        if (valid && !ctl->abort) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (b < B) {
+                    float* o = cJ + (row * B + b) * 4;
+                    o[0] = acc[b][0];
+                    o[1] = acc[b][1];
+                    o[2] = acc[b][2];
+                    o[3] = acc[b][3];
+                }
+        }
+    }
+    tc_teardown<kFwdBN, kFwdStages>(ctl, warp);
+}
+
+// ---------------------------------------------------------------- adjoint
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+         const __grid_constant__ Consts c, const Grid grid, int64_t n, float* __restrict__ Wbar,
+         int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    Ctl* ctl;
+    uint8_t* ring = carve<kAdjBN, kAdjStages>(smem_raw, ctl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTM;
+    const int n_tiles = (c.K + kAdjBN - 1) / kAdjBN;
+    const int n_kb = c.lam_pad / kBK;
+    tc_setup<kAdjStages>(ctl, warp);
+    if (warp == 0) {
+        if (lane == 0) tc_produce<kAdjBN, kAdjStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
+    } else if (warp == 1) {
+        if (lane == 0) tc_mma<kAdjBN, kAdjStages>(ctl, ring, n_tiles, n_kb, err);
+    } else {
+        const int q = warp & 3;
+        const int64_t row = (int64_t)m0 + 32 * q + lane;
+        const bool live = row < n;
+        for (int nt = 0; nt < n_tiles; ++nt) {
+            const int buf = nt & 1;
+            const uint32_t use = (uint32_t)(nt >> 1);
+            if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
+            tc::tc_fence_after();
+            for (int cc = 0; cc < kAdjBN / 32; ++cc) {
+                float S[32];
+                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kAdjBN + cc * 32), S);
+                const int k0 = nt * kAdjBN + cc * 32;
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int k = k0 + j;
+                        if (k < c.K) Wbar[row * c.k_pad + k] = S[j] * __ldg(grid.row_scale + k / c.n_met);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&ctl->tempty[buf]);
+        }
+    }
+    tc_teardown<kAdjBN, kAdjStages>(ctl, warp);
+}
+
+}  // namespace
+
+size_t tc_fwd_smem() { return Ring<kFwdBN, kFwdStages>::kBytes + sizeof(Ctl) + 1024; }
+size_t tc_adj_smem() { return Ring<kAdjBN, kAdjStages>::kBytes + sizeof(Ctl) + 1024; }
+
+cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
+                          const Grid& grid, const Galaxies& g, const float* theta,
+                          const int32_t* gal_idx, int64_t n, float* cJ, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
+    const size_t smem = tc_fwd_smem();
+    cudaError_t e;
+    if (c.n_band <= 8) {
+        e = cudaFuncSetAttribute(k_fwd_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fwd_tc<8><<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
+    } else {
+        e = cudaFuncSetAttribute(k_fwd_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fwd_tc<32><<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
+                          const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
+    const size_t smem = tc_adj_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adj_tc<<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, n, Wbar, err);
+    return cudaGetLastError();
+}
+
+}  // namespace sps

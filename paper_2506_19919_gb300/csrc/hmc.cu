@@ -6,12 +6,17 @@
 // trajectory lengths; uneven band counts and trajectory lengths are balanced
 // by the queue.
 //
-// Per iteration (identity mass matrix): p ~ N(0, I), L ~ U{L_min..L_max};
-// L leapfrog steps (half kick, drift, gradient, half kick); Metropolis accept
-// on the FP64 energy difference; during warm-up the step size follows the
-// dual averaging of Hoffman & Gelman (2014, Sec. 3.2.1), afterwards the
-// averaged step size.  Draws: Philox-4x32-10, counter (iteration, block,
-// chain, 0), key = seed; Box-Muller in FP64.
+// Per iteration: p = z / sqrt(minv), z ~ N(0, I), L ~ U{L_min..L_max}; L
+// leapfrog steps (half kick, drift x += eps minv p, gradient, half kick);
+// Metropolis accept on the FP64 energy difference.  Warm-up: the step size
+// follows the dual averaging of Hoffman & Gelman (2014, Sec. 3.2.1); the
+// diagonal inverse metric minv is adapted in the windowed scheme of the Stan
+// reference manual (75-iteration initial buffer, slow windows of 25, 50, 100,
+// ... iterations, 50-iteration terminal buffer; regularised Welford variance
+// n/(n+5) var + 1e-3 * 5/(n+5) of each window's positions, after which dual
+// averaging restarts at mu = log(10 eps)).  Sampling uses the averaged step
+// size.  Draws: Philox-4x32-10, counter (iteration, block, chain, 0),
+// key = seed; Box-Muller in FP64.
 #include "philox.cuh"
 #include "sps_eval.cuh"
 
@@ -82,19 +87,57 @@ __device__ __forceinline__ void draws(uint64_t seed, uint32_t chain, uint32_t it
     L = L_min + (int)(((uint64_t)w31 * span) >> 32);
 }
 
+// Windowed metric-adaptation schedule for n_warm warm-up iterations.
+struct Windows {
+    int start, end, width, stop;
+    __device__ void init(int n_warm) {
+        int init_b, term_b;
+        if (n_warm >= 150) {
+            init_b = 75;
+            term_b = 50;
+            width = 25;
+        } else {
+            init_b = (int)(0.15 * n_warm);
+            term_b = (int)(0.1 * n_warm);
+            width = n_warm - init_b - term_b;
+        }
+        stop = n_warm - term_b;
+        start = init_b;
+        set_end();
+    }
+    __device__ void set_end() {
+        end = start + width;
+        if (end + 2 * width > stop) end = stop;
+        if (width <= 0 || start >= stop) start = end = 0x7fffffff;
+    }
+    __device__ void next() {
+        start = end;
+        width *= 2;
+        set_end();
+    }
+};
+
 __device__ void run_chain(const ChainCtx& cc, const HmcParams hp, uint32_t chain,
                           const float* __restrict__ x0, float* __restrict__ samples,
                           float* acc_out, float* eps_out, int32_t* div_out, int64_t* nev_out,
                           int32_t* status_out) {
     const Consts& c = *cc.c;
     const int lane = lane_id();
-    float x[SPS_NPARAM], g[SPS_NPARAM];
+    float x[SPS_NPARAM], g[SPS_NPARAM], minv[SPS_NPARAM];
 #pragma unroll
-    for (int k = 0; k < SPS_NPARAM; ++k) x[k] = x0[(size_t)chain * SPS_NPARAM + k];
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        x[k] = x0[(size_t)chain * SPS_NPARAM + k];
+        minv[k] = 1.0f;
+    }
     double lp = logp_grad(cc, x, g);
     float eps = hp.eps0;
-    const double mu = log(10.0 * (double)hp.eps0);
+    double mu = log(10.0 * (double)hp.eps0);
     double hbar = 0.0, log_eps_bar = 0.0;
+    int m_da = 0;
+    Windows win;
+    win.init(hp.adapt_mass ? hp.n_warm : 0);
+    int wn = 0;
+    double wmean = 0.0, wm2 = 0.0;          // lane k < 12: Welford state of parameter k
     double acc_sum = 0.0;
     int ndiv = 0;
     long long nev = 1;
@@ -107,6 +150,7 @@ __device__ void run_chain(const ChainCtx& cc, const HmcParams hp, uint32_t chain
         float x1[SPS_NPARAM], p1[SPS_NPARAM], g1[SPS_NPARAM];
 #pragma unroll
         for (int k = 0; k < SPS_NPARAM; ++k) {
+            p[k] = p[k] * rsqrtf(minv[k]);
             x1[k] = x[k];
             p1[k] = p[k];
             g1[k] = g[k];
@@ -116,7 +160,7 @@ __device__ void run_chain(const ChainCtx& cc, const HmcParams hp, uint32_t chain
 #pragma unroll
             for (int k = 0; k < SPS_NPARAM; ++k) {
                 p1[k] = fmaf(0.5f * eps, g1[k], p1[k]);
-                x1[k] = fmaf(eps, p1[k], x1[k]);
+                x1[k] = fmaf(eps * minv[k], p1[k], x1[k]);
             }
             lp1 = logp_grad(cc, x1, g1);
 #pragma unroll
@@ -126,8 +170,8 @@ __device__ void run_chain(const ChainCtx& cc, const HmcParams hp, uint32_t chain
         double k0 = 0.0, k1 = 0.0;
 #pragma unroll
         for (int k = 0; k < SPS_NPARAM; ++k) {
-            k0 += (double)p[k] * (double)p[k];
-            k1 += (double)p1[k] * (double)p1[k];
+            k0 += (double)minv[k] * (double)p[k] * (double)p[k];
+            k1 += (double)minv[k] * (double)p1[k] * (double)p1[k];
         }
         const double dH = (-lp1 + 0.5 * k1) - (-lp + 0.5 * k0);
         const bool fin = isfinite(dH);
@@ -141,23 +185,41 @@ __device__ void run_chain(const ChainCtx& cc, const HmcParams hp, uint32_t chain
             }
             lp = lp1;
         }
+        float xs = x[0];                      // this lane's parameter (lanes < 12)
+#pragma unroll
+        for (int k = 1; k < SPS_NPARAM; ++k)
+            if (lane == k) xs = x[k];
         if (it < hp.n_warm) {
-            const double m = (double)(it + 1);
+            const double m = (double)(++m_da);
             hbar = (1.0 - 1.0 / (m + 10.0)) * hbar + ((double)hp.target_accept - a) / (m + 10.0);
             const double log_eps = mu - sqrt(m) / 0.05 * hbar;
             const double wgt = pow(m, -0.75);
             log_eps_bar = wgt * log_eps + (1.0 - wgt) * log_eps_bar;
             eps = (float)exp(it < hp.n_warm - 1 ? log_eps : log_eps_bar);
+            if (it >= win.start && it < win.end) {
+                ++wn;
+                const double d = (double)xs - wmean;
+                wmean += d / (double)wn;
+                wm2 += d * ((double)xs - wmean);
+                if (it == win.end - 1) {
+                    const double var = wm2 / ((double)wn - 1.0);
+                    const float mk = (float)(((double)wn / (wn + 5.0)) * var + 1e-3 * (5.0 / (wn + 5.0)));
+#pragma unroll
+                    for (int k = 0; k < SPS_NPARAM; ++k) minv[k] = __shfl_sync(kFull, mk, k);
+                    wn = 0;
+                    wmean = wm2 = 0.0;
+                    mu = log(10.0 * (double)eps);
+                    hbar = 0.0;
+                    log_eps_bar = 0.0;
+                    m_da = 0;
+                    win.next();
+                }
+            }
         } else {
             acc_sum += a;
-            if (samples && lane < SPS_NPARAM) {
-                float xs = x[0];
-#pragma unroll
-                for (int k = 1; k < SPS_NPARAM; ++k)
-                    if (lane == k) xs = x[k];
+            if (samples && lane < SPS_NPARAM)
                 samples[((size_t)chain * hp.n_samp + (it - hp.n_warm)) * SPS_NPARAM + lane] =
                     c.prior_lo[lane] + c.prior_span[lane] * sigmoidf_(xs);
-            }
         }
     }
     if (lane == 0) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host runtime and the CUDA kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -88,12 +89,21 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
                               cudaStream_t s);
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
-                              const float* gbar, float* V32, cudaStream_t s);
+                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s);
 cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int bf16,
                              const float* V32, float* Wbar, cudaStream_t s);
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
                               const float* Wbar, float* grad_out, cudaStream_t s);
+
+// Tensor-core (tcgen05) contractions; the tensor maps describe the operands.
+size_t tc_fwd_smem();
+size_t tc_adj_smem();
+cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
+                          const Grid& grid, const Galaxies& g, const float* theta,
+                          const int32_t* gal_idx, int64_t n, float* cJ, int* err, cudaStream_t s);
+cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
+                          const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s);
 
 cudaError_t launch_weights_rows(const Consts& c, const Galaxies& g, const float* theta,
                                 const int32_t* gal_idx, int64_t n, float* W_out,
@@ -107,7 +117,7 @@ struct HmcParams {
     int chains_per_gal, n_warm, n_samp, L_min, L_max;
     float target_accept, eps0;
     uint64_t seed;
-    long long spin_limit;   // bound on the work-queue wait
+    int adapt_mass;         // windowed diagonal metric adaptation during warm-up
 };
 struct HmcState;            // per-chain state, device
 cudaError_t launch_hmc_approx(const Consts& c, const Galaxies& g, const HmcParams& hp,

@@ -123,3 +123,34 @@ def test_ess_and_rhat_pins():
     tot, per = D.posteriors_at_ess(np.stack([iid.T, iid.T[::-1]], 0).reshape(2, 2000, 4)
                                    .transpose(0, 1, 2), chains_per_gal=1)
     assert tot == pytest.approx(2.0)
+
+
+def test_warmup_windows_schedule():
+    # 75 / 25, 50, 100, 200 / 50 for 500 warm-up iterations; shorter warm-ups
+    # split 15% / 75% / 10%
+    assert H.warmup_windows(500) == (75, [(75, 100), (100, 150), (150, 250), (250, 450)], 450)
+    init, wins, term = H.warmup_windows(100)
+    assert (init, term) == (15, 90) and wins[0][0] == 15 and wins[-1][1] == 90
+
+
+class _Gauss:
+    """Independent Gaussians with scales spanning three decades."""
+    scale = np.array([0.01, 0.03, 0.1, 0.3, 1.0, 3.0, 0.02, 0.05, 0.2, 0.5, 2.0, 1.5])
+    lo = torch.full((12,), -1e9, dtype=torch.float64)
+    hi = torch.full((12,), 1e9, dtype=torch.float64)
+
+    def __call__(self, x, rows):
+        z = np.asarray(x) / self.scale
+        return -0.5 * (z * z).sum(1), -z / self.scale
+
+
+def test_metric_adaptation_learns_the_scales():
+    C = 16
+    x0 = np.random.default_rng(2).normal(size=(C, 12)) * _Gauss.scale
+    out = H.run_hmc(_Gauss(), x0, np.zeros(C, int), seed=3, n_warm=300, n_samp=10, L_min=4,
+                    L_max=12)
+    ratio = out["minv"] / _Gauss.scale ** 2
+    assert np.median(ratio) == pytest.approx(1.0, rel=0.25)
+    assert (ratio > 0.3).all() and (ratio < 3.0).all()
+    # the adapted step size is set by the metric, not by the narrowest scale
+    assert np.median(out["eps"]) > 0.2
