@@ -227,6 +227,26 @@ sps_status sps_get_info(const sps_ctx* ctx, sps_info* out);
  * nodes[order], weights[order] on [-1, 1]. */
 sps_status sps_gl_rule(const sps_ctx* ctx, double* nodes, double* weights);
 
+/* Exact FP32 photometry (the computation of sps_photometry with SPS_EXACT,
+ * SPS_FP32) for callers that cannot allocate device memory while running:
+ * services that reserve a fixed device-memory budget at start-up, hosts whose
+ * allocator owns the device memory, and loops where cudaMalloc would
+ * synchronise the device or fail on a fragmented heap.  This call performs no
+ * cudaMalloc, cudaFree or other allocation: its scratch is a fixed 32 MiB
+ * array compiled into the library (resident on every GPU that loads the
+ * library until the process exits), so at most
+ * floor(32 MiB / (4 * k_pad + 16 * n_band)) rows fit in one call, about 6,100
+ * rows for a 107 x 12 x 5994 grid with 6 bands; larger n returns SPS_E_SHAPE
+ * with a message.  theta, gal_idx and mag_out must be device pointers (host
+ * arrays would need staging buffers): SPS_E_INVALID_ARG otherwise.  The first
+ * call on a device looks the array's device address up (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls share the array;
+ * calls that overlap on the GPU race.  The call synchronises `stream` to
+ * report SPS_E_NONFINITE.  The paper has no counterpart: this is a deployment
+ * variant of Eq. photo_integral_exact's evaluation. */
+sps_status sps_photometry_exact_noalloc(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
+                                        int64_t n, float* mag_out, void* stream);
+
 const char* sps_error_string(sps_status status);
 const char* sps_last_error_message(void);
 

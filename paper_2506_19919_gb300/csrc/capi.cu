@@ -16,6 +16,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "ctx.h"
 #include "sps_internal.h"
 
 namespace sps {
@@ -34,6 +35,12 @@ sps_status fail(sps_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+}  // namespace
+
+void sps::set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 sps_status cuda_fail(cudaError_t e, const char* where) {
     return fail(SPS_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -42,28 +49,6 @@ sps_status cuda_fail(cudaError_t e, const char* where) {
         cudaError_t _e = (call);                              \
         if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
     } while (0)
-
-// Grow-only device buffer.
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    cudaError_t reserve(size_t bytes) {
-        if (bytes <= cap) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e == cudaSuccess) cap = bytes;
-        return e;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    template <typename T>
-    T* as() const { return reinterpret_cast<T*>(p); }
-};
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -135,66 +120,6 @@ bool make_tmap_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t r
 }
 
 }  // namespace
-
-struct sps_ctx {
-    int device = 0;
-    Consts c{};
-    double h0 = 70.0, om = 0.3;
-    double gl_x[kMaxGL], gl_w[kMaxGL];
-    std::vector<double> band_p0, band_p1;
-    // tables
-    DevBuf lam64, lam32, lamc, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, age_edges, bp0, bp1;
-    // galaxies
-    int64_t n_gal = 0;
-    bool has_approx = false;
-    DevBuf gz, glnT, glT10, gbins, gzp, gsup, ggauss, gcssp, gdust;
-    // scratch
-    DevBuf nonfinite, queue, err;
-    DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr;
-    bool use_tc = true;   // tcgen05 contraction for BF16 operands
-    DevBuf stage[12];
-    // HMC graph cache
-    cudaGraphExec_t graph = nullptr;
-    std::string graph_key;
-    std::map<std::string, std::pair<int, int>> tuned;  // key -> (warps, blocks)
-
-    Grid grid() const {
-        Grid g;
-        g.lam = lam32.as<float>();
-        g.lamc = lamc.as<float4>();
-        g.lam64 = lam64.as<double>();
-        g.ssp = ssp.as<float>();
-        g.ssp_t = ssp_t.as<float>();
-        g.ssp_bf = ssp_bf.as<uint16_t>();
-        g.ssp_t_bf = ssp_t_bf.as<uint16_t>();
-        g.row_scale = row_scale.as<float>();
-        return g;
-    }
-    Galaxies gal() const {
-        Galaxies g;
-        g.n = n_gal;
-        g.z = gz.as<float>();
-        g.lnT = glnT.as<float>();
-        g.lT10 = glT10.as<float>();
-        g.bins = gbins.as<float2>();
-        g.zp = gzp.as<double>();
-        g.support = gsup.as<int2>();
-        g.gauss = ggauss.as<float2>();
-        g.cssp = has_approx ? gcssp.as<float>() : nullptr;
-        g.dust_eff = gdust.as<float4>();
-        return g;
-    }
-    ~sps_ctx() {
-        cudaSetDevice(device);
-        if (graph) cudaGraphExecDestroy(graph);
-        DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
-                         &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
-                         &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
-                         &rowinfo, &tcerr};
-        for (DevBuf* b : all) b->release();
-        for (auto& b : stage) b.release();
-    }
-};
 
 namespace {
 

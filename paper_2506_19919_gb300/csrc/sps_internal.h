@@ -56,6 +56,9 @@ struct Grid {
     const float* row_scale;  // [A] 2^e_i
 };
 
+// Records the message returned by sps_last_error_message() on this thread.
+void set_last_error(const char* msg);
+
 // Launchers (defined in the .cu files); all return cudaError_t of the launch.
 cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const double* lam64,
                                     const double* band_p0, const double* band_p1,
