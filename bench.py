@@ -234,7 +234,7 @@ def run_ours(args):
                 "accept_mean": float(stats["accept_prob"].mean()),
                 "divergences": int(stats["divergences"].sum())},
         "grad_evals_per_s": float(nev.sum()) * ws / (ms_step / 1e3),
-        "roofline": {"kernel": "k_hmc_approx", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "k_hmc_team", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived)",
@@ -298,17 +298,25 @@ def _loglike_grad_rates(ctx_hmc, dev):
     mobs = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev),
                           mode="approx") + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)
     res = {"pairs": wl.n_gal, "workload": W.CONFIG_NAMES[2]}
-    for mode, prec, reps in (("approx", "fp32", 10), ("exact", "fp32", 2), ("exact", "bf16", 2)):
-        ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+    for mode, prec, reps in (("approx", "fp32", 10), ("plain", "fp32", 3), ("exact", "fp32", 2),
+                             ("exact", "bf16", 3)):
+        def call():
+            if mode == "plain":
+                ctx.loglike_grad_forward_mode(th, mobs, wl.sigma, wl.mask)
+            else:
+                ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+        call()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+            call()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[f"{mode}_{prec}"] = {"evals_per_s": wl.n_gal / (ms / 1e3), "ms": ms}
+    res["fused_adjoint_vs_plain_forward_mode"] = (res["approx_fp32"]["evals_per_s"]
+                                                  / res["plain_fp32"]["evals_per_s"])
     ctx.close()
     return res
 
@@ -359,13 +367,18 @@ def run_loglike_only(args):
     out = {"pairs": wl.n_gal}
     for spec in args.loglike_only.split(","):
         mode, prec = spec.split("_")
+        def call():
+            if mode == "plain":
+                ctx.loglike_grad_forward_mode(th, mobs, wl.sigma, wl.mask)
+            else:
+                ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
         for _ in range(args.warmup):
-            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+            call()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            ctx.loglike_grad(th, mobs, wl.sigma, wl.mask, mode=mode, prec=prec)
+            call()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps

@@ -143,6 +143,17 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
                             sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
                             void* stream);
 
+/* Comparison baseline, not a product path: the same approximate-path log L and
+ * gradient as sps_loglike_grad (SPS_APPROX), computed the plain way a direct
+ * GPU port would: unfused kernels with their intermediates in HBM and the
+ * gradient by forward-mode tangents (one contraction per weight parameter,
+ * 9 in all, against ~2 for the hand-written adjoint).  Same arguments and
+ * layouts as sps_loglike_grad. */
+sps_status sps_loglike_grad_forward_mode(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
+                                         int64_t n, const float* mag_obs, const float* sigma,
+                                         const uint32_t* mask, float* loglike_out, float* grad_out,
+                                         void* stream);
+
 /* Batched HMC configuration (Sec. 4, App. D.2). */
 typedef struct {
     int32_t chains_per_gal; /* C >= 1; chain c of galaxy g is row g*C + c          */
@@ -156,7 +167,7 @@ typedef struct {
     int32_t prec;           /* sps_prec (EXACT only)                              */
     int32_t use_graph;      /* capture the device work in a CUDA graph             */
     int32_t autotune;       /* pick the launch shape by timing candidates          */
-    int32_t adapt_mass;     /* adapt a diagonal inverse metric in the warm-up       */
+    int32_t adapt_mass;     /* warm-up metric: 0 identity (default), 1 diagonal, 2 dense */
 } sps_hmc_config;
 
 sps_status sps_hmc_config_default(sps_hmc_config* cfg);
@@ -172,9 +183,10 @@ typedef struct {
 
 /* Run batched HMC for every chain of every galaxy of the current set.
  * Warm-up adapts, per chain, the step size by dual averaging (Hoffman & Gelman
- * 2014) and, if adapt_mass, a diagonal inverse metric in windows (75-iteration
- * initial buffer, slow windows of 25, 50, 100, ..., 50-iteration terminal
- * buffer; regularised variances of each window's positions).
+ * 2014) and, if adapt_mass is 1 (2), a diagonal (dense) inverse metric in
+ * windows (75-iteration initial buffer, slow windows of 25, 50, 100, ...,
+ * 50-iteration terminal buffer; regularised variances (covariance) of each
+ * window's positions; a dense metric M^-1 = L L^T gives momenta L^-T z).
  * The target is log L (App. D.1) plus the log-Jacobian of the bounding map
  * theta = lo + (hi - lo) / (1 + exp(-x)) (Eq. BoundingFunction, k = 1, x0 = 0),
  * i.e. a prior uniform in each bounded parameter; sampling is in x.

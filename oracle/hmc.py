@@ -7,7 +7,9 @@ adaptation during a warm-up phase.  The paper runs Blackjax HMC; it does not
 print the adaptation constants or the trajectory-length rule, so the
 declared readings are:
 
-* trajectory length L ~ U{L_min .. L_max} per iteration;
+* trajectory length L ~ U{L_min .. L_max} per iteration; the inverse metric
+  is the identity unless adapt_mass is set (the workloads adapt only the step
+  size);
 * step size adapted per chain by the dual-averaging scheme of Hoffman &
   Gelman (2014, Sec. 3.2.1) with target 0.8, gamma 0.05, t0 10, kappa 0.75,
   mu = log(10 eps0); warm-up uses eps_m, sampling uses the averaged eps-bar;
@@ -16,12 +18,17 @@ declared readings are:
   adaptation is of this family): an initial buffer of 75 iterations, slow
   windows of 25, 50, 100, ... iterations (the last one stretched to the
   terminal buffer), a terminal buffer of 50 (15% / 75% / 10% of the warm-up
-  when it is shorter than 150).  At the end of each slow window the inverse
+  when it is shorter than 150).  At the end of each slow window holding at
+  least two draws the inverse
   metric becomes the regularised variance n/(n+5) var + 1e-3 * 5/(n+5) of the
   window's positions (Welford, FP64) and dual averaging restarts with
   mu = log(10 eps).  Momenta p = z / sqrt(minv), kinetic energy
   sum minv p^2 / 2, drift x += eps minv p.  With adapt_mass False the metric
   stays the identity;
+* metric="dense" adapts a dense inverse metric the same way (Stan's dense
+  variant): the window's covariance (Welford), regularised as
+  n/(n+5) cov + 1e-3 * 5/(n+5) I, with Cholesky factor L (cov = L L^T);
+  momenta p = L^-T z, kinetic energy |L^T p|^2 / 2, drift x += eps L L^T p;
 * random numbers from Philox-4x32-10 (Salmon et al. 2011), keyed by the
   64-bit seed, counter (iteration, block, chain, 0): blocks 0-2 give twelve
   uniforms -> six Box-Muller pairs of momenta, block 3 gives the accept
@@ -150,9 +157,10 @@ def warmup_windows(n_warm):
     return init, wins, stop
 
 
-def leapfrog(target, rows, x, p, g, eps, L, minv=None):
+def leapfrog(target, rows, x, p, g, eps, L, minv=None, chol=None):
     """L leapfrog steps (half kick, drift, gradient, half kick), per chain
-    lengths L; returns the end point, its momentum, log p and gradient."""
+    lengths L; returns the end point, its momentum, log p and gradient.  The
+    inverse metric is diagonal (minv) or dense (chol: its Cholesky factor)."""
     x, p, g = x.copy(), p.copy(), g.copy()
     minv = np.ones_like(x) if minv is None else minv
     lp = np.full(x.shape[0], np.nan)
@@ -163,7 +171,12 @@ def leapfrog(target, rows, x, p, g, eps, L, minv=None):
             break
         e = eps[act, None]
         p[act] += 0.5 * e * g[act]
-        x[act] += e * minv[act] * p[act]
+        if chol is None:
+            x[act] += e * minv[act] * p[act]
+        else:
+            Lc = chol[act]
+            u = np.einsum("ckj,ck->cj", Lc, p[act])              # L^T p
+            x[act] += e * np.einsum("ckj,cj->ck", Lc, u)           # L (L^T p)
         lpa, ga = target(x[act], rows[act])
         g[act] = ga
         lp[act] = lpa
@@ -173,7 +186,7 @@ def leapfrog(target, rows, x, p, g, eps, L, minv=None):
 
 def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
             eps0=0.1, target_accept=0.8, gamma=0.05, t0=10.0, kappa=0.75,
-            chain_ids=None, adapt_mass=True):
+            chain_ids=None, adapt_mass=False, metric="diag"):
     """Batched HMC over independent chains (Sec. 4, App. D.2).
 
     Returns dict with samples [C, n_samp, 12] (bounded parameters),
@@ -190,8 +203,11 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
     log_eps_bar = np.zeros(C)
     m_da = 0                                   # iterations since the last restart
     minv = np.ones_like(x)
+    dense = metric == "dense"
+    chol = np.tile(np.eye(x.shape[1]), (C, 1, 1)) if dense else None
     _, wins, _ = warmup_windows(n_warm) if adapt_mass else (0, [], 0)
     w_n, w_mean, w_m2 = 0, np.zeros_like(x), np.zeros_like(x)
+    w_cov = np.zeros((C, x.shape[1], x.shape[1]))
     samples = np.zeros((C, n_samp, x.shape[1]))
     acc_sum = np.zeros(C)
     warm_acc = np.zeros(C)
@@ -199,11 +215,17 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
     nevals = np.zeros(C, np.int64)
     for it in range(n_warm + n_samp):
         z, u, L = draws(seed, ids, it, L_min, L_max)
-        p = z / np.sqrt(minv)
-        x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L, minv)
+        if dense:
+            p = np.stack([np.linalg.solve(chol[i].T, z[i]) for i in range(C)])
+            x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L, chol=chol)
+            kin = lambda q: 0.5 * (np.einsum("ckj,ck->cj", chol, q) ** 2).sum(1)
+        else:
+            p = z / np.sqrt(minv)
+            x1, p1, g1, lp1 = leapfrog(target, rows, x, p, g, eps, L, minv)
+            kin = lambda q: 0.5 * (minv * q * q).sum(1)
         nevals += L
-        h0 = -lp + 0.5 * (minv * p * p).sum(1)
-        h1 = -lp1 + 0.5 * (minv * p1 * p1).sum(1)
+        h0 = -lp + kin(p)
+        h1 = -lp1 + kin(p1)
         dh = h1 - h0
         finite = np.isfinite(dh)
         a = np.where(finite, np.minimum(1.0, np.exp(-np.where(finite, dh, 0.0))), 0.0)
@@ -226,10 +248,18 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
                     d = x - w_mean
                     w_mean = w_mean + d / w_n
                     w_m2 = w_m2 + d * (x - w_mean)
+                    w_cov = w_cov + np.einsum("ci,cj->cij", d, x - w_mean)
+                    if it == we_ - 1 and w_n >= 2:       # variance needs two draws
+                        if dense:
+                            cov = w_cov / (w_n - 1.0)
+                            reg = (w_n / (w_n + 5.0)) * cov + 1e-3 * (5.0 / (w_n + 5.0)) * np.eye(x.shape[1])
+                            chol = np.linalg.cholesky(reg)
+                        else:
+                            var = w_m2 / (w_n - 1.0)
+                            minv = (w_n / (w_n + 5.0)) * var + 1e-3 * (5.0 / (w_n + 5.0))
                     if it == we_ - 1:
-                        var = w_m2 / (w_n - 1.0)
-                        minv = (w_n / (w_n + 5.0)) * var + 1e-3 * (5.0 / (w_n + 5.0))
                         w_n, w_mean, w_m2 = 0, np.zeros_like(x), np.zeros_like(x)
+                        w_cov = np.zeros_like(w_cov)
                         mu = np.log(10.0 * eps)
                         hbar = np.zeros(C)
                         log_eps_bar = np.zeros(C)
@@ -239,6 +269,6 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
             th = O.bound(torch.as_tensor(x), target.lo, target.hi).numpy()
             samples[:, s] = th
             acc_sum += a
-    return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps, minv=minv,
+    return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps, minv=minv, chol=chol,
                 warm_accept=warm_acc / max(n_warm - n_warm // 2, 1),
                 divergences=div, grad_evals=nevals)

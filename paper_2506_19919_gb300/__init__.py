@@ -137,9 +137,27 @@ class Context:
               "sps_loglike_grad")
         return ll, g
 
+    def loglike_grad_forward_mode(self, theta, mag_obs, sigma, mask, gal_idx=None):
+        """The plain forward-mode comparison path (approximate photometry)."""
+        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        dev = th.device
+        n = th.shape[0]
+        mo = _f32(mag_obs, dev)
+        sg = _f32(sigma, dev)
+        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
+            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=dev).contiguous()
+        ll = torch.empty(n, dtype=torch.float32, device=dev)
+        g = torch.empty((n, _lib.NPARAM), dtype=torch.float32, device=dev)
+        check(self._lib.sps_loglike_grad_forward_mode(self.h, _vp(th), _vp(gi), n, _vp(mo), _vp(sg),
+                                                      _vp(mk), _vp(ll), _vp(g), _stream(th)),
+              "sps_loglike_grad_forward_mode")
+        return ll, g
+
     def hmc_run(self, theta0_unb, mag_obs, sigma, mask, chains_per_gal=4, n_warm=500,
                 n_samp=500, L_min=8, L_max=64, target_accept=0.8, eps0=0.1, seed=2506199190,
-                use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=True):
+                use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=0):
         x0 = theta0_unb if isinstance(theta0_unb, torch.Tensor) else _f32(theta0_unb, self.device)
         dev = x0.device
         mo = _f32(mag_obs, dev)
@@ -154,7 +172,7 @@ class Context:
         cfg.target_accept, cfg.eps0, cfg.seed = target_accept, eps0, seed
         cfg.mode = MODES[mode]
         cfg.use_graph, cfg.autotune = int(use_graph), int(autotune)
-        cfg.adapt_mass = int(adapt_mass)
+        cfg.adapt_mass = {False: 0, True: 1, "diag": 1, "dense": 2, "none": 0}.get(adapt_mass, adapt_mass)
         out = {
             "samples": torch.empty((nc, n_samp, _lib.NPARAM), dtype=torch.float32, device=dev)
             if samples else None,

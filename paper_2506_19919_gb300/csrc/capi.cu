@@ -19,12 +19,6 @@
 #include "ctx.h"
 #include "sps_internal.h"
 
-namespace sps {
-size_t hmc_warp_smem_bytes();
-cudaError_t hmc_set_smem(size_t bytes);
-cudaError_t hmc_occupancy(int warps, size_t smem, int* blocks_per_sm);
-}  // namespace sps
-
 using namespace sps;
 
 namespace {
@@ -234,7 +228,7 @@ sps_status sps_hmc_config_default(sps_hmc_config* cfg) {
     cfg->prec = SPS_FP32;
     cfg->use_graph = 1;
     cfg->autotune = 1;
-    cfg->adapt_mass = 1;
+    cfg->adapt_mass = 0;
     return SPS_OK;
 }
 
@@ -584,6 +578,54 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     return finish_call(ctx, st, s);
 }
 
+sps_status sps_loglike_grad_forward_mode(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
+                                         int64_t n, const float* mag_obs, const float* sigma,
+                                         const uint32_t* mask, float* loglike_out, float* grad_out,
+                                         void* stream) {
+    sps_status st0 = check_rows(ctx, theta, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
+        return fail(SPS_E_INVALID_ARG, "null data or output pointer");
+    if (n == 0) return SPS_OK;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const Consts& c = ctx->c;
+    const size_t GB = (size_t)ctx->n_gal * c.n_band;
+    Stager st{ctx, s};
+    const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
+    float* llo = st.out(loglike_out, (size_t)n);
+    float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
+    const int64_t chunk = 32768;
+    const int64_t rows = std::min<int64_t>(n, chunk);
+    CK(ctx->plainT.reserve((size_t)rows * 9 * c.K * sizeof(float)));
+    CK(ctx->plainC.reserve((size_t)rows * c.n_band * 9 * sizeof(float)));
+    const Galaxies gal = ctx->gal();
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t m = std::min(chunk, n - r0);
+        Galaxies gv = gal;
+        const float* mo2 = mo;
+        const float* sg2 = sg;
+        const uint32_t* mk2 = mk;
+        if (!gi) {
+            mo2 += r0 * c.n_band; sg2 += r0 * c.n_band; mk2 += r0;
+            gv.z += r0; gv.lnT += r0; gv.lT10 += r0; gv.bins += r0 * c.n_age;
+            gv.zp += r0 * c.n_band; gv.support += r0 * c.n_band; gv.gauss += r0 * c.n_band;
+            gv.dust_eff += r0 * c.n_band; gv.cssp += r0 * c.n_band * c.K; gv.n = m;
+        }
+        CK(launch_plain(c, gv, th + r0 * SPS_NPARAM, gi ? gi + r0 : nullptr, m, mo2, sg2, mk2,
+                        llo + r0, gro ? gro + r0 * SPS_NPARAM : nullptr, ctx->plainT.as<float>(),
+                        ctx->plainC.as<float>(), s));
+    }
+    return finish_call(ctx, st, s);
+}
+
 sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const float* eps,
                         const int32_t* L, const int32_t* gal_idx, int64_t n, const float* mag_obs,
                         const float* sigma, const uint32_t* mask, float* x_out, float* p_out,
@@ -739,75 +781,74 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
 
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
-                 cfg->seed, cfg->adapt_mass ? 1 : 0};
-    const size_t table_bytes = (size_t)nb_max * c.K * sizeof(float);
+                 cfg->seed, cfg->adapt_mass < 0 ? 0 : (cfg->adapt_mass > 2 ? 2 : cfg->adapt_mass)};
+    if (c.n_met > 12) return fail(SPS_E_UNSUPPORTED, "HMC kernel holds at most 12 metallicity bins in registers");
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, ctx->device));
     const int sms = prop.multiProcessorCount;
-    // launch shape: warps per block from {C, 2C (>= 2 warps)}, blocks = occupancy x SMs
-    std::vector<int> cand_w = {C};
-    if (2 * C <= 16) cand_w.push_back(2 * C);
-    if (C < 4 && 4 <= 16) cand_w.push_back(4);
-    const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max);
-    auto shape_for = [&](int warps, int& blocks) -> cudaError_t {
-        size_t smem = hmc_warp_smem_bytes() * warps + table_bytes;
-        cudaError_t e = hmc_set_smem(smem);
-        if (e != cudaSuccess) return e;
+    // launch shapes: chains of a galaxy per warp (cpw) x warps per block; the
+    // grid is persistent (occupancy x SMs) and pulls (galaxy, chain group)
+    // items from the queue
+    const int cpw0 = C >= 4 ? 4 : (C >= 2 ? 2 : 1);
+    std::vector<std::pair<int, int>> cands = {{cpw0, 2}, {cpw0, 4}};
+    if (cpw0 == 4) cands.push_back({2, 4});
+    auto blocks_for = [&](int cpw, int warps, int& blocks) -> cudaError_t {
         int per_sm = 0;
-        e = hmc_occupancy(warps, smem, &per_sm);
+        cudaError_t e = hmc_team_occupancy(cpw, warps, &per_sm);
         if (e != cudaSuccess) return e;
         blocks = std::max(1, per_sm) * sms;
         return cudaSuccess;
     };
-    int warps = C, blocks = sms;
+    const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max);
+    int cpw = cpw0, warps = 4, blocks = sms;
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        warps = it->second.first;
+        cpw = it->second.first / 100;
+        warps = it->second.first % 100;
         blocks = it->second.second;
-        CK(hmc_set_smem(hmc_warp_smem_bytes() * warps + table_bytes));
-    } else if (cfg->autotune && cand_w.size() > 1 && G >= 64) {
+    } else if (cfg->autotune && G >= 2 * sms) {
         // time each candidate on a short run over a slice of the galaxies
         float best = 1e30f;
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         HmcParams tp = hp;
-        tp.n_warm = 2;
+        tp.n_warm = 3;
         tp.n_samp = 0;
         Galaxies gsub = ctx->gal();
-        for (int w : cand_w) {
+        for (auto cw : cands) {
             int b = 0;
-            CK(shape_for(w, b));
-            gsub.n = std::min<int64_t>(G, (int64_t)b * std::max(1, w / C) * 2);
+            CK(blocks_for(cw.first, cw.second, b));
+            const int groups = (C + cw.first - 1) / cw.first;
+            gsub.n = std::min<int64_t>(G, ((int64_t)b * cw.second * 2 + groups - 1) / groups);
             CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s));
             CK(cudaEventRecord(e0, s));
-            CK(launch_hmc_approx(c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr, ctx->queue.as<int>(), ctx->err.as<int>(), b, w,
-                                 table_bytes, s));
+            CK(launch_hmc_team(cw.first, c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, ctx->queue.as<int>(), b, cw.second, s));
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
-            float per = ms / (float)gsub.n;
+            const float per = ms / (float)(gsub.n * C);
             if (per < best) {
                 best = per;
-                warps = w;
+                cpw = cw.first;
+                warps = cw.second;
                 blocks = b;
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        ctx->tuned[key] = {warps, blocks};
-        CK(hmc_set_smem(hmc_warp_smem_bytes() * warps + table_bytes));
+        ctx->tuned[key] = {cpw * 100 + warps, blocks};
     } else {
-        CK(shape_for(warps, blocks));
+        CK(blocks_for(cpw, warps, blocks));
     }
 
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        return launch_hmc_approx(c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
-                                 ctx->queue.as<int>(), ctx->err.as<int>(), blocks, warps, table_bytes, s);
+        return launch_hmc_team(cpw, c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+                               ctx->queue.as<int>(), blocks, warps, s);
     };
     if (cfg->use_graph) {
         char kb[512];
@@ -816,7 +857,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
                       (void*)acc, (void*)epo, (void*)dv, (void*)nev, (void*)sto, (long long)G, C,
                       hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, hp.adapt_mass, (unsigned long long)hp.seed,
                       (double)hp.eps0, (double)hp.target_accept);
-        std::string gk = std::string(kb) + ":" + std::to_string(blocks);
+        std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw);
         if (!ctx->graph || gk != ctx->graph_key) {
             if (ctx->graph) {
                 cudaGraphExecDestroy(ctx->graph);

@@ -25,7 +25,9 @@ namespace {
 
 constexpr int kTM = 128;       // rows per tile (MMA M)
 constexpr int kBK = 64;        // bf16 per k-block row (128 bytes)
-constexpr int kThreadsTC = 192;
+constexpr int kThreadsTC = 192;   // adjoint: TMA warp, MMA warp, 4 epilogue warps
+constexpr int kFwdEpiWarps = 8;   // forward: two epilogue warps per TMEM lane quarter
+constexpr int kThreadsFwd = 64 + 32 * kFwdEpiWarps;
 constexpr int kFwdBN = 256;
 constexpr int kFwdStages = 4;
 constexpr int kAdjBN = 192;
@@ -69,7 +71,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ct
 
 // Shared prologue: barriers and TMEM allocation.  Returns the ring base.
 template <int STAGES>
-__device__ __forceinline__ void tc_setup(Ctl* ctl, int warp) {
+__device__ __forceinline__ void tc_setup(Ctl* ctl, int warp, int epi_threads = 4 * 32) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             tc::mbar_init(&ctl->full[s], 1);
@@ -77,7 +79,7 @@ __device__ __forceinline__ void tc_setup(Ctl* ctl, int warp) {
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&ctl->tfull[b], 1);
-            tc::mbar_init(&ctl->tempty[b], 4 * 32);
+            tc::mbar_init(&ctl->tempty[b], epi_threads);
         }
         tc::mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -176,6 +178,14 @@ __device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
     }
 }
 
+static_assert(sizeof(Ctl) <= 256, "control block must fit before the staging area");
+
+// Per-warp staging of a tile's per-wavelength constants (forward epilogue).
+struct LamStage {
+    float4 lc[kFwdBN / 2];
+    float lam[kFwdBN / 2];
+};
+
 template <int BN, int STAGES>
 __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
     uintptr_t p = reinterpret_cast<uintptr_t>(raw);
@@ -187,7 +197,7 @@ __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
 
 // ---------------------------------------------------------------- forward
 template <int NB>
-__global__ void __launch_bounds__(kThreadsTC, 1)
+__global__ void __launch_bounds__(kThreadsFwd, 1)
 k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
          const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
          const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
@@ -199,13 +209,16 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
     const int m0 = blockIdx.x * kTM;
     const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
     const int n_kb = c.k_pad / kBK;
-    tc_setup<kFwdStages>(ctl, warp);
+    LamStage* stage = reinterpret_cast<LamStage*>(reinterpret_cast<unsigned char*>(ctl) + 256);
+    tc_setup<kFwdStages>(ctl, warp, kFwdEpiWarps * 32);
     if (warp == 0) {
         if (lane == 0) tc_produce<kFwdBN, kFwdStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
     } else if (warp == 1) {
         if (lane == 0) tc_mma<kFwdBN, kFwdStages>(ctl, ring, n_tiles, n_kb, err);
     } else {
         const int q = warp & 3;                    // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;          // which half of each tile's columns
+        LamStage& ls = stage[warp - 2];
         const int rl = 32 * q + lane;
         const int64_t row = (int64_t)m0 + rl;
         const bool live = row < n;
@@ -242,15 +255,23 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
             const uint32_t use = (uint32_t)(nt >> 1);
             if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
             tc::tc_fence_after();
-            for (int cc = 0; cc < kFwdBN / 32; ++cc) {
+            const int col0 = nt * kFwdBN + half * (kFwdBN / 2);
+            for (int t = lane; t < kFwdBN / 2; t += 32) {
+                const int nn = min(col0 + t, c.n_lam - 1);    // columns past the grid hold S = 0
+                ls.lc[t] = __ldg(grid.lamc + nn);
+                ls.lam[t] = __ldg(grid.lam + nn);
+            }
+            __syncwarp();
+            for (int cc = 0; cc < kFwdBN / 64; ++cc) {
                 float S[32];
-                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kFwdBN + cc * 32), S);
-                const int nb0 = nt * kFwdBN + cc * 32;
+                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
+                                  (uint32_t)(buf * kFwdBN + half * (kFwdBN / 2) + cc * 32), S);
+                const int nb0 = col0 + cc * 32;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int nn = min(nb0 + j, c.n_lam - 1);   // columns past the grid hold S = 0
-                    const float4 L4 = __ldg(grid.lamc + nn);
-                    const float lam = __ldg(grid.lam + nn);
+                    const int nn = min(nb0 + j, c.n_lam - 1);
+                    const float4 L4 = ls.lc[cc * 32 + j];
+                    const float lam = ls.lam[cc * 32 + j];
                     const float pw = __expf(dl * L4.z);
                     const float base = L4.y * pw + eb * L4.w;
                     const float E = exp2f(cA * base);
@@ -273,18 +294,22 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
                     }
                 }
             }
+            __syncwarp();
             tc::tc_fence_before();
             tc::mbar_arrive(&ctl->tempty[buf]);
         }
+        // the two column halves of a row meet here: cJ is zeroed before the
+        // launch and gets exactly two addends, so the sum does not depend on
+        // their order
         if (valid && !ctl->abort) {
 #pragma unroll
             for (int b = 0; b < NB; ++b)
                 if (b < B) {
                     float* o = cJ + (row * B + b) * 4;
-                    o[0] = acc[b][0];
-                    o[1] = acc[b][1];
-                    o[2] = acc[b][2];
-                    o[3] = acc[b][3];
+                    atomicAdd(o + 0, acc[b][0]);
+                    atomicAdd(o + 1, acc[b][1]);
+                    atomicAdd(o + 2, acc[b][2]);
+                    atomicAdd(o + 3, acc[b][3]);
                 }
         }
     }
@@ -338,7 +363,9 @@ k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
 
 }  // namespace
 
-size_t tc_fwd_smem() { return Ring<kFwdBN, kFwdStages>::kBytes + sizeof(Ctl) + 1024; }
+size_t tc_fwd_smem() {
+    return Ring<kFwdBN, kFwdStages>::kBytes + 256 + sizeof(LamStage) * kFwdEpiWarps + 1024;
+}
 size_t tc_adj_smem() { return Ring<kAdjBN, kAdjStages>::kBytes + sizeof(Ctl) + 1024; }
 
 cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
@@ -347,15 +374,16 @@ cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Co
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
     const size_t smem = tc_fwd_smem();
-    cudaError_t e;
+    cudaError_t e = cudaMemsetAsync(cJ, 0, (size_t)n * c.n_band * 4 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
     if (c.n_band <= 8) {
         e = cudaFuncSetAttribute(k_fwd_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_fwd_tc<8><<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
+        k_fwd_tc<8><<<blocks, kThreadsFwd, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
     } else {
         e = cudaFuncSetAttribute(k_fwd_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_fwd_tc<32><<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
+        k_fwd_tc<32><<<blocks, kThreadsFwd, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
     }
     return cudaGetLastError();
 }

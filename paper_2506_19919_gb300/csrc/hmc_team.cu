@@ -1,0 +1,688 @@
+// Batched HMC on the approximate path with the chains of one galaxy in lock
+// step on one warp (Sec. 4, App. D.2).
+//
+// A warp ("team") takes up to kCPW chains of one galaxy from a global work
+// queue (atomic counter, no waiting) and advances all of them one gradient
+// evaluation per step.  Chains stay trajectory-asynchronous: each has its own
+// trajectory length, step size, inverse metric and iteration count, and ends
+// and restarts its trajectories on its own; a chain that has finished keeps
+// its last position until the team's other chains are done.  The contraction
+// with the galaxy's c_SSP table is organised by age bin: every table row
+// c_SSP[b][i][0..Zn) is loaded once and used by all chains of the team for
+// R = sum_j q_j C_ij (forward), and again in the adjoint pass for
+// wbar_i += g_b R and qbar_j += g_b w_i C_ij.  Warps never wait on one another.
+//
+// Sampler (same definition as the per-chain kernel): p = z / sqrt(minv),
+// leapfrog (half kick, drift x += eps minv p, gradient, half kick), FP64
+// energy accept, dual-averaged step size and windowed diagonal metric in the
+// warm-up, Philox-4x32-10 draws with counter (iteration, block, chain, 0).
+#include "philox.cuh"
+#include "sps_device.cuh"
+
+namespace sps {
+
+namespace {
+
+constexpr int kZnReg = 12;   // metallicity bins held in registers (Zn <= 12)
+
+template <int CPW>
+struct TeamWork {
+    float m[CPW][kMaxAges], dm0[CPW][kMaxAges], dm1[CPW][kMaxAges], dm2[CPW][kMaxAges];
+    float pi[CPW][kMaxAges], w[CPW][kMaxAges], wb[CPW][kMaxAges];
+    float q[CPW][kMaxMets], qb[CPW][kMaxMets];
+    union {
+        PanelScratch ps;
+        float red[32][CPW * kZnReg + 1];
+        struct {
+            double tll[CPW][kMaxBands];
+            float tg[CPW][kMaxBands][4];
+        } t;
+    } u;
+    float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM], lpe[CPW][SPS_NPARAM];
+    double M[CPW], lpri[CPW], ll[CPW];
+    float gd[CPW][4];                       // d logL / d(lgM, A_V, delta, F_floor)
+    float S[CPW][kMaxBands], gh[CPW][kMaxBands];
+    // galaxy slots
+    const float* ptr[kMaxBands];
+    float4 dust[kMaxBands];
+    double zp[kMaxBands];
+    float mobs[kMaxBands], isig2[kMaxBands];
+    // chain state
+    float x[CPW][SPS_NPARAM], p[CPW][SPS_NPARAM], g[CPW][SPS_NPARAM];
+    float xs[CPW][SPS_NPARAM], gs[CPW][SPS_NPARAM], minv[CPW][SPS_NPARAM];
+    double lp[CPW], lps[CPW], h0[CPW];
+    double mu[CPW], hbar[CPW], leb[CPW], acc[CPW];
+    double wmean[CPW][SPS_NPARAM], wm2[CPW][SPS_NPARAM];
+    float chol[CPW][78];                    // dense inverse metric L L^T, packed lower
+    float wcov[CPW][78];                    // Welford co-moments of the window
+    float v[CPW][SPS_NPARAM], lu[CPW][SPS_NPARAM], dv[CPW][2][SPS_NPARAM];
+    double uacc[CPW];
+    float eps[CPW];
+    int L[CPW], l[CPW], it[CPW], mda[CPW], wn[CPW], ndiv[CPW], done[CPW];
+    int wstart[CPW], wend[CPW], wwidth[CPW], wstop[CPW];
+    long long nev[CPW];
+    uint32_t chain[CPW];
+};
+
+template <int CPW>
+__device__ __forceinline__ AgeView age_view(TeamWork<CPW>& t, int ch) {
+    return AgeView{t.m[ch], t.dm0[ch], t.dm1[ch], t.dm2[ch], t.pi[ch], t.w[ch], t.wb[ch],
+                   t.q[ch], t.qb[ch], &t.u.ps};
+}
+
+// Row i of a band's c_SSP table: Zn consecutive floats.
+__device__ __forceinline__ void load_row(const float* __restrict__ p, int Zn, float* cv) {
+    if (Zn == 12) {
+        const float4* v = reinterpret_cast<const float4*>(p);
+        float4 a = v[0], b = v[1], c = v[2];
+        cv[0] = a.x; cv[1] = a.y; cv[2] = a.z; cv[3] = a.w;
+        cv[4] = b.x; cv[5] = b.y; cv[6] = b.z; cv[7] = b.w;
+        cv[8] = c.x; cv[9] = c.y; cv[10] = c.z; cv[11] = c.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) cv[j] = (j < Zn) ? p[j] : 0.0f;
+    }
+}
+
+// log posterior (unbounded space) and its gradient for every chain of the
+// team at t.x; writes t.lp and t.g.
+template <int CPW>
+__device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, const float2* __restrict__ bins,
+                          float lnT, float lT10, int nb) {
+    const int lane = lane_id();
+    const int A = c.n_age, Zn = c.n_met;
+    for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
+        const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
+        const float x = t.x[ch][k];
+        const float sg = 1.0f / (1.0f + __expf(-x));
+        t.th[ch][k] = c.prior_lo[k] + c.prior_span[k] * sg;
+        t.dth[ch][k] = c.prior_span[k] * sg * (1.0f - sg);
+        const float ax = fabsf(x);
+        t.lpe[ch][k] = -ax - 2.0f * log1pf(__expf(-ax));
+    }
+    __syncwarp();
+    if (lane < CPW) {
+        double s = 0.0;
+        for (int k = 0; k < SPS_NPARAM; ++k) s += (double)t.lpe[lane][k];
+        t.lpri[lane] = s;
+    }
+#pragma unroll 1
+    for (int ch = 0; ch < CPW; ++ch) {
+        const double M = age_met_weights(c, age_view(t, ch), bins, lnT, lT10, t.th[ch], true);
+        if (lane == 0) t.M[ch] = M;
+    }
+    __syncwarp();
+    // ---- forward pass: S[ch][b] = sum_i w_i sum_j q_j C[b][i][j]
+    float qr[CPW][kZnReg], wl[CPW][4];
+#pragma unroll
+    for (int ch = 0; ch < CPW; ++ch) {
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) qr[ch][j] = (j < Zn) ? t.q[ch][j] : 0.0f;
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            wl[ch][tt] = (i < A) ? t.w[ch][i] : 0.0f;
+        }
+    }
+    for (int b = 0; b < nb; ++b) {
+        const float* C = t.ptr[b];
+        float sacc[CPW];
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) sacc[ch] = 0.0f;
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            if (i < A) {
+                float cv[kZnReg];
+                load_row(C + i * Zn, Zn, cv);
+#pragma unroll
+                for (int ch = 0; ch < CPW; ++ch) {
+                    float R = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < kZnReg; ++j) R = fmaf(qr[ch][j], cv[j], R);
+                    sacc[ch] = fmaf(wl[ch][tt], R, sacc[ch]);
+                }
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) {
+            const float v = warp_sum(sacc[ch]);
+            if (lane == 0) t.S[ch][b] = v;
+        }
+    }
+    __syncwarp();
+    // ---- magnitudes, likelihood and dust / lgM gradients per (chain, band)
+    for (int e = lane; e < CPW * nb; e += 32) {
+        const int ch = e / nb, b = e - ch * nb;
+        const float4 dc = t.dust[b];
+        const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
+        const float Sv = t.S[ch][b];
+        const double lc = log10((double)d.F * (double)Sv) + (double)t.th[ch][0] + 9.0;
+        const double r = (t.zp[b] - 2.5 * lc) - (double)t.mobs[b];
+        const double is2 = (double)t.isig2[b];
+        t.u.t.tll[ch][b] = -0.5 * r * r * is2;
+        const float gam = (float)(2.5 * r * is2 / 2.302585092994046);
+        const float gF = gam / d.F;
+        t.gh[ch][b] = gam / Sv;
+        t.u.t.tg[ch][b][0] = gam * kLn10f;
+        t.u.t.tg[ch][b][1] = gF * d.dF_AV;
+        t.u.t.tg[ch][b][2] = gF * d.dF_delta;
+        t.u.t.tg[ch][b][3] = gF * d.dF_floor;
+    }
+    __syncwarp();
+    if (lane < CPW) {
+        double s = 0.0;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        for (int b = 0; b < nb; ++b) {
+            s += t.u.t.tll[lane][b];
+            g0 += t.u.t.tg[lane][b][0];
+            g1 += t.u.t.tg[lane][b][1];
+            g2 += t.u.t.tg[lane][b][2];
+            g3 += t.u.t.tg[lane][b][3];
+        }
+        t.ll[lane] = s;
+        t.gd[lane][0] = g0;
+        t.gd[lane][1] = g1;
+        t.gd[lane][2] = g2;
+        t.gd[lane][3] = g3;
+    }
+    __syncwarp();
+    // ---- adjoint pass: wbar_i = sum_b g_b R_bi, qbar_j = sum_b g_b sum_i w_i C_bij
+    float qbr[CPW][kZnReg], wbl[CPW][4];
+#pragma unroll
+    for (int ch = 0; ch < CPW; ++ch) {
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = 0.0f;
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) wbl[ch][tt] = 0.0f;
+    }
+    for (int b = 0; b < nb; ++b) {
+        const float* C = t.ptr[b];
+        float ghr[CPW];
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) ghr[ch] = t.gh[ch][b];
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            if (i < A) {
+                float cv[kZnReg];
+                load_row(C + i * Zn, Zn, cv);
+#pragma unroll
+                for (int ch = 0; ch < CPW; ++ch) {
+                    float R = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < kZnReg; ++j) R = fmaf(qr[ch][j], cv[j], R);
+                    wbl[ch][tt] = fmaf(ghr[ch], R, wbl[ch][tt]);
+                    const float gw = ghr[ch] * wl[ch][tt];
+#pragma unroll
+                    for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = fmaf(gw, cv[j], qbr[ch][j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < CPW; ++ch)
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            if (i < A) t.wb[ch][i] = wbl[ch][tt];
+        }
+#pragma unroll
+    for (int ch = 0; ch < CPW; ++ch)
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) t.u.red[lane][ch * kZnReg + j] = qbr[ch][j];
+    __syncwarp();
+    for (int e = lane; e < CPW * kZnReg; e += 32) {
+        float s = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) s += t.u.red[r][e];
+        const int ch = e / kZnReg, j = e - ch * kZnReg;
+        if (j < Zn) t.qb[ch][j] = s;
+    }
+    __syncwarp();
+    // ---- through the SFH, burst and MDF weights; then to unbounded space
+#pragma unroll 1
+    for (int ch = 0; ch < CPW; ++ch) {
+        float gr[SPS_NPARAM];
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) gr[k] = 0.0f;
+        gr[0] = t.gd[ch][0];
+        gr[9] = t.gd[ch][1];
+        gr[10] = t.gd[ch][2];
+        gr[11] = t.gd[ch][3];
+        age_met_adjoint(c, age_view(t, ch), lT10, t.M[ch], t.th[ch], gr);
+        if (lane < SPS_NPARAM) {
+            float v = gr[0];
+#pragma unroll
+            for (int k = 1; k < SPS_NPARAM; ++k)
+                if (lane == k) v = gr[k];
+            const float sg = 1.0f / (1.0f + __expf(-t.x[ch][lane]));
+            t.g[ch][lane] = v * t.dth[ch][lane] + (1.0f - 2.0f * sg);
+        }
+        if (lane == 0) t.lp[ch] = t.ll[ch] + t.lpri[ch];
+    }
+    __syncwarp();
+}
+
+// Draws of iteration `it` for one chain (FP64 Box-Muller): z[12] and, in
+// lane 0's view, the accept uniform and L (all lanes get them).
+__device__ __forceinline__ void team_draws(uint64_t seed, uint32_t chain, uint32_t it, int L_min,
+                                           int L_max, float* z, double& u_acc, int& L) {
+    const int lane = lane_id();
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (lane < 4)
+        w = philox4x32_10(make_uint4(it, (uint32_t)lane, chain, 0u), (uint32_t)(seed & 0xffffffffu),
+                          (uint32_t)(seed >> 32));
+    const int m = lane % 6;
+    const int ia = 2 * m, ib = 2 * m + 1;
+    const uint32_t ax = __shfl_sync(kFull, w.x, ia >> 2), ay = __shfl_sync(kFull, w.y, ia >> 2);
+    const uint32_t az = __shfl_sync(kFull, w.z, ia >> 2), aw = __shfl_sync(kFull, w.w, ia >> 2);
+    const uint32_t bx = __shfl_sync(kFull, w.x, ib >> 2), by = __shfl_sync(kFull, w.y, ib >> 2);
+    const uint32_t bz = __shfl_sync(kFull, w.z, ib >> 2), bw = __shfl_sync(kFull, w.w, ib >> 2);
+    const int sa = ia & 3, sb = ib & 3;
+    const uint32_t wa = sa == 0 ? ax : sa == 1 ? ay : sa == 2 ? az : aw;
+    const uint32_t wb = sb == 0 ? bx : sb == 1 ? by : sb == 2 ? bz : bw;
+    const double r = sqrt(-2.0 * log(u01_d(wa)));
+    double sn, cs;
+    sincospi(2.0 * u01_d(wb), &sn, &cs);
+    const double z0 = r * cs, z1 = r * sn;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        z[2 * k] = (float)__shfl_sync(kFull, z0, k);
+        z[2 * k + 1] = (float)__shfl_sync(kFull, z1, k);
+    }
+    const uint32_t w30 = __shfl_sync(kFull, w.x, 3), w31 = __shfl_sync(kFull, w.y, 3);
+    u_acc = u01_d(w30);
+    L = L_min + (int)(((uint64_t)w31 * (uint64_t)(L_max - L_min + 1)) >> 32);
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// v = Minv p for chain ch (diagonal minv, or dense L L^T).
+template <int CPW>
+__device__ __forceinline__ void metric_apply(TeamWork<CPW>& t, int ch, bool dense) {
+    const int lane = lane_id();
+    if (!dense) {
+        if (lane < SPS_NPARAM) t.v[ch][lane] = t.minv[ch][lane] * t.p[ch][lane];
+        __syncwarp();
+        return;
+    }
+    if (lane < SPS_NPARAM) {
+        float a = 0.0f;
+        for (int k = lane; k < SPS_NPARAM; ++k) a = fmaf(t.chol[ch][tri(k, lane)], t.p[ch][k], a);
+        t.lu[ch][lane] = a;                                      // (L^T p)_j
+    }
+    __syncwarp();
+    if (lane < SPS_NPARAM) {
+        float a = 0.0f;
+        for (int j = 0; j <= lane; ++j) a = fmaf(t.chol[ch][tri(lane, j)], t.lu[ch][j], a);
+        t.v[ch][lane] = a;                                       // (L L^T p)_k
+    }
+    __syncwarp();
+}
+
+// p^T Minv p / 2 (needs metric_apply first).
+template <int CPW>
+__device__ __forceinline__ double kinetic(TeamWork<CPW>& t, int ch) {
+    const int lane = lane_id();
+    double v = 0.0;
+    if (lane < SPS_NPARAM) v = (double)t.p[ch][lane] * (double)t.v[ch][lane];
+    return 0.5 * warp_sum_d(v);
+}
+
+// Start a trajectory for chain ch: draws, momentum, record the start state,
+// first half kick and drift.
+template <int CPW>
+__device__ __noinline__ void start_traj(TeamWork<CPW>& t, int ch, const HmcParams& hp) {
+    const int lane = lane_id();
+    float z[SPS_NPARAM];
+    double u;
+    int L;
+    team_draws(hp.seed, t.chain[ch], (uint32_t)t.it[ch], hp.L_min, hp.L_max, z, u, L);
+    const bool dense = hp.adapt_mass == 2;
+    if (lane < SPS_NPARAM) {
+        float zz = z[0];
+#pragma unroll
+        for (int k = 1; k < SPS_NPARAM; ++k)
+            if (lane == k) zz = z[k];
+        t.p[ch][lane] = dense ? zz : zz * rsqrtf(t.minv[ch][lane]);
+        t.xs[ch][lane] = t.x[ch][lane];
+        t.gs[ch][lane] = t.g[ch][lane];
+    }
+    __syncwarp();
+    if (dense && lane == 0) {                 // p = L^-T z by back substitution
+        for (int i = SPS_NPARAM - 1; i >= 0; --i) {
+            float a = t.p[ch][i];
+            for (int k = i + 1; k < SPS_NPARAM; ++k) a -= t.chol[ch][tri(k, i)] * t.p[ch][k];
+            t.p[ch][i] = a / t.chol[ch][tri(i, i)];
+        }
+    }
+    __syncwarp();
+    metric_apply(t, ch, dense);
+    const double h0 = -t.lp[ch] + kinetic(t, ch);
+    if (lane == 0) {
+        t.uacc[ch] = u;
+        t.L[ch] = L;
+        t.l[ch] = 0;
+        t.lps[ch] = t.lp[ch];
+        t.h0[ch] = h0;
+    }
+    if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+    __syncwarp();
+    metric_apply(t, ch, dense);
+    if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void win_set_end(int& start, int& end, int width, int stop) {
+    end = start + width;
+    if (end + 2 * width > stop) end = stop;
+    if (width <= 0 || start >= stop) start = end = 0x7fffffff;
+}
+
+// End of chain ch's trajectory: accept / reject, adaptation, sample.
+template <int CPW>
+__device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                      float* __restrict__ samples) {
+    const int lane = lane_id();
+    const bool dense = hp.adapt_mass == 2;
+    metric_apply(t, ch, dense);
+    const double dH = (-t.lp[ch] + kinetic(t, ch)) - t.h0[ch];
+    const bool fin = isfinite(dH);
+    const double a = fin ? fmin(1.0, exp(-dH)) : 0.0;
+    const bool take = fin && log(t.uacc[ch]) < -dH;
+    if (!take && lane < SPS_NPARAM) {
+        t.x[ch][lane] = t.xs[ch][lane];
+        t.g[ch][lane] = t.gs[ch][lane];
+    }
+    __syncwarp();
+    const int it = t.it[ch];
+    if (lane == 0) {
+        if (!take) t.lp[ch] = t.lps[ch];
+        if (!fin || dH > 1000.0) t.ndiv[ch] += 1;
+        t.nev[ch] += t.L[ch];
+    }
+    if (it < hp.n_warm) {
+        const double m = (double)(t.mda[ch] + 1);
+        const double hbar = (1.0 - 1.0 / (m + 10.0)) * t.hbar[ch] + ((double)hp.target_accept - a) / (m + 10.0);
+        const double log_eps = t.mu[ch] - sqrt(m) / 0.05 * hbar;
+        const double wgt = pow(m, -0.75);
+        const double leb = wgt * log_eps + (1.0 - wgt) * t.leb[ch];
+        const float eps = (float)exp(it < hp.n_warm - 1 ? log_eps : leb);
+        __syncwarp();
+        if (lane == 0) {
+            t.mda[ch] += 1;
+            t.hbar[ch] = hbar;
+            t.leb[ch] = leb;
+            t.eps[ch] = eps;
+        }
+        __syncwarp();
+        if (it >= t.wstart[ch] && it < t.wend[ch]) {
+            const int wn = t.wn[ch] + 1;
+            if (lane < SPS_NPARAM) {
+                const double xv = (double)t.x[ch][lane];
+                const double d = xv - t.wmean[ch][lane];
+                const double mean = t.wmean[ch][lane] + d / (double)wn;
+                t.wmean[ch][lane] = mean;
+                t.wm2[ch][lane] += d * (xv - mean);
+                t.dv[ch][0][lane] = (float)d;
+                t.dv[ch][1][lane] = (float)(xv - mean);
+            }
+            __syncwarp();
+            if (dense) {
+                for (int e = lane; e < 78; e += 32) {
+                    int i = 0;
+                    while (tri(i + 1, 0) <= e) ++i;
+                    const int j = e - tri(i, 0);
+                    t.wcov[ch][e] += t.dv[ch][0][i] * t.dv[ch][1][j];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) t.wn[ch] = wn;
+            if (it == t.wend[ch] - 1) {
+                if (wn >= 2 && !dense && lane < SPS_NPARAM) {
+                    const double var = t.wm2[ch][lane] / ((double)wn - 1.0);
+                    t.minv[ch][lane] = (float)(((double)wn / (wn + 5.0)) * var + 1e-3 * (5.0 / (wn + 5.0)));
+                }
+                if (wn >= 2 && dense && lane == 0) {
+                    // regularised covariance, then its Cholesky factor in place
+                    const float a = (float)wn / (wn + 5.0f), b = 1e-3f * (5.0f / (wn + 5.0f));
+                    float Lm[78];
+                    for (int e = 0; e < 78; ++e) Lm[e] = a * t.wcov[ch][e] / ((float)wn - 1.0f);
+                    for (int i = 0; i < SPS_NPARAM; ++i) Lm[tri(i, i)] += b;
+                    bool ok = true;
+                    for (int j = 0; j < SPS_NPARAM && ok; ++j) {
+                        float dgl = Lm[tri(j, j)];
+                        for (int k = 0; k < j; ++k) dgl -= Lm[tri(j, k)] * Lm[tri(j, k)];
+                        if (!(dgl > 0.0f)) {
+                            ok = false;
+                            break;
+                        }
+                        const float ljj = sqrtf(dgl);
+                        Lm[tri(j, j)] = ljj;
+                        for (int i = j + 1; i < SPS_NPARAM; ++i) {
+                            float sv = Lm[tri(i, j)];
+                            for (int k = 0; k < j; ++k) sv -= Lm[tri(i, k)] * Lm[tri(j, k)];
+                            Lm[tri(i, j)] = sv / ljj;
+                        }
+                    }
+                    if (ok)
+                        for (int e = 0; e < 78; ++e) t.chol[ch][e] = Lm[e];
+                }
+                if (lane < SPS_NPARAM) {
+                    t.wmean[ch][lane] = 0.0;
+                    t.wm2[ch][lane] = 0.0;
+                }
+                for (int e = lane; e < 78; e += 32) t.wcov[ch][e] = 0.0f;
+                __syncwarp();
+                if (lane == 0) {
+                    t.wn[ch] = 0;
+                    t.mu[ch] = log(10.0 * (double)t.eps[ch]);
+                    t.hbar[ch] = 0.0;
+                    t.leb[ch] = 0.0;
+                    t.mda[ch] = 0;
+                    int s = t.wend[ch], e = 0, wdt = 2 * t.wwidth[ch];
+                    win_set_end(s, e, wdt, t.wstop[ch]);
+                    t.wstart[ch] = s;
+                    t.wend[ch] = e;
+                    t.wwidth[ch] = wdt;
+                }
+            }
+        }
+    } else {
+        if (lane == 0) t.acc[ch] += a;
+        if (samples && lane < SPS_NPARAM)
+            samples[((size_t)t.chain[ch] * hp.n_samp + (it - hp.n_warm)) * SPS_NPARAM + lane] =
+                c.prior_lo[lane] + c.prior_span[lane] / (1.0f + __expf(-t.x[ch][lane]));
+    }
+    __syncwarp();
+    if (lane == 0) t.it[ch] = it + 1;
+    __syncwarp();
+}
+
+template <int CPW>
+__global__ void __launch_bounds__(128)
+k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
+           const float* __restrict__ theta0, const float* __restrict__ mag_obs,
+           const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
+           const int32_t* __restrict__ gal_order, float* __restrict__ samples, float* acc_out,
+           float* eps_out, int32_t* div_out, int64_t* nev_out, int32_t* status_out, int* queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TeamWork<CPW>& t = reinterpret_cast<TeamWork<CPW>*>(smem)[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int B = c.n_band, K = c.K;
+    const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
+    const int C = hp.chains_per_gal;
+    const int groups = (C + CPW - 1) / CPW;
+    const int n_it = hp.n_warm + hp.n_samp;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(queue, 1);
+        q = __shfl_sync(kFull, q, 0);
+        if ((int64_t)q >= g.n * groups) break;
+        const int64_t gi = gal_order ? (int64_t)gal_order[q / groups] : (int64_t)(q / groups);
+        const int c0 = (q % groups) * CPW;
+        const int nch = min(CPW, C - c0);
+        const uint32_t bits = mask[gi] & all;
+        const int nb = __popc(bits);
+        if (lane < B && ((bits >> lane) & 1u)) {
+            const int slot = __popc(bits & ((1u << lane) - 1u));
+            const size_t gb = (size_t)gi * B + lane;
+            t.ptr[slot] = g.cssp + gb * K;
+            t.dust[slot] = g.dust_eff[gb];
+            t.zp[slot] = g.zp[gb];
+            t.mobs[slot] = mag_obs[gb];
+            const float sg = sigma[gb];
+            t.isig2[slot] = 1.0f / (sg * sg);
+        }
+        // chain state; unused chain slots mirror the first chain and never write
+        for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
+            const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
+            const int cc = (ch < nch) ? ch : 0;
+            t.x[ch][k] = theta0[((size_t)gi * C + c0 + cc) * SPS_NPARAM + k];
+            t.minv[ch][k] = 1.0f;
+            t.wmean[ch][k] = 0.0;
+            t.wm2[ch][k] = 0.0;
+        }
+        for (int e = lane; e < CPW * 78; e += 32) {
+            const int ch = e / 78, r = e - ch * 78;
+            int i = 0;
+            while (tri(i + 1, 0) <= r) ++i;
+            t.chol[ch][r] = (r == tri(i, i)) ? 1.0f : 0.0f;
+            t.wcov[ch][r] = 0.0f;
+        }
+        if (lane < CPW) {
+            const int ch = lane;
+            t.chain[ch] = (uint32_t)(gi * C + c0 + ((ch < nch) ? ch : 0));
+            t.eps[ch] = hp.eps0;
+            t.mu[ch] = log(10.0 * (double)hp.eps0);
+            t.hbar[ch] = t.leb[ch] = t.acc[ch] = 0.0;
+            t.it[ch] = 0;
+            t.mda[ch] = t.wn[ch] = t.ndiv[ch] = 0;
+            t.nev[ch] = 1;
+            t.done[ch] = (ch < nch) ? (n_it <= 0) : 1;
+            int init_b, term_b, width;
+            const int nw = hp.adapt_mass ? hp.n_warm : 0;
+            if (nw >= 150) {
+                init_b = 75;
+                term_b = 50;
+                width = 25;
+            } else {
+                init_b = (int)(0.15 * nw);
+                term_b = (int)(0.1 * nw);
+                width = nw - init_b - term_b;
+            }
+            int s = init_b, e = 0;
+            win_set_end(s, e, width, nw - term_b);
+            t.wstart[ch] = s;
+            t.wend[ch] = e;
+            t.wwidth[ch] = width;
+            t.wstop[ch] = nw - term_b;
+        }
+        __syncwarp();
+        const float2* bins = g.bins + (size_t)gi * c.n_age;
+        const float lnT = g.lnT[gi], lT10 = g.lT10[gi];
+        team_eval<CPW>(c, t, bins, lnT, lT10, nb);
+#pragma unroll 1
+        for (int ch = 0; ch < CPW; ++ch)
+            if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
+        for (;;) {
+            bool any = false;
+            for (int ch = 0; ch < CPW; ++ch) any = any || !t.done[ch];
+            if (!any) break;
+            team_eval<CPW>(c, t, bins, lnT, lT10, nb);
+#pragma unroll 1
+            for (int ch = 0; ch < CPW; ++ch) {
+                if (t.done[ch]) continue;
+                if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+                __syncwarp();
+                const int l = t.l[ch] + 1;
+                if (l == t.L[ch]) {
+                    end_traj<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
+                    if (t.it[ch] >= n_it) {
+                        if (lane == 0) t.done[ch] = 1;
+                        __syncwarp();
+                    } else {
+                        start_traj<CPW>(t, ch, hp);
+                    }
+                } else {
+                    if (lane < SPS_NPARAM)
+                        t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+                    __syncwarp();
+                    metric_apply(t, ch, hp.adapt_mass == 2);
+                    if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
+                    __syncwarp();
+                    if (lane == 0) t.l[ch] = l;
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane < nch) {
+            const uint32_t chn = t.chain[lane];
+            if (acc_out) acc_out[chn] = (float)(t.acc[lane] / (double)max(hp.n_samp, 1));
+            if (eps_out) eps_out[chn] = t.eps[lane];
+            if (div_out) div_out[chn] = t.ndiv[lane];
+            if (nev_out) nev_out[chn] = t.nev[lane];
+            if (status_out) status_out[chn] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t hmc_team_smem_per_warp(int cpw) {
+    return cpw >= 4 ? sizeof(TeamWork<4>) : cpw == 2 ? sizeof(TeamWork<2>) : sizeof(TeamWork<1>);
+}
+
+template <int CPW>
+static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcParams& hp,
+                               const float* theta0, const float* mag_obs, const float* sigma,
+                               const uint32_t* mask, const int32_t* gal_order, float* samples,
+                               float* acc, float* eps_out, int32_t* div, int64_t* nevals,
+                               int32_t* status, int* queue, int blocks, int warps, cudaStream_t s) {
+    const size_t smem = sizeof(TeamWork<CPW>) * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_hmc_team<CPW><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask,
+                                                     gal_order, samples, acc, eps_out, div,
+                                                     nevals, status, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm) {
+    const size_t smem = hmc_team_smem_per_warp(cpw) * warps;
+    cudaError_t e;
+    if (cpw >= 4) {
+        e = cudaFuncSetAttribute(k_hmc_team<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<4>, warps * 32, smem);
+    } else if (cpw == 2) {
+        e = cudaFuncSetAttribute(k_hmc_team<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<2>, warps * 32, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_hmc_team<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<1>, warps * 32, smem);
+    }
+    return e;
+}
+
+cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const HmcParams& hp,
+                            const float* theta0, const float* mag_obs, const float* sigma,
+                            const uint32_t* mask, const int32_t* gal_order, float* samples,
+                            float* acc, float* eps_out, int32_t* div, int64_t* nevals,
+                            int32_t* status, int* queue, int blocks, int warps, cudaStream_t s) {
+    if (cpw >= 4)
+        return team_launch<4>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                              eps_out, div, nevals, status, queue, blocks, warps, s);
+    if (cpw == 2)
+        return team_launch<2>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                              eps_out, div, nevals, status, queue, blocks, warps, s);
+    return team_launch<1>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                          div, nevals, status, queue, blocks, warps, s);
+}
+
+}  // namespace sps

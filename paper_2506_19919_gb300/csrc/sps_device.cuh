@@ -88,6 +88,29 @@ __device__ __forceinline__ DustTerms dust_eval(float k0, float lnr, float drude,
 }
 
 // ---------------------------------------------------------------- per-warp scratch
+// Panel bookkeeping of the SFH quadrature of one row.
+struct PanelScratch {
+    float px0[kMaxAges];        // first panel centre (ln t)
+    float php[kMaxAges];        // panel half-width
+    unsigned short pn[kMaxAges];
+    unsigned short pstart[kMaxAges + 1];
+    unsigned char pmap[kMaxPanels];
+};
+
+// Where the age / metallicity stage of one row keeps its arrays.
+struct AgeView {
+    float* m;          // [A] bin integrals
+    float* dm0;        // [A] d m / d tau
+    float* dm1;        // [A] d m / d alpha
+    float* dm2;        // [A] d m / d beta
+    float* pi;         // [A] burst weights
+    float* w;          // [A] age weights
+    float* wb;         // [A] adjoint of w
+    float* q;          // [Zn] metallicity weights
+    float* qb;         // [Zn] adjoint of q
+    PanelScratch* ps;
+};
+
 struct RowScratch {
     float m[kMaxAges];          // bin integrals tau * int hh du [Gyr]
     float dm[3][kMaxAges];      // d m / d(tau, alpha, beta)
@@ -95,13 +118,7 @@ struct RowScratch {
     float w[kMaxAges];          // age weights w_i
     float wb[kMaxAges];         // adjoint of w_i
     union {
-        struct {
-            float px0[kMaxAges];        // first panel centre (ln t)
-            float php[kMaxAges];        // panel half-width
-            unsigned short pn[kMaxAges];
-            unsigned short pstart[kMaxAges + 1];
-            unsigned char pmap[kMaxPanels];
-        } s;
+        PanelScratch s;
         float kbuf[kKTileMax * 32];     // v_ij during the adjoint
     } u;
     float q[kMaxMets];
@@ -110,6 +127,9 @@ struct RowScratch {
     float slot_S[kMaxBands];
     float slot_F[kMaxBands];
     float slot_g[kMaxBands];    // gamma_b
+    __device__ AgeView view() {
+        return AgeView{m, dm[0], dm[1], dm[2], pi, w, wb, q, qb, &u.s};
+    }
 };
 
 // ---------------------------------------------------------------- SFH bins
@@ -121,8 +141,9 @@ __device__ __forceinline__ int panel_count(float w, float panel) {
 }
 
 // Fills s.m and (if grad) s.dm; returns M = sum_i m_i (FP64).
-__device__ inline double sfh_bins(const Consts& c, RowScratch& s, const float2* __restrict__ bins,
+__device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
                            float lnT, float tau, float alpha, float beta, bool grad) {
+    PanelScratch& ps = *v.ps;
     const int lane = lane_id();
     const int A = c.n_age;
     const float lntau = __logf(tau);
@@ -155,46 +176,46 @@ __device__ inline double sfh_bins(const Consts& c, RowScratch& s, const float2* 
                 }
             }
         }
-        s.u.s.pn[i] = (unsigned short)n;
-        s.u.s.px0[i] = x0;
-        s.u.s.php[i] = hp;
-        s.m[i] = 0.0f;
-        s.dm[0][i] = 0.0f;
-        s.dm[1][i] = 0.0f;
-        s.dm[2][i] = 0.0f;
+        ps.pn[i] = (unsigned short)n;
+        ps.px0[i] = x0;
+        ps.php[i] = hp;
+        v.m[i] = 0.0f;
+        v.dm0[i] = 0.0f;
+        v.dm1[i] = 0.0f;
+        v.dm2[i] = 0.0f;
     }
     __syncwarp();
     int carry = 0;
     for (int base = 0; base < A; base += 32) {
         int i = base + lane;
-        int n = (i < A) ? (int)s.u.s.pn[i] : 0;
+        int n = (i < A) ? (int)ps.pn[i] : 0;
         int incl = n;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
         }
-        if (i < A) s.u.s.pstart[i] = (unsigned short)min(carry + incl - n, kMaxPanels);
+        if (i < A) ps.pstart[i] = (unsigned short)min(carry + incl - n, kMaxPanels);
         carry += __shfl_sync(kFull, incl, 31);
     }
     const int P = min(carry, kMaxPanels);
     __syncwarp();
     for (int i = lane; i < A; i += 32) {
-        int p0 = s.u.s.pstart[i];
-        int p1 = min(p0 + (int)s.u.s.pn[i], kMaxPanels);
-        for (int p = p0; p < p1; ++p) s.u.s.pmap[p] = (unsigned char)i;
+        int p0 = ps.pstart[i];
+        int p1 = min(p0 + (int)ps.pn[i], kMaxPanels);
+        for (int p = p0; p < p1; ++p) ps.pmap[p] = (unsigned char)i;
     }
     __syncwarp();
     const float am1 = alpha - 1.0f, bp1 = beta + 1.0f;
     for (int base = 0; base < P; base += 32) {
         const int p = base + lane;
         const bool act = p < P;
-        int bin = act ? (int)s.u.s.pmap[p] : -1;
+        int bin = act ? (int)ps.pmap[p] : -1;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
         if (act) {
-            const int k = p - (int)s.u.s.pstart[bin];
-            const float hp = s.u.s.php[bin];
-            const float xc = s.u.s.px0[bin] + 2.0f * (float)k * hp - lntau;
+            const int k = p - (int)ps.pstart[bin];
+            const float hp = ps.php[bin];
+            const float xc = ps.px0[bin] + 2.0f * (float)k * hp - lntau;
             for (int gq = 0; gq < c.gl_order; ++gq) {
                 float uu = fmaf(hp, c.gl_x[gq], xc);
                 float P_ = __expf(am1 * uu);
@@ -224,22 +245,22 @@ __device__ inline double sfh_bins(const Consts& c, RowScratch& s, const float2* 
         }
         int bnext = __shfl_down_sync(kFull, bin, 1);
         if (act && (lane == 31 || bnext != bin)) {
-            s.m[bin] += v0 * tau;
+            v.m[bin] += v0 * tau;
             if (grad) {
-                s.dm[0][bin] += v1;
-                s.dm[1][bin] += v2 * tau;
-                s.dm[2][bin] += v3 * tau;
+                v.dm0[bin] += v1;
+                v.dm1[bin] += v2 * tau;
+                v.dm2[bin] += v3 * tau;
             }
         }
         __syncwarp();
     }
     double acc = 0.0;
-    for (int i = lane; i < A; i += 32) acc += (double)s.m[i];
+    for (int i = lane; i < A; i += 32) acc += (double)v.m[i];
     return warp_sum_d(acc);
 }
 
 // ---------------------------------------------------------------- burst + MDF
-__device__ __forceinline__ float burst_weights(const Consts& c, RowScratch& s, float lT10,
+__device__ __forceinline__ float burst_weights(const Consts& c, const AgeView& v, float lT10,
                                                float mu, float sig) {
     const float xT = (lT10 - mu) / sig;
     const float D = tri_cdf(xT);
@@ -247,17 +268,17 @@ __device__ __forceinline__ float burst_weights(const Consts& c, RowScratch& s, f
     for (int i = lane_id(); i < c.n_age; i += 32) {
         float lo = fminf(c.log_age_edge[i], lT10);
         float hi = fminf(c.log_age_edge[i + 1], lT10);
-        s.pi[i] = (tri_cdf((hi - mu) / sig) - tri_cdf((lo - mu) / sig)) * invD;
+        v.pi[i] = (tri_cdf((hi - mu) / sig) - tri_cdf((lo - mu) / sig)) * invD;
     }
     return D;
 }
 
-__device__ __forceinline__ void met_weights(const Consts& c, RowScratch& s, float mu, float sd) {
+__device__ __forceinline__ void met_weights(const Consts& c, const AgeView& v, float mu, float sd) {
     int j = lane_id();
     if (j < c.n_met) {
         float ylo = (c.lgz_edge[j] - mu) / sd;
         float yhi = (c.lgz_edge[j + 1] - mu) / sd;
-        s.q[j] = (ylo > 0.0f) ? normcdff(-ylo) - normcdff(-yhi) : normcdff(yhi) - normcdff(ylo);
+        v.q[j] = (ylo > 0.0f) ? normcdff(-ylo) - normcdff(-yhi) : normcdff(yhi) - normcdff(ylo);
     }
 }
 
@@ -302,28 +323,33 @@ __device__ __forceinline__ void load_params(const Consts& c, const float* __rest
 }
 
 // ---------------------------------------------------------------- weights stage
-// Fills s.m/dm, s.pi, s.q, s.w; returns M (FP64).
+// Fills v.m/dm, v.pi, v.q, v.w for parameters th[12]; returns M (FP64).
+__device__ __forceinline__ double age_met_weights(const Consts& c, const AgeView& v,
+                                                  const float2* __restrict__ bins, float lnT,
+                                                  float lT10, const float* th, bool grad) {
+    double M = sfh_bins(c, v, bins, lnT, th[1], th[2], th[3], grad);
+    burst_weights(c, v, lT10, th[5], th[6] * (1.0f / 3.0f));
+    met_weights(c, v, th[7], th[8]);
+    __syncwarp();
+    const float fb = th[4];
+    const float Mf = (float)M;
+    for (int i = lane_id(); i < c.n_age; i += 32) v.w[i] = (1.0f - fb) * v.m[i] + fb * v.pi[i] * Mf;
+    __syncwarp();
+    return M;
+}
 __device__ __forceinline__ double age_met_weights(const Consts& c, RowScratch& s,
                                                   const float2* __restrict__ bins, float lnT,
                                                   float lT10, const RowParams& p, bool grad) {
-    double M = sfh_bins(c, s, bins, lnT, p.th[1], p.th[2], p.th[3], grad);
-    burst_weights(c, s, lT10, p.th[5], p.th[6] * (1.0f / 3.0f));
-    met_weights(c, s, p.th[7], p.th[8]);
-    __syncwarp();
-    const float fb = p.th[4];
-    const float Mf = (float)M;
-    for (int i = lane_id(); i < c.n_age; i += 32) s.w[i] = (1.0f - fb) * s.m[i] + fb * s.pi[i] * Mf;
-    __syncwarp();
-    return M;
+    return age_met_weights(c, s.view(), bins, lnT, lT10, p.th, grad);
 }
 
 // Adjoint of age_met_weights: given s.wb (dlogL/dw_i) and s.qb (dlogL/dq_j)
 // returns d/dtheta for columns 1-8 added into g[].
-__device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT10, double M,
-                                const RowParams& p, float* g) {
+__device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& s, float lT10, double M,
+                                             const float* th, float* g) {
     const int lane = lane_id();
     const int A = c.n_age;
-    const float fb = p.th[4];
+    const float fb = th[4];
     const float Mf = (float)M;
     // sum_i wbar_i pi_i  and  F_burst-bar
     float a_wp = 0.f, a_fb = 0.f;
@@ -338,16 +364,16 @@ __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT1
     float gt = 0.f, ga = 0.f, gbt = 0.f;
     for (int i = lane; i < A; i += 32) {
         float mb = (1.0f - fb) * s.wb[i] + fb * a_wp;
-        gt += mb * s.dm[0][i];
-        ga += mb * s.dm[1][i];
-        gbt += mb * s.dm[2][i];
+        gt += mb * s.dm0[i];
+        ga += mb * s.dm1[i];
+        gbt += mb * s.dm2[i];
     }
     g[1] += warp_sum(gt);
     g[2] += warp_sum(ga);
     g[3] += warp_sum(gbt);
     g[4] += a_fb;
     // burst: pi_i = raw_i / D, pibar_i = fb M wbar_i
-    const float mu = p.th[5], sig = p.th[6] * (1.0f / 3.0f);
+    const float mu = th[5], sig = th[6] * (1.0f / 3.0f);
     const float xT = (lT10 - mu) / sig;
     const float D = tri_cdf(xT);
     float s_mu = 0.f, s_sg = 0.f, s_pp = 0.f;
@@ -371,7 +397,7 @@ __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT1
     g[5] += gmu;
     g[6] += gsg * (1.0f / 3.0f);
     // metallicity: q_j = Phi(yh) - Phi(yl)
-    const float mz = p.th[7], sz = p.th[8];
+    const float mz = th[7], sz = th[8];
     float gz = 0.f, gs = 0.f;
     int j = lane;
     if (j < c.n_met) {
@@ -382,6 +408,10 @@ __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT1
     }
     g[7] += warp_sum(gz);
     g[8] += warp_sum(gs);
+}
+__device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT10, double M,
+                                       const RowParams& p, float* g) {
+    age_met_adjoint(c, s.view(), lT10, M, p.th, g);
 }
 
 }  // namespace sps

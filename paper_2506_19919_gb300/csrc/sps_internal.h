@@ -108,6 +108,13 @@ cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Co
 cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
                           const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s);
 
+// Plain per-galaxy forward-mode path (comparison baseline).
+size_t plain_scratch_bytes_per_row(const Consts& c);
+cudaError_t launch_plain(const Consts& c, const Galaxies& g, const float* theta,
+                         const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                         const float* sigma, const uint32_t* mask, float* ll_out, float* grad_out,
+                         float* T, float* cd, cudaStream_t s);
+
 cudaError_t launch_weights_rows(const Consts& c, const Galaxies& g, const float* theta,
                                 const int32_t* gal_idx, int64_t n, float* W_out,
                                 double* mstar_out, cudaStream_t s);
@@ -122,13 +129,13 @@ struct HmcParams {
     uint64_t seed;
     int adapt_mass;         // windowed diagonal metric adaptation during warm-up
 };
-struct HmcState;            // per-chain state, device
-cudaError_t launch_hmc_approx(const Consts& c, const Galaxies& g, const HmcParams& hp,
-                              const float* theta0, const float* mag_obs, const float* sigma,
-                              const uint32_t* mask, const int32_t* gal_order, float* samples,
-                              float* acc, float* eps_out, int32_t* div, int64_t* nevals,
-                              int32_t* status, int* queue, int* err, int grid_blocks,
-                              int warps_per_block, size_t smem_cssp_bytes, cudaStream_t s);
+size_t hmc_team_smem_per_warp(int cpw);
+cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm);
+cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const HmcParams& hp,
+                            const float* theta0, const float* mag_obs, const float* sigma,
+                            const uint32_t* mask, const int32_t* gal_order, float* samples,
+                            float* acc, float* eps_out, int32_t* div, int64_t* nevals,
+                            int32_t* status, int* queue, int blocks, int warps, cudaStream_t s);
 cudaError_t launch_leapfrog(const Consts& c, const Galaxies& g, const float* x0,
                             const float* p0, const float* eps, const int32_t* L,
                             const int32_t* gal_idx, int64_t n, const float* mag_obs,

@@ -90,6 +90,19 @@ def test_loglike_grad_production_grid(prod96, mode):
 NEAR_TRUTH_GRAD_TOL = 2e-3
 
 
+def test_forward_mode_baseline_matches_oracle(prod96):
+    """The plain forward-mode comparison path computes the same log L and
+    gradient (same FP32 tolerance)."""
+    wl, ctx = prod96
+    th_true = torch.as_tensor(wl.theta_true, dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z, wl.tables, "approx").numpy() + wl.noise
+    ev = W.prior_draw(np.random.default_rng(17), wl.n_gal)
+    ll, g = ctx.loglike_grad_forward_mode(ev, mobs, wl.sigma, wl.mask)
+    llr, gr, _ = O.loglike_and_grad(ev, wl.z, wl.tables, mobs, wl.sigma, wl.mask, "approx")
+    np.testing.assert_allclose(ll.cpu().numpy(), llr.numpy(), rtol=2e-4)
+    assert _grad_rel(g.cpu().numpy(), gr.numpy()) < GRAD_TOL
+
+
 @pytest.mark.parametrize("mode", ["approx", "exact"])
 def test_loglike_grad_near_truth(prod96, mode):
     """Near the data the residuals are ~ sigma, the gradient is a sum of
@@ -208,20 +221,53 @@ def test_hmc_prior_only_matches_oracle_draws(parity64):
     assert (out["grad_evals"].cpu().numpy() == ref["grad_evals"] + 1).all()
 
 
+def test_hmc_with_likelihood_matches_oracle_draws(prod96):
+    """The batched sampler with the photometric likelihood on (4 chains per
+    galaxy evaluated in lock step): at a fixed step size its draws follow the
+    oracle's HMC draw by draw."""
+    wl, ctx = prod96
+    G, C = 3, 4
+    th_true = torch.as_tensor(wl.theta_true[:G], dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z[:G], wl.tables, "approx").numpy() + wl.noise[:G]
+    mobs_all = np.full((wl.n_gal, 6), 30.0)
+    mobs_all[:G] = mobs
+    mask = np.zeros(wl.n_gal, np.uint32)
+    mask[:G] = wl.mask[:G]
+    x0 = np.repeat(W.unbounded_of(wl.theta_true[:G]), C, axis=0)
+    x0 = (x0 + np.random.default_rng(5).normal(0, 0.02, x0.shape)).astype(np.float32)
+    x0_all = np.zeros((wl.n_gal * C, 12), np.float32)
+    x0_all[:G * C] = x0
+    out = ctx.hmc_run(x0_all, mobs_all, wl.sigma, mask, chains_per_gal=C, n_warm=0, n_samp=6,
+                      L_min=6, L_max=6, seed=11, eps0=2e-3, autotune=False)
+    s = out["samples"].cpu().numpy()[:G * C]
+    tgt = OH.ApproxTarget(wl.tables, wl.z[:G], mobs, wl.sigma[:G], wl.mask[:G], W.PRIOR_LO,
+                          W.PRIOR_HI)
+    ref = OH.run_hmc(tgt, x0.astype(np.float64), np.repeat(np.arange(G), C), seed=11, n_warm=0,
+                     n_samp=6, L_min=6, L_max=6, eps0=2e-3)
+    span = W.PRIOR_HI - W.PRIOR_LO
+    d = np.abs((s - ref["samples"]) / span).max(axis=(1, 2))
+    assert (d < 2e-5).mean() >= 11 / 12
+    np.testing.assert_allclose(out["accept_prob"].cpu().numpy()[:G * C], ref["accept_prob"], atol=1e-2)
+
+
 def test_hmc_adaptation_matches_oracle_statistically(parity64):
-    """Warm-up adaptation (dual averaging + windowed diagonal metric) on the
-    prior-only target: adapted step sizes and sampling acceptance agree with
-    the oracle's in distribution."""
+    """Warm-up adaptation (dual averaging with the identity, windowed diagonal
+    or windowed dense metric) on the prior-only target: adapted step sizes and
+    sampling acceptance agree with the oracle's in distribution."""
     wl, ctx = parity64
     C = 2
     x0 = np.random.default_rng(2).normal(0, 1.5, size=(64 * C, 12)).astype(np.float32)
-    out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32),
-                      chains_per_gal=C, n_warm=200, n_samp=50, L_min=4, L_max=12, seed=7)
-    ref = OH.run_hmc(_Prior(), x0.astype(np.float64), np.zeros(64 * C, int), seed=7, n_warm=200,
-                     n_samp=50, L_min=4, L_max=12)
-    eg, er = out["step_size"].cpu().numpy(), ref["eps"]
-    assert np.median(eg) == pytest.approx(np.median(er), rel=0.15)
-    assert out["accept_prob"].cpu().numpy().mean() == pytest.approx(ref["accept_prob"].mean(), abs=0.05)
+    for gpu_mode, ref_kw in ((1, dict(adapt_mass=True)), (2, dict(adapt_mass=True, metric="dense")),
+                             (0, dict(adapt_mass=False))):
+        out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32),
+                          chains_per_gal=C, n_warm=200, n_samp=50, L_min=4, L_max=12, seed=7,
+                          adapt_mass=gpu_mode)
+        ref = OH.run_hmc(_Prior(), x0.astype(np.float64), np.zeros(64 * C, int), seed=7,
+                         n_warm=200, n_samp=50, L_min=4, L_max=12, **ref_kw)
+        eg, er = out["step_size"].cpu().numpy(), ref["eps"]
+        assert np.median(eg) == pytest.approx(np.median(er), rel=0.15), gpu_mode
+        assert out["accept_prob"].cpu().numpy().mean() == pytest.approx(ref["accept_prob"].mean(),
+                                                                         abs=0.05), gpu_mode
 
 
 def test_hmc_prior_only_is_uniform(parity64):

@@ -66,7 +66,7 @@ def test_hmc_samples_the_prior_when_no_band_is_observed():
     C = 64
     x0 = np.random.default_rng(0).normal(0, 2, size=(C, 12))
     out = H.run_hmc(_Uniform(), x0, np.zeros(C, int), seed=7, n_warm=150, n_samp=150,
-                    L_min=4, L_max=12)
+                    L_min=4, L_max=12, adapt_mass=True)
     s = out["samples"].reshape(-1, 12)
     for k in range(12):
         assert stats.kstest(s[::7, k], "uniform").pvalue > 1e-4
@@ -148,9 +148,37 @@ def test_metric_adaptation_learns_the_scales():
     C = 16
     x0 = np.random.default_rng(2).normal(size=(C, 12)) * _Gauss.scale
     out = H.run_hmc(_Gauss(), x0, np.zeros(C, int), seed=3, n_warm=300, n_samp=10, L_min=4,
-                    L_max=12)
+                    L_max=12, adapt_mass=True)
     ratio = out["minv"] / _Gauss.scale ** 2
     assert np.median(ratio) == pytest.approx(1.0, rel=0.25)
     assert (ratio > 0.3).all() and (ratio < 3.0).all()
     # the adapted step size is set by the metric, not by the narrowest scale
     assert np.median(out["eps"]) > 0.2
+
+
+class _CorrGauss:
+    """A strongly correlated Gaussian (correlation 0.99 between pairs)."""
+    lo = torch.full((12,), -1e9, dtype=torch.float64)
+    hi = torch.full((12,), 1e9, dtype=torch.float64)
+    cov = np.eye(12)
+    for i in range(0, 12, 2):
+        cov[i:i + 2, i:i + 2] = [[1.0, 0.99], [0.99, 1.0]]
+    prec = np.linalg.inv(cov)
+
+    def __call__(self, x, rows):
+        x = np.asarray(x)
+        return -0.5 * np.einsum("ci,ij,cj->c", x, self.prec, x), -x @ self.prec
+
+
+def test_dense_metric_learns_the_covariance():
+    C = 16
+    x0 = np.random.default_rng(4).normal(size=(C, 12))
+    out = H.run_hmc(_CorrGauss(), x0, np.zeros(C, int), seed=5, n_warm=300, n_samp=10, L_min=4,
+                    L_max=12, adapt_mass=True, metric="dense")
+    cov = np.einsum("cij,ckj->cik", out["chol"], out["chol"]).mean(0)
+    np.testing.assert_allclose(cov, _CorrGauss.cov, atol=0.25)
+    # the step size is no longer limited by the narrow direction (sd 0.1)
+    assert np.median(out["eps"]) > 0.4
+    diag = H.run_hmc(_CorrGauss(), x0, np.zeros(C, int), seed=5, n_warm=300, n_samp=10, L_min=4,
+                     L_max=12, adapt_mass=True, metric="diag")
+    assert np.median(out["eps"]) > 3 * np.median(diag["eps"])
