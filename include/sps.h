@@ -94,7 +94,11 @@ typedef struct {
 /* Context configuration.  sps_config_default() fills the declared defaults:
  * flat LambdaCDM with H0 = 70 km/s/Mpc, Omega_m = 0.3 (the paper states none),
  * the package's prior bounds, device 0, Gauss-Legendre order 6 and panel width
- * 0.25 in ln t for the SFH bin integrals. */
+ * 0.25 in ln t for the SFH bin integrals.  The SFH bin integrals use panels of
+ * sfh_panel * 10 / kappa in ln t, kappa = max(alpha + beta, beta + 1), clamped
+ * to [1, 8] x sfh_panel, with the sfh_gl_order rule on each; a bin that fits in
+ * one panel and is narrow against 1 / kappa takes a 2- or 3-node rule (never
+ * more nodes than sfh_gl_order). */
 typedef struct {
     double h0_kms_mpc;
     double omega_m;
@@ -102,7 +106,7 @@ typedef struct {
     double prior_hi[SPS_NPARAM];
     int32_t device;
     int32_t sfh_gl_order; /* 2..16 */
-    double sfh_panel;     /* max panel width in ln t, (0, 2] */
+    double sfh_panel;     /* panel width in ln t at kappa = 10, (0, 2] */
 } sps_config;
 
 sps_status sps_config_default(sps_config* cfg);

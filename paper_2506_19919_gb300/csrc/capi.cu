@@ -306,6 +306,19 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         c.gl_x[i] = (float)ctx->gl_x[i];
         c.gl_w[i] = (float)ctx->gl_w[i];
     }
+    {
+        double x2[2], w2[2], x3[3], w3[3];
+        gauss_legendre(2, x2, w2);
+        gauss_legendre(3, x3, w3);
+        for (int i = 0; i < 2; ++i) {
+            c.gl2_x[i] = (float)x2[i];
+            c.gl2_w[i] = (float)w2[i];
+        }
+        for (int i = 0; i < 3; ++i) {
+            c.gl3_x[i] = (float)x3[i];
+            c.gl3_w[i] = (float)w3[i];
+        }
+    }
     std::vector<double> edges(A + 1);
     edges[0] = 0.0;
     for (int i = 1; i < A; ++i) edges[i] = std::sqrt(t->age_yr[i - 1] * t->age_yr[i]);
@@ -786,6 +799,8 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, ctx->device));
     const int sms = prop.multiProcessorCount;
+    CK(ctx->hmcm.reserve(sizeof(ChainMetric) * (size_t)std::max<int64_t>(NC, 1)));
+    ChainMetric* cmet = ctx->hmcm.as<ChainMetric>();
     // launch shapes: chains of a galaxy per warp (cpw) x warps per block; the
     // grid is persistent (occupancy x SMs) and pulls (galaxy, chain group)
     // items from the queue
@@ -824,7 +839,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
             CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s));
             CK(cudaEventRecord(e0, s));
             CK(launch_hmc_team(cw.first, c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr,
-                               nullptr, nullptr, nullptr, ctx->queue.as<int>(), b, cw.second, s));
+                               nullptr, nullptr, nullptr, ctx->queue.as<int>(), cmet, b, cw.second, s));
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -848,7 +863,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
         return launch_hmc_team(cpw, c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
-                               ctx->queue.as<int>(), blocks, warps, s);
+                               ctx->queue.as<int>(), cmet, blocks, warps, s);
     };
     if (cfg->use_graph) {
         char kb[512];
@@ -857,7 +872,9 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
                       (void*)acc, (void*)epo, (void*)dv, (void*)nev, (void*)sto, (long long)G, C,
                       hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, hp.adapt_mass, (unsigned long long)hp.seed,
                       (double)hp.eps0, (double)hp.target_accept);
-        std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw);
+        char kc[64];
+        std::snprintf(kc, sizeof(kc), "%p", (void*)cmet);
+        std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw) + kc;
         if (!ctx->graph || gk != ctx->graph_key) {
             if (ctx->graph) {
                 cudaGraphExecDestroy(ctx->graph);

@@ -55,7 +55,7 @@ struct sps_ctx {
     DevBuf gz, glnT, glT10, gbins, gzp, gsup, ggauss, gcssp, gdust;
     // scratch
     DevBuf nonfinite, queue, err;
-    DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC;
+    DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -95,7 +95,7 @@ struct sps_ctx {
         DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
-                         &rowinfo, &tcerr, &plainT, &plainC};
+                         &rowinfo, &tcerr, &plainT, &plainC, &hmcm};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

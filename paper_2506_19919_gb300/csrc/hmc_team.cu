@@ -28,11 +28,12 @@ constexpr int kZnReg = 12;   // metallicity bins held in registers (Zn <= 12)
 template <int CPW>
 struct TeamWork {
     float m[CPW][kMaxAges], dm0[CPW][kMaxAges], dm1[CPW][kMaxAges], dm2[CPW][kMaxAges];
-    float pi[CPW][kMaxAges], w[CPW][kMaxAges], wb[CPW][kMaxAges];
+    float pi[CPW][kMaxAges];
+    float w[CPW][kMaxAges];                 // age weights; their adjoint overwrites them
     float q[CPW][kMaxMets], qb[CPW][kMaxMets];
     union {
         PanelScratch ps;
-        float red[32][CPW * kZnReg + 1];
+        float red[32][kZnReg + 1];          // qbar partials of one chain
         struct {
             double tll[CPW][kMaxBands];
             float tg[CPW][kMaxBands][4];
@@ -52,9 +53,7 @@ struct TeamWork {
     float xs[CPW][SPS_NPARAM], gs[CPW][SPS_NPARAM], minv[CPW][SPS_NPARAM];
     double lp[CPW], lps[CPW], h0[CPW];
     double mu[CPW], hbar[CPW], leb[CPW], acc[CPW];
-    double wmean[CPW][SPS_NPARAM], wm2[CPW][SPS_NPARAM];
-    float chol[CPW][78];                    // dense inverse metric L L^T, packed lower
-    float wcov[CPW][78];                    // Welford co-moments of the window
+    ChainMetric* cm[CPW];                   // metric-adaptation state (global memory)
     float v[CPW][SPS_NPARAM], lu[CPW][SPS_NPARAM], dv[CPW][2][SPS_NPARAM];
     double uacc[CPW];
     float eps[CPW];
@@ -66,7 +65,7 @@ struct TeamWork {
 
 template <int CPW>
 __device__ __forceinline__ AgeView age_view(TeamWork<CPW>& t, int ch) {
-    return AgeView{t.m[ch], t.dm0[ch], t.dm1[ch], t.dm2[ch], t.pi[ch], t.w[ch], t.wb[ch],
+    return AgeView{t.m[ch], t.dm0[ch], t.dm1[ch], t.dm2[ch], t.pi[ch], t.w[ch], t.w[ch],
                    t.q[ch], t.qb[ch], &t.u.ps};
 }
 
@@ -94,11 +93,12 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
     for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
         const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
         const float x = t.x[ch][k];
-        const float sg = 1.0f / (1.0f + __expf(-x));
+        const float ex = __expf(-fabsf(x));
+        const float r = __frcp_rn(1.0f + ex);
+        const float sg = (x >= 0.0f) ? r : ex * r;          // 1 / (1 + e^-x)
         t.th[ch][k] = c.prior_lo[k] + c.prior_span[k] * sg;
         t.dth[ch][k] = c.prior_span[k] * sg * (1.0f - sg);
-        const float ax = fabsf(x);
-        t.lpe[ch][k] = -ax - 2.0f * log1pf(__expf(-ax));
+        t.lpe[ch][k] = -fabsf(x) - 2.0f * __logf(1.0f + ex);   // log sg (1 - sg)
     }
     __syncwarp();
     if (lane < CPW) {
@@ -187,59 +187,63 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         t.gd[lane][3] = g3;
     }
     __syncwarp();
-    // ---- adjoint pass: wbar_i = sum_b g_b R_bi, qbar_j = sum_b g_b sum_i w_i C_bij
-    float qbr[CPW][kZnReg], wbl[CPW][4];
+    // ---- adjoint pass, row by row: V_ij = sum_b g_b C_bij (g_b = gamma_b / S_b),
+    //      wbar_i = sum_j q_j V_ij, qbar_j = sum_i w_i V_ij
+    float qbr[CPW][kZnReg];
+#pragma unroll
+    for (int ch = 0; ch < CPW; ++ch)
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = 0.0f;
+#pragma unroll 1
+    for (int i = lane; i < A; i += 32) {
+        float V[CPW][kZnReg];
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch)
+#pragma unroll
+            for (int j = 0; j < kZnReg; ++j) V[ch][j] = 0.0f;
+        float cv[kZnReg];
+#pragma unroll
+        for (int j = 0; j < kZnReg; ++j) cv[j] = 0.0f;
+        if (nb > 0) load_row(t.ptr[0] + i * Zn, Zn, cv);
+        for (int b = 0; b < nb; ++b) {
+            float cn[kZnReg];
+            if (b + 1 < nb) load_row(t.ptr[b + 1] + i * Zn, Zn, cn);
+#pragma unroll
+            for (int ch = 0; ch < CPW; ++ch) {
+                const float gg = t.gh[ch][b];
+#pragma unroll
+                for (int j = 0; j < kZnReg; ++j) V[ch][j] = fmaf(gg, cv[j], V[ch][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kZnReg; ++j) cv[j] = cn[j];
+        }
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) {
+            float wbv = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kZnReg; ++j) wbv = fmaf((j < Zn) ? t.q[ch][j] : 0.0f, V[ch][j], wbv);
+            const float wi = t.w[ch][i];
+            t.w[ch][i] = wbv;                                   // wbar_i replaces w_i
+#pragma unroll
+            for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = fmaf(wi, V[ch][j], qbr[ch][j]);
+        }
+    }
+    // qbar: sum the lanes' partials, one chain per round (two half sums)
 #pragma unroll
     for (int ch = 0; ch < CPW; ++ch) {
 #pragma unroll
-        for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = 0.0f;
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) wbl[ch][tt] = 0.0f;
-    }
-    for (int b = 0; b < nb; ++b) {
-        const float* C = t.ptr[b];
-        float ghr[CPW];
-#pragma unroll
-        for (int ch = 0; ch < CPW; ++ch) ghr[ch] = t.gh[ch][b];
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const int i = lane + 32 * tt;
-            if (i < A) {
-                float cv[kZnReg];
-                load_row(C + i * Zn, Zn, cv);
-#pragma unroll
-                for (int ch = 0; ch < CPW; ++ch) {
-                    float R = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < kZnReg; ++j) R = fmaf(qr[ch][j], cv[j], R);
-                    wbl[ch][tt] = fmaf(ghr[ch], R, wbl[ch][tt]);
-                    const float gw = ghr[ch] * wl[ch][tt];
-#pragma unroll
-                    for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = fmaf(gw, cv[j], qbr[ch][j]);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int ch = 0; ch < CPW; ++ch)
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const int i = lane + 32 * tt;
-            if (i < A) t.wb[ch][i] = wbl[ch][tt];
-        }
-#pragma unroll
-    for (int ch = 0; ch < CPW; ++ch)
-#pragma unroll
-        for (int j = 0; j < kZnReg; ++j) t.u.red[lane][ch * kZnReg + j] = qbr[ch][j];
-    __syncwarp();
-    for (int e = lane; e < CPW * kZnReg; e += 32) {
+        for (int j = 0; j < kZnReg; ++j) t.u.red[lane][j] = qbr[ch][j];
+        __syncwarp();
+        const int j = lane & 15, h = lane >> 4;
         float s = 0.0f;
+        if (j < kZnReg) {
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) s += t.u.red[r][e];
-        const int ch = e / kZnReg, j = e - ch * kZnReg;
-        if (j < Zn) t.qb[ch][j] = s;
+            for (int r = 0; r < 16; ++r) s += t.u.red[16 * h + r][j];
+        }
+        s += __shfl_down_sync(kFull, s, 16);
+        if (lane < Zn) t.qb[ch][lane] = s;
+        __syncwarp();
     }
-    __syncwarp();
     // ---- through the SFH, burst and MDF weights; then to unbounded space
 #pragma unroll 1
     for (int ch = 0; ch < CPW; ++ch) {
@@ -309,13 +313,13 @@ __device__ __forceinline__ void metric_apply(TeamWork<CPW>& t, int ch, bool dens
     }
     if (lane < SPS_NPARAM) {
         float a = 0.0f;
-        for (int k = lane; k < SPS_NPARAM; ++k) a = fmaf(t.chol[ch][tri(k, lane)], t.p[ch][k], a);
+        for (int k = lane; k < SPS_NPARAM; ++k) a = fmaf(t.cm[ch]->chol[tri(k, lane)], t.p[ch][k], a);
         t.lu[ch][lane] = a;                                      // (L^T p)_j
     }
     __syncwarp();
     if (lane < SPS_NPARAM) {
         float a = 0.0f;
-        for (int j = 0; j <= lane; ++j) a = fmaf(t.chol[ch][tri(lane, j)], t.lu[ch][j], a);
+        for (int j = 0; j <= lane; ++j) a = fmaf(t.cm[ch]->chol[tri(lane, j)], t.lu[ch][j], a);
         t.v[ch][lane] = a;                                       // (L L^T p)_k
     }
     __syncwarp();
@@ -353,8 +357,8 @@ __device__ __noinline__ void start_traj(TeamWork<CPW>& t, int ch, const HmcParam
     if (dense && lane == 0) {                 // p = L^-T z by back substitution
         for (int i = SPS_NPARAM - 1; i >= 0; --i) {
             float a = t.p[ch][i];
-            for (int k = i + 1; k < SPS_NPARAM; ++k) a -= t.chol[ch][tri(k, i)] * t.p[ch][k];
-            t.p[ch][i] = a / t.chol[ch][tri(i, i)];
+            for (int k = i + 1; k < SPS_NPARAM; ++k) a -= t.cm[ch]->chol[tri(k, i)] * t.p[ch][k];
+            t.p[ch][i] = a / t.cm[ch]->chol[tri(i, i)];
         }
     }
     __syncwarp();
@@ -421,10 +425,11 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
             const int wn = t.wn[ch] + 1;
             if (lane < SPS_NPARAM) {
                 const double xv = (double)t.x[ch][lane];
-                const double d = xv - t.wmean[ch][lane];
-                const double mean = t.wmean[ch][lane] + d / (double)wn;
-                t.wmean[ch][lane] = mean;
-                t.wm2[ch][lane] += d * (xv - mean);
+                ChainMetric* cm = t.cm[ch];
+                const double d = xv - cm->wmean[lane];
+                const double mean = cm->wmean[lane] + d / (double)wn;
+                cm->wmean[lane] = mean;
+                cm->wm2[lane] += d * (xv - mean);
                 t.dv[ch][0][lane] = (float)d;
                 t.dv[ch][1][lane] = (float)(xv - mean);
             }
@@ -434,21 +439,21 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
                     int i = 0;
                     while (tri(i + 1, 0) <= e) ++i;
                     const int j = e - tri(i, 0);
-                    t.wcov[ch][e] += t.dv[ch][0][i] * t.dv[ch][1][j];
+                    t.cm[ch]->wcov[e] += t.dv[ch][0][i] * t.dv[ch][1][j];
                 }
             }
             __syncwarp();
             if (lane == 0) t.wn[ch] = wn;
             if (it == t.wend[ch] - 1) {
                 if (wn >= 2 && !dense && lane < SPS_NPARAM) {
-                    const double var = t.wm2[ch][lane] / ((double)wn - 1.0);
+                    const double var = t.cm[ch]->wm2[lane] / ((double)wn - 1.0);
                     t.minv[ch][lane] = (float)(((double)wn / (wn + 5.0)) * var + 1e-3 * (5.0 / (wn + 5.0)));
                 }
                 if (wn >= 2 && dense && lane == 0) {
                     // regularised covariance, then its Cholesky factor in place
                     const float a = (float)wn / (wn + 5.0f), b = 1e-3f * (5.0f / (wn + 5.0f));
                     float Lm[78];
-                    for (int e = 0; e < 78; ++e) Lm[e] = a * t.wcov[ch][e] / ((float)wn - 1.0f);
+                    for (int e = 0; e < 78; ++e) Lm[e] = a * t.cm[ch]->wcov[e] / ((float)wn - 1.0f);
                     for (int i = 0; i < SPS_NPARAM; ++i) Lm[tri(i, i)] += b;
                     bool ok = true;
                     for (int j = 0; j < SPS_NPARAM && ok; ++j) {
@@ -467,13 +472,13 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
                         }
                     }
                     if (ok)
-                        for (int e = 0; e < 78; ++e) t.chol[ch][e] = Lm[e];
+                        for (int e = 0; e < 78; ++e) t.cm[ch]->chol[e] = Lm[e];
                 }
                 if (lane < SPS_NPARAM) {
-                    t.wmean[ch][lane] = 0.0;
-                    t.wm2[ch][lane] = 0.0;
+                    t.cm[ch]->wmean[lane] = 0.0;
+                    t.cm[ch]->wm2[lane] = 0.0;
                 }
-                for (int e = lane; e < 78; e += 32) t.wcov[ch][e] = 0.0f;
+                for (int e = lane; e < 78; e += 32) t.cm[ch]->wcov[e] = 0.0f;
                 __syncwarp();
                 if (lane == 0) {
                     t.wn[ch] = 0;
@@ -501,12 +506,13 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
 }
 
 template <int CPW>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, (CPW >= 4) ? 2 : 4)
 k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
            const float* __restrict__ theta0, const float* __restrict__ mag_obs,
            const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
            const int32_t* __restrict__ gal_order, float* __restrict__ samples, float* acc_out,
-           float* eps_out, int32_t* div_out, int64_t* nev_out, int32_t* status_out, int* queue) {
+           float* eps_out, int32_t* div_out, int64_t* nev_out, int32_t* status_out, int* queue,
+           ChainMetric* __restrict__ metric) {
     extern __shared__ __align__(16) unsigned char smem[];
     TeamWork<CPW>& t = reinterpret_cast<TeamWork<CPW>*>(smem)[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -541,19 +547,26 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
             const int cc = (ch < nch) ? ch : 0;
             t.x[ch][k] = theta0[((size_t)gi * C + c0 + cc) * SPS_NPARAM + k];
             t.minv[ch][k] = 1.0f;
-            t.wmean[ch][k] = 0.0;
-            t.wm2[ch][k] = 0.0;
+            if (ch < nch && hp.adapt_mass) {
+                ChainMetric* cm = metric + (gi * C + c0 + ch);
+                cm->wmean[k] = 0.0;
+                cm->wm2[k] = 0.0;
+            }
         }
-        for (int e = lane; e < CPW * 78; e += 32) {
-            const int ch = e / 78, r = e - ch * 78;
-            int i = 0;
-            while (tri(i + 1, 0) <= r) ++i;
-            t.chol[ch][r] = (r == tri(i, i)) ? 1.0f : 0.0f;
-            t.wcov[ch][r] = 0.0f;
+        if (hp.adapt_mass == 2) {
+            for (int e = lane; e < nch * 78; e += 32) {
+                const int ch = e / 78, r = e - ch * 78;
+                int i = 0;
+                while (tri(i + 1, 0) <= r) ++i;
+                ChainMetric* cm = metric + (gi * C + c0 + ch);
+                cm->chol[r] = (r == tri(i, i)) ? 1.0f : 0.0f;
+                cm->wcov[r] = 0.0f;
+            }
         }
         if (lane < CPW) {
             const int ch = lane;
             t.chain[ch] = (uint32_t)(gi * C + c0 + ((ch < nch) ? ch : 0));
+            t.cm[ch] = metric + t.chain[ch];
             t.eps[ch] = hp.eps0;
             t.mu[ch] = log(10.0 * (double)hp.eps0);
             t.hbar[ch] = t.leb[ch] = t.acc[ch] = 0.0;
@@ -582,15 +595,20 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
         __syncwarp();
         const float2* bins = g.bins + (size_t)gi * c.n_age;
         const float lnT = g.lnT[gi], lT10 = g.lT10[gi];
-        team_eval<CPW>(c, t, bins, lnT, lT10, nb);
-#pragma unroll 1
-        for (int ch = 0; ch < CPW; ++ch)
-            if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
-        for (;;) {
-            bool any = false;
-            for (int ch = 0; ch < CPW; ++ch) any = any || !t.done[ch];
-            if (!any) break;
+        // one evaluation per pass; the first pass only starts the trajectories
+        for (int pass = 0;; ++pass) {
+            if (pass > 0) {
+                bool any = false;
+                for (int ch = 0; ch < CPW; ++ch) any = any || !t.done[ch];
+                if (!any) break;
+            }
             team_eval<CPW>(c, t, bins, lnT, lT10, nb);
+            if (pass == 0) {
+#pragma unroll 1
+                for (int ch = 0; ch < CPW; ++ch)
+                    if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
+                continue;
+            }
 #pragma unroll 1
             for (int ch = 0; ch < CPW; ++ch) {
                 if (t.done[ch]) continue;
@@ -640,14 +658,15 @@ static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcPara
                                const float* theta0, const float* mag_obs, const float* sigma,
                                const uint32_t* mask, const int32_t* gal_order, float* samples,
                                float* acc, float* eps_out, int32_t* div, int64_t* nevals,
-                               int32_t* status, int* queue, int blocks, int warps, cudaStream_t s) {
+                               int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
+                               cudaStream_t s) {
     const size_t smem = sizeof(TeamWork<CPW>) * warps;
     cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_hmc_team<CPW><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask,
                                                      gal_order, samples, acc, eps_out, div,
-                                                     nevals, status, queue);
+                                                     nevals, status, queue, metric);
     return cudaGetLastError();
 }
 
@@ -674,15 +693,16 @@ cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const H
                             const float* theta0, const float* mag_obs, const float* sigma,
                             const uint32_t* mask, const int32_t* gal_order, float* samples,
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
-                            int32_t* status, int* queue, int blocks, int warps, cudaStream_t s) {
+                            int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
+                            cudaStream_t s) {
     if (cpw >= 4)
         return team_launch<4>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                              eps_out, div, nevals, status, queue, blocks, warps, s);
+                              eps_out, div, nevals, status, queue, metric, blocks, warps, s);
     if (cpw == 2)
         return team_launch<2>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                              eps_out, div, nevals, status, queue, blocks, warps, s);
+                              eps_out, div, nevals, status, queue, metric, blocks, warps, s);
     return team_launch<1>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
-                          div, nevals, status, queue, blocks, warps, s);
+                          div, nevals, status, queue, metric, blocks, warps, s);
 }
 
 }  // namespace sps

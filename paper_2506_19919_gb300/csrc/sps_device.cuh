@@ -90,11 +90,9 @@ __device__ __forceinline__ DustTerms dust_eval(float k0, float lnr, float drude,
 // ---------------------------------------------------------------- per-warp scratch
 // Panel bookkeeping of the SFH quadrature of one row.
 struct PanelScratch {
-    float px0[kMaxAges];        // first panel centre (ln t)
-    float php[kMaxAges];        // panel half-width
-    unsigned short pn[kMaxAges];
-    unsigned short pstart[kMaxAges + 1];
-    unsigned char pmap[kMaxPanels];
+    float4 info[kMaxAges];            // per bin: (first panel centre, half-width,
+                                      //  first panel index, rule order) - ints as bits
+    unsigned char pmap[kMaxPanels];   // bin index at each bin's first panel, 0xFF elsewhere
 };
 
 // Where the age / metallicity stage of one row keeps its arrays.
@@ -133,118 +131,184 @@ struct RowScratch {
 };
 
 // ---------------------------------------------------------------- SFH bins
-// Panel count ceil(w / panel) clamped to [1, kMaxPanels]; NaN or inf give a
-// bounded count so that no input can index outside the scratch arrays.
-__device__ __forceinline__ int panel_count(float w, float panel) {
-    float f = ceilf(w / panel);
+// Panel count ceil(f) clamped to [1, kMaxPanels]; NaN or inf give a bounded
+// count so that no input can index outside the scratch arrays.
+__device__ __forceinline__ int panel_count(float f) {
+    f = ceilf(f);
     return (f >= 1.0f) ? ((f < (float)kMaxPanels) ? (int)f : kMaxPanels) : 1;
 }
 
-// Fills s.m and (if grad) s.dm; returns M = sum_i m_i (FP64).
+// One panel of an N-node Gauss-Legendre rule (nodes gx, weights gw on [-1, 1])
+// centred at u = xc with half-width hp: accumulates int hh du into v0 and, if
+// grad, int dhh/d(alpha), d/d(beta) and the tau-derivative integrand into v1..v3.
+template <int N>
+__device__ __forceinline__ void gl_panel(const float* __restrict__ gx, const float* __restrict__ gw,
+                                         float hp, float xc, float alpha, float beta, bool grad,
+                                         float& v0, float& v1, float& v2, float& v3) {
+    const float am1 = alpha - 1.0f, bp1 = beta + 1.0f;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const float uu = fmaf(hp, gx[q], xc);
+        const float P_ = __expf(am1 * uu);
+        const float Q_ = __expf(-bp1 * uu);
+        const float hh = __frcp_rn(P_ + Q_);
+        const float wq = gw[q] * hp;
+        v0 = fmaf(wq, hh, v0);
+        if (grad) {
+            const float h2 = hh * hh * wq;
+            v1 = fmaf(h2, alpha * P_ - beta * Q_, v1);
+            v2 = fmaf(-h2 * P_, uu, v2);
+            v3 = fmaf(h2 * Q_, uu, v3);
+        }
+    }
+}
+__device__ __forceinline__ void gl_panel_any(int n, const float* __restrict__ gx,
+                                             const float* __restrict__ gw, float hp, float xc,
+                                             float alpha, float beta, bool grad, float& v0,
+                                             float& v1, float& v2, float& v3) {
+#pragma unroll 1
+    for (int q = 0; q < n; ++q) gl_panel<1>(gx + q, gw + q, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+}
+
+// Fills v.m and (if grad) v.dm0..2; returns M = sum_i m_i (FP64).
+//
+// Quadrature rule.  In u = ln(t / tau) the integrand hh(u) is analytic in the
+// strip |Im u| < pi / (alpha + beta) and grows at most like e^{kappa |u|},
+// kappa = max(alpha + beta, beta + 1).  Panels of the full rule (order
+// c.gl_order) are c.panel * 10 / kappa wide, clamped to [1, 8] x c.panel, so the
+// ratio of singularity distance to half-width stays >= 2.5 and kappa x
+// half-width <= 1.25: a relative error below 1e-8 per panel for order 6.  A bin
+// that fits in one panel with kappa x half-width <= 0.25 uses 3 nodes, <= 0.04
+// 2 nodes (relative error below 1e-8 by the same bounds).  Below x_min =
+// min(ln t_obs - ln tau, 0) - 30 / (beta + 1) the remaining mass is < 1e-10 of
+// the total and is dropped.
 __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
-                           float lnT, float tau, float alpha, float beta, bool grad) {
+                                           float lnT, float tau, float alpha, float beta, bool grad) {
     PanelScratch& ps = *v.ps;
     const int lane = lane_id();
     const int A = c.n_age;
     const float lntau = __logf(tau);
-    const float xmin = lntau + fminf(lnT - lntau, 0.0f) - 30.0f / (beta + 1.0f);
-    const float panel = c.panel;
-    for (int i = lane; i < A; i += 32) {
-        float2 b = bins[i];
+    const float bp1 = beta + 1.0f;
+    const float xmin = lntau + fminf(lnT - lntau, 0.0f) - 30.0f / bp1;
+    const float kap = fmaxf(alpha + beta, bp1);
+    const float pw = fminf(fmaxf(c.panel * 10.0f / kap, c.panel), 8.0f * c.panel);
+    const float ipw = 1.0f / pw;
+    const int G = c.gl_order;
+    const int o2 = min(2, G), o3 = min(3, G);
+    // bins 4 lane .. 4 lane + 3: panel count, first centre, half-width, order
+    int nl[4];
+    float x0l[4], hpl[4];
+    int ol[4];
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = 4 * lane + k;
         int n = 0;
         float x0 = 0.0f, hp = 0.0f;
-        if (b.y < 0.0f) {                          // reaches t = 0
-            float w = b.x - xmin;
-            if (w > 0.0f) {
-                n = panel_count(w, panel);
-                hp = 0.5f * w / (float)n;
-                x0 = xmin + hp;
-            }
-        } else if (b.y > 0.0f) {
-            float hi = b.x + b.y;
-            float lo = b.x - b.y;
-            if (hi > xmin) {
-                if (lo < xmin) {
-                    float w = hi - xmin;
-                    n = panel_count(w, panel);
-                    hp = 0.5f * w / (float)n;
+        if (i < A) {
+            const float2 b = bins[i];
+            if (b.y < 0.0f) {                      // reaches t = 0
+                const float w = b.x - xmin;
+                if (w > 0.0f) {
+                    n = panel_count(w * ipw);
+                    hp = 0.5f * w * __frcp_rn((float)n);
                     x0 = xmin + hp;
-                } else {
-                    n = panel_count(2.0f * b.y, panel);
-                    hp = b.y / (float)n;
-                    x0 = b.x + (float)(1 - n) * hp;
+                }
+            } else if (b.y > 0.0f) {
+                const float hi = b.x + b.y;
+                const float lo = b.x - b.y;
+                if (hi > xmin) {
+                    if (lo < xmin) {
+                        const float w = hi - xmin;
+                        n = panel_count(w * ipw);
+                        hp = 0.5f * w * __frcp_rn((float)n);
+                        x0 = xmin + hp;
+                    } else {                       // centre / half-width kept exact
+                        n = panel_count(2.0f * b.y * ipw);
+                        hp = b.y * __frcp_rn((float)n);
+                        x0 = b.x + (float)(1 - n) * hp;
+                    }
                 }
             }
+            v.m[i] = 0.0f;
+            v.dm0[i] = 0.0f;
+            v.dm1[i] = 0.0f;
+            v.dm2[i] = 0.0f;
         }
-        ps.pn[i] = (unsigned short)n;
-        ps.px0[i] = x0;
-        ps.php[i] = hp;
-        v.m[i] = 0.0f;
-        v.dm0[i] = 0.0f;
-        v.dm1[i] = 0.0f;
-        v.dm2[i] = 0.0f;
+        const float hk = hp * kap;
+        ol[k] = (n == 1) ? (hk <= 0.04f ? o2 : (hk <= 0.25f ? o3 : G)) : G;
+        nl[k] = n;
+        x0l[k] = x0;
+        hpl[k] = hp;
+        tot += n;
     }
-    __syncwarp();
-    int carry = 0;
-    for (int base = 0; base < A; base += 32) {
-        int i = base + lane;
-        int n = (i < A) ? (int)ps.pn[i] : 0;
-        int incl = n;
+    int incl = tot;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (i < A) ps.pstart[i] = (unsigned short)min(carry + incl - n, kMaxPanels);
-        carry += __shfl_sync(kFull, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
     }
-    const int P = min(carry, kMaxPanels);
+    const int P = min(__shfl_sync(kFull, incl, 31), kMaxPanels);
+    for (int p = lane; p < P; p += 32) ps.pmap[p] = 0xFF;
     __syncwarp();
-    for (int i = lane; i < A; i += 32) {
-        int p0 = ps.pstart[i];
-        int p1 = min(p0 + (int)ps.pn[i], kMaxPanels);
-        for (int p = p0; p < p1; ++p) ps.pmap[p] = (unsigned char)i;
+    int st = incl - tot;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = 4 * lane + k;
+        if (i < A) ps.info[i] = make_float4(x0l[k], hpl[k], __int_as_float(st), __int_as_float(ol[k]));
+        if (nl[k] > 0 && st < kMaxPanels) ps.pmap[st] = (unsigned char)i;
+        st += nl[k];
     }
     __syncwarp();
-    const float am1 = alpha - 1.0f, bp1 = beta + 1.0f;
+    int carry = -1;
     for (int base = 0; base < P; base += 32) {
         const int p = base + lane;
         const bool act = p < P;
-        int bin = act ? (int)ps.pmap[p] : -1;
+        int f = act ? (int)ps.pmap[p] : 0xFF;
+        f = (f == 0xFF) ? -1 : f;
+        // the bin of panel p: the last bin whose first panel is at or before p
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, f, o);
+            if (lane >= o) f = max(f, t);
+        }
+        f = max(f, carry);
+        carry = __shfl_sync(kFull, f, 31);
+        const int bin = (act && f >= 0) ? f : -1;
+        float4 inf = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (bin >= 0) inf = ps.info[bin];
+        const int oc = __reduce_max_sync(kFull, (bin >= 0) ? __float_as_int(inf.w) : 0);
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-        if (act) {
-            const int k = p - (int)ps.pstart[bin];
-            const float hp = ps.php[bin];
-            const float xc = ps.px0[bin] + 2.0f * (float)k * hp - lntau;
-            for (int gq = 0; gq < c.gl_order; ++gq) {
-                float uu = fmaf(hp, c.gl_x[gq], xc);
-                float P_ = __expf(am1 * uu);
-                float Q_ = __expf(-bp1 * uu);
-                float hh = __frcp_rn(P_ + Q_);
-                float wq = c.gl_w[gq] * hp;
-                v0 = fmaf(wq, hh, v0);
-                if (grad) {
-                    float h2 = hh * hh * wq;
-                    v1 = fmaf(h2, alpha * P_ - beta * Q_, v1);
-                    v2 = fmaf(-h2 * P_, uu, v2);
-                    v3 = fmaf(h2 * Q_, uu, v3);
+        if (bin >= 0) {
+            const float hp = inf.y;
+            const float xc = inf.x + 2.0f * (float)(p - __float_as_int(inf.z)) * hp - lntau;
+            if (oc <= 2)
+                gl_panel<2>(c.gl2_x, c.gl2_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+            else if (oc == 3)
+                gl_panel<3>(c.gl3_x, c.gl3_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+            else if (oc == 6)
+                gl_panel<6>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+            else
+                gl_panel_any(G, c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+        }
+        // panels of one bin are consecutive: sum them unless every panel of the
+        // chunk belongs to its own bin
+        const int prev = __shfl_up_sync(kFull, bin, 1);
+        if (__any_sync(kFull, bin >= 0 && lane > 0 && prev == bin)) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float t0 = __shfl_up_sync(kFull, v0, o);
+                const float t1 = __shfl_up_sync(kFull, v1, o);
+                const float t2 = __shfl_up_sync(kFull, v2, o);
+                const float t3 = __shfl_up_sync(kFull, v3, o);
+                const int bo = __shfl_up_sync(kFull, bin, o);
+                if (lane >= o && bo == bin) {
+                    v0 += t0; v1 += t1; v2 += t2; v3 += t3;
                 }
             }
         }
-        // segmented inclusive scan over panels of the same bin (bins are sorted)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            float t0 = __shfl_up_sync(kFull, v0, o);
-            float t1 = __shfl_up_sync(kFull, v1, o);
-            float t2 = __shfl_up_sync(kFull, v2, o);
-            float t3 = __shfl_up_sync(kFull, v3, o);
-            int bo = __shfl_up_sync(kFull, bin, o);
-            if (lane >= o && bo == bin) {
-                v0 += t0; v1 += t1; v2 += t2; v3 += t3;
-            }
-        }
-        int bnext = __shfl_down_sync(kFull, bin, 1);
-        if (act && (lane == 31 || bnext != bin)) {
+        const int bnext = __shfl_down_sync(kFull, bin, 1);
+        if (bin >= 0 && (lane == 31 || bnext != bin)) {
             v.m[bin] += v0 * tau;
             if (grad) {
                 v.dm0[bin] += v1;
@@ -255,29 +319,34 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
         __syncwarp();
     }
     double acc = 0.0;
-    for (int i = lane; i < A; i += 32) acc += (double)v.m[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = 4 * lane + k;
+        if (i < A) acc += (double)v.m[i];
+    }
     return warp_sum_d(acc);
 }
 
 // ---------------------------------------------------------------- burst + MDF
 __device__ __forceinline__ float burst_weights(const Consts& c, const AgeView& v, float lT10,
                                                float mu, float sig) {
-    const float xT = (lT10 - mu) / sig;
-    const float D = tri_cdf(xT);
+    const float isig = 1.0f / sig;
+    const float D = tri_cdf((lT10 - mu) * isig);
     const float invD = 1.0f / D;
     for (int i = lane_id(); i < c.n_age; i += 32) {
-        float lo = fminf(c.log_age_edge[i], lT10);
-        float hi = fminf(c.log_age_edge[i + 1], lT10);
-        v.pi[i] = (tri_cdf((hi - mu) / sig) - tri_cdf((lo - mu) / sig)) * invD;
+        const float lo = fminf(c.log_age_edge[i], lT10);
+        const float hi = fminf(c.log_age_edge[i + 1], lT10);
+        v.pi[i] = (tri_cdf((hi - mu) * isig) - tri_cdf((lo - mu) * isig)) * invD;
     }
     return D;
 }
 
 __device__ __forceinline__ void met_weights(const Consts& c, const AgeView& v, float mu, float sd) {
-    int j = lane_id();
+    const int j = lane_id();
+    const float isd = 1.0f / sd;
     if (j < c.n_met) {
-        float ylo = (c.lgz_edge[j] - mu) / sd;
-        float yhi = (c.lgz_edge[j + 1] - mu) / sd;
+        const float ylo = (c.lgz_edge[j] - mu) * isd;
+        const float yhi = (c.lgz_edge[j + 1] - mu) * isd;
         v.q[j] = (ylo > 0.0f) ? normcdff(-ylo) - normcdff(-yhi) : normcdff(yhi) - normcdff(ylo);
     }
 }
@@ -344,70 +413,78 @@ __device__ __forceinline__ double age_met_weights(const Consts& c, RowScratch& s
 }
 
 // Adjoint of age_met_weights: given s.wb (dlogL/dw_i) and s.qb (dlogL/dq_j)
-// returns d/dtheta for columns 1-8 added into g[].
+// returns d/dtheta for columns 1-8 added into g[].  Every bin sum is taken in
+// one pass and reduced in one round:
+//   mbar_l = (1 - F_b) wbar_l + F_b sum_i wbar_i pi_i   (smooth SFH)
+//   pibar_i = F_b M wbar_i                               (burst, through pi = raw / D)
+//   F_b-bar = sum_i wbar_i (pi_i M - m_i)
 __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& s, float lT10, double M,
-                                             const float* th, float* g) {
+                                                const float* th, float* g) {
     const int lane = lane_id();
     const int A = c.n_age;
     const float fb = th[4];
     const float Mf = (float)M;
-    // sum_i wbar_i pi_i  and  F_burst-bar
-    float a_wp = 0.f, a_fb = 0.f;
-    for (int i = lane; i < A; i += 32) {
-        float wb = s.wb[i];
-        a_wp += wb * s.pi[i];
-        a_fb += wb * (s.pi[i] * Mf - s.m[i]);
-    }
-    a_wp = warp_sum(a_wp);
-    a_fb = warp_sum(a_fb);
-    // smooth SFH: mbar_l = (1 - fb) wbar_l + fb sum_i wbar_i pi_i
-    float gt = 0.f, ga = 0.f, gbt = 0.f;
-    for (int i = lane; i < A; i += 32) {
-        float mb = (1.0f - fb) * s.wb[i] + fb * a_wp;
-        gt += mb * s.dm0[i];
-        ga += mb * s.dm1[i];
-        gbt += mb * s.dm2[i];
-    }
-    g[1] += warp_sum(gt);
-    g[2] += warp_sum(ga);
-    g[3] += warp_sum(gbt);
-    g[4] += a_fb;
-    // burst: pi_i = raw_i / D, pibar_i = fb M wbar_i
     const float mu = th[5], sig = th[6] * (1.0f / 3.0f);
-    const float xT = (lT10 - mu) / sig;
-    const float D = tri_cdf(xT);
-    float s_mu = 0.f, s_sg = 0.f, s_pp = 0.f;
+    const float isig = 1.0f / sig;
+    float s_wp = 0.f, s_wm = 0.f, s_w0 = 0.f, s_w1 = 0.f, s_w2 = 0.f;
+    float s_d0 = 0.f, s_d1 = 0.f, s_d2 = 0.f, s_mu = 0.f, s_sg = 0.f;
     for (int i = lane; i < A; i += 32) {
-        float lo = fminf(c.log_age_edge[i], lT10);
-        float hi = fminf(c.log_age_edge[i + 1], lT10);
-        float xl = (lo - mu) / sig, xh = (hi - mu) / sig;
-        float pib = fb * Mf * s.wb[i];
-        float tl = tri_pdf(xl), th = tri_pdf(xh);
-        s_mu += pib * (-(th - tl));
-        s_sg += pib * (-(xh * th - xl * tl));
-        s_pp += pib * s.pi[i];
+        const float wb = s.wb[i];
+        const float d0 = s.dm0[i], d1 = s.dm1[i], d2 = s.dm2[i];
+        s_wp = fmaf(wb, s.pi[i], s_wp);
+        s_wm = fmaf(wb, s.m[i], s_wm);
+        s_w0 = fmaf(wb, d0, s_w0);
+        s_w1 = fmaf(wb, d1, s_w1);
+        s_w2 = fmaf(wb, d2, s_w2);
+        s_d0 += d0;
+        s_d1 += d1;
+        s_d2 += d2;
+        const float lo = fminf(c.log_age_edge[i], lT10);
+        const float hi = fminf(c.log_age_edge[i + 1], lT10);
+        const float xl = (lo - mu) * isig, xh = (hi - mu) * isig;
+        const float tl = tri_pdf(xl), tH = tri_pdf(xh);
+        s_mu = fmaf(wb, tl - tH, s_mu);
+        s_sg = fmaf(wb, xl * tl - xh * tH, s_sg);
     }
-    s_mu = warp_sum(s_mu);
-    s_sg = warp_sum(s_sg);
-    s_pp = warp_sum(s_pp);
-    const float tT = tri_pdf(xT);
-    // d raw/d mu = -(T(xh) - T(xl))/sig ; dD/dmu = -T(xT)/sig  (and x T(x) for sigma)
-    float gmu = (s_mu - s_pp * (-tT)) / (sig * D);
-    float gsg = (s_sg - s_pp * (-xT * tT)) / (sig * D);
-    g[5] += gmu;
-    g[6] += gsg * (1.0f / 3.0f);
     // metallicity: q_j = Phi(yh) - Phi(yl)
     const float mz = th[7], sz = th[8];
-    float gz = 0.f, gs = 0.f;
-    int j = lane;
-    if (j < c.n_met) {
-        float yl = (c.lgz_edge[j] - mz) / sz, yh = (c.lgz_edge[j + 1] - mz) / sz;
-        float qb = s.qb[j];
-        gz = qb * (-(phi_(yh) - phi_(yl)) / sz);
-        gs = qb * (-(phi_y(yh) - phi_y(yl)) / sz);
+    const float isz = 1.0f / sz;
+    float s_gz = 0.f, s_gs = 0.f;
+    if (lane < c.n_met) {
+        const float yl = (c.lgz_edge[lane] - mz) * isz, yh = (c.lgz_edge[lane + 1] - mz) * isz;
+        const float qb = s.qb[lane];
+        s_gz = qb * (phi_(yl) - phi_(yh));
+        s_gs = qb * (phi_y(yl) - phi_y(yh));
     }
-    g[7] += warp_sum(gz);
-    g[8] += warp_sum(gs);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s_wp += __shfl_xor_sync(kFull, s_wp, o);
+        s_wm += __shfl_xor_sync(kFull, s_wm, o);
+        s_w0 += __shfl_xor_sync(kFull, s_w0, o);
+        s_w1 += __shfl_xor_sync(kFull, s_w1, o);
+        s_w2 += __shfl_xor_sync(kFull, s_w2, o);
+        s_d0 += __shfl_xor_sync(kFull, s_d0, o);
+        s_d1 += __shfl_xor_sync(kFull, s_d1, o);
+        s_d2 += __shfl_xor_sync(kFull, s_d2, o);
+        s_mu += __shfl_xor_sync(kFull, s_mu, o);
+        s_sg += __shfl_xor_sync(kFull, s_sg, o);
+        s_gz += __shfl_xor_sync(kFull, s_gz, o);
+        s_gs += __shfl_xor_sync(kFull, s_gs, o);
+    }
+    const float omf = 1.0f - fb, fa = fb * s_wp;
+    g[1] += omf * s_w0 + fa * s_d0;
+    g[2] += omf * s_w1 + fa * s_d1;
+    g[3] += omf * s_w2 + fa * s_d2;
+    g[4] += Mf * s_wp - s_wm;
+    // burst: d raw_i/d mu = -(T(xh) - T(xl)) / sig, dD/dmu = -T(xT) / sig; x T(x) for sigma
+    const float xT = (lT10 - mu) * isig;
+    const float D = tri_cdf(xT);
+    const float tT = tri_pdf(xT);
+    const float k = fb * Mf / (sig * D);
+    g[5] += k * (s_mu + s_wp * tT);
+    g[6] += k * (s_sg + s_wp * xT * tT) * (1.0f / 3.0f);
+    g[7] += s_gz * isz;
+    g[8] += s_gs * isz;
 }
 __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT10, double M,
                                        const RowParams& p, float* g) {

@@ -22,8 +22,10 @@ struct Consts {
     int n_age, n_met, n_lam, n_band, K, k_pad;
     int lam_pad;                          // wavelength stride of the padded tables
     int gl_order;
-    float panel;                          // max panel width in ln t
-    float gl_x[kMaxGL], gl_w[kMaxGL];     // Gauss-Legendre rule on [-1, 1]
+    float panel;                          // panel width in ln t at kappa = 10 (SFH quadrature)
+    float gl_x[kMaxGL], gl_w[kMaxGL];     // Gauss-Legendre rule on [-1, 1] for full panels
+    float gl2_x[2], gl2_w[2];             // 2- and 3-node rules for narrow bins
+    float gl3_x[3], gl3_w[3];
     float log_age_edge[kMaxAges + 1];     // log10 age-bin edges [yr]; [0] = -100 stand-in
     float lgz_edge[kMaxMets + 1];         // metallicity-bin edges; outer +-inf
     float prior_lo[SPS_NPARAM], prior_span[SPS_NPARAM];
@@ -54,6 +56,14 @@ struct Grid {
     const uint16_t* ssp_bf;  // [k_pad][lam_pad] SSP table, BF16 bits, row-scaled by 2^-e_i
     const uint16_t* ssp_t_bf;// [lam_pad][k_pad] transposed BF16 row-scaled
     const float* row_scale;  // [A] 2^e_i
+};
+
+// Metric-adaptation state of one HMC chain, kept in global memory (read at
+// trajectory ends; chol every leapfrog step with the dense metric).
+struct ChainMetric {
+    double wmean[SPS_NPARAM], wm2[SPS_NPARAM];   // Welford moments of the window
+    float chol[78];                              // dense inverse metric L L^T, packed lower
+    float wcov[78];                              // window co-moments (dense)
 };
 
 // Records the message returned by sps_last_error_message() on this thread.
@@ -127,7 +137,7 @@ struct HmcParams {
     int chains_per_gal, n_warm, n_samp, L_min, L_max;
     float target_accept, eps0;
     uint64_t seed;
-    int adapt_mass;         // windowed diagonal metric adaptation during warm-up
+    int adapt_mass;         // 0 identity, 1 windowed diagonal, 2 windowed dense metric
 };
 size_t hmc_team_smem_per_warp(int cpw);
 cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm);
@@ -135,7 +145,8 @@ cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const H
                             const float* theta0, const float* mag_obs, const float* sigma,
                             const uint32_t* mask, const int32_t* gal_order, float* samples,
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
-                            int32_t* status, int* queue, int blocks, int warps, cudaStream_t s);
+                            int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
+                            cudaStream_t s);
 cudaError_t launch_leapfrog(const Consts& c, const Galaxies& g, const float* x0,
                             const float* p0, const float* eps, const int32_t* L,
                             const int32_t* gal_idx, int64_t n, const float* mag_obs,
