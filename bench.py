@@ -12,8 +12,10 @@ observed magnitudes are the model at a seeded truth plus N(0, 0.05) noise.
 value = sum_g min(1, ESS_g / 100) / (minutes per step), ESS_g the minimum over
 the 12 parameters of the multi-chain ESS of galaxy g.
 
-Also reported: log-likelihood + gradient evaluations per second on 100,000
-(galaxy, chain) pairs (approximate FP32, exact FP32, exact BF16), the
+Also reported: the same sampler run as the plain lock-step forward-mode
+baseline (posteriors/min at equal ESS), log-likelihood + gradient
+evaluations per second on 100,000 (galaxy, chain) pairs (approximate FP32,
+exact FP32, exact BF16), the
 roofline of the dominant kernel, the clocks seen during the timed region,
 an end-to-end number through the C ABI with host buffers, and the FP64
 oracle timed on a bounded sample on the host cores.
@@ -245,6 +247,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.skip_extra:
         out["loglike_grad"] = _loglike_grad_rates(ctx, dev)
+    if rank == 0 and not args.skip_plain:
+        out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
     if rank == 0 and not args.skip_e2e:
         out["e2e"] = _e2e(ctx, cfg, lib, wl, mobs, x0, post, ws)
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -255,6 +259,51 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, full):
+    """The lock-step forward-mode baseline (sps_hmc_run_forward_mode) on the
+    same workload and sampler.  By default a bounded run (its cost per
+    iteration is fixed: L_max rounds of every chain) is timed and scaled to the
+    full iteration count; the two paths run the same sampler on the same Philox
+    streams, so posteriors/min is compared at the fused run's ESS.  With full,
+    the whole run is timed and its own ESS reported as well."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    G, C = wl.n_gal, wl.chains
+    n_it = wl.extra["n_warm"] + wl.extra["n_samp"]
+    kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"],
+              seed=2506199190, path="plain")
+    res = {"path": "sps_hmc_run_forward_mode: chains in lock step, L_max rounds per iteration, "
+                   "unfused forward-mode gradient of every chain every round"}
+    if full:
+        nw, ns = wl.extra["n_warm"], wl.extra["n_samp"]
+    else:
+        nw, ns = 12, 12
+    ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=2, n_samp=2, samples=False, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o = ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=nw, n_samp=ns, samples=full, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    s_run = e0.elapsed_time(e1) / 1e3
+    s_step = s_run * n_it / (nw + ns)
+    nev = float(o["grad_evals"].sum())
+    res.update({"iterations_timed": nw + ns, "s_timed": s_run, "s_per_step": s_step,
+                "grad_evals_per_s": nev / s_run,
+                "posteriors_per_min_at_equal_ess": post / (s_step / 60.0),
+                "fused_vs_plain_posteriors_per_min": value / (post / (s_step / 60.0)),
+                "fused_vs_plain_step_time": s_step / (ms_step / 1e3)})
+    if full:
+        ess, rhat = pkg.diagnostics(o["samples"], G, C)
+        ess_g = ess.min(1)
+        own = float(np.minimum(1.0, ess_g / ESS_TARGET).sum())
+        res.update({"own_median_ess": float(np.median(ess_g)),
+                    "own_posteriors_per_min": own / (s_run / 60.0),
+                    "own_frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean())})
+    return res
 
 
 def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
@@ -425,6 +474,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--plain-full", action="store_true",
+                    help="run the whole lock-step baseline HMC (minutes) and report its own ESS")
     # profiling captures only (not bench values): smaller galaxy count / iterations
     ap.add_argument("--gal", type=int, default=None)
     ap.add_argument("--warm", type=int, default=None)

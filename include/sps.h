@@ -202,6 +202,19 @@ sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* the
                        const float* mag_obs, const float* sigma, const uint32_t* mask,
                        float* samples_out, sps_hmc_stats* stats, void* stream);
 
+/* Comparison baseline for sps_hmc_run (not a product path): the same sampler
+ * (identity metric, same Philox streams, dual averaging, FP64 accept) run the
+ * way a vectorised port of the paper's batched HMC (Sec. 4, App. D.2) runs it.
+ * All chains advance in lock step; each iteration takes L_max rounds, and every
+ * round evaluates every chain with the unfused forward-mode gradient of
+ * sps_loglike_grad_forward_mode whether or not its trajectory has ended.
+ * Arguments, layouts and outputs as sps_hmc_run; stats->grad_evals counts the
+ * evaluations performed (1 + (n_warm + n_samp) L_max per chain).
+ * SPS_E_UNSUPPORTED unless cfg->adapt_mass == 0 and cfg->mode == SPS_APPROX. */
+sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
+                                    const float* mag_obs, const float* sigma, const uint32_t* mask,
+                                    float* samples_out, sps_hmc_stats* stats, void* stream);
+
 /* Deterministic leapfrog trajectories (the HMC integrator of App. D.2 without
  * the random draws): for each row, L[row] steps of size eps[row] from
  * (x0, p0) in unbounded space; writes the end point, its momentum and log

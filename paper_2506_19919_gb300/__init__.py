@@ -157,7 +157,11 @@ class Context:
 
     def hmc_run(self, theta0_unb, mag_obs, sigma, mask, chains_per_gal=4, n_warm=500,
                 n_samp=500, L_min=8, L_max=64, target_accept=0.8, eps0=0.1, seed=2506199190,
-                use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=0):
+                use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=0,
+                path="fused"):
+        """Batched HMC.  path="fused" runs the persistent sampler (sps_hmc_run);
+        path="plain" the lock-step forward-mode comparison baseline
+        (sps_hmc_run_forward_mode, identity metric only)."""
         x0 = theta0_unb if isinstance(theta0_unb, torch.Tensor) else _f32(theta0_unb, self.device)
         dev = x0.device
         mo = _f32(mag_obs, dev)
@@ -184,8 +188,9 @@ class Context:
         }
         st = sps_hmc_stats(*(C.c_void_p(out[k].data_ptr()) for k in
                              ("accept_prob", "step_size", "divergences", "grad_evals", "status")))
-        check(self._lib.sps_hmc_run(self.h, C.byref(cfg), _vp(x0), _vp(mo), _vp(sg), _vp(mk),
-                                    _vp(out["samples"]), C.byref(st), _stream(x0)), "sps_hmc_run")
+        fn = {"fused": "sps_hmc_run", "plain": "sps_hmc_run_forward_mode"}[path]
+        check(getattr(self._lib, fn)(self.h, C.byref(cfg), _vp(x0), _vp(mo), _vp(sg), _vp(mk),
+                                     _vp(out["samples"]), C.byref(st), _stream(x0)), fn)
         return out
 
     def leapfrog(self, x0, p0, eps, L, mag_obs, sigma, mask, gal_idx=None):

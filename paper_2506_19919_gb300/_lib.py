@@ -68,6 +68,8 @@ _PROTOS = {
     "sps_loglike_grad_forward_mode": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P]),
     "sps_hmc_run": (C.c_int, [_P, C.POINTER(sps_hmc_config), _P, _P, _P, _P, _P,
                               C.POINTER(sps_hmc_stats), _P]),
+    "sps_hmc_run_forward_mode": (C.c_int, [_P, C.POINTER(sps_hmc_config), _P, _P, _P, _P, _P,
+                                           C.POINTER(sps_hmc_stats), _P]),
     "sps_leapfrog": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "sps_philox": (C.c_int, [_P, _P, C.c_int64, C.c_uint64, _P, _P]),
     "sps_weights": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),

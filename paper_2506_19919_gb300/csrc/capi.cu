@@ -903,3 +903,107 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     CK(st.finish());
     return SPS_OK;
 }
+
+extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_config* cfg,
+                                               const float* theta0_unb, const float* mag_obs,
+                                               const float* sigma, const uint32_t* mask,
+                                               float* samples_out, sps_hmc_stats* stats, void* stream) {
+    if (!ctx || !cfg) return fail(SPS_E_INVALID_ARG, "null argument");
+    if (ctx->n_gal <= 0) return fail(SPS_E_STATE, "no galaxy set");
+    if (cfg->mode != SPS_APPROX) return fail(SPS_E_UNSUPPORTED, "HMC runs on the approximate path");
+    if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (cfg->adapt_mass != 0) return fail(SPS_E_UNSUPPORTED, "the plain sampler uses the identity metric");
+    if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
+    if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
+        return fail(SPS_E_SHAPE, "iteration counts");
+    if (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096) return fail(SPS_E_SHAPE, "L range");
+    if (!(cfg->eps0 > 0) || !(cfg->target_accept > 0 && cfg->target_accept < 1))
+        return fail(SPS_E_INVALID_ARG, "eps0 / target_accept");
+    if (!theta0_unb || !mag_obs || !sigma || !mask) return fail(SPS_E_INVALID_ARG, "null input");
+    const int64_t G = ctx->n_gal;
+    const int C = cfg->chains_per_gal;
+    const int64_t NC = G * C;
+    if (NC > ((int64_t)1 << 31)) return fail(SPS_E_SHAPE, "too many chains");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const Consts& c = ctx->c;
+    const size_t GB = (size_t)G * c.n_band;
+    Stager st{ctx, s};
+    const float* x0 = st.in(theta0_unb, (size_t)NC * SPS_NPARAM);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)G);
+    float* so = st.out(samples_out, (size_t)NC * cfg->n_samp * SPS_NPARAM);
+    float* acc = stats ? st.out(stats->accept_prob, (size_t)NC) : nullptr;
+    float* epo = stats ? st.out(stats->step_size, (size_t)NC) : nullptr;
+    int32_t* dv = stats ? st.out(stats->divergences, (size_t)NC) : nullptr;
+    int64_t* nev = stats ? st.out(stats->grad_evals, (size_t)NC) : nullptr;
+    int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
+    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
+                 cfg->seed, 0};
+    // state, theta, FP64 log L, gradient, chain -> galaxy, forward-mode scratch
+    const int64_t chunk = std::min<int64_t>(NC, 32768);
+    CK(ctx->pst.reserve(sizeof(PlainChain) * (size_t)NC));
+    CK(ctx->pth.reserve(sizeof(float) * SPS_NPARAM * (size_t)NC));
+    CK(ctx->pll.reserve(sizeof(double) * (size_t)NC));
+    CK(ctx->pgr.reserve(sizeof(float) * SPS_NPARAM * (size_t)NC));
+    CK(ctx->pgi.reserve(sizeof(int32_t) * (size_t)NC));
+    CK(ctx->plainT.reserve((size_t)chunk * 9 * c.K * sizeof(float)));
+    CK(ctx->plainC.reserve((size_t)chunk * c.n_band * 9 * sizeof(float)));
+    PlainChain* pst = ctx->pst.as<PlainChain>();
+    float* th = ctx->pth.as<float>();
+    double* ll = ctx->pll.as<double>();
+    float* gr = ctx->pgr.as<float>();
+    int32_t* gi = ctx->pgi.as<int32_t>();
+    const Galaxies gal = ctx->gal();
+    auto gradient = [&](cudaStream_t q) -> cudaError_t {
+        for (int64_t r0 = 0; r0 < NC; r0 += chunk) {
+            const int64_t m = std::min(chunk, NC - r0);
+            cudaError_t e = launch_plain(c, gal, th + r0 * SPS_NPARAM, gi + r0, m, mo, sg, mk, nullptr,
+                                         gr + r0 * SPS_NPARAM, ctx->plainT.as<float>(),
+                                         ctx->plainC.as<float>(), q, ll + r0);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    // one iteration: start every trajectory, then L_max rounds of gradient + step
+    auto iteration = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = plain_hmc_start(c, hp, NC, pst, th, q);
+        for (int r = 0; r < hp.L_max && e == cudaSuccess; ++r) {
+            e = gradient(q);
+            if (e == cudaSuccess) e = plain_hmc_step(c, hp, NC, pst, ll, gr, th, so, q);
+        }
+        return e;
+    };
+    CK(plain_hmc_init(c, NC, C, x0, hp.eps0, pst, th, gi, s));
+    CK(gradient(s));
+    CK(plain_hmc_absorb(c, NC, pst, ll, gr, s));
+    const int n_it = hp.n_warm + hp.n_samp;
+    if (cfg->use_graph) {
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr_it;
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = iteration(cs);
+            cudaError_t e2 = cudaStreamEndCapture(cs, &gr_it);
+            e = (e1 != cudaSuccess) ? e1 : e2;
+            if (e == cudaSuccess) {
+                e = cudaGraphInstantiate(&ex, gr_it, 0);
+                cudaGraphDestroy(gr_it);
+            }
+        }
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "plain HMC capture");
+        for (int it = 0; it < n_it && e == cudaSuccess; ++it) e = cudaGraphLaunch(ex, s);
+        cudaGraphExecDestroy(ex);
+        if (e != cudaSuccess) return cuda_fail(e, "plain HMC launch");
+    } else {
+        for (int it = 0; it < n_it; ++it) CK(iteration(s));
+    }
+    CK(plain_hmc_stats(hp, NC, pst, acc, epo, dv, nev, sto, s));
+    CK(st.finish());
+    return SPS_OK;
+}

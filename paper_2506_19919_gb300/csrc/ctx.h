@@ -56,6 +56,7 @@ struct sps_ctx {
     // scratch
     DevBuf nonfinite, queue, err;
     DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
+    DevBuf pst, pth, pll, pgr, pgi;   // plain lock-step HMC state and gradient buffers
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -95,7 +96,8 @@ struct sps_ctx {
         DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
-                         &rowinfo, &tcerr, &plainT, &plainC, &hmcm};
+                         &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
+                         &pgi};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

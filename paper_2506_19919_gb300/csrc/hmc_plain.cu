@@ -1,0 +1,258 @@
+// Plain batched HMC: the comparison baseline for the fused persistent sampler
+// (Sec. 4, App. D.2), run as a straightforward GPU port of the paper's
+// vectorised sampler would run it.
+//
+// Every chain advances in lock step, one leapfrog step per round of kernel
+// launches: all chains start their trajectory together, and every round
+// evaluates the gradient of every chain with the unfused forward-mode path
+// (plain.cu) whether or not the chain's trajectory has already ended, up to
+// L_max rounds per iteration (a vectorised loop over chains runs until its
+// longest member finishes).  The sampler itself is the fused kernel's, step for
+// step: identity metric, Philox-4x32-10 draws with counter (iteration, block,
+// chain, 0), FP64 Box-Muller momenta, L = L_min + (w n) >> 32, leapfrog with
+// half kicks around each drift, FP64 energy accept, dual-averaged step size in
+// the warm-up and its average in the sampling phase.  One thread per chain.
+#include <math.h>
+
+#include "philox.cuh"
+#include "sps_internal.h"
+
+namespace sps {
+
+namespace {
+
+__device__ __forceinline__ void bound_param(const Consts& c, int k, float x, float& th, float& dth,
+                                            float& lpe, float& dlp) {
+    const float ex = __expf(-fabsf(x));
+    const float r = __frcp_rn(1.0f + ex);
+    const float sg = (x >= 0.0f) ? r : ex * r;        // 1 / (1 + e^-x)
+    th = c.prior_lo[k] + c.prior_span[k] * sg;
+    dth = c.prior_span[k] * sg * (1.0f - sg);
+    lpe = -fabsf(x) - 2.0f * __logf(1.0f + ex);       // log sg (1 - sg)
+    dlp = 1.0f - 2.0f * sg;
+}
+
+// theta = F_B(x) for the next gradient evaluation.
+__device__ __forceinline__ void write_theta(const Consts& c, const PlainChain& s, float* __restrict__ th) {
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        float t, d, l, q;
+        bound_param(c, k, s.x[k], t, d, l, q);
+        th[k] = t;
+    }
+}
+
+// log posterior and its gradient in unbounded space from the physical-space
+// log-likelihood and gradient at s.x.
+__device__ __forceinline__ void absorb(const Consts& c, PlainChain& s, double ll, const float* __restrict__ gth) {
+    double lpri = 0.0;
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        float t, d, l, q;
+        bound_param(c, k, s.x[k], t, d, l, q);
+        lpri += (double)l;
+        s.g[k] = gth[k] * d + q;
+    }
+    s.lp = ll + lpri;
+}
+
+__global__ void k_plain_init(const __grid_constant__ Consts c, int64_t n, int C, const float* __restrict__ x0,
+                             float eps0, PlainChain* __restrict__ st, float* __restrict__ theta,
+                             int32_t* __restrict__ gal_idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s;
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) s.x[k] = x0[i * SPS_NPARAM + k];
+    s.eps = eps0;
+    s.mu = log(10.0 * (double)eps0);
+    s.hbar = s.leb = s.acc = 0.0;
+    s.it = s.mda = s.ndiv = s.l = s.L = 0;
+    s.active = 0;
+    s.nev = 1;
+    st[i] = s;
+    write_theta(c, s, theta + i * SPS_NPARAM);
+    gal_idx[i] = (int32_t)(i / C);
+}
+
+__global__ void k_plain_absorb(const __grid_constant__ Consts c, int64_t n, PlainChain* __restrict__ st,
+                               const double* __restrict__ ll, const float* __restrict__ gth) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s = st[i];
+    absorb(c, s, ll[i], gth + i * SPS_NPARAM);
+    st[i] = s;
+}
+
+// Start of iteration s.it for every chain: momentum, start state, half kick, drift.
+__global__ void k_plain_start(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
+                              PlainChain* __restrict__ st, float* __restrict__ theta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s = st[i];
+    if (s.it >= hp.n_warm + hp.n_samp) {
+        s.active = 0;
+        st[i] = s;
+        return;
+    }
+    const uint32_t k0 = (uint32_t)(hp.seed & 0xffffffffu), k1 = (uint32_t)(hp.seed >> 32);
+    uint32_t w[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)s.it, (uint32_t)b, (uint32_t)i, 0u), k0, k1);
+        w[4 * b] = r.x;
+        w[4 * b + 1] = r.y;
+        w[4 * b + 2] = r.z;
+        w[4 * b + 3] = r.w;
+    }
+    double kin = 0.0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const double rr = sqrt(-2.0 * log(u01_d(w[2 * m])));
+        double sn, cs;
+        sincospi(2.0 * u01_d(w[2 * m + 1]), &sn, &cs);
+        s.p[2 * m] = (float)(rr * cs);
+        s.p[2 * m + 1] = (float)(rr * sn);
+    }
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        kin += (double)s.p[k] * (double)s.p[k];
+        s.xs[k] = s.x[k];
+        s.gs[k] = s.g[k];
+    }
+    s.uacc = u01_d(w[12]);
+    s.L = hp.L_min + (int)(((uint64_t)w[13] * (uint64_t)(hp.L_max - hp.L_min + 1)) >> 32);
+    s.l = 0;
+    s.lps = s.lp;
+    s.h0 = -s.lp + 0.5 * kin;
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+        s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
+    }
+    s.active = 1;
+    st[i] = s;
+    write_theta(c, s, theta + i * SPS_NPARAM);
+}
+
+// One leapfrog round after the gradient evaluation at every chain's x.
+__global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
+                             PlainChain* __restrict__ st, const double* __restrict__ ll,
+                             const float* __restrict__ gth, float* __restrict__ theta,
+                             float* __restrict__ samples) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s = st[i];
+    s.nev += 1;                                   // every round evaluates every chain
+    if (!s.active) {
+        st[i] = s;
+        return;
+    }
+    absorb(c, s, ll[i], gth + i * SPS_NPARAM);
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+    if (s.l + 1 < s.L) {
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) {
+            s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+            s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
+        }
+        s.l += 1;
+        st[i] = s;
+        write_theta(c, s, theta + i * SPS_NPARAM);
+        return;
+    }
+    // end of the trajectory: accept / reject, adaptation, sample
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) kin += (double)s.p[k] * (double)s.p[k];
+    const double dH = (-s.lp + 0.5 * kin) - s.h0;
+    const bool fin = isfinite(dH);
+    const double a = fin ? fmin(1.0, exp(-dH)) : 0.0;
+    const bool take = fin && log(s.uacc) < -dH;
+    if (!take) {
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) {
+            s.x[k] = s.xs[k];
+            s.g[k] = s.gs[k];
+        }
+        s.lp = s.lps;
+    }
+    if (!fin || dH > 1000.0) s.ndiv += 1;
+    const int it = s.it;
+    if (it < hp.n_warm) {
+        const double m = (double)(s.mda + 1);
+        const double hbar = (1.0 - 1.0 / (m + 10.0)) * s.hbar + ((double)hp.target_accept - a) / (m + 10.0);
+        const double log_eps = s.mu - sqrt(m) / 0.05 * hbar;
+        const double wgt = exp(-0.75 * log(m));
+        const double leb = wgt * log_eps + (1.0 - wgt) * s.leb;
+        s.eps = (float)exp(it < hp.n_warm - 1 ? log_eps : leb);
+        s.mda += 1;
+        s.hbar = hbar;
+        s.leb = leb;
+    } else {
+        s.acc += a;
+        if (samples) {
+            float* o = samples + ((size_t)i * hp.n_samp + (it - hp.n_warm)) * SPS_NPARAM;
+#pragma unroll
+            for (int k = 0; k < SPS_NPARAM; ++k)
+                o[k] = c.prior_lo[k] + c.prior_span[k] / (1.0f + __expf(-s.x[k]));
+        }
+    }
+    s.it = it + 1;
+    s.active = 0;
+    st[i] = s;
+}
+
+__global__ void k_plain_stats(const HmcParams hp, int64_t n, const PlainChain* __restrict__ st, float* acc,
+                              float* eps_out, int32_t* div_out, int64_t* nev_out, int32_t* status_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PlainChain& s = st[i];
+    if (acc) acc[i] = (float)(s.acc / (double)max(hp.n_samp, 1));
+    if (eps_out) eps_out[i] = s.eps;
+    if (div_out) div_out[i] = s.ndiv;
+    if (nev_out) nev_out[i] = s.nev;
+    if (status_out) status_out[i] = 0;
+}
+
+inline unsigned grid_for(int64_t n) { return (unsigned)((n + 127) / 128); }
+
+}  // namespace
+
+cudaError_t plain_hmc_init(const Consts& c, int64_t n, int C, const float* x0, float eps0, PlainChain* st,
+                           float* theta, int32_t* gal_idx, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_plain_init<<<grid_for(n), 128, 0, s>>>(c, n, C, x0, eps0, st, theta, gal_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t plain_hmc_absorb(const Consts& c, int64_t n, PlainChain* st, const double* ll, const float* gth,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_plain_absorb<<<grid_for(n), 128, 0, s>>>(c, n, st, ll, gth);
+    return cudaGetLastError();
+}
+
+cudaError_t plain_hmc_start(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, float* theta,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_plain_start<<<grid_for(n), 128, 0, s>>>(c, hp, n, st, theta);
+    return cudaGetLastError();
+}
+
+cudaError_t plain_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, const double* ll,
+                           const float* gth, float* theta, float* samples, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_plain_step<<<grid_for(n), 128, 0, s>>>(c, hp, n, st, ll, gth, theta, samples);
+    return cudaGetLastError();
+}
+
+cudaError_t plain_hmc_stats(const HmcParams& hp, int64_t n, const PlainChain* st, float* acc, float* eps_out,
+                            int32_t* div_out, int64_t* nev_out, int32_t* status_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_plain_stats<<<grid_for(n), 128, 0, s>>>(hp, n, st, acc, eps_out, div_out, nev_out, status_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sps

@@ -384,6 +384,37 @@ __device__ __forceinline__ void win_set_end(int& start, int& end, int width, int
     if (width <= 0 || start >= stop) start = end = 0x7fffffff;
 }
 
+// Window end of the dense metric: regularised covariance (n/(n+5)) S + 1e-3
+// (5/(n+5)) I of the window's co-moments, replaced by its Cholesky factor in
+// place; a factorisation that fails keeps the previous metric.  One thread.
+__device__ __noinline__ void dense_metric_update(ChainMetric* cm, int wn) {
+    const float a = (float)wn / (wn + 5.0f), b = 1e-3f * (5.0f / (wn + 5.0f));
+    const float inv = 1.0f / ((float)wn - 1.0f);
+    float Lm[78];
+#pragma unroll 1
+    for (int e = 0; e < 78; ++e) Lm[e] = a * cm->wcov[e] * inv;
+#pragma unroll 1
+    for (int i = 0; i < SPS_NPARAM; ++i) Lm[tri(i, i)] += b;
+#pragma unroll 1
+    for (int j = 0; j < SPS_NPARAM; ++j) {
+        float dgl = Lm[tri(j, j)];
+#pragma unroll 1
+        for (int k = 0; k < j; ++k) dgl -= Lm[tri(j, k)] * Lm[tri(j, k)];
+        if (!(dgl > 0.0f)) return;
+        const float ljj = sqrtf(dgl);
+        Lm[tri(j, j)] = ljj;
+#pragma unroll 1
+        for (int i = j + 1; i < SPS_NPARAM; ++i) {
+            float sv = Lm[tri(i, j)];
+#pragma unroll 1
+            for (int k = 0; k < j; ++k) sv -= Lm[tri(i, k)] * Lm[tri(j, k)];
+            Lm[tri(i, j)] = sv / ljj;
+        }
+    }
+#pragma unroll 1
+    for (int e = 0; e < 78; ++e) cm->chol[e] = Lm[e];
+}
+
 // End of chain ch's trajectory: accept / reject, adaptation, sample.
 template <int CPW>
 __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
@@ -410,7 +441,7 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
         const double m = (double)(t.mda[ch] + 1);
         const double hbar = (1.0 - 1.0 / (m + 10.0)) * t.hbar[ch] + ((double)hp.target_accept - a) / (m + 10.0);
         const double log_eps = t.mu[ch] - sqrt(m) / 0.05 * hbar;
-        const double wgt = pow(m, -0.75);
+        const double wgt = exp(-0.75 * log(m));
         const double leb = wgt * log_eps + (1.0 - wgt) * t.leb[ch];
         const float eps = (float)exp(it < hp.n_warm - 1 ? log_eps : leb);
         __syncwarp();
@@ -449,31 +480,7 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
                     const double var = t.cm[ch]->wm2[lane] / ((double)wn - 1.0);
                     t.minv[ch][lane] = (float)(((double)wn / (wn + 5.0)) * var + 1e-3 * (5.0 / (wn + 5.0)));
                 }
-                if (wn >= 2 && dense && lane == 0) {
-                    // regularised covariance, then its Cholesky factor in place
-                    const float a = (float)wn / (wn + 5.0f), b = 1e-3f * (5.0f / (wn + 5.0f));
-                    float Lm[78];
-                    for (int e = 0; e < 78; ++e) Lm[e] = a * t.cm[ch]->wcov[e] / ((float)wn - 1.0f);
-                    for (int i = 0; i < SPS_NPARAM; ++i) Lm[tri(i, i)] += b;
-                    bool ok = true;
-                    for (int j = 0; j < SPS_NPARAM && ok; ++j) {
-                        float dgl = Lm[tri(j, j)];
-                        for (int k = 0; k < j; ++k) dgl -= Lm[tri(j, k)] * Lm[tri(j, k)];
-                        if (!(dgl > 0.0f)) {
-                            ok = false;
-                            break;
-                        }
-                        const float ljj = sqrtf(dgl);
-                        Lm[tri(j, j)] = ljj;
-                        for (int i = j + 1; i < SPS_NPARAM; ++i) {
-                            float sv = Lm[tri(i, j)];
-                            for (int k = 0; k < j; ++k) sv -= Lm[tri(i, k)] * Lm[tri(j, k)];
-                            Lm[tri(i, j)] = sv / ljj;
-                        }
-                    }
-                    if (ok)
-                        for (int e = 0; e < 78; ++e) t.cm[ch]->chol[e] = Lm[e];
-                }
+                if (wn >= 2 && dense && lane == 0) dense_metric_update(t.cm[ch], wn);
                 if (lane < SPS_NPARAM) {
                     t.cm[ch]->wmean[lane] = 0.0;
                     t.cm[ch]->wm2[lane] = 0.0;

@@ -121,7 +121,8 @@ __global__ void k_plain_like(const __grid_constant__ Consts c, const Galaxies g,
                              const float* __restrict__ theta, const int32_t* __restrict__ gal_idx,
                              int64_t n, const float* __restrict__ cd, const float* __restrict__ mag_obs,
                              const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
-                             float* __restrict__ ll_out, float* __restrict__ grad_out) {
+                             float* __restrict__ ll_out, float* __restrict__ grad_out,
+                             double* __restrict__ ll64_out) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const int B = c.n_band;
@@ -159,7 +160,8 @@ __global__ void k_plain_like(const __grid_constant__ Consts c, const Galaxies g,
         gr[10] += gF * d.dF_delta;
         gr[11] += gF * d.dF_floor;
     }
-    ll_out[row] = (float)ll;
+    if (ll_out) ll_out[row] = (float)ll;
+    if (ll64_out) ll64_out[row] = ll;
     if (grad_out)
 #pragma unroll
         for (int k = 0; k < SPS_NPARAM; ++k) grad_out[row * SPS_NPARAM + k] = gr[k];
@@ -174,7 +176,7 @@ size_t plain_scratch_bytes_per_row(const Consts& c) {
 cudaError_t launch_plain(const Consts& c, const Galaxies& g, const float* theta,
                          const int32_t* gal_idx, int64_t n, const float* mag_obs,
                          const float* sigma, const uint32_t* mask, float* ll_out, float* grad_out,
-                         float* T, float* cd, cudaStream_t s) {
+                         float* T, float* cd, cudaStream_t s, double* ll64_out) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + kWarpsApprox - 1) / kWarpsApprox;
     if (blocks > 152LL * 64) blocks = 152LL * 64;
@@ -185,7 +187,7 @@ cudaError_t launch_plain(const Consts& c, const Galaxies& g, const float* theta,
     k_plain_contract<<<(unsigned)((items + 7) / 8), 256, 0, s>>>(c, g, gal_idx, n, T, cd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_plain_like<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, g, theta, gal_idx, n, cd, mag_obs, sigma,
-                                                             mask, ll_out, grad_out);
+                                                             mask, ll_out, grad_out, ll64_out);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,15 @@ struct ChainMetric {
     float wcov[78];                              // window co-moments (dense)
 };
 
+// State of one chain of the plain lock-step HMC (hmc_plain.cu).
+struct PlainChain {
+    float x[SPS_NPARAM], p[SPS_NPARAM], g[SPS_NPARAM], xs[SPS_NPARAM], gs[SPS_NPARAM];
+    double lp, lps, h0, mu, hbar, leb, acc, uacc;
+    float eps;
+    int L, l, it, mda, ndiv, active;
+    long long nev;
+};
+
 // Records the message returned by sps_last_error_message() on this thread.
 void set_last_error(const char* msg);
 
@@ -123,7 +132,7 @@ size_t plain_scratch_bytes_per_row(const Consts& c);
 cudaError_t launch_plain(const Consts& c, const Galaxies& g, const float* theta,
                          const int32_t* gal_idx, int64_t n, const float* mag_obs,
                          const float* sigma, const uint32_t* mask, float* ll_out, float* grad_out,
-                         float* T, float* cd, cudaStream_t s);
+                         float* T, float* cd, cudaStream_t s, double* ll64_out = nullptr);
 
 cudaError_t launch_weights_rows(const Consts& c, const Galaxies& g, const float* theta,
                                 const int32_t* gal_idx, int64_t n, float* W_out,
@@ -147,6 +156,16 @@ cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const H
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
                             int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                             cudaStream_t s);
+cudaError_t plain_hmc_init(const Consts& c, int64_t n, int C, const float* x0, float eps0, PlainChain* st,
+                           float* theta, int32_t* gal_idx, cudaStream_t s);
+cudaError_t plain_hmc_absorb(const Consts& c, int64_t n, PlainChain* st, const double* ll, const float* gth,
+                             cudaStream_t s);
+cudaError_t plain_hmc_start(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, float* theta,
+                            cudaStream_t s);
+cudaError_t plain_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, const double* ll,
+                           const float* gth, float* theta, float* samples, cudaStream_t s);
+cudaError_t plain_hmc_stats(const HmcParams& hp, int64_t n, const PlainChain* st, float* acc, float* eps_out,
+                            int32_t* div_out, int64_t* nev_out, int32_t* status_out, cudaStream_t s);
 cudaError_t launch_leapfrog(const Consts& c, const Galaxies& g, const float* x0,
                             const float* p0, const float* eps, const int32_t* L,
                             const int32_t* gal_idx, int64_t n, const float* mag_obs,

@@ -199,10 +199,12 @@ class _Prior:
         return lp, 1.0 - 2.0 / (1.0 + np.exp(-x))
 
 
-def test_hmc_prior_only_matches_oracle_draws(parity64):
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_hmc_prior_only_matches_oracle_draws(parity64, path):
     """At a fixed step size the GPU chains reproduce the oracle's chains draw by
     draw (same Philox stream, same leapfrog, same accept rule), up to FP32
-    rounding.  (With adaptation on, the dual-averaging feedback amplifies
+    rounding, for the fused sampler and for the lock-step forward-mode
+    baseline.  (With adaptation on, the dual-averaging feedback amplifies
     rounding differences iteration by iteration, so adaptation is checked by
     distribution below.)"""
     wl, ctx = parity64
@@ -210,7 +212,7 @@ def test_hmc_prior_only_matches_oracle_draws(parity64):
     x0 = np.random.default_rng(1).normal(0, 1.5, size=(64 * C, 12)).astype(np.float32)
     mask = np.zeros(64, np.uint32)
     out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), mask, chains_per_gal=C, n_warm=0,
-                      n_samp=30, L_min=4, L_max=12, seed=99, eps0=0.7)
+                      n_samp=30, L_min=4, L_max=12, seed=99, eps0=0.7, path=path)
     s = out["samples"].cpu().numpy()
     ref = OH.run_hmc(_Prior(), x0.astype(np.float64), np.zeros(64 * C, int), seed=99, n_warm=0,
                      n_samp=30, L_min=4, L_max=12, eps0=0.7)
@@ -218,13 +220,18 @@ def test_hmc_prior_only_matches_oracle_draws(parity64):
     d = np.abs((s - W.PRIOR_LO) / span - (ref["samples"] - W.PRIOR_LO) / span).max(axis=(1, 2))
     assert (d < 1e-4).mean() > 0.97          # an accept decision may flip at |dH + ln u| ~ 1e-6
     np.testing.assert_allclose(out["accept_prob"].cpu().numpy(), ref["accept_prob"], atol=2e-2)
-    assert (out["grad_evals"].cpu().numpy() == ref["grad_evals"] + 1).all()
+    nev = out["grad_evals"].cpu().numpy()
+    if path == "fused":
+        assert (nev == ref["grad_evals"] + 1).all()
+    else:                                    # every round evaluates every chain
+        assert (nev == 1 + 30 * 12).all()
 
 
-def test_hmc_with_likelihood_matches_oracle_draws(prod96):
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_hmc_with_likelihood_matches_oracle_draws(prod96, path):
     """The batched sampler with the photometric likelihood on (4 chains per
-    galaxy evaluated in lock step): at a fixed step size its draws follow the
-    oracle's HMC draw by draw."""
+    galaxy evaluated in lock step), and the forward-mode lock-step baseline:
+    at a fixed step size their draws follow the oracle's HMC draw by draw."""
     wl, ctx = prod96
     G, C = 3, 4
     th_true = torch.as_tensor(wl.theta_true[:G], dtype=torch.float64)
@@ -238,7 +245,7 @@ def test_hmc_with_likelihood_matches_oracle_draws(prod96):
     x0_all = np.zeros((wl.n_gal * C, 12), np.float32)
     x0_all[:G * C] = x0
     out = ctx.hmc_run(x0_all, mobs_all, wl.sigma, mask, chains_per_gal=C, n_warm=0, n_samp=6,
-                      L_min=6, L_max=6, seed=11, eps0=2e-3, autotune=False)
+                      L_min=6, L_max=6, seed=11, eps0=2e-3, autotune=False, path=path)
     s = out["samples"].cpu().numpy()[:G * C]
     tgt = OH.ApproxTarget(wl.tables, wl.z[:G], mobs, wl.sigma[:G], wl.mask[:G], W.PRIOR_LO,
                           W.PRIOR_HI)
@@ -268,6 +275,13 @@ def test_hmc_adaptation_matches_oracle_statistically(parity64):
         assert np.median(eg) == pytest.approx(np.median(er), rel=0.15), gpu_mode
         assert out["accept_prob"].cpu().numpy().mean() == pytest.approx(ref["accept_prob"].mean(),
                                                                          abs=0.05), gpu_mode
+        if gpu_mode == 0:
+            pl = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32),
+                             chains_per_gal=C, n_warm=200, n_samp=50, L_min=4, L_max=12, seed=7,
+                             path="plain")
+            assert np.median(pl["step_size"].cpu().numpy()) == pytest.approx(np.median(er), rel=0.15)
+            assert pl["accept_prob"].cpu().numpy().mean() == pytest.approx(
+                ref["accept_prob"].mean(), abs=0.05)
 
 
 def test_hmc_prior_only_is_uniform(parity64):
