@@ -804,9 +804,11 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     // launch shapes: chains of a galaxy per warp (cpw) x warps per block; the
     // grid is persistent (occupancy x SMs) and pulls (galaxy, chain group)
     // items from the queue
-    const int cpw0 = C >= 4 ? 4 : (C >= 2 ? 2 : 1);
-    std::vector<std::pair<int, int>> cands = {{cpw0, 2}, {cpw0, 4}};
-    if (cpw0 == 4) cands.push_back({2, 4});
+    // first candidate = default; another replaces it only if >3% faster in the probe
+    std::vector<std::pair<int, int>> cands = {{1, 8}, {1, 16}};
+    if (C >= 2) cands.insert(cands.begin(), {{2, 4}, {2, 8}, {2, 16}});
+    if (C >= 4) cands.push_back({4, 8});
+    const int cpw0 = cands[0].first;
     auto blocks_for = [&](int cpw, int warps, int& blocks) -> cudaError_t {
         int per_sm = 0;
         cudaError_t e = hmc_team_occupancy(cpw, warps, &per_sm);
@@ -815,9 +817,16 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         return cudaSuccess;
     };
     const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max);
-    int cpw = cpw0, warps = 4, blocks = sms;
+    int cpw = cpw0, warps = cands[0].second, blocks = sms;
     auto it = ctx->tuned.find(key);
-    if (it != ctx->tuned.end()) {
+    const char* force = std::getenv("SPS_HMC_SHAPE");   // "cpw,warps": fixed launch shape
+    int fc = 0, fw = 0;
+    if (force && std::sscanf(force, "%d,%d", &fc, &fw) == 2 && (fc == 1 || fc == 2 || fc == 4) &&
+        fc <= std::max(C, 1) && fw >= 1 && fw <= 16) {
+        cpw = fc;
+        warps = fw;
+        CK(blocks_for(cpw, warps, blocks));
+    } else if (it != ctx->tuned.end()) {
         cpw = it->second.first / 100;
         warps = it->second.first % 100;
         blocks = it->second.second;
@@ -828,7 +837,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         HmcParams tp = hp;
-        tp.n_warm = 3;
+        tp.n_warm = 8;
         tp.n_samp = 0;
         Galaxies gsub = ctx->gal();
         for (auto cw : cands) {
@@ -845,7 +854,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             const float per = ms / (float)(gsub.n * C);
-            if (per < best) {
+            if (cw == cands[0] ? per < best : per < 0.97f * best) {
                 best = per;
                 cpw = cw.first;
                 warps = cw.second;

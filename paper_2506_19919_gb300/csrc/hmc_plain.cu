@@ -9,9 +9,10 @@
 // L_max rounds per iteration (a vectorised loop over chains runs until its
 // longest member finishes).  The sampler itself is the fused kernel's, step for
 // step: identity metric, Philox-4x32-10 draws with counter (iteration, block,
-// chain, 0), FP64 Box-Muller momenta, L = L_min + (w n) >> 32, leapfrog with
-// half kicks around each drift, FP64 energy accept, dual-averaged step size in
-// the warm-up and its average in the sampling phase.  One thread per chain.
+// chain, 0), Box-Muller momenta, L = L_min + (w n) >> 32, leapfrog with half
+// kicks around each drift, accept on the FP64 energy difference, dual-averaged
+// step size in the warm-up and its average in the sampling phase.  One thread
+// per chain.
 #include <math.h>
 
 #include "philox.cuh"
@@ -65,8 +66,8 @@ __global__ void k_plain_init(const __grid_constant__ Consts c, int64_t n, int C,
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) s.x[k] = x0[i * SPS_NPARAM + k];
     s.eps = eps0;
-    s.mu = log(10.0 * (double)eps0);
-    s.hbar = s.leb = s.acc = 0.0;
+    s.mu = logf(10.0f * eps0);
+    s.hbar = s.leb = s.acc = 0.0f;
     s.it = s.mda = s.ndiv = s.l = s.L = 0;
     s.active = 0;
     s.nev = 1;
@@ -105,26 +106,26 @@ __global__ void k_plain_start(const __grid_constant__ Consts c, const HmcParams 
         w[4 * b + 2] = r.z;
         w[4 * b + 3] = r.w;
     }
-    double kin = 0.0;
+    float kin = 0.0f;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-        const double rr = sqrt(-2.0 * log(u01_d(w[2 * m])));
-        double sn, cs;
-        sincospi(2.0 * u01_d(w[2 * m + 1]), &sn, &cs);
-        s.p[2 * m] = (float)(rr * cs);
-        s.p[2 * m + 1] = (float)(rr * sn);
+        const float rr = sqrtf(-2.0f * logf(u01_f(w[2 * m])));
+        float sn, cs;
+        sincospif(2.0f * u01_f(w[2 * m + 1]), &sn, &cs);
+        s.p[2 * m] = rr * cs;
+        s.p[2 * m + 1] = rr * sn;
     }
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) {
-        kin += (double)s.p[k] * (double)s.p[k];
+        kin = fmaf(s.p[k], s.p[k], kin);
         s.xs[k] = s.x[k];
         s.gs[k] = s.g[k];
     }
-    s.uacc = u01_d(w[12]);
+    s.uacc = (double)logf(u01_f(w[12]));
     s.L = hp.L_min + (int)(((uint64_t)w[13] * (uint64_t)(hp.L_max - hp.L_min + 1)) >> 32);
     s.l = 0;
     s.lps = s.lp;
-    s.h0 = -s.lp + 0.5 * kin;
+    s.h0 = -s.lp + 0.5 * (double)kin;
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) {
         s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
@@ -163,13 +164,13 @@ __global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams h
         return;
     }
     // end of the trajectory: accept / reject, adaptation, sample
-    double kin = 0.0;
+    float kin = 0.0f;
 #pragma unroll
-    for (int k = 0; k < SPS_NPARAM; ++k) kin += (double)s.p[k] * (double)s.p[k];
-    const double dH = (-s.lp + 0.5 * kin) - s.h0;
+    for (int k = 0; k < SPS_NPARAM; ++k) kin = fmaf(s.p[k], s.p[k], kin);
+    const double dH = (-s.lp + 0.5 * (double)kin) - s.h0;
     const bool fin = isfinite(dH);
-    const double a = fin ? fmin(1.0, exp(-dH)) : 0.0;
-    const bool take = fin && log(s.uacc) < -dH;
+    const float a = fin ? fminf(1.0f, __expf(-(float)dH)) : 0.0f;
+    const bool take = fin && s.uacc < -dH;
     if (!take) {
 #pragma unroll
         for (int k = 0; k < SPS_NPARAM; ++k) {
@@ -181,12 +182,13 @@ __global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams h
     if (!fin || dH > 1000.0) s.ndiv += 1;
     const int it = s.it;
     if (it < hp.n_warm) {
-        const double m = (double)(s.mda + 1);
-        const double hbar = (1.0 - 1.0 / (m + 10.0)) * s.hbar + ((double)hp.target_accept - a) / (m + 10.0);
-        const double log_eps = s.mu - sqrt(m) / 0.05 * hbar;
-        const double wgt = exp(-0.75 * log(m));
-        const double leb = wgt * log_eps + (1.0 - wgt) * s.leb;
-        s.eps = (float)exp(it < hp.n_warm - 1 ? log_eps : leb);
+        const float m = (float)(s.mda + 1);
+        const float im = __frcp_rn(m + 10.0f);
+        const float hbar = (1.0f - im) * s.hbar + (hp.target_accept - a) * im;
+        const float log_eps = s.mu - sqrtf(m) * 20.0f * hbar;
+        const float wgt = exp2f(-0.75f * log2f(m));
+        const float leb = wgt * log_eps + (1.0f - wgt) * s.leb;
+        s.eps = expf(it < hp.n_warm - 1 ? log_eps : leb);
         s.mda += 1;
         s.hbar = hbar;
         s.leb = leb;
@@ -209,7 +211,7 @@ __global__ void k_plain_stats(const HmcParams hp, int64_t n, const PlainChain* _
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const PlainChain& s = st[i];
-    if (acc) acc[i] = (float)(s.acc / (double)max(hp.n_samp, 1));
+    if (acc) acc[i] = s.acc / (float)max(hp.n_samp, 1);
     if (eps_out) eps_out[i] = s.eps;
     if (div_out) div_out[i] = s.ndiv;
     if (nev_out) nev_out[i] = s.nev;

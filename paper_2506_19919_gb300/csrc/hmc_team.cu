@@ -44,6 +44,8 @@ struct TeamWork {
     float gd[CPW][4];                       // d logL / d(lgM, A_V, delta, F_floor)
     float S[CPW][kMaxBands], gh[CPW][kMaxBands];
     // galaxy slots
+    float2 bins[kMaxAges];                  // age bins of the galaxy (centre, half-width in ln t)
+    float lnT, lT10;                        // ln t_obs [Gyr], log10 t_obs [yr]
     const float* ptr[kMaxBands];
     float4 dust[kMaxBands];
     double zp[kMaxBands];
@@ -52,10 +54,10 @@ struct TeamWork {
     float x[CPW][SPS_NPARAM], p[CPW][SPS_NPARAM], g[CPW][SPS_NPARAM];
     float xs[CPW][SPS_NPARAM], gs[CPW][SPS_NPARAM], minv[CPW][SPS_NPARAM];
     double lp[CPW], lps[CPW], h0[CPW];
-    double mu[CPW], hbar[CPW], leb[CPW], acc[CPW];
+    float mu[CPW], hbar[CPW], leb[CPW], acc[CPW];   // dual averaging, accept sum
     ChainMetric* cm[CPW];                   // metric-adaptation state (global memory)
     float v[CPW][SPS_NPARAM], lu[CPW][SPS_NPARAM], dv[CPW][2][SPS_NPARAM];
-    double uacc[CPW];
+    double uacc[CPW];                       // log of the accept uniform
     float eps[CPW];
     int L[CPW], l[CPW], it[CPW], mda[CPW], wn[CPW], ndiv[CPW], done[CPW];
     int wstart[CPW], wend[CPW], wwidth[CPW], wstop[CPW];
@@ -63,10 +65,16 @@ struct TeamWork {
     uint32_t chain[CPW];
 };
 
+// Age and metallicity bin edges of the tables, staged once per block.
+struct EdgeTables {
+    float age[kMaxAges + 1];
+    float lgz[kMaxMets + 1];
+};
+
 template <int CPW>
-__device__ __forceinline__ AgeView age_view(TeamWork<CPW>& t, int ch) {
+__device__ __forceinline__ AgeView age_view(TeamWork<CPW>& t, int ch, const EdgeTables& et) {
     return AgeView{t.m[ch], t.dm0[ch], t.dm1[ch], t.dm2[ch], t.pi[ch], t.w[ch], t.w[ch],
-                   t.q[ch], t.qb[ch], &t.u.ps};
+                   t.q[ch], t.qb[ch], &t.u.ps, et.age, et.lgz};
 }
 
 // Row i of a band's c_SSP table: Zn consecutive floats.
@@ -86,10 +94,11 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, int Zn, fl
 // log posterior (unbounded space) and its gradient for every chain of the
 // team at t.x; writes t.lp and t.g.
 template <int CPW>
-__device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, const float2* __restrict__ bins,
-                          float lnT, float lT10, int nb) {
+__device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, const EdgeTables& et,
+                                          float lnT, float lT10, int nb) {
     const int lane = lane_id();
     const int A = c.n_age, Zn = c.n_met;
+#pragma unroll 1
     for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
         const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
         const float x = t.x[ch][k];
@@ -108,7 +117,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
     }
 #pragma unroll 1
     for (int ch = 0; ch < CPW; ++ch) {
-        const double M = age_met_weights(c, age_view(t, ch), bins, lnT, lT10, t.th[ch], true);
+        const double M = age_met_weights(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
         if (lane == 0) t.M[ch] = M;
     }
     __syncwarp();
@@ -124,6 +133,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             wl[ch][tt] = (i < A) ? t.w[ch][i] : 0.0f;
         }
     }
+#pragma unroll 1
     for (int b = 0; b < nb; ++b) {
         const float* C = t.ptr[b];
         float sacc[CPW];
@@ -152,18 +162,24 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
     }
     __syncwarp();
     // ---- magnitudes, likelihood and dust / lgM gradients per (chain, band)
+#pragma unroll 1
     for (int e = lane; e < CPW * nb; e += 32) {
         const int ch = e / nb, b = e - ch * nb;
         const float4 dc = t.dust[b];
         const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
         const float Sv = t.S[ch][b];
-        const double lc = log10((double)d.F * (double)Sv) + (double)t.th[ch][0] + 9.0;
+        // log10(F S): F S = f 2^e with f in [0.5, 1); e ln 2 exact in FP64, ln f to
+        // ~6e-8 absolute in FP32, the sum and the magnitude in FP64
+        int e2;
+        const float f = frexpf(d.F * Sv, &e2);
+        const double lc = fma((double)e2, 0.6931471805599453, (double)logf(f)) * 0.4342944819032518 +
+                          ((double)t.th[ch][0] + 9.0);
         const double r = (t.zp[b] - 2.5 * lc) - (double)t.mobs[b];
         const double is2 = (double)t.isig2[b];
         t.u.t.tll[ch][b] = -0.5 * r * r * is2;
-        const float gam = (float)(2.5 * r * is2 / 2.302585092994046);
-        const float gF = gam / d.F;
-        t.gh[ch][b] = gam / Sv;
+        const float gam = (float)(r * is2 * 1.0857362047581294);   // 2.5 / ln 10
+        const float gF = __fdividef(gam, d.F);
+        t.gh[ch][b] = __fdividef(gam, Sv);
         t.u.t.tg[ch][b][0] = gam * kLn10f;
         t.u.t.tg[ch][b][1] = gF * d.dF_AV;
         t.u.t.tg[ch][b][2] = gF * d.dF_delta;
@@ -205,6 +221,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
 #pragma unroll
         for (int j = 0; j < kZnReg; ++j) cv[j] = 0.0f;
         if (nb > 0) load_row(t.ptr[0] + i * Zn, Zn, cv);
+#pragma unroll 1
         for (int b = 0; b < nb; ++b) {
             float cn[kZnReg];
             if (b + 1 < nb) load_row(t.ptr[b + 1] + i * Zn, Zn, cn);
@@ -254,13 +271,13 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         gr[9] = t.gd[ch][1];
         gr[10] = t.gd[ch][2];
         gr[11] = t.gd[ch][3];
-        age_met_adjoint(c, age_view(t, ch), lT10, t.M[ch], t.th[ch], gr);
+        age_met_adjoint(c, age_view(t, ch, et), lT10, t.M[ch], t.th[ch], gr);
         if (lane < SPS_NPARAM) {
             float v = gr[0];
 #pragma unroll
             for (int k = 1; k < SPS_NPARAM; ++k)
                 if (lane == k) v = gr[k];
-            const float sg = 1.0f / (1.0f + __expf(-t.x[ch][lane]));
+            const float sg = __frcp_rn(1.0f + __expf(-t.x[ch][lane]));
             t.g[ch][lane] = v * t.dth[ch][lane] + (1.0f - 2.0f * sg);
         }
         if (lane == 0) t.lp[ch] = t.ll[ch] + t.lpri[ch];
@@ -271,7 +288,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
 // Draws of iteration `it` for one chain (FP64 Box-Muller): z[12] and, in
 // lane 0's view, the accept uniform and L (all lanes get them).
 __device__ __forceinline__ void team_draws(uint64_t seed, uint32_t chain, uint32_t it, int L_min,
-                                           int L_max, float* z, double& u_acc, int& L) {
+                                           int L_max, float* z, double& log_u, int& L) {
     const int lane = lane_id();
     uint4 w = make_uint4(0, 0, 0, 0);
     if (lane < 4)
@@ -286,31 +303,26 @@ __device__ __forceinline__ void team_draws(uint64_t seed, uint32_t chain, uint32
     const int sa = ia & 3, sb = ib & 3;
     const uint32_t wa = sa == 0 ? ax : sa == 1 ? ay : sa == 2 ? az : aw;
     const uint32_t wb = sb == 0 ? bx : sb == 1 ? by : sb == 2 ? bz : bw;
-    const double r = sqrt(-2.0 * log(u01_d(wa)));
-    double sn, cs;
-    sincospi(2.0 * u01_d(wb), &sn, &cs);
-    const double z0 = r * cs, z1 = r * sn;
+    const float r = sqrtf(-2.0f * logf(u01_f(wa)));
+    float sn, cs;
+    sincospif(2.0f * u01_f(wb), &sn, &cs);
+    const float z0 = r * cs, z1 = r * sn;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         z[2 * k] = (float)__shfl_sync(kFull, z0, k);
         z[2 * k + 1] = (float)__shfl_sync(kFull, z1, k);
     }
     const uint32_t w30 = __shfl_sync(kFull, w.x, 3), w31 = __shfl_sync(kFull, w.y, 3);
-    u_acc = u01_d(w30);
+    log_u = (double)logf(u01_f(w30));
     L = L_min + (int)(((uint64_t)w31 * (uint64_t)(L_max - L_min + 1)) >> 32);
 }
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// v = Minv p for chain ch (diagonal minv, or dense L L^T).
+// v = L L^T p for chain ch (dense metric).
 template <int CPW>
-__device__ __forceinline__ void metric_apply(TeamWork<CPW>& t, int ch, bool dense) {
+__device__ __noinline__ void metric_apply_dense(TeamWork<CPW>& t, int ch) {
     const int lane = lane_id();
-    if (!dense) {
-        if (lane < SPS_NPARAM) t.v[ch][lane] = t.minv[ch][lane] * t.p[ch][lane];
-        __syncwarp();
-        return;
-    }
     if (lane < SPS_NPARAM) {
         float a = 0.0f;
         for (int k = lane; k < SPS_NPARAM; ++k) a = fmaf(t.cm[ch]->chol[tri(k, lane)], t.p[ch][k], a);
@@ -325,13 +337,37 @@ __device__ __forceinline__ void metric_apply(TeamWork<CPW>& t, int ch, bool dens
     __syncwarp();
 }
 
+// v = Minv p for chain ch (diagonal minv, or dense L L^T).
+template <int CPW>
+__device__ __forceinline__ void metric_apply(TeamWork<CPW>& t, int ch, bool dense) {
+    if (dense) {
+        metric_apply_dense(t, ch);
+        return;
+    }
+    const int lane = lane_id();
+    if (lane < SPS_NPARAM) t.v[ch][lane] = t.minv[ch][lane] * t.p[ch][lane];
+    __syncwarp();
+}
+
+// p = L^-T p by back substitution (dense metric; one thread).
+template <int CPW>
+__device__ __noinline__ void dense_momentum(TeamWork<CPW>& t, int ch) {
+#pragma unroll 1
+    for (int i = SPS_NPARAM - 1; i >= 0; --i) {
+        float a = t.p[ch][i];
+#pragma unroll 1
+        for (int k = i + 1; k < SPS_NPARAM; ++k) a -= t.cm[ch]->chol[tri(k, i)] * t.p[ch][k];
+        t.p[ch][i] = a / t.cm[ch]->chol[tri(i, i)];
+    }
+}
+
 // p^T Minv p / 2 (needs metric_apply first).
 template <int CPW>
 __device__ __forceinline__ double kinetic(TeamWork<CPW>& t, int ch) {
     const int lane = lane_id();
-    double v = 0.0;
-    if (lane < SPS_NPARAM) v = (double)t.p[ch][lane] * (double)t.v[ch][lane];
-    return 0.5 * warp_sum_d(v);
+    float v = 0.0f;
+    if (lane < SPS_NPARAM) v = t.p[ch][lane] * t.v[ch][lane];
+    return 0.5 * (double)warp_sum(v);
 }
 
 // Start a trajectory for chain ch: draws, momentum, record the start state,
@@ -354,13 +390,7 @@ __device__ __noinline__ void start_traj(TeamWork<CPW>& t, int ch, const HmcParam
         t.gs[ch][lane] = t.g[ch][lane];
     }
     __syncwarp();
-    if (dense && lane == 0) {                 // p = L^-T z by back substitution
-        for (int i = SPS_NPARAM - 1; i >= 0; --i) {
-            float a = t.p[ch][i];
-            for (int k = i + 1; k < SPS_NPARAM; ++k) a -= t.cm[ch]->chol[tri(k, i)] * t.p[ch][k];
-            t.p[ch][i] = a / t.cm[ch]->chol[tri(i, i)];
-        }
-    }
+    if (dense && lane == 0) dense_momentum(t, ch);     // p = L^-T z
     __syncwarp();
     metric_apply(t, ch, dense);
     const double h0 = -t.lp[ch] + kinetic(t, ch);
@@ -424,8 +454,8 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
     metric_apply(t, ch, dense);
     const double dH = (-t.lp[ch] + kinetic(t, ch)) - t.h0[ch];
     const bool fin = isfinite(dH);
-    const double a = fin ? fmin(1.0, exp(-dH)) : 0.0;
-    const bool take = fin && log(t.uacc[ch]) < -dH;
+    const float a = fin ? fminf(1.0f, __expf(-(float)dH)) : 0.0f;
+    const bool take = fin && t.uacc[ch] < -dH;
     if (!take && lane < SPS_NPARAM) {
         t.x[ch][lane] = t.xs[ch][lane];
         t.g[ch][lane] = t.gs[ch][lane];
@@ -438,12 +468,13 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
         t.nev[ch] += t.L[ch];
     }
     if (it < hp.n_warm) {
-        const double m = (double)(t.mda[ch] + 1);
-        const double hbar = (1.0 - 1.0 / (m + 10.0)) * t.hbar[ch] + ((double)hp.target_accept - a) / (m + 10.0);
-        const double log_eps = t.mu[ch] - sqrt(m) / 0.05 * hbar;
-        const double wgt = exp(-0.75 * log(m));
-        const double leb = wgt * log_eps + (1.0 - wgt) * t.leb[ch];
-        const float eps = (float)exp(it < hp.n_warm - 1 ? log_eps : leb);
+        const float m = (float)(t.mda[ch] + 1);
+        const float im = __frcp_rn(m + 10.0f);
+        const float hbar = (1.0f - im) * t.hbar[ch] + (hp.target_accept - a) * im;
+        const float log_eps = t.mu[ch] - sqrtf(m) * 20.0f * hbar;        // gamma = 0.05
+        const float wgt = exp2f(-0.75f * log2f(m));                        // kappa = 0.75
+        const float leb = wgt * log_eps + (1.0f - wgt) * t.leb[ch];
+        const float eps = expf(it < hp.n_warm - 1 ? log_eps : leb);
         __syncwarp();
         if (lane == 0) {
             t.mda[ch] += 1;
@@ -455,14 +486,14 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
         if (it >= t.wstart[ch] && it < t.wend[ch]) {
             const int wn = t.wn[ch] + 1;
             if (lane < SPS_NPARAM) {
-                const double xv = (double)t.x[ch][lane];
+                const float xv = t.x[ch][lane];
                 ChainMetric* cm = t.cm[ch];
-                const double d = xv - cm->wmean[lane];
-                const double mean = cm->wmean[lane] + d / (double)wn;
+                const float d = xv - cm->wmean[lane];
+                const float mean = cm->wmean[lane] + d * __frcp_rn((float)wn);
                 cm->wmean[lane] = mean;
                 cm->wm2[lane] += d * (xv - mean);
-                t.dv[ch][0][lane] = (float)d;
-                t.dv[ch][1][lane] = (float)(xv - mean);
+                t.dv[ch][0][lane] = d;
+                t.dv[ch][1][lane] = xv - mean;
             }
             __syncwarp();
             if (dense) {
@@ -477,21 +508,22 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
             if (lane == 0) t.wn[ch] = wn;
             if (it == t.wend[ch] - 1) {
                 if (wn >= 2 && !dense && lane < SPS_NPARAM) {
-                    const double var = t.cm[ch]->wm2[lane] / ((double)wn - 1.0);
-                    t.minv[ch][lane] = (float)(((double)wn / (wn + 5.0)) * var + 1e-3 * (5.0 / (wn + 5.0)));
+                    const float var = t.cm[ch]->wm2[lane] / ((float)wn - 1.0f);
+                    const float iw = __frcp_rn((float)wn + 5.0f);
+                    t.minv[ch][lane] = ((float)wn * iw) * var + 1e-3f * (5.0f * iw);
                 }
                 if (wn >= 2 && dense && lane == 0) dense_metric_update(t.cm[ch], wn);
                 if (lane < SPS_NPARAM) {
-                    t.cm[ch]->wmean[lane] = 0.0;
-                    t.cm[ch]->wm2[lane] = 0.0;
+                    t.cm[ch]->wmean[lane] = 0.0f;
+                    t.cm[ch]->wm2[lane] = 0.0f;
                 }
                 for (int e = lane; e < 78; e += 32) t.cm[ch]->wcov[e] = 0.0f;
                 __syncwarp();
                 if (lane == 0) {
                     t.wn[ch] = 0;
-                    t.mu[ch] = log(10.0 * (double)t.eps[ch]);
-                    t.hbar[ch] = 0.0;
-                    t.leb[ch] = 0.0;
+                    t.mu[ch] = logf(10.0f * t.eps[ch]);
+                    t.hbar[ch] = 0.0f;
+                    t.leb[ch] = 0.0f;
                     t.mda[ch] = 0;
                     int s = t.wend[ch], e = 0, wdt = 2 * t.wwidth[ch];
                     win_set_end(s, e, wdt, t.wstop[ch]);
@@ -512,8 +544,135 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
     __syncwarp();
 }
 
+// Take work item q (a galaxy and a group of CPW of its chains) into the
+// team: the galaxy's observed-band slots and the chains' initial state.
+// Returns the galaxy index; *nch / *nb get the live chains and observed bands.
 template <int CPW>
-__global__ void __launch_bounds__(128, (CPW >= 4) ? 2 : 4)
+__device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, const HmcParams& hp,
+                                          TeamWork<CPW>& t, int q, const float* __restrict__ theta0,
+                                          const float* __restrict__ mag_obs, const float* __restrict__ sigma,
+                                          const uint32_t* __restrict__ mask, const int32_t* __restrict__ gal_order,
+                                          ChainMetric* __restrict__ metric, int* nch_out, int* nb_out) {
+    const int lane = lane_id();
+    const int B = c.n_band, K = c.K;
+    const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
+    const int C = hp.chains_per_gal;
+    const int groups = (C + CPW - 1) / CPW;
+    const int n_it = hp.n_warm + hp.n_samp;
+    const int64_t gi = gal_order ? (int64_t)gal_order[q / groups] : (int64_t)(q / groups);
+    const int c0 = (q % groups) * CPW;
+    const int nch = min(CPW, C - c0);
+    const uint32_t bits = mask[gi] & all;
+    for (int i = lane; i < c.n_age; i += 32) t.bins[i] = g.bins[(size_t)gi * c.n_age + i];
+    if (lane == 0) {
+        t.lnT = g.lnT[gi];
+        t.lT10 = g.lT10[gi];
+    }
+    if (lane < B && ((bits >> lane) & 1u)) {
+        const int slot = __popc(bits & ((1u << lane) - 1u));
+        const size_t gb = (size_t)gi * B + lane;
+        t.ptr[slot] = g.cssp + gb * K;
+        t.dust[slot] = g.dust_eff[gb];
+        t.zp[slot] = g.zp[gb];
+        t.mobs[slot] = mag_obs[gb];
+        const float sg = sigma[gb];
+        t.isig2[slot] = 1.0f / (sg * sg);
+    }
+    // chain state; unused chain slots mirror the first chain and never write
+    for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
+        const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
+        const int cc = (ch < nch) ? ch : 0;
+        t.x[ch][k] = theta0[((size_t)gi * C + c0 + cc) * SPS_NPARAM + k];
+        t.minv[ch][k] = 1.0f;
+        if (ch < nch && hp.adapt_mass) {
+            ChainMetric* cm = metric + (gi * C + c0 + ch);
+            cm->wmean[k] = 0.0f;
+            cm->wm2[k] = 0.0f;
+        }
+    }
+    if (hp.adapt_mass == 2) {
+        for (int e = lane; e < nch * 78; e += 32) {
+            const int ch = e / 78, r = e - ch * 78;
+            int i = 0;
+            while (tri(i + 1, 0) <= r) ++i;
+            ChainMetric* cm = metric + (gi * C + c0 + ch);
+            cm->chol[r] = (r == tri(i, i)) ? 1.0f : 0.0f;
+            cm->wcov[r] = 0.0f;
+        }
+    }
+    if (lane < CPW) {
+        const int ch = lane;
+        t.chain[ch] = (uint32_t)(gi * C + c0 + ((ch < nch) ? ch : 0));
+        t.cm[ch] = metric + t.chain[ch];
+        t.eps[ch] = hp.eps0;
+        t.mu[ch] = logf(10.0f * hp.eps0);
+        t.hbar[ch] = t.leb[ch] = t.acc[ch] = 0.0f;
+        t.it[ch] = 0;
+        t.mda[ch] = t.wn[ch] = t.ndiv[ch] = 0;
+        t.nev[ch] = 1;
+        t.done[ch] = (ch < nch) ? (n_it <= 0) : 1;
+        int init_b, term_b, width;
+        const int nw = hp.adapt_mass ? hp.n_warm : 0;
+        if (nw >= 150) {
+            init_b = 75;
+            term_b = 50;
+            width = 25;
+        } else {
+            init_b = (int)(0.15 * nw);
+            term_b = (int)(0.1 * nw);
+            width = nw - init_b - term_b;
+        }
+        int s = init_b, e = 0;
+        win_set_end(s, e, width, nw - term_b);
+        t.wstart[ch] = s;
+        t.wend[ch] = e;
+        t.wwidth[ch] = width;
+        t.wstop[ch] = nw - term_b;
+    }
+    __syncwarp();
+    *nch_out = nch;
+    *nb_out = __popc(bits);
+    return gi;
+}
+
+// One leapfrog step of every live chain after the team's evaluation.
+template <int CPW>
+__device__ __forceinline__ void team_step(const Consts& c, TeamWork<CPW>& t, const HmcParams& hp, int nch,
+                                          float* __restrict__ samples) {
+    const int lane = lane_id();
+    const int n_it = hp.n_warm + hp.n_samp;
+#pragma unroll 1
+    for (int ch = 0; ch < CPW; ++ch) {
+        if (t.done[ch]) continue;
+        if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+        __syncwarp();
+        const int l = t.l[ch] + 1;
+        if (l == t.L[ch]) {
+            end_traj<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
+            if (t.it[ch] >= n_it) {
+                if (lane == 0) t.done[ch] = 1;
+                __syncwarp();
+            } else {
+                start_traj<CPW>(t, ch, hp);
+            }
+        } else {
+            if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+            __syncwarp();
+            metric_apply(t, ch, hp.adapt_mass == 2);
+            if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
+            __syncwarp();
+            if (lane == 0) t.l[ch] = l;
+            __syncwarp();
+        }
+    }
+}
+
+// Persistent kernel: each warp is a team working through the queue of
+// (galaxy, chain group) items; the warps of a block advance one evaluation per
+// pass together (one block barrier per pass), so that they run the same code
+// at the same time and share the instruction cache.
+template <int CPW>
+__global__ void __launch_bounds__(512, 1)
 k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
            const float* __restrict__ theta0, const float* __restrict__ mag_obs,
            const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
@@ -521,136 +680,55 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
            float* eps_out, int32_t* div_out, int64_t* nev_out, int32_t* status_out, int* queue,
            ChainMetric* __restrict__ metric) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ EdgeTables et;
     TeamWork<CPW>& t = reinterpret_cast<TeamWork<CPW>*>(smem)[threadIdx.x >> 5];
     const int lane = lane_id();
-    const int B = c.n_band, K = c.K;
-    const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
     const int C = hp.chains_per_gal;
+    for (int i = threadIdx.x; i <= c.n_age; i += blockDim.x) et.age[i] = c.log_age_edge[i];
+    for (int i = threadIdx.x; i <= c.n_met; i += blockDim.x) et.lgz[i] = c.lgz_edge[i];
+    __syncthreads();
     const int groups = (C + CPW - 1) / CPW;
-    const int n_it = hp.n_warm + hp.n_samp;
+    bool have = false, drained = false;     // warp-uniform
+    int64_t gi = 0;
+    int nch = 0, nb = 0, pass = 0;
     for (;;) {
-        int q = 0;
-        if (lane == 0) q = atomicAdd(queue, 1);
-        q = __shfl_sync(kFull, q, 0);
-        if ((int64_t)q >= g.n * groups) break;
-        const int64_t gi = gal_order ? (int64_t)gal_order[q / groups] : (int64_t)(q / groups);
-        const int c0 = (q % groups) * CPW;
-        const int nch = min(CPW, C - c0);
-        const uint32_t bits = mask[gi] & all;
-        const int nb = __popc(bits);
-        if (lane < B && ((bits >> lane) & 1u)) {
-            const int slot = __popc(bits & ((1u << lane) - 1u));
-            const size_t gb = (size_t)gi * B + lane;
-            t.ptr[slot] = g.cssp + gb * K;
-            t.dust[slot] = g.dust_eff[gb];
-            t.zp[slot] = g.zp[gb];
-            t.mobs[slot] = mag_obs[gb];
-            const float sg = sigma[gb];
-            t.isig2[slot] = 1.0f / (sg * sg);
-        }
-        // chain state; unused chain slots mirror the first chain and never write
-        for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
-            const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
-            const int cc = (ch < nch) ? ch : 0;
-            t.x[ch][k] = theta0[((size_t)gi * C + c0 + cc) * SPS_NPARAM + k];
-            t.minv[ch][k] = 1.0f;
-            if (ch < nch && hp.adapt_mass) {
-                ChainMetric* cm = metric + (gi * C + c0 + ch);
-                cm->wmean[k] = 0.0;
-                cm->wm2[k] = 0.0;
-            }
-        }
-        if (hp.adapt_mass == 2) {
-            for (int e = lane; e < nch * 78; e += 32) {
-                const int ch = e / 78, r = e - ch * 78;
-                int i = 0;
-                while (tri(i + 1, 0) <= r) ++i;
-                ChainMetric* cm = metric + (gi * C + c0 + ch);
-                cm->chol[r] = (r == tri(i, i)) ? 1.0f : 0.0f;
-                cm->wcov[r] = 0.0f;
-            }
-        }
-        if (lane < CPW) {
-            const int ch = lane;
-            t.chain[ch] = (uint32_t)(gi * C + c0 + ((ch < nch) ? ch : 0));
-            t.cm[ch] = metric + t.chain[ch];
-            t.eps[ch] = hp.eps0;
-            t.mu[ch] = log(10.0 * (double)hp.eps0);
-            t.hbar[ch] = t.leb[ch] = t.acc[ch] = 0.0;
-            t.it[ch] = 0;
-            t.mda[ch] = t.wn[ch] = t.ndiv[ch] = 0;
-            t.nev[ch] = 1;
-            t.done[ch] = (ch < nch) ? (n_it <= 0) : 1;
-            int init_b, term_b, width;
-            const int nw = hp.adapt_mass ? hp.n_warm : 0;
-            if (nw >= 150) {
-                init_b = 75;
-                term_b = 50;
-                width = 25;
+        if (!have && !drained) {
+            int q = 0;
+            if (lane == 0) q = atomicAdd(queue, 1);
+            q = __shfl_sync(kFull, q, 0);
+            if ((int64_t)q >= g.n * groups) {
+                drained = true;
             } else {
-                init_b = (int)(0.15 * nw);
-                term_b = (int)(0.1 * nw);
-                width = nw - init_b - term_b;
+                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb);
+                have = true;
+                pass = 0;
             }
-            int s = init_b, e = 0;
-            win_set_end(s, e, width, nw - term_b);
-            t.wstart[ch] = s;
-            t.wend[ch] = e;
-            t.wwidth[ch] = width;
-            t.wstop[ch] = nw - term_b;
         }
-        __syncwarp();
-        const float2* bins = g.bins + (size_t)gi * c.n_age;
-        const float lnT = g.lnT[gi], lT10 = g.lT10[gi];
-        // one evaluation per pass; the first pass only starts the trajectories
-        for (int pass = 0;; ++pass) {
-            if (pass > 0) {
-                bool any = false;
-                for (int ch = 0; ch < CPW; ++ch) any = any || !t.done[ch];
-                if (!any) break;
-            }
-            team_eval<CPW>(c, t, bins, lnT, lT10, nb);
-            if (pass == 0) {
+        if (!__syncthreads_or(have ? 1 : 0)) break;
+        if (!have) continue;
+        team_eval<CPW>(c, t, et, t.lnT, t.lT10, nb);
+        if (pass == 0) {
 #pragma unroll 1
-                for (int ch = 0; ch < CPW; ++ch)
-                    if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
-                continue;
-            }
-#pragma unroll 1
-            for (int ch = 0; ch < CPW; ++ch) {
-                if (t.done[ch]) continue;
-                if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
-                __syncwarp();
-                const int l = t.l[ch] + 1;
-                if (l == t.L[ch]) {
-                    end_traj<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
-                    if (t.it[ch] >= n_it) {
-                        if (lane == 0) t.done[ch] = 1;
-                        __syncwarp();
-                    } else {
-                        start_traj<CPW>(t, ch, hp);
-                    }
-                } else {
-                    if (lane < SPS_NPARAM)
-                        t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
-                    __syncwarp();
-                    metric_apply(t, ch, hp.adapt_mass == 2);
-                    if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
-                    __syncwarp();
-                    if (lane == 0) t.l[ch] = l;
-                    __syncwarp();
-                }
-            }
+            for (int ch = 0; ch < CPW; ++ch)
+                if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
+        } else {
+            team_step<CPW>(c, t, hp, nch, samples);
         }
-        if (lane < nch) {
-            const uint32_t chn = t.chain[lane];
-            if (acc_out) acc_out[chn] = (float)(t.acc[lane] / (double)max(hp.n_samp, 1));
-            if (eps_out) eps_out[chn] = t.eps[lane];
-            if (div_out) div_out[chn] = t.ndiv[lane];
-            if (nev_out) nev_out[chn] = t.nev[lane];
-            if (status_out) status_out[chn] = 0;
+        ++pass;
+        bool any = false;
+        for (int ch = 0; ch < CPW; ++ch) any = any || !t.done[ch];
+        if (!any) {
+            if (lane < nch) {
+                const uint32_t chn = t.chain[lane];
+                if (acc_out) acc_out[chn] = t.acc[lane] / (float)max(hp.n_samp, 1);
+                if (eps_out) eps_out[chn] = t.eps[lane];
+                if (div_out) div_out[chn] = t.ndiv[lane];
+                if (nev_out) nev_out[chn] = t.nev[lane];
+                if (status_out) status_out[chn] = 0;
+            }
+            __syncwarp();
+            have = false;
         }
-        __syncwarp();
     }
 }
 

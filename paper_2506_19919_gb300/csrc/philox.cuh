@@ -26,5 +26,7 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
 
 // (word + 1/2) 2^-32, in (0, 1), exact in FP64.
 __device__ __forceinline__ double u01_d(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
+// The same in FP32, rounded; in (0, 1].
+__device__ __forceinline__ float u01_f(uint32_t w) { return fmaf((float)w, 2.3283064e-10f, 1.1641532e-10f); }
 
 }  // namespace sps

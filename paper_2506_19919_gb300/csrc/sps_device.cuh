@@ -107,6 +107,8 @@ struct AgeView {
     float* q;          // [Zn] metallicity weights
     float* qb;         // [Zn] adjoint of q
     PanelScratch* ps;
+    const float* age_edge;   // [A + 1] log10 age-bin edges (shared or parameter memory)
+    const float* lgz_edge;   // [Zn + 1] metallicity-bin edges
 };
 
 struct RowScratch {
@@ -125,8 +127,8 @@ struct RowScratch {
     float slot_S[kMaxBands];
     float slot_F[kMaxBands];
     float slot_g[kMaxBands];    // gamma_b
-    __device__ AgeView view() {
-        return AgeView{m, dm[0], dm[1], dm[2], pi, w, wb, q, qb, &u.s};
+    __device__ AgeView view(const Consts& c) {
+        return AgeView{m, dm[0], dm[1], dm[2], pi, w, wb, q, qb, &u.s, c.log_age_edge, c.lgz_edge};
     }
 };
 
@@ -196,50 +198,44 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
     const int G = c.gl_order;
     const int o2 = min(2, G), o3 = min(3, G);
     // bins 4 lane .. 4 lane + 3: panel count, first centre, half-width, order
-    int nl[4];
-    float x0l[4], hpl[4];
-    int ol[4];
     int tot = 0;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
         const int i = 4 * lane + k;
+        if (i >= A) break;
         int n = 0;
         float x0 = 0.0f, hp = 0.0f;
-        if (i < A) {
-            const float2 b = bins[i];
-            if (b.y < 0.0f) {                      // reaches t = 0
-                const float w = b.x - xmin;
-                if (w > 0.0f) {
+        const float2 b = bins[i];
+        if (b.y < 0.0f) {                          // reaches t = 0
+            const float w = b.x - xmin;
+            if (w > 0.0f) {
+                n = panel_count(w * ipw);
+                hp = 0.5f * w * __frcp_rn((float)n);
+                x0 = xmin + hp;
+            }
+        } else if (b.y > 0.0f) {
+            const float hi = b.x + b.y;
+            const float lo = b.x - b.y;
+            if (hi > xmin) {
+                if (lo < xmin) {
+                    const float w = hi - xmin;
                     n = panel_count(w * ipw);
                     hp = 0.5f * w * __frcp_rn((float)n);
                     x0 = xmin + hp;
-                }
-            } else if (b.y > 0.0f) {
-                const float hi = b.x + b.y;
-                const float lo = b.x - b.y;
-                if (hi > xmin) {
-                    if (lo < xmin) {
-                        const float w = hi - xmin;
-                        n = panel_count(w * ipw);
-                        hp = 0.5f * w * __frcp_rn((float)n);
-                        x0 = xmin + hp;
-                    } else {                       // centre / half-width kept exact
-                        n = panel_count(2.0f * b.y * ipw);
-                        hp = b.y * __frcp_rn((float)n);
-                        x0 = b.x + (float)(1 - n) * hp;
-                    }
+                } else {                           // centre / half-width kept exact
+                    n = panel_count(2.0f * b.y * ipw);
+                    hp = b.y * __frcp_rn((float)n);
+                    x0 = b.x + (float)(1 - n) * hp;
                 }
             }
-            v.m[i] = 0.0f;
-            v.dm0[i] = 0.0f;
-            v.dm1[i] = 0.0f;
-            v.dm2[i] = 0.0f;
         }
+        v.m[i] = 0.0f;
+        v.dm0[i] = 0.0f;
+        v.dm1[i] = 0.0f;
+        v.dm2[i] = 0.0f;
         const float hk = hp * kap;
-        ol[k] = (n == 1) ? (hk <= 0.04f ? o2 : (hk <= 0.25f ? o3 : G)) : G;
-        nl[k] = n;
-        x0l[k] = x0;
-        hpl[k] = hp;
+        const int ord = (n == 1) ? (hk <= 0.04f ? o2 : (hk <= 0.25f ? o3 : G)) : G;
+        ps.info[i] = make_float4(x0, hp, __int_as_float(n), __int_as_float(ord));
         tot += n;
     }
     int incl = tot;
@@ -252,12 +248,14 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
     for (int p = lane; p < P; p += 32) ps.pmap[p] = 0xFF;
     __syncwarp();
     int st = incl - tot;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
         const int i = 4 * lane + k;
-        if (i < A) ps.info[i] = make_float4(x0l[k], hpl[k], __int_as_float(st), __int_as_float(ol[k]));
-        if (nl[k] > 0 && st < kMaxPanels) ps.pmap[st] = (unsigned char)i;
-        st += nl[k];
+        if (i >= A) break;
+        const int n = __float_as_int(ps.info[i].z);
+        ps.info[i].z = __int_as_float(st);         // first panel index replaces the count
+        if (n > 0 && st < kMaxPanels) ps.pmap[st] = (unsigned char)i;
+        st += n;
     }
     __syncwarp();
     int carry = -1;
@@ -319,11 +317,8 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
         __syncwarp();
     }
     double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int i = 4 * lane + k;
-        if (i < A) acc += (double)v.m[i];
-    }
+#pragma unroll 4
+    for (int i = lane; i < A; i += 32) acc += (double)v.m[i];
     return warp_sum_d(acc);
 }
 
@@ -333,9 +328,10 @@ __device__ __forceinline__ float burst_weights(const Consts& c, const AgeView& v
     const float isig = 1.0f / sig;
     const float D = tri_cdf((lT10 - mu) * isig);
     const float invD = 1.0f / D;
+#pragma unroll 4
     for (int i = lane_id(); i < c.n_age; i += 32) {
-        const float lo = fminf(c.log_age_edge[i], lT10);
-        const float hi = fminf(c.log_age_edge[i + 1], lT10);
+        const float lo = fminf(v.age_edge[i], lT10);
+        const float hi = fminf(v.age_edge[i + 1], lT10);
         v.pi[i] = (tri_cdf((hi - mu) * isig) - tri_cdf((lo - mu) * isig)) * invD;
     }
     return D;
@@ -345,8 +341,8 @@ __device__ __forceinline__ void met_weights(const Consts& c, const AgeView& v, f
     const int j = lane_id();
     const float isd = 1.0f / sd;
     if (j < c.n_met) {
-        const float ylo = (c.lgz_edge[j] - mu) * isd;
-        const float yhi = (c.lgz_edge[j + 1] - mu) * isd;
+        const float ylo = (v.lgz_edge[j] - mu) * isd;
+        const float yhi = (v.lgz_edge[j + 1] - mu) * isd;
         v.q[j] = (ylo > 0.0f) ? normcdff(-ylo) - normcdff(-yhi) : normcdff(yhi) - normcdff(ylo);
     }
 }
@@ -402,6 +398,7 @@ __device__ __forceinline__ double age_met_weights(const Consts& c, const AgeView
     __syncwarp();
     const float fb = th[4];
     const float Mf = (float)M;
+#pragma unroll 4
     for (int i = lane_id(); i < c.n_age; i += 32) v.w[i] = (1.0f - fb) * v.m[i] + fb * v.pi[i] * Mf;
     __syncwarp();
     return M;
@@ -409,7 +406,7 @@ __device__ __forceinline__ double age_met_weights(const Consts& c, const AgeView
 __device__ __forceinline__ double age_met_weights(const Consts& c, RowScratch& s,
                                                   const float2* __restrict__ bins, float lnT,
                                                   float lT10, const RowParams& p, bool grad) {
-    return age_met_weights(c, s.view(), bins, lnT, lT10, p.th, grad);
+    return age_met_weights(c, s.view(c), bins, lnT, lT10, p.th, grad);
 }
 
 // Adjoint of age_met_weights: given s.wb (dlogL/dw_i) and s.qb (dlogL/dq_j)
@@ -428,6 +425,7 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
     const float isig = 1.0f / sig;
     float s_wp = 0.f, s_wm = 0.f, s_w0 = 0.f, s_w1 = 0.f, s_w2 = 0.f;
     float s_d0 = 0.f, s_d1 = 0.f, s_d2 = 0.f, s_mu = 0.f, s_sg = 0.f;
+#pragma unroll 4
     for (int i = lane; i < A; i += 32) {
         const float wb = s.wb[i];
         const float d0 = s.dm0[i], d1 = s.dm1[i], d2 = s.dm2[i];
@@ -439,8 +437,8 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
         s_d0 += d0;
         s_d1 += d1;
         s_d2 += d2;
-        const float lo = fminf(c.log_age_edge[i], lT10);
-        const float hi = fminf(c.log_age_edge[i + 1], lT10);
+        const float lo = fminf(s.age_edge[i], lT10);
+        const float hi = fminf(s.age_edge[i + 1], lT10);
         const float xl = (lo - mu) * isig, xh = (hi - mu) * isig;
         const float tl = tri_pdf(xl), tH = tri_pdf(xh);
         s_mu = fmaf(wb, tl - tH, s_mu);
@@ -451,7 +449,7 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
     const float isz = 1.0f / sz;
     float s_gz = 0.f, s_gs = 0.f;
     if (lane < c.n_met) {
-        const float yl = (c.lgz_edge[lane] - mz) * isz, yh = (c.lgz_edge[lane + 1] - mz) * isz;
+        const float yl = (s.lgz_edge[lane] - mz) * isz, yh = (s.lgz_edge[lane + 1] - mz) * isz;
         const float qb = s.qb[lane];
         s_gz = qb * (phi_(yl) - phi_(yh));
         s_gs = qb * (phi_y(yl) - phi_y(yh));
@@ -488,7 +486,7 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
 }
 __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT10, double M,
                                        const RowParams& p, float* g) {
-    age_met_adjoint(c, s.view(), lT10, M, p.th, g);
+    age_met_adjoint(c, s.view(c), lT10, M, p.th, g);
 }
 
 }  // namespace sps

@@ -61,7 +61,7 @@ struct Grid {
 // Metric-adaptation state of one HMC chain, kept in global memory (read at
 // trajectory ends; chol every leapfrog step with the dense metric).
 struct ChainMetric {
-    double wmean[SPS_NPARAM], wm2[SPS_NPARAM];   // Welford moments of the window
+    float wmean[SPS_NPARAM], wm2[SPS_NPARAM];    // Welford moments of the window
     float chol[78];                              // dense inverse metric L L^T, packed lower
     float wcov[78];                              // window co-moments (dense)
 };
@@ -69,8 +69,8 @@ struct ChainMetric {
 // State of one chain of the plain lock-step HMC (hmc_plain.cu).
 struct PlainChain {
     float x[SPS_NPARAM], p[SPS_NPARAM], g[SPS_NPARAM], xs[SPS_NPARAM], gs[SPS_NPARAM];
-    double lp, lps, h0, mu, hbar, leb, acc, uacc;
-    float eps;
+    double lp, lps, h0, uacc;        // log posterior, energies, log of the accept uniform
+    float mu, hbar, leb, acc, eps;   // dual averaging, accept sum, step size
     int L, l, it, mda, ndiv, active;
     long long nev;
 };
