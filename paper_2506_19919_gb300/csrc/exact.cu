@@ -254,7 +254,7 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
     for (int b = 0; b < B; ++b) {
         const float* a = cJ + (row * B + b) * 4;
         float cprime = ff * a[0] + (1.0f - ff) * a[1];
-        double m = g.zp[gi * B + b] - 2.5 * (log10((double)cprime) + (double)lgM + 9.0);
+        double m = g.zp[gi * B + b] - 2.5 * (log10_flux(cprime) + (double)lgM + 9.0);
         bad = bad || !isfinite(m);
         if (mag_out) mag_out[row * B + b] = (float)m;
         float gb = 0.0f;

@@ -110,17 +110,33 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         t.lpe[ch][k] = -fabsf(x) - 2.0f * __logf(1.0f + ex);   // log sg (1 - sg)
     }
     __syncwarp();
-    if (lane < CPW) {
-        double s = 0.0;
-        for (int k = 0; k < SPS_NPARAM; ++k) s += (double)t.lpe[lane][k];
-        t.lpri[lane] = s;
+    // log prior, FP64: two chains per round, 16 lanes each
+#pragma unroll
+    for (int c0 = 0; c0 < CPW; c0 += 2) {
+        const int ch = c0 + (lane >> 4), k = lane & 15;
+        double s = (ch < CPW && k < SPS_NPARAM) ? (double)t.lpe[ch][k] : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (k == 0 && ch < CPW) t.lpri[ch] = s;
     }
 #pragma unroll 1
-    for (int ch = 0; ch < CPW; ++ch) {
-        const double M = age_met_weights(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
-        if (lane == 0) t.M[ch] = M;
-    }
+    for (int ch = 0; ch < CPW; ++ch) age_met_parts(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
     __syncwarp();
+    // M = sum_i m_i in FP64, the chains' reductions interleaved
+    {
+        double mp[CPW];
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) mp[ch] = mass_partial(c, age_view(t, ch, et));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int ch = 0; ch < CPW; ++ch) mp[ch] += __shfl_xor_sync(kFull, mp[ch], o);
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) {
+            if (lane == 0) t.M[ch] = mp[ch];
+            age_weights(c, age_view(t, ch, et), t.th[ch], mp[ch]);
+        }
+    }
     // ---- forward pass: S[ch][b] = sum_i w_i sum_j q_j C[b][i][j]
     float qr[CPW][kZnReg], wl[CPW][4];
 #pragma unroll
@@ -168,12 +184,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         const float4 dc = t.dust[b];
         const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
         const float Sv = t.S[ch][b];
-        // log10(F S): F S = f 2^e with f in [0.5, 1); e ln 2 exact in FP64, ln f to
-        // ~6e-8 absolute in FP32, the sum and the magnitude in FP64
-        int e2;
-        const float f = frexpf(d.F * Sv, &e2);
-        const double lc = fma((double)e2, 0.6931471805599453, (double)logf(f)) * 0.4342944819032518 +
-                          ((double)t.th[ch][0] + 9.0);
+        const double lc = log10_flux(d.F * Sv) + ((double)t.th[ch][0] + 9.0);
         const double r = (t.zp[b] - 2.5 * lc) - (double)t.mobs[b];
         const double is2 = (double)t.isig2[b];
         t.u.t.tll[ch][b] = -0.5 * r * r * is2;

@@ -3,12 +3,12 @@
 //
 // Forward, per row (App. A.1-A.3):
 //   m_i    = int_{bin i} SFR shape dt  (Eq. SFRsmooth, Eq. smoothPsfh), by
-//            Gauss-Legendre panels in x = ln t with the substitution
+//            Gauss-Legendre rules in x = ln t with the substitution
 //            t = tau e^u:  m_i = tau int hh(u) du, hh = 1 / (e^{(a-1)u} + e^{-(b+1)u}).
-//            The integrand is analytic in a strip of half-width pi/(a+b) around
-//            the real axis, so panels of width <= 0.25 give ~1e-9 accuracy.
-//            Below x_min = min(ln t_obs - ln tau, 0) - 30/(b+1) the remaining
-//            mass is < 1e-10 of the total and is dropped.
+//            Narrow bins take one 2- or 3-node panel, wide bins panels of the
+//            full rule sized by the analyticity strip (see sfh_bins); the part
+//            of the oldest bin below e^-22 of the peak integrand is dropped.
+//   q_j, pi_i are differences of CDFs at the bin edges, one CDF per edge.
 //   M      = sum_i m_i in FP64 (the cumulative mass integral, Eq. totalMstarFormed)
 //   pi_i   = triweight CDF mass of bin i in log age, clipped at t_obs and
 //            renormalised (Eq. triweight)
@@ -16,7 +16,8 @@
 //   w_i    = (1 - F_burst) m_i + F_burst pi_i M  (Eq. composite_age_weights x M_star)
 //   W_ij   = 1e9 10^lgM w_i q_j                    (Eq. galSED_decomposed)
 //   S_b    = sum_ij w_i q_j c_SSP[b][ij]           (Eq. photo_integral_approx)
-//   c_b    = 1e9 10^lgM F_att(lambda_eff,b) S_b;  m_b = zp_b - 2.5 log10 c_b (FP64)
+//   c_b    = 1e9 10^lgM F_att(lambda_eff,b) S_b;  m_b = zp_b - 2.5 log10 c_b (FP64
+//            magnitude; the log's exponent part exact, its mantissa part FP32)
 //
 // Adjoint (reverse order; recomputes the per-SSP products):
 //   gamma_b = dlogL / dln c_b = 2.5 r_b / (sigma_b^2 ln 10)
@@ -65,6 +66,17 @@ __device__ __forceinline__ float tri_pdf(float x) {
     return (fabsf(x) <= 3.0f) ? (35.0f / 96.0f) * t * t * t : 0.0f;
 }
 
+// ---------------------------------------------------------------- magnitudes
+// log10 of a positive FP32 flux for the magnitude m = zp - 2.5 log10 c: with
+// x = f 2^e, f in [0.5, 1), the exponent part e log10(2) is exact in FP64 and
+// log10(f) (|.| < 0.31) is an FP32 log, so the result is good to ~5e-8 at any
+// flux, faint or bright; x = 0 gives -inf.
+__device__ __forceinline__ double log10_flux(float x) {
+    int e;
+    const float f = frexpf(x, &e);
+    return fma((double)e, 0.30102999566398120, (double)logf(f) * 0.43429448190325182);
+}
+
 // ---------------------------------------------------------------- dust
 // F_att = F_floor + (1 - F_floor) 10^{-0.4 A},  A = (A_V/4.05)(k0 (l/l_V)^delta + E_b D),
 // E_b = max(0.85 - 1.9 delta, 0)  (Eq. DustAtt, App. A.3).
@@ -90,9 +102,9 @@ __device__ __forceinline__ DustTerms dust_eval(float k0, float lnr, float drude,
 // ---------------------------------------------------------------- per-warp scratch
 // Panel bookkeeping of the SFH quadrature of one row.
 struct PanelScratch {
-    float4 info[kMaxAges];            // per bin: (first panel centre, half-width,
-                                      //  first panel index, rule order) - ints as bits
-    unsigned char pmap[kMaxPanels];   // bin index at each bin's first panel, 0xFF elsewhere
+    float4 info[kMaxAges];            // per queued bin: (first panel centre, half-width,
+                                      //  first panel index as int bits or -1, unused)
+    unsigned char pmap[kMaxPanels];   // bin index at each queued bin's first panel
 };
 
 // Where the age / metallicity stage of one row keeps its arrays.
@@ -142,25 +154,35 @@ __device__ __forceinline__ int panel_count(float f) {
 
 // One panel of an N-node Gauss-Legendre rule (nodes gx, weights gw on [-1, 1])
 // centred at u = xc with half-width hp: accumulates int hh du into v0 and, if
-// grad, int dhh/d(alpha), d/d(beta) and the tau-derivative integrand into v1..v3.
+// grad, the integrands of d/d(alpha), d/d(ln tau-free parts) into v1..v3, with
+// hh = 1 / (P + Q), P = e^{(alpha-1)u}, Q = e^{-(beta+1)u}.  Written with the
+// exponent of the ratio Q/P or P/Q kept <= 0 (no overflow):
+//   u < 0:  hh = e^{(beta+1)u} r,  r = 1 / (1 + e^{(alpha+beta)u}),  hh P = 1 - r, hh Q = r
+//   u >= 0: hh = e^{(1-alpha)u} r, r = 1 / (1 + e^{-(alpha+beta)u}), hh P = r,     hh Q = 1 - r
+// so that dhh/dalpha = -u hh (hh P), dhh/dbeta = u hh (hh Q) and
+// alpha P - beta Q = (alpha hhP - beta hhQ) / hh.
 template <int N>
 __device__ __forceinline__ void gl_panel(const float* __restrict__ gx, const float* __restrict__ gw,
                                          float hp, float xc, float alpha, float beta, bool grad,
                                          float& v0, float& v1, float& v2, float& v3) {
-    const float am1 = alpha - 1.0f, bp1 = beta + 1.0f;
+    const float kL2E = 1.4426950408889634f;
+    const float cneg = (beta + 1.0f) * kL2E, cpos = (1.0f - alpha) * kL2E, cs = -(alpha + beta) * kL2E;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         const float uu = fmaf(hp, gx[q], xc);
-        const float P_ = __expf(am1 * uu);
-        const float Q_ = __expf(-bp1 * uu);
-        const float hh = __frcp_rn(P_ + Q_);
-        const float wq = gw[q] * hp;
-        v0 = fmaf(wq, hh, v0);
+        const bool pos = uu >= 0.0f;
+        const float E = exp2f(uu * (pos ? cpos : cneg));
+        const float R = exp2f(fabsf(uu) * cs);
+        const float r = __fdividef(1.0f, 1.0f + R);
+        const float wh = gw[q] * hp * E * r;                      // w hh
+        v0 += wh;
         if (grad) {
-            const float h2 = hh * hh * wq;
-            v1 = fmaf(h2, alpha * P_ - beta * Q_, v1);
-            v2 = fmaf(-h2 * P_, uu, v2);
-            v3 = fmaf(h2 * Q_, uu, v3);
+            const float hP = pos ? r : 1.0f - r;                  // hh P
+            const float hQ = 1.0f - hP;                           // hh Q
+            v1 = fmaf(wh, alpha * hP - beta * hQ, v1);
+            const float whu = wh * uu;
+            v2 = fmaf(-whu, hP, v2);
+            v3 = fmaf(whu, hQ, v3);
         }
     }
 }
@@ -182,104 +204,62 @@ __device__ __forceinline__ void gl_panel_any(int n, const float* __restrict__ gx
 // half-width <= 1.25: a relative error below 1e-8 per panel for order 6.  A bin
 // that fits in one panel with kappa x half-width <= 0.25 uses 3 nodes, <= 0.04
 // 2 nodes (relative error below 1e-8 by the same bounds).  Below x_min =
-// min(ln t_obs - ln tau, 0) - 30 / (beta + 1) the remaining mass is < 1e-10 of
-// the total and is dropped.
-__device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
-                                           float lnT, float tau, float alpha, float beta, bool grad) {
+// ln tau + min(ln t_obs - ln tau, 0) - 22 / (beta + 1) the integrand is below
+// e^-22 of its value at the peak or at t_obs, and the remaining mass (< 1e-9
+// of the total) is dropped.
+__device__ __forceinline__ void sfh_bins_raw(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
+                                             float lnT, float tau, float alpha, float beta, bool grad) {
     PanelScratch& ps = *v.ps;
     const int lane = lane_id();
     const int A = c.n_age;
     const float lntau = __logf(tau);
     const float bp1 = beta + 1.0f;
-    const float xmin = lntau + fminf(lnT - lntau, 0.0f) - 30.0f / bp1;
+    const float xmin = lntau + fminf(lnT - lntau, 0.0f) - 22.0f / bp1;
     const float kap = fmaxf(alpha + beta, bp1);
     const float pw = fminf(fmaxf(c.panel * 10.0f / kap, c.panel), 8.0f * c.panel);
     const float ipw = 1.0f / pw;
     const int G = c.gl_order;
     const int o2 = min(2, G), o3 = min(3, G);
-    // bins 4 lane .. 4 lane + 3: panel count, first centre, half-width, order
-    int tot = 0;
+    // Pass 1, bins i = lane + 32 k: panel layout; a bin that fits one panel is
+    // integrated here, a bin of several panels is queued for pass 2.
+    int base = 0;                               // panels queued so far (warp-uniform)
 #pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        const int i = 4 * lane + k;
-        if (i >= A) break;
+    for (int i0 = 0; i0 < A; i0 += 32) {
+        const int i = i0 + lane;
         int n = 0;
         float x0 = 0.0f, hp = 0.0f;
-        const float2 b = bins[i];
-        if (b.y < 0.0f) {                          // reaches t = 0
-            const float w = b.x - xmin;
-            if (w > 0.0f) {
-                n = panel_count(w * ipw);
-                hp = 0.5f * w * __frcp_rn((float)n);
-                x0 = xmin + hp;
-            }
-        } else if (b.y > 0.0f) {
-            const float hi = b.x + b.y;
-            const float lo = b.x - b.y;
-            if (hi > xmin) {
-                if (lo < xmin) {
-                    const float w = hi - xmin;
+        if (i < A) {
+            const float2 b = bins[i];
+            if (b.y < 0.0f) {                          // reaches t = 0
+                const float w = b.x - xmin;
+                if (w > 0.0f) {
                     n = panel_count(w * ipw);
                     hp = 0.5f * w * __frcp_rn((float)n);
                     x0 = xmin + hp;
-                } else {                           // centre / half-width kept exact
-                    n = panel_count(2.0f * b.y * ipw);
-                    hp = b.y * __frcp_rn((float)n);
-                    x0 = b.x + (float)(1 - n) * hp;
+                }
+            } else if (b.y > 0.0f) {
+                const float hi = b.x + b.y;
+                const float lo = b.x - b.y;
+                if (hi > xmin) {
+                    if (lo < xmin) {
+                        const float w = hi - xmin;
+                        n = panel_count(w * ipw);
+                        hp = 0.5f * w * __frcp_rn((float)n);
+                        x0 = xmin + hp;
+                    } else {                           // centre / half-width kept exact
+                        n = panel_count(2.0f * b.y * ipw);
+                        hp = b.y * __frcp_rn((float)n);
+                        x0 = b.x + (float)(1 - n) * hp;
+                    }
                 }
             }
         }
-        v.m[i] = 0.0f;
-        v.dm0[i] = 0.0f;
-        v.dm1[i] = 0.0f;
-        v.dm2[i] = 0.0f;
         const float hk = hp * kap;
-        const int ord = (n == 1) ? (hk <= 0.04f ? o2 : (hk <= 0.25f ? o3 : G)) : G;
-        ps.info[i] = make_float4(x0, hp, __int_as_float(n), __int_as_float(ord));
-        tot += n;
-    }
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int P = min(__shfl_sync(kFull, incl, 31), kMaxPanels);
-    for (int p = lane; p < P; p += 32) ps.pmap[p] = 0xFF;
-    __syncwarp();
-    int st = incl - tot;
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        const int i = 4 * lane + k;
-        if (i >= A) break;
-        const int n = __float_as_int(ps.info[i].z);
-        ps.info[i].z = __int_as_float(st);         // first panel index replaces the count
-        if (n > 0 && st < kMaxPanels) ps.pmap[st] = (unsigned char)i;
-        st += n;
-    }
-    __syncwarp();
-    int carry = -1;
-    for (int base = 0; base < P; base += 32) {
-        const int p = base + lane;
-        const bool act = p < P;
-        int f = act ? (int)ps.pmap[p] : 0xFF;
-        f = (f == 0xFF) ? -1 : f;
-        // the bin of panel p: the last bin whose first panel is at or before p
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, f, o);
-            if (lane >= o) f = max(f, t);
-        }
-        f = max(f, carry);
-        carry = __shfl_sync(kFull, f, 31);
-        const int bin = (act && f >= 0) ? f : -1;
-        float4 inf = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (bin >= 0) inf = ps.info[bin];
-        const int oc = __reduce_max_sync(kFull, (bin >= 0) ? __float_as_int(inf.w) : 0);
+        const int ord = (n == 1) ? (hk <= 0.04f ? o2 : (hk <= 0.25f ? o3 : G)) : 0;
+        const int oc = __reduce_max_sync(kFull, ord);
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-        if (bin >= 0) {
-            const float hp = inf.y;
-            const float xc = inf.x + 2.0f * (float)(p - __float_as_int(inf.z)) * hp - lntau;
+        if (oc > 0 && ord > 0) {
+            const float xc = x0 - lntau;
             if (oc <= 2)
                 gl_panel<2>(c.gl2_x, c.gl2_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
             else if (oc == 3)
@@ -289,20 +269,72 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
             else
                 gl_panel_any(G, c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
         }
-        // panels of one bin are consecutive: sum them unless every panel of the
-        // chunk belongs to its own bin
-        const int prev = __shfl_up_sync(kFull, bin, 1);
-        if (__any_sync(kFull, bin >= 0 && lane > 0 && prev == bin)) {
+        if (i < A) {
+            v.m[i] = v0 * tau;
+            if (grad) {
+                v.dm0[i] = v1;
+                v.dm1[i] = v2 * tau;
+                v.dm2[i] = v3 * tau;
+            }
+        }
+        // queue the panels of multi-panel bins: exclusive scan of their counts
+        const int nq = (n >= 2) ? n : 0;
+        int incl = nq;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float t0 = __shfl_up_sync(kFull, v0, o);
-                const float t1 = __shfl_up_sync(kFull, v1, o);
-                const float t2 = __shfl_up_sync(kFull, v2, o);
-                const float t3 = __shfl_up_sync(kFull, v3, o);
-                const int bo = __shfl_up_sync(kFull, bin, o);
-                if (lane >= o && bo == bin) {
-                    v0 += t0; v1 += t1; v2 += t2; v3 += t3;
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int st = base + incl - nq;
+        if (nq > 0) {
+            ps.info[i] = make_float4(x0, hp, __int_as_float(st), 0.0f);
+            if (st < kMaxPanels) ps.pmap[st] = (unsigned char)i;
+        } else if (i < A) {
+            ps.info[i].z = __int_as_float(-1);       // not queued in this call
+        }
+        base += __shfl_sync(kFull, incl, 31);
+    }
+    const int P = min(base, kMaxPanels);
+    __syncwarp();
+    // Pass 2: the queued panels, 32 per chunk, full rule; the panels of a bin
+    // are consecutive and summed by a segmented scan.
+    int carry = -1;
+    for (int c0 = 0; c0 < P; c0 += 32) {
+        const int p = c0 + lane;
+        const bool act = p < P;
+        // flag = bin index at a bin's first panel; the running max gives the bin
+        int f = -1;
+        if (act) {
+            const int cand = ps.pmap[p];
+            if (cand < A && __float_as_int(ps.info[cand].z) == p) f = cand;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, f, o);
+            if (lane >= o) f = max(f, t);
+        }
+        f = max(f, carry);
+        carry = __shfl_sync(kFull, f, 31);
+        const int bin = (act && f >= 0) ? f : -1;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+        if (bin >= 0) {
+            const float4 inf = ps.info[bin];
+            const float hp = inf.y;
+            const float xc = inf.x + 2.0f * (float)(p - __float_as_int(inf.z)) * hp - lntau;
+            if (G == 6)
+                gl_panel<6>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+            else
+                gl_panel_any(G, c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float t0 = __shfl_up_sync(kFull, v0, o);
+            const float t1 = __shfl_up_sync(kFull, v1, o);
+            const float t2 = __shfl_up_sync(kFull, v2, o);
+            const float t3 = __shfl_up_sync(kFull, v3, o);
+            const int bo = __shfl_up_sync(kFull, bin, o);
+            if (lane >= o && bo == bin) {
+                v0 += t0; v1 += t1; v2 += t2; v3 += t3;
             }
         }
         const int bnext = __shfl_down_sync(kFull, bin, 1);
@@ -316,35 +348,68 @@ __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, co
         }
         __syncwarp();
     }
+}
+
+// This lane's FP64 partial of M = sum_i m_i (the cumulative mass integral);
+// warp_sum_d of it gives M.
+__device__ __forceinline__ double mass_partial(const Consts& c, const AgeView& v) {
     double acc = 0.0;
 #pragma unroll 4
-    for (int i = lane; i < A; i += 32) acc += (double)v.m[i];
-    return warp_sum_d(acc);
+    for (int i = lane_id(); i < c.n_age; i += 32) acc += (double)v.m[i];
+    return acc;
+}
+
+__device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
+                                           float lnT, float tau, float alpha, float beta, bool grad) {
+    sfh_bins_raw(c, v, bins, lnT, tau, alpha, beta, grad);
+    return warp_sum_d(mass_partial(c, v));
 }
 
 // ---------------------------------------------------------------- burst + MDF
+// Burst weights pi_i = (T(x_{i+1}) - T(x_i)) / D over the log-age edges
+// clipped at t_obs, T the triweight CDF.  Each lane evaluates the CDF at one
+// edge; the lower edge of a bin comes from the neighbouring lane.
 __device__ __forceinline__ float burst_weights(const Consts& c, const AgeView& v, float lT10,
                                                float mu, float sig) {
+    const int lane = lane_id();
+    const int A = c.n_age;
     const float isig = 1.0f / sig;
     const float D = tri_cdf((lT10 - mu) * isig);
     const float invD = 1.0f / D;
-#pragma unroll 4
-    for (int i = lane_id(); i < c.n_age; i += 32) {
-        const float lo = fminf(v.age_edge[i], lT10);
-        const float hi = fminf(v.age_edge[i + 1], lT10);
-        v.pi[i] = (tri_cdf((hi - mu) * isig) - tri_cdf((lo - mu) * isig)) * invD;
+    float carry = 0.0f;                          // CDF at the last edge of the previous group
+#pragma unroll 1
+    for (int e0 = 0; e0 <= A; e0 += 32) {
+        const int e = e0 + lane;
+        const float F = (e <= A) ? tri_cdf((fminf(v.age_edge[e], lT10) - mu) * isig) : 0.0f;
+        float Fl = __shfl_up_sync(kFull, F, 1);
+        if (lane == 0) Fl = carry;
+        if (e >= 1 && e <= A) v.pi[e - 1] = (F - Fl) * invD;
+        carry = __shfl_sync(kFull, F, 31);
     }
     return D;
 }
 
+// Metallicity weights q_j = Phi(y_{j+1}) - Phi(y_j), y = (edge - mu) / sd.
+// Each lane takes one edge and the smaller tail T = Phi(-|y|) there, so that a
+// bin in either tail is a difference of small numbers.
 __device__ __forceinline__ void met_weights(const Consts& c, const AgeView& v, float mu, float sd) {
-    const int j = lane_id();
+    const int e = lane_id();
+    const int Zn = c.n_met;
     const float isd = 1.0f / sd;
-    if (j < c.n_met) {
-        const float ylo = (v.lgz_edge[j] - mu) * isd;
-        const float yhi = (v.lgz_edge[j + 1] - mu) * isd;
-        v.q[j] = (ylo > 0.0f) ? normcdff(-ylo) - normcdff(-yhi) : normcdff(yhi) - normcdff(ylo);
+    float T = 0.0f;
+    bool pos = false;
+    if (e <= Zn) {
+        const float y = (v.lgz_edge[e] - mu) * isd;
+        T = 0.5f * erfcf(fabsf(y) * 0.70710678118654752f);
+        pos = y >= 0.0f;
     }
+    float Th = __shfl_down_sync(kFull, T, 1);
+    bool ph = __shfl_down_sync(kFull, pos ? 1 : 0, 1) != 0;
+    if (e == Zn - 1) {                           // the top edge is +inf
+        Th = 0.0f;
+        ph = true;
+    }
+    if (e < Zn) v.q[e] = pos ? (T - Th) : (ph ? (1.0f - Th) - T : Th - T);
 }
 
 __device__ __forceinline__ float phi_y(float y) {  // y phi(y), 0 at +-inf
@@ -388,19 +453,30 @@ __device__ __forceinline__ void load_params(const Consts& c, const float* __rest
 }
 
 // ---------------------------------------------------------------- weights stage
-// Fills v.m/dm, v.pi, v.q, v.w for parameters th[12]; returns M (FP64).
-__device__ __forceinline__ double age_met_weights(const Consts& c, const AgeView& v,
-                                                  const float2* __restrict__ bins, float lnT,
-                                                  float lT10, const float* th, bool grad) {
-    double M = sfh_bins(c, v, bins, lnT, th[1], th[2], th[3], grad);
+// Bin integrals, burst and metallicity weights (everything but M and w).
+__device__ __forceinline__ void age_met_parts(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
+                                              float lnT, float lT10, const float* th, bool grad) {
+    sfh_bins_raw(c, v, bins, lnT, th[1], th[2], th[3], grad);
     burst_weights(c, v, lT10, th[5], th[6] * (1.0f / 3.0f));
     met_weights(c, v, th[7], th[8]);
+}
+// w_i = (1 - F_burst) m_i + F_burst pi_i M.
+__device__ __forceinline__ void age_weights(const Consts& c, const AgeView& v, const float* th, double M) {
     __syncwarp();
     const float fb = th[4];
     const float Mf = (float)M;
 #pragma unroll 4
     for (int i = lane_id(); i < c.n_age; i += 32) v.w[i] = (1.0f - fb) * v.m[i] + fb * v.pi[i] * Mf;
     __syncwarp();
+}
+// Fills v.m/dm, v.pi, v.q, v.w for parameters th[12]; returns M (FP64).
+__device__ __forceinline__ double age_met_weights(const Consts& c, const AgeView& v,
+                                                  const float2* __restrict__ bins, float lnT,
+                                                  float lT10, const float* th, bool grad) {
+    age_met_parts(c, v, bins, lnT, lT10, th, grad);
+    __syncwarp();
+    const double M = warp_sum_d(mass_partial(c, v));
+    age_weights(c, v, th, M);
     return M;
 }
 __device__ __forceinline__ double age_met_weights(const Consts& c, RowScratch& s,
@@ -437,22 +513,25 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
         s_d0 += d0;
         s_d1 += d1;
         s_d2 += d2;
-        const float lo = fminf(s.age_edge[i], lT10);
-        const float hi = fminf(s.age_edge[i + 1], lT10);
-        const float xl = (lo - mu) * isig, xh = (hi - mu) * isig;
-        const float tl = tri_pdf(xl), tH = tri_pdf(xh);
-        s_mu = fmaf(wb, tl - tH, s_mu);
-        s_sg = fmaf(wb, xl * tl - xh * tH, s_sg);
     }
-    // metallicity: q_j = Phi(yh) - Phi(yl)
+    // burst, edge by edge: sum_i wbar_i (T(x_i) - T(x_{i+1})) = sum_e T(x_e) (wbar_e - wbar_{e-1})
+#pragma unroll 1
+    for (int e = lane; e <= A; e += 32) {
+        const float x = (fminf(s.age_edge[e], lT10) - mu) * isig;
+        const float d = ((e < A) ? s.wb[e] : 0.0f) - ((e > 0) ? s.wb[e - 1] : 0.0f);
+        const float tp = tri_pdf(x) * d;
+        s_mu += tp;
+        s_sg = fmaf(x, tp, s_sg);
+    }
+    // metallicity: q_j = Phi(y_{j+1}) - Phi(y_j), edge by edge
     const float mz = th[7], sz = th[8];
     const float isz = 1.0f / sz;
     float s_gz = 0.f, s_gs = 0.f;
-    if (lane < c.n_met) {
-        const float yl = (s.lgz_edge[lane] - mz) * isz, yh = (s.lgz_edge[lane + 1] - mz) * isz;
-        const float qb = s.qb[lane];
-        s_gz = qb * (phi_(yl) - phi_(yh));
-        s_gs = qb * (phi_y(yl) - phi_y(yh));
+    if (lane <= c.n_met) {
+        const float y = (s.lgz_edge[lane] - mz) * isz;
+        const float d = ((lane < c.n_met) ? s.qb[lane] : 0.0f) - ((lane > 0) ? s.qb[lane - 1] : 0.0f);
+        s_gz = phi_(y) * d;
+        s_gs = phi_y(y) * d;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

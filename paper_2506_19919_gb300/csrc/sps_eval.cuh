@@ -89,7 +89,7 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
         float4 dc = d.dust[lane];
         dt = dust_eval(dc.x, dc.y, dc.z, p.th[9], p.th[10], p.th[11]);
         S = s.slot_S[lane];
-        double lc = log10((double)dt.F * (double)S) + (double)p.th[0] + 9.0;
+        double lc = log10_flux(dt.F * S) + (double)p.th[0] + 9.0;
         double m = d.zp[lane] - 2.5 * lc;
         d.mag[lane] = m;
         if (like) {
