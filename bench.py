@@ -42,6 +42,22 @@ ESS_TARGET = 100.0
 METRIC = "posteriors/min at fixed ESS"
 UNIT = "posteriors/min"
 
+# DRAM traffic of one k_hmc_team launch on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of five full-size launches in one ncu capture,
+# profiles/k_hmc_team_hmc4096gal_x4_launches.md), valid only while the
+# kernel's sources hash to the recorded value; otherwise reported as null.
+KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_internal.h", "philox.cuh")
+TRAFFIC = {"sha": "adf03b15b2bd83fa", "bytes": 116.0e9 + 0.39e9}
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_19919_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -238,7 +254,7 @@ def run_ours(args):
         "grad_evals_per_s": float(nev.sum()) * ws / (ms_step / 1e3),
         "roofline": {"kernel": "k_hmc_team", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     "traffic": TRAFFIC["bytes"] if _kernel_sha() == TRAFFIC["sha"] else None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived)",
                      "algorithmic": "4 * n_obs_bands * K FLOP per gradient evaluation"},
         "clocks": clocks,
