@@ -451,6 +451,69 @@ def run_loglike_only(args):
     print(json.dumps(out))
 
 
+def run_survey(args):
+    """Throughput on the large bursty survey batch (1,000,000 galaxies x 2
+    chains, 20 bands, 6-20 observed, burst on, 300 + 300 iterations): table
+    build, log L + gradient on all 2,000,000 (galaxy, chain) pairs (FP32
+    approximate and BF16 exact), and the HMC kernel on all chains for a few
+    iterations, projected to the full run by its cost per iteration."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    wl = W.config(4)
+    G, C = wl.n_gal, wl.chains
+    dev = torch.device("cuda", 0)
+    ctx = pkg.Context(wl.tables, device=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.set_galaxies(wl.z, build_approx=True)
+    torch.cuda.synchronize()
+    t_tables = time.perf_counter() - t0
+    th = torch.as_tensor(np.repeat(wl.theta_true, C, axis=0), dtype=torch.float32, device=dev)
+    gi = torch.as_tensor(np.repeat(np.arange(G, dtype=np.int32), C), device=dev)
+    mobs = torch.as_tensor((np.full((G, 20), 23.0) + wl.noise).astype(np.float32), device=dev)
+    sigma = torch.as_tensor(wl.sigma, device=dev)
+    mask = torch.as_tensor(wl.mask.view(np.int32), device=dev)
+    out = {"workload": W.CONFIG_NAMES[4], "galaxies": G, "chains_per_gal": C, "bands": 20,
+           "table_build_s": t_tables}
+
+    def rate(fn, n, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms": ms, "evals_per_s": n / (ms / 1e3)}
+    out["loglike_grad_approx_fp32"] = rate(
+        lambda: ctx.loglike_grad(th, mobs, sigma, mask, gal_idx=gi, mode="approx"), G * C, 3)
+    out["loglike_grad_exact_bf16"] = rate(
+        lambda: ctx.loglike_grad(th[::C].contiguous(), mobs, sigma, mask, mode="exact", prec="bf16"), G, 2)
+    x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
+    n_it = wl.extra["n_warm"] + wl.extra["n_samp"]
+    kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"], samples=False)
+    ctx.hmc_run(x0, mobs, sigma, mask, n_warm=2, n_samp=0, **kw)
+    torch.cuda.synchronize()
+    runs = {}
+    for it in (4, 12):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = ctx.hmc_run(x0, mobs, sigma, mask, n_warm=it, n_samp=0, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        runs[it] = (e0.elapsed_time(e1) / 1e3, float(o["grad_evals"].sum()))
+    per_it = (runs[12][0] - runs[4][0]) / 8.0
+    out["hmc"] = {"iterations_timed": [4, 12], "s": [runs[4][0], runs[12][0]],
+                  "s_per_iteration": per_it, "grad_evals_per_s": (runs[12][1] - runs[4][1]) / (runs[12][0] - runs[4][0]),
+                  "projected_s_for_300_plus_300": runs[4][0] + per_it * (n_it - 4),
+                  "note": "warm-up iterations from prior draws; cost per iteration from the 12-4 difference"}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_reference(args):
     """The FP64 oracle timed on the host cores (rank 0 only)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -497,6 +560,8 @@ def main():
     ap.add_argument("--gal", type=int, default=None)
     ap.add_argument("--warm", type=int, default=None)
     ap.add_argument("--samp", type=int, default=None)
+    ap.add_argument("--survey", action="store_true",
+                    help="throughput on the 1,000,000-galaxy survey batch (not the bench line)")
     ap.add_argument("--loglike-only", default=None,
                     help="comma list of mode_prec (e.g. exact_bf16,approx_fp32)")
     args = ap.parse_args()
@@ -508,6 +573,8 @@ def main():
         run_reference(args)
     elif args.loglike_only:
         run_loglike_only(args)
+    elif args.survey:
+        run_survey(args)
     else:
         run_ours(args)
 

@@ -453,6 +453,10 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
     CK(ctx->cJ.reserve((size_t)rows * c.n_band * 4 * 4));
     CK(ctx->rowinfo.reserve((size_t)rows * 4 * 4));
     CK(ctx->gbar.reserve((size_t)rows * c.n_band * 4));
+    if (tc) CK(ctx->zperm.reserve(sizeof(int32_t) * (2 * (size_t)rows + (size_t)zsort_buckets())));
+    int32_t* perm = tc ? ctx->zperm.as<int32_t>() : nullptr;
+    int32_t* pos_of = tc ? perm + rows : nullptr;
+    int32_t* zcounts = tc ? perm + 2 * rows : nullptr;
     if (grad_out) {
         CK(ctx->V.reserve((size_t)rows * c.lam_pad * 4));
         CK(ctx->Wbar.reserve((size_t)rows * c.k_pad * 4));
@@ -481,13 +485,15 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
             if (gv.cssp) gv.cssp += r0 * c.n_band * c.K;
             gv.n = m;
         }
-        CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s));
+        if (tc) CK(launch_zsort(gv, gi, m, perm, pos_of, zcounts, s));
+        CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s,
+                                pos_of));
         if (tc) {
             CUtensorMap ta, tb;
             if (!make_tmap_bf16(&ta, ctx->W.p, c.k_pad, m, c.k_pad, 128) ||
                 !make_tmap_bf16(&tb, ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256))
                 return fail(SPS_E_CUDA, "tensor map encoding failed");
-            CK(launch_fwd_tc(ta, tb, c, grid, gv, th, gi, m, ctx->cJ.as<float>(), terr, s));
+            CK(launch_fwd_tc(ta, tb, c, grid, gv, th, gi, perm, m, ctx->cJ.as<float>(), terr, s));
         } else {
             CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
                                 ctx->cJ.as<float>(), s));

@@ -57,6 +57,7 @@ struct sps_ctx {
     DevBuf nonfinite, queue, err;
     DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
     DevBuf pst, pth, pll, pgr, pgi;   // plain lock-step HMC state and gradient buffers
+    DevBuf zperm;                     // redshift order of the rows of a tensor-core chunk
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -97,7 +98,7 @@ struct sps_ctx {
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
-                         &pgi};
+                         &pgi, &zperm};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

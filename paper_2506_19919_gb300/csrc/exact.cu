@@ -35,7 +35,8 @@ __device__ __forceinline__ float ld_elem<uint16_t>(const uint16_t* p) { return b
 __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
           const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
-          int bf16, float* __restrict__ W32, uint16_t* __restrict__ Wbf) {
+          int bf16, float* __restrict__ W32, uint16_t* __restrict__ Wbf,
+          const int32_t* __restrict__ pos_of) {
     __shared__ RowScratch scratch[kWarpsApprox];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     RowScratch& s = scratch[warp];
@@ -52,6 +53,7 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
             if (lane < c.n_met) s.q[lane] = 1.0f;
             __syncwarp();
         }
+        const int64_t wr = pos_of ? (int64_t)pos_of[row] : row;
         for (int k = lane; k < c.k_pad; k += 32) {
             float v = 0.0f;
             int i = 0;
@@ -59,8 +61,8 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
                 i = k / c.n_met;
                 v = s.w[i] * s.q[k % c.n_met];
             }
-            if (bf16) Wbf[row * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
-            else W32[row * c.k_pad + k] = v;
+            if (bf16) Wbf[wr * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
+            else W32[wr * c.k_pad + k] = v;
         }
         __syncwarp();
     }
@@ -415,10 +417,68 @@ int blocks_rows(int64_t rows, int per_block) {
 
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
                                  const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
-                                 float* W32, uint16_t* Wbf, cudaStream_t s) {
+                                 float* W32, uint16_t* Wbf, cudaStream_t s, const int32_t* pos_of) {
     if (n <= 0) return cudaSuccess;
     k_weights<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, grid, g, theta, gal_idx,
-                                                                         n, bf16, W32, Wbf);
+                                                                         n, bf16, W32, Wbf, pos_of);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- redshift order
+// Rows bucketed by log(1 + z) of their galaxy (2048 buckets over [0, 2.5]),
+// so that the rows of a tensor-core tile see nearly the same band supports.
+constexpr int kZBuckets = 2048;
+
+int zsort_buckets() { return kZBuckets; }
+
+namespace {
+__device__ __forceinline__ int zbucket(const Galaxies& g, const int32_t* gal_idx, int64_t row) {
+    const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+    const float z = (gi >= 0 && gi < g.n) ? g.z[gi] : 0.0f;
+    const float u = log1pf(fmaxf(z, 0.0f)) * ((float)kZBuckets / 2.5f);
+    return (u < (float)(kZBuckets - 1)) ? (int)u : kZBuckets - 1;   // NaN goes last
+}
+__global__ void k_zcount(const Galaxies g, const int32_t* __restrict__ gal_idx, int64_t n, int32_t* counts) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row < n) atomicAdd(&counts[zbucket(g, gal_idx, row)], 1);
+}
+// Exclusive scan of the bucket counts in place (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_zscan(int32_t* counts) {
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int a = counts[2 * t], b = counts[2 * t + 1];
+    part[t] = a + b;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = (t >= o) ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    const int base = part[t] - (a + b);
+    counts[2 * t] = base;
+    counts[2 * t + 1] = base + a;
+}
+__global__ void k_zscatter(const Galaxies g, const int32_t* __restrict__ gal_idx, int64_t n, int32_t* cursor,
+                           int32_t* __restrict__ perm, int32_t* __restrict__ pos_of) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int pos = atomicAdd(&cursor[zbucket(g, gal_idx, row)], 1);
+    perm[pos] = (int32_t)row;
+    pos_of[row] = pos;
+}
+}  // namespace
+
+cudaError_t launch_zsort(const Galaxies& g, const int32_t* gal_idx, int64_t n, int32_t* perm,
+                         int32_t* pos_of, int32_t* counts, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    static_assert(kZBuckets == 2 * 1024, "scan layout");
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kZBuckets, s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_zcount<<<blocks, 256, 0, s>>>(g, gal_idx, n, counts);
+    k_zscan<<<1, 1024, 0, s>>>(counts);
+    k_zscatter<<<blocks, 256, 0, s>>>(g, gal_idx, n, counts, perm, pos_of);
     return cudaGetLastError();
 }
 

@@ -26,8 +26,8 @@ namespace {
 constexpr int kTM = 128;       // rows per tile (MMA M)
 constexpr int kBK = 64;        // bf16 per k-block row (128 bytes)
 constexpr int kThreadsTC = 192;   // adjoint: TMA warp, MMA warp, 4 epilogue warps
-constexpr int kFwdEpiWarps = 8;   // forward: two epilogue warps per TMEM lane quarter
-constexpr int kThreadsFwd = 64 + 32 * kFwdEpiWarps;
+constexpr int kFwdGroupBands = 8; // forward: bands per epilogue warp
+constexpr int kFwdMaxEpiWarps = 16;
 constexpr int kFwdBN = 256;
 constexpr int kFwdStages = 4;
 constexpr int kAdjBN = 192;
@@ -180,12 +180,6 @@ __device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
 
 static_assert(sizeof(Ctl) <= 256, "control block must fit before the staging area");
 
-// Per-warp staging of a tile's per-wavelength constants (forward epilogue).
-struct LamStage {
-    float4 lc[kFwdBN / 2];
-    float lam[kFwdBN / 2];
-};
-
 template <int BN, int STAGES>
 __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
     uintptr_t p = reinterpret_cast<uintptr_t>(raw);
@@ -196,12 +190,19 @@ __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
 }
 
 // ---------------------------------------------------------------- forward
-template <int NB>
-__global__ void __launch_bounds__(kThreadsFwd, 1)
+// Epilogue layout: 4 x n_groups x n_halves warps.  A warp reads the TMEM lane
+// quarter q = (warp id mod 4) (32 rows) of each tile, for the bands of its group (<= 8, held in
+// registers) and, when one group covers all bands, for one half of the tile's
+// columns.  Rows arrive sorted by redshift (perm), so the 32 rows of a warp see
+// nearly the same band supports: a band is visited in a 32-column chunk only if
+// it overlaps the chunk in some lane.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
 k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
          const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
-         const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
-         float* __restrict__ cJ, int* err) {
+         const float* __restrict__ theta, const int32_t* __restrict__ gal_idx,
+         const int32_t* __restrict__ perm, int64_t n, int n_halves, float* __restrict__ cJ, int* err) {
+    constexpr int NB = kFwdGroupBands;
     extern __shared__ unsigned char smem_raw[];
     Ctl* ctl;
     uint8_t* ring = carve<kFwdBN, kFwdStages>(smem_raw, ctl);
@@ -209,19 +210,22 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
     const int m0 = blockIdx.x * kTM;
     const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
     const int n_kb = c.k_pad / kBK;
-    LamStage* stage = reinterpret_cast<LamStage*>(reinterpret_cast<unsigned char*>(ctl) + 256);
-    tc_setup<kFwdStages>(ctl, warp, kFwdEpiWarps * 32);
+    const int epi_threads = (int)blockDim.x - 64;
+    tc_setup<kFwdStages>(ctl, warp, epi_threads);
     if (warp == 0) {
         if (lane == 0) tc_produce<kFwdBN, kFwdStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
     } else if (warp == 1) {
         if (lane == 0) tc_mma<kFwdBN, kFwdStages>(ctl, ring, n_tiles, n_kb, err);
     } else {
-        const int q = warp & 3;                    // TMEM lane quarter of this warp
-        const int half = (warp - 2) >> 2;          // which half of each tile's columns
-        LamStage& ls = stage[warp - 2];
+        const int e = warp - 2;
+        const int q = warp & 3;                    // TMEM lane quarter this warp may access (warp id mod 4)
+        const int half = (e >> 2) % n_halves;      // column half (one group only)
+        const int b0 = ((e >> 2) / n_halves) * NB; // first band of this warp's group
+        const int ncol = kFwdBN / n_halves;
         const int rl = 32 * q + lane;
-        const int64_t row = (int64_t)m0 + rl;
-        const bool live = row < n;
+        const int64_t pos = (int64_t)m0 + rl;
+        const bool live = pos < n;
+        const int64_t row = live ? (perm ? (int64_t)perm[pos] : pos) : 0;
         const int B = c.n_band;
         int64_t gi = live ? (gal_idx ? (int64_t)gal_idx[row] : row) : 0;
         const bool valid = live && gi >= 0 && gi < g.n;
@@ -233,83 +237,83 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
             dl = t[10];
             eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
         }
-        int sx[NB], sy[NB];
+        uint32_t sxy[NB];                          // support [lo, hi): lo | hi << 16
         float gc[NB], gs[NB];
         float acc[NB][4];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
+        for (int k = 0; k < NB; ++k) {
+            const int b = b0 + k;
             int2 sp = make_int2(0, 0);
             float2 ga = make_float2(0.f, 0.f);
             if (b < B && valid) {
                 sp = g.support[gi * B + b];
                 ga = g.gauss[gi * B + b];
             }
-            sx[b] = sp.x;
-            sy[b] = sp.y;
-            gc[b] = ga.x;
-            gs[b] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 marks a top-hat
-            acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0f;
+            sxy[k] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
+            gc[k] = ga.x;
+            gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 marks a top-hat
+            acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
         }
         for (int nt = 0; nt < n_tiles; ++nt) {
             const int buf = nt & 1;
             const uint32_t use = (uint32_t)(nt >> 1);
             if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
             tc::tc_fence_after();
-            const int col0 = nt * kFwdBN + half * (kFwdBN / 2);
-            for (int t = lane; t < kFwdBN / 2; t += 32) {
-                const int nn = min(col0 + t, c.n_lam - 1);    // columns past the grid hold S = 0
-                ls.lc[t] = __ldg(grid.lamc + nn);
-                ls.lam[t] = __ldg(grid.lam + nn);
-            }
-            __syncwarp();
-            for (int cc = 0; cc < kFwdBN / 64; ++cc) {
+            const int col0 = nt * kFwdBN + half * ncol;
+            for (int cc = 0; cc < ncol / 32; ++cc) {
+                const int nb0 = col0 + cc * 32;
+                if (nb0 >= c.n_lam) break;                 // warp-uniform
                 float S[32];
                 tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
-                                  (uint32_t)(buf * kFwdBN + half * (kFwdBN / 2) + cc * 32), S);
-                const int nb0 = col0 + cc * 32;
+                                  (uint32_t)(buf * kFwdBN + half * ncol + cc * 32), S);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int nn = min(nb0 + j, c.n_lam - 1);
-                    const float4 L4 = ls.lc[cc * 32 + j];
-                    const float lam = ls.lam[cc * 32 + j];
-                    const float pw = __expf(dl * L4.z);
-                    const float base = L4.y * pw + eb * L4.w;
-                    const float E = exp2f(cA * base);
-                    const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
+                for (int k = 0; k < NB; ++k) {
+                    const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+                    const bool ov = lo < nb0 + 32 && hi > nb0;
+                    if (!__any_sync(0xffffffffu, ov)) continue;
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        if (nn >= sx[b] && nn < sy[b]) {
+                    for (int j = 0; j < 32; ++j) {
+                        const int nn = nb0 + j;
+                        if (nn >= lo && nn < hi) {
+                            const float4 L4 = __ldg(grid.lamc + nn);
+                            const float pw = __expf(dl * L4.z);
+                            const float base = L4.y * pw + eb * L4.w;
+                            const float E = exp2f(cA * base);
+                            const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
                             float w = L4.x;
-                            if (gs[b] != 0.0f) {
-                                const float u = (lam - gc[b]) * gs[b];
+                            if (gs[k] != 0.0f) {
+                                const float u = (__ldg(grid.lam + nn) - gc[k]) * gs[k];
                                 w *= __expf(-0.5f * u * u);
                             }
                             const float Sw = S[j] * w;
                             const float es = Sw * E;
-                            acc[b][0] += Sw;
-                            acc[b][1] += es;
-                            acc[b][2] += es * base;
-                            acc[b][3] += es * dterm;
+                            a0 += Sw;
+                            a1 += es;
+                            a2 = fmaf(es, base, a2);
+                            a3 = fmaf(es, dterm, a3);
                         }
                     }
+                    acc[k][0] += a0;
+                    acc[k][1] += a1;
+                    acc[k][2] += a2;
+                    acc[k][3] += a3;
                 }
             }
-            __syncwarp();
             tc::tc_fence_before();
             tc::mbar_arrive(&ctl->tempty[buf]);
         }
-        // the two column halves of a row meet here: cJ is zeroed before the
-        // launch and gets exactly two addends, so the sum does not depend on
-        // their order
+        // cJ is zeroed before the launch; a (row, band) gets one addend per
+        // column half, so the sum does not depend on their order
         if (valid && !ctl->abort) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
-                if (b < B) {
-                    float* o = cJ + (row * B + b) * 4;
-                    atomicAdd(o + 0, acc[b][0]);
-                    atomicAdd(o + 1, acc[b][1]);
-                    atomicAdd(o + 2, acc[b][2]);
-                    atomicAdd(o + 3, acc[b][3]);
+            for (int k = 0; k < NB; ++k)
+                if (b0 + k < B) {
+                    float* o = cJ + (row * B + b0 + k) * 4;
+                    atomicAdd(o + 0, acc[k][0]);
+                    atomicAdd(o + 1, acc[k][1]);
+                    atomicAdd(o + 2, acc[k][2]);
+                    atomicAdd(o + 3, acc[k][3]);
                 }
         }
     }
@@ -363,28 +367,31 @@ k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
 
 }  // namespace
 
-size_t tc_fwd_smem() {
-    return Ring<kFwdBN, kFwdStages>::kBytes + 256 + sizeof(LamStage) * kFwdEpiWarps + 1024;
-}
+size_t tc_fwd_smem() { return Ring<kFwdBN, kFwdStages>::kBytes + 256 + 1024; }
 size_t tc_adj_smem() { return Ring<kAdjBN, kAdjStages>::kBytes + sizeof(Ctl) + 1024; }
 
 cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
                           const Grid& grid, const Galaxies& g, const float* theta,
-                          const int32_t* gal_idx, int64_t n, float* cJ, int* err, cudaStream_t s) {
+                          const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ, int* err,
+                          cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
     const size_t smem = tc_fwd_smem();
+    const int groups = (c.n_band + kFwdGroupBands - 1) / kFwdGroupBands;   // <= 4 (B <= 32)
+    const int halves = groups == 1 ? 2 : 1;
+    const int threads = 64 + 32 * 4 * groups * halves;
     cudaError_t e = cudaMemsetAsync(cJ, 0, (size_t)n * c.n_band * 4 * sizeof(float), s);
     if (e != cudaSuccess) return e;
-    if (c.n_band <= 8) {
-        e = cudaFuncSetAttribute(k_fwd_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_fwd_tc<8><<<blocks, kThreadsFwd, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
-    } else {
-        e = cudaFuncSetAttribute(k_fwd_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_fwd_tc<32><<<blocks, kThreadsFwd, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, n, cJ, err);
-    }
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
+        kern<<<blocks, threads, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, perm, n, halves, cJ, err);
+        return cudaSuccess;
+    };
+    if (threads <= 64 + 32 * 8) e = go(k_fwd_tc<64 + 32 * 8>);            // up to 16 bands
+    else if (threads <= 64 + 32 * 12) e = go(k_fwd_tc<64 + 32 * 12>);     // up to 24 bands
+    else e = go(k_fwd_tc<64 + 32 * kFwdMaxEpiWarps>);                    // up to 32 bands
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -98,7 +98,8 @@ cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* 
 // Exact path pieces.
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
                                  const float* theta, const int32_t* gal_idx, int64_t n,
-                                 int bf16, float* W32, uint16_t* Wbf, cudaStream_t s);
+                                 int bf16, float* W32, uint16_t* Wbf, cudaStream_t s,
+                                 const int32_t* pos_of = nullptr);   // W row of each row (or itself)
 cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
                              const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s);
@@ -123,7 +124,13 @@ size_t tc_fwd_smem();
 size_t tc_adj_smem();
 cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
                           const Grid& grid, const Galaxies& g, const float* theta,
-                          const int32_t* gal_idx, int64_t n, float* cJ, int* err, cudaStream_t s);
+                          const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ, int* err,
+                          cudaStream_t s);
+// Rows ordered by redshift (bucketed in log(1+z)): perm[pos] = row,
+// pos_of[row] = pos; counts is scratch of zsort_buckets() ints.
+int zsort_buckets();
+cudaError_t launch_zsort(const Galaxies& g, const int32_t* gal_idx, int64_t n, int32_t* perm,
+                         int32_t* pos_of, int32_t* counts, cudaStream_t s);
 cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
                           const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s);
 
