@@ -364,7 +364,7 @@ def _loglike_grad_rates(ctx_hmc, dev):
                           mode="approx") + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)
     res = {"pairs": wl.n_gal, "workload": W.CONFIG_NAMES[2]}
     for mode, prec, reps in (("approx", "fp32", 10), ("plain", "fp32", 3), ("exact", "fp32", 2),
-                             ("exact", "bf16", 3)):
+                             ("exact", "bf16", 3), ("exact", "tf32x3", 3)):
         def call():
             if mode == "plain":
                 ctx.loglike_grad_forward_mode(th, mobs, wl.sigma, wl.mask)

@@ -69,7 +69,14 @@ typedef enum {
 } sps_status;
 
 typedef enum { SPS_EXACT = 0, SPS_APPROX = 1 } sps_mode;
-typedef enum { SPS_FP32 = 0, SPS_BF16 = 1 } sps_prec;
+/* Arithmetic of the exact path's SSP contraction:
+ *  SPS_FP32   FP32 SIMT (the reference precision: ~4e-6 mag, gradients ~1e-5);
+ *  SPS_BF16   BF16 operands with per-age-row power-of-two scaling, FP32
+ *             accumulation on the tensor cores (~1e-3 mag);
+ *  SPS_TF32X3 FP32 operands split into TF32 halves, hi*hi + hi*lo + lo*hi on
+ *             the tensor cores (~3e-5 mag, gradients ~1e-3: the tensor-core
+ *             accumulation over the 1284-term contraction limits it). */
+typedef enum { SPS_FP32 = 0, SPS_BF16 = 1, SPS_TF32X3 = 2 } sps_prec;
 typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1 } sps_band_kind;
 
 /* Model grids, SSP table and filters (host memory, float64; copied in).
@@ -129,8 +136,7 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
 /* AB magnitudes of n rows: theta[n][12] -> mag_out[n][n_band].
  * mode EXACT: Eq. photo_integral_exact (SSP contraction over the full
  * wavelength grid, dust and filters applied per wavelength); prec selects the
- * contraction arithmetic (FP32, or BF16 operands with per-age-row power-of-two
- * scaling and FP32 accumulation).  mode APPROX: Eq. photo_integral_approx
+ * contraction arithmetic (sps_prec).  mode APPROX: Eq. photo_integral_approx
  * (FP32; prec must be SPS_FP32).  Rows whose theta is non-finite give NaN
  * magnitudes and SPS_E_NONFINITE (the other rows are still valid). */
 sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,

@@ -13,13 +13,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (SPS_APPROX, SPS_BF16, SPS_EXACT, SPS_FP32, SpsError, check, load, sps_config,
+from ._lib import (SPS_APPROX, SPS_BF16, SPS_EXACT, SPS_FP32, SPS_TF32X3, SpsError, check, load, sps_config,
                    sps_hmc_config, sps_hmc_stats, sps_info, sps_tables)
 
 __all__ = ["Context", "diagnostics", "SpsError", "load", "MODES", "PRECS"]
 
 MODES = {"exact": SPS_EXACT, "approx": SPS_APPROX}
-PRECS = {"fp32": SPS_FP32, "bf16": SPS_BF16}
+PRECS = {"fp32": SPS_FP32, "bf16": SPS_BF16, "tf32x3": SPS_TF32X3}
 
 
 def _vp(t):

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "SPS_OK", 1: "SPS_E_INVALID_ARG", 2: "SPS_E_SHAPE", 3: "SPS_E
                 4: "SPS_E_CUDA", 5: "SPS_E_TIMEOUT", 6: "SPS_E_UNSUPPORTED", 7: "SPS_E_STATE",
                 8: "SPS_E_NOMEM"}
 SPS_EXACT, SPS_APPROX = 0, 1
-SPS_FP32, SPS_BF16 = 0, 1
+SPS_FP32, SPS_BF16, SPS_TF32X3 = 0, 1, 2
 
 
 class sps_tables(C.Structure):

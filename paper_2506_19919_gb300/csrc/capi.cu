@@ -113,6 +113,33 @@ bool make_tmap_bf16(CUtensorMap* m, const void* base, uint64_t inner, uint64_t r
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D FP32 tensor [rows][inner] (row stride `ld` elements), box {32, box_rows}
+// (128-byte rows), 128-byte swizzle, zero fill outside the tensor.
+bool make_tmap_f32(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
+                   uint32_t box_rows) {
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {ld * 4};
+    cuuint32_t box[2] = {32, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// hi = x rounded to nearest (ties away) to TF32, lo = x - hi.
+void tf32_split_host(float x, float& hi, float& lo) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {      // finite: round at mantissa bit 13
+        u += 0x1000u;
+        u &= 0xffffe000u;
+    }
+    std::memcpy(&hi, &u, 4);
+    lo = x - hi;
+}
+
 }  // namespace
 
 namespace {
@@ -366,8 +393,16 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         if (e != cudaSuccess) return e;
         return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
     };
+    // 3xTF32 halves of the FP32 tables
+    std::vector<float> s_hi(s32.size()), s_lo(s32.size()), st_hi(st32.size()), st_lo(st32.size());
+    for (size_t i = 0; i < s32.size(); ++i) tf32_split_host(s32[i], s_hi[i], s_lo[i]);
+    for (size_t i = 0; i < st32.size(); ++i) tf32_split_host(st32[i], st_hi[i], st_lo[i]);
     cudaError_t e = cudaSuccess;
     if ((e = upload(ctx->lam64, t->lam_ang, sizeof(double) * L)) != cudaSuccess ||
+        (e = upload(ctx->ssp_hi, s_hi.data(), s_hi.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->ssp_lo, s_lo.data(), s_lo.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->ssp_t_hi, st_hi.data(), st_hi.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->ssp_t_lo, st_lo.data(), st_lo.size() * 4)) != cudaSuccess ||
         (e = upload(ctx->ssp, s32.data(), s32.size() * 4)) != cudaSuccess ||
         (e = upload(ctx->ssp_t, st32.data(), st32.size() * 4)) != cudaSuccess ||
         (e = upload(ctx->ssp_bf, sbf.data(), sbf.size() * 2)) != cudaSuccess ||
@@ -443,13 +478,18 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
 }
 
 static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gidx, int64_t n,
-                            const float* mobs, const float* sigma, const uint32_t* mask, int bf16,
+                            const float* mobs, const float* sigma, const uint32_t* mask, sps_prec prec,
                             float* mag_out, float* ll_out, float* grad_out, cudaStream_t s) {
     const Consts& c = ctx->c;
-    const bool tc = bf16 && ctx->use_tc;
-    const int64_t chunk = tc ? 131072 : 32768;
+    // tcgen05 for BF16 operands (SIMT when disabled) and for 3xTF32; FP32 is SIMT
+    if (prec == SPS_TF32X3 && !ctx->use_tc) return fail(SPS_E_UNSUPPORTED, "3xTF32 needs the tensor cores");
+    const int bf16 = prec == SPS_BF16 ? 1 : 0;
+    const bool tf = prec == SPS_TF32X3;
+    const bool tc = tf || (bf16 && ctx->use_tc);
+    const int64_t chunk = tc ? (tf ? 65536 : 131072) : 32768;
     const int64_t rows = std::min<int64_t>(n, chunk);
     CK(ctx->W.reserve((size_t)rows * c.k_pad * 4));
+    if (tf) CK(ctx->Wlo.reserve((size_t)rows * c.k_pad * 4));
     CK(ctx->cJ.reserve((size_t)rows * c.n_band * 4 * 4));
     CK(ctx->rowinfo.reserve((size_t)rows * 4 * 4));
     CK(ctx->gbar.reserve((size_t)rows * c.n_band * 4));
@@ -460,6 +500,7 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
     if (grad_out) {
         CK(ctx->V.reserve((size_t)rows * c.lam_pad * 4));
         CK(ctx->Wbar.reserve((size_t)rows * c.k_pad * 4));
+        if (tf) CK(ctx->Vlo.reserve((size_t)rows * c.lam_pad * 4));
     }
     const Grid grid = ctx->grid();
     const Galaxies gal = ctx->gal();
@@ -487,13 +528,18 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
         }
         if (tc) CK(launch_zsort(gv, gi, m, perm, pos_of, zcounts, s));
         CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s,
-                                pos_of));
+                                pos_of, tf ? ctx->Wlo.as<float>() : nullptr));
         if (tc) {
-            CUtensorMap ta, tb;
-            if (!make_tmap_bf16(&ta, ctx->W.p, c.k_pad, m, c.k_pad, 128) ||
-                !make_tmap_bf16(&tb, ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256))
-                return fail(SPS_E_CUDA, "tensor map encoding failed");
-            CK(launch_fwd_tc(ta, tb, c, grid, gv, th, gi, perm, m, ctx->cJ.as<float>(), terr, s));
+            TcMaps tm;
+            const bool ok = tf ? (make_tmap_f32(&tm.a[0], ctx->W.p, c.k_pad, m, c.k_pad, 128) &&
+                                  make_tmap_f32(&tm.a[1], ctx->Wlo.p, c.k_pad, m, c.k_pad, 128) &&
+                                  make_tmap_f32(&tm.b[0], ctx->ssp_t_hi.p, c.k_pad, c.n_lam, c.k_pad, 256) &&
+                                  make_tmap_f32(&tm.b[1], ctx->ssp_t_lo.p, c.k_pad, c.n_lam, c.k_pad, 256))
+                               : (make_tmap_bf16(&tm.a[0], ctx->W.p, c.k_pad, m, c.k_pad, 128) &&
+                                  make_tmap_bf16(&tm.b[0], ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256));
+            if (!ok) return fail(SPS_E_CUDA, "tensor map encoding failed");
+            if (!tf) tm.a[1] = tm.a[0], tm.b[1] = tm.b[0];
+            CK(launch_fwd_tc(tm, tf, c, grid, gv, th, gi, perm, m, ctx->cJ.as<float>(), terr, s));
         } else {
             CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
                                 ctx->cJ.as<float>(), s));
@@ -503,13 +549,22 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                              ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s));
         if (grad_out) {
             if (tc) {
-                CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), nullptr,
-                                     ctx->V.as<uint16_t>(), s));
-                CUtensorMap ta, tb;
-                if (!make_tmap_bf16(&ta, ctx->V.p, c.lam_pad, m, c.lam_pad, 128) ||
-                    !make_tmap_bf16(&tb, ctx->ssp_bf.p, c.lam_pad, c.K, c.lam_pad, 192))
-                    return fail(SPS_E_CUDA, "tensor map encoding failed");
-                CK(launch_adj_tc(ta, tb, c, grid, m, ctx->Wbar.as<float>(), terr, s));
+                if (tf)
+                    CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), ctx->V.as<float>(),
+                                         nullptr, s, ctx->Vlo.as<float>()));
+                else
+                    CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), nullptr,
+                                         ctx->V.as<uint16_t>(), s));
+                TcMaps tm;
+                const bool ok = tf ? (make_tmap_f32(&tm.a[0], ctx->V.p, c.lam_pad, m, c.lam_pad, 128) &&
+                                      make_tmap_f32(&tm.a[1], ctx->Vlo.p, c.lam_pad, m, c.lam_pad, 128) &&
+                                      make_tmap_f32(&tm.b[0], ctx->ssp_hi.p, c.lam_pad, c.K, c.lam_pad, 192) &&
+                                      make_tmap_f32(&tm.b[1], ctx->ssp_lo.p, c.lam_pad, c.K, c.lam_pad, 192))
+                                   : (make_tmap_bf16(&tm.a[0], ctx->V.p, c.lam_pad, m, c.lam_pad, 128) &&
+                                      make_tmap_bf16(&tm.b[0], ctx->ssp_bf.p, c.lam_pad, c.K, c.lam_pad, 192));
+                if (!ok) return fail(SPS_E_CUDA, "tensor map encoding failed");
+                if (!tf) tm.a[1] = tm.a[0], tm.b[1] = tm.b[0];
+                CK(launch_adj_tc(tm, tf, c, grid, m, ctx->Wbar.as<float>(), terr, s));
             } else {
                 CK(launch_exact_vgen(c, grid, gv, th, gi, m, ctx->gbar.as<float>(), ctx->V.as<float>(),
                                      nullptr, s));
@@ -537,7 +592,7 @@ sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_i
     sps_status st0 = check_rows(ctx, theta, gal_idx, n);
     if (st0 != SPS_OK) return st0;
     if (mode != SPS_EXACT && mode != SPS_APPROX) return fail(SPS_E_INVALID_ARG, "bad mode");
-    if (prec != SPS_FP32 && prec != SPS_BF16) return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (prec != SPS_FP32 && prec != SPS_BF16 && prec != SPS_TF32X3) return fail(SPS_E_INVALID_ARG, "bad precision");
     if (mode == SPS_APPROX && prec != SPS_FP32) return fail(SPS_E_UNSUPPORTED, "approximate path is FP32");
     if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (n > 0 && !mag_out) return fail(SPS_E_INVALID_ARG, "mag_out is NULL");
@@ -554,7 +609,7 @@ sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_i
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, nullptr, nullptr, nullptr, mo, nullptr,
                               nullptr, nullptr, ctx->nonfinite.as<int>(), s));
     } else {
-        sps_status r = run_exact(ctx, th, gi, n, nullptr, nullptr, nullptr, prec == SPS_BF16, mo,
+        sps_status r = run_exact(ctx, th, gi, n, nullptr, nullptr, nullptr, prec, mo,
                                  nullptr, nullptr, s);
         if (r != SPS_OK) return r;
     }
@@ -568,7 +623,7 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     sps_status st0 = check_rows(ctx, theta, gal_idx, n);
     if (st0 != SPS_OK) return st0;
     if (mode != SPS_EXACT && mode != SPS_APPROX) return fail(SPS_E_INVALID_ARG, "bad mode");
-    if (prec != SPS_FP32 && prec != SPS_BF16) return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (prec != SPS_FP32 && prec != SPS_BF16 && prec != SPS_TF32X3) return fail(SPS_E_INVALID_ARG, "bad precision");
     if (mode == SPS_APPROX && prec != SPS_FP32) return fail(SPS_E_UNSUPPORTED, "approximate path is FP32");
     if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
@@ -591,7 +646,7 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, mo, sg, mk, nullptr, llo, gro, nullptr,
                               ctx->nonfinite.as<int>(), s));
     } else {
-        sps_status r = run_exact(ctx, th, gi, n, mo, sg, mk, prec == SPS_BF16, nullptr, llo, gro, s);
+        sps_status r = run_exact(ctx, th, gi, n, mo, sg, mk, prec, nullptr, llo, gro, s);
         if (r != SPS_OK) return r;
     }
     return finish_call(ctx, st, s);

@@ -49,6 +49,7 @@ struct sps_ctx {
     std::vector<double> band_p0, band_p1;
     // tables
     DevBuf lam64, lam32, lamc, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, age_edges, bp0, bp1;
+    DevBuf ssp_hi, ssp_lo, ssp_t_hi, ssp_t_lo;   // 3xTF32 halves of the FP32 tables
     // galaxies
     int64_t n_gal = 0;
     bool has_approx = false;
@@ -58,6 +59,7 @@ struct sps_ctx {
     DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
     DevBuf pst, pth, pll, pgr, pgi;   // plain lock-step HMC state and gradient buffers
     DevBuf zperm;                     // redshift order of the rows of a tensor-core chunk
+    DevBuf Wlo, Vlo;                  // low TF32 halves of W and v (3xTF32 exact path)
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -98,7 +100,7 @@ struct sps_ctx {
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
-                         &pgi, &zperm};
+                         &pgi, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

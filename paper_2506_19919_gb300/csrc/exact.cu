@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
           const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
           int bf16, float* __restrict__ W32, uint16_t* __restrict__ Wbf,
-          const int32_t* __restrict__ pos_of) {
+          const int32_t* __restrict__ pos_of, float* __restrict__ W32lo) {
     __shared__ RowScratch scratch[kWarpsApprox];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     RowScratch& s = scratch[warp];
@@ -61,8 +61,16 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
                 i = k / c.n_met;
                 v = s.w[i] * s.q[k % c.n_met];
             }
-            if (bf16) Wbf[wr * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
-            else W32[wr * c.k_pad + k] = v;
+            if (bf16) {
+                Wbf[wr * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
+            } else if (W32lo) {                        // 3xTF32 operand halves
+                float hi, lo;
+                tf32_split(v, hi, lo);
+                W32[wr * c.k_pad + k] = hi;
+                W32lo[wr * c.k_pad + k] = lo;
+            } else {
+                W32[wr * c.k_pad + k] = v;
+            }
         }
         __syncwarp();
     }
@@ -288,7 +296,8 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
 __global__ void __launch_bounds__(256)
 k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
              const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
-             const float* __restrict__ gbar, float* __restrict__ V, uint16_t* __restrict__ Vbf) {
+             const float* __restrict__ gbar, float* __restrict__ V, uint16_t* __restrict__ Vbf,
+             float* __restrict__ Vlo) {
     __shared__ float gb[kMaxBands];
     __shared__ int2 sp[kMaxBands];
     __shared__ float2 gg[kMaxBands];
@@ -323,8 +332,16 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
             }
             if (sum != 0.0f) v = dust_eval(L4.y, L4.z, L4.w, AV, dl, ff).F * sum;
         }
-        if (Vbf) Vbf[row * c.lam_pad + nn] = f_to_bf16(v);
-        else V[row * c.lam_pad + nn] = v;
+        if (Vbf) {
+            Vbf[row * c.lam_pad + nn] = f_to_bf16(v);
+        } else if (Vlo) {                              // 3xTF32 operand halves
+            float hi, lo;
+            tf32_split(v, hi, lo);
+            V[row * c.lam_pad + nn] = hi;
+            Vlo[row * c.lam_pad + nn] = lo;
+        } else {
+            V[row * c.lam_pad + nn] = v;
+        }
     }
 }
 
@@ -417,10 +434,11 @@ int blocks_rows(int64_t rows, int per_block) {
 
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
                                  const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
-                                 float* W32, uint16_t* Wbf, cudaStream_t s, const int32_t* pos_of) {
+                                 float* W32, uint16_t* Wbf, cudaStream_t s, const int32_t* pos_of,
+                                 float* W32lo) {
     if (n <= 0) return cudaSuccess;
     k_weights<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, grid, g, theta, gal_idx,
-                                                                         n, bf16, W32, Wbf, pos_of);
+                                                                         n, bf16, W32, Wbf, pos_of, W32lo);
     return cudaGetLastError();
 }
 
@@ -514,9 +532,9 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
 
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
-                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s) {
+                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s, float* V32lo) {
     if (n <= 0) return cudaSuccess;
-    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32, Vbf);
+    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32, Vbf, V32lo);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,9 @@
 // Tensor-core (tcgen05) contractions of the exact path (Eq. photo_integral_exact)
-// for sm_103a, BF16 operands with per-age-row power-of-two scaling and FP32
-// accumulation in TMEM.
+// for sm_103a, FP32 accumulation in TMEM, with either
+//   BF16 operands (kind::f16) with per-age-row power-of-two scaling, or
+//   FP32 operands as 3xTF32 (kind::tf32): x = x_hi + x_lo with x_hi the TF32
+//   rounding of x, and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped
+//   A_lo B_lo term is ~2^-22 relative), which keeps FP32-level accuracy.
 //
 // Forward: S[r][n] = sum_k W[r][k] L[k][n] for a 128-row tile and 256-wide
 // wavelength tiles, with the dust x filter reduction over n fused into the
@@ -24,21 +27,26 @@ namespace sps {
 namespace {
 
 constexpr int kTM = 128;       // rows per tile (MMA M)
-constexpr int kBK = 64;        // bf16 per k-block row (128 bytes)
+constexpr int kRowBytes = 128; // one k-block row: 64 BF16 or 32 FP32 (128-byte swizzle)
 constexpr int kThreadsTC = 192;   // adjoint: TMA warp, MMA warp, 4 epilogue warps
 constexpr int kFwdGroupBands = 8; // forward: bands per epilogue warp
 constexpr int kFwdMaxEpiWarps = 16;
 constexpr int kFwdBN = 256;
-constexpr int kFwdStages = 4;
+constexpr int kFwdStages = 4;    // BF16 ring depth (TF32: 2; four tiles per stage)
 constexpr int kAdjBN = 192;
-constexpr int kAdjStages = 5;
+constexpr int kAdjStages = 5;    // BF16 ring depth (TF32: 2)
 constexpr uint32_t kTmemCols = 512;
 
-template <int BN, int STAGES>
+// Ring of STAGES stages; a stage holds an A tile (kTM rows) and a B tile (BN
+// rows) of one k-block, twice (hi and lo parts) for 3xTF32.
+template <int BN, int STAGES, bool TF>
 struct Ring {
-    static constexpr int kA = kTM * kBK * 2;
-    static constexpr int kB = BN * kBK * 2;
-    static constexpr int kBytes = STAGES * (kA + kB);
+    static constexpr int kBK = TF ? 32 : 64;          // k per block row
+    static constexpr int kParts = TF ? 2 : 1;
+    static constexpr int kA = kTM * kRowBytes;
+    static constexpr int kB = BN * kRowBytes;
+    static constexpr int kStage = kParts * (kA + kB);
+    static constexpr int kBytes = STAGES * kStage;
 };
 
 struct Ctl {
@@ -96,41 +104,58 @@ __device__ __forceinline__ void tc_setup(Ctl* ctl, int warp, int epi_threads = 4
 }
 
 // Producer (one lane): k-blocks of A (rows m0..) and B (rows of the n tile).
-template <int BN, int STAGES>
+// Stage layout: A_hi, B_hi, then (3xTF32) A_lo, B_lo.  tA[1], tB[1] are the
+// lo-part maps (unused for BF16).
+// Work items: (output tile nt, k chunk kc) for nt < n_tiles, kc < ceil(n_kb / kchunk);
+// an item accumulates k-blocks [kc kchunk, min((kc + 1) kchunk, n_kb)) from zero.
+template <int BN, int STAGES, bool TF>
 __device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtensorMap* tA,
                                            const CUtensorMap* tB, int m0, int n_tiles, int n_kb,
-                                           int* err) {
-    using R = Ring<BN, STAGES>;
+                                           int* err, int kchunk) {
+    using R = Ring<BN, STAGES, TF>;
     int it = 0;
-    for (int nt = 0; nt < n_tiles && !ctl->abort; ++nt) {
-        for (int kb = 0; kb < n_kb; ++kb, ++it) {
+    const int n_items = n_tiles * ((n_kb + kchunk - 1) / kchunk);
+    const int n_kc = (n_kb + kchunk - 1) / kchunk;
+    for (int item = 0; item < n_items && !ctl->abort; ++item) {
+        const int nt = item / n_kc, kc = item - nt * n_kc;
+        const int kb_end = min((kc + 1) * kchunk, n_kb);
+        for (int kb = kc * kchunk; kb < kb_end; ++kb, ++it) {
             const int s = it % STAGES;
             const uint32_t round = (uint32_t)(it / STAGES);
             if (!wait_or_abort(&ctl->empty[s], (round & 1u) ^ 1u, ctl, err)) return;
-            uint8_t* a = ring + s * (R::kA + R::kB);
+            uint8_t* a = ring + s * R::kStage;
             uint8_t* b = a + R::kA;
-            tc::mbar_expect_tx(&ctl->full[s], R::kA + R::kB);
-            tc::tma_load_2d(a, tA, kb * kBK, m0, &ctl->full[s]);
-            tc::tma_load_2d(b, tB, kb * kBK, nt * BN, &ctl->full[s]);
+            tc::mbar_expect_tx(&ctl->full[s], R::kStage);
+            tc::tma_load_2d(a, &tA[0], kb * R::kBK, m0, &ctl->full[s]);
+            tc::tma_load_2d(b, &tB[0], kb * R::kBK, nt * BN, &ctl->full[s]);
+            if (TF) {
+                tc::tma_load_2d(b + R::kB, &tA[1], kb * R::kBK, m0, &ctl->full[s]);
+                tc::tma_load_2d(b + R::kB + R::kA, &tB[1], kb * R::kBK, nt * BN, &ctl->full[s]);
+            }
             ctl->issued = it + 1;
         }
     }
 }
 
 // MMA issuer (one lane).
-template <int BN, int STAGES>
-__device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int n_kb, int* err) {
-    using R = Ring<BN, STAGES>;
-    constexpr uint32_t idesc = tc::idesc_bf16(kTM, BN);
+template <int BN, int STAGES, bool TF>
+__device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int n_kb, int* err,
+                                       int kchunk) {
+    using R = Ring<BN, STAGES, TF>;
+    constexpr uint32_t idesc = TF ? tc::idesc_tf32(kTM, BN) : tc::idesc_bf16(kTM, BN);
     int it = 0;
-    for (int nt = 0; nt < n_tiles; ++nt) {
-        const int buf = nt & 1;
-        const uint32_t use = (uint32_t)(nt >> 1);
+    const int n_kc = (n_kb + kchunk - 1) / kchunk;
+    const int n_items = n_tiles * n_kc;
+    for (int item = 0; item < n_items; ++item) {
+        const int buf = item & 1;
+        const uint32_t use = (uint32_t)(item >> 1);
+        const int kc = item % n_kc;
+        const int kb0 = kc * kchunk, kb_end = min(kb0 + kchunk, n_kb);
         if (!wait_or_abort(&ctl->tempty[buf], (use & 1u) ^ 1u, ctl, err)) break;
         tc::tc_fence_after();
         const uint32_t d = ctl->tmem_base + (uint32_t)(buf * BN);
         bool ok = true;
-        for (int kb = 0; kb < n_kb; ++kb, ++it) {
+        for (int kb = kb0; kb < kb_end; ++kb, ++it) {
             const int s = it % STAGES;
             const uint32_t round = (uint32_t)(it / STAGES);
             if (!wait_or_abort(&ctl->full[s], round & 1u, ctl, err)) {
@@ -138,12 +163,23 @@ __device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int
                 break;
             }
             tc::tc_fence_after();
-            uint8_t* a = ring + s * (R::kA + R::kB);
+            uint8_t* a = ring + s * R::kStage;
             uint8_t* b = a + R::kA;
             const uint64_t da = tc::sw128_desc(a), db = tc::sw128_desc(b);
+            if (TF) {
+                const uint64_t dal = tc::sw128_desc(b + R::kB), dbl = tc::sw128_desc(b + R::kB + R::kA);
+                // four k-steps of 8 FP32 (32 bytes) per 128-byte row
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                tc::mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                for (int k = 0; k < 4; ++k) {
+                    tc::mma_tf32(d, da + 2 * k, dbl + 2 * k, idesc, ((kb - kb0) | k) != 0);   // hi lo
+                    tc::mma_tf32(d, dal + 2 * k, db + 2 * k, idesc, 1);              // lo hi
+                    tc::mma_tf32(d, da + 2 * k, db + 2 * k, idesc, 1);               // hi hi
+                }
+            } else {
+                // four k-steps of 16 BF16 (32 bytes) per 128-byte row
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tc::mma_bf16(d, da + 2 * k, db + 2 * k, idesc, ((kb - kb0) | k) != 0);
+            }
             tc::mma_commit(&ctl->empty[s]);
         }
         if (!ok) break;
@@ -157,7 +193,7 @@ __device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int
 
 // Teardown: wait (bounded) for the producer's copies still in flight, then
 // free TMEM from the allocating warp.
-template <int BN, int STAGES>
+template <int STAGES>
 __device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
     __syncwarp();
     tc::tc_fence_before();
@@ -180,12 +216,12 @@ __device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
 
 static_assert(sizeof(Ctl) <= 256, "control block must fit before the staging area");
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool TF>
 __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
     uintptr_t p = reinterpret_cast<uintptr_t>(raw);
     p = (p + 1023) & ~uintptr_t(1023);
     uint8_t* ring = reinterpret_cast<uint8_t*>(p);
-    ctl = reinterpret_cast<Ctl*>(ring + Ring<BN, STAGES>::kBytes);
+    ctl = reinterpret_cast<Ctl*>(ring + Ring<BN, STAGES, TF>::kBytes);
     return ring;
 }
 
@@ -196,26 +232,27 @@ __device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
 // columns.  Rows arrive sorted by redshift (perm), so the 32 rows of a warp see
 // nearly the same band supports: a band is visited in a 32-column chunk only if
 // it overlaps the chunk in some lane.
-template <int MAXT>
+template <int MAXT, bool TF>
 __global__ void __launch_bounds__(MAXT, 1)
-k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
-         const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
+k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
          const float* __restrict__ theta, const int32_t* __restrict__ gal_idx,
          const int32_t* __restrict__ perm, int64_t n, int n_halves, float* __restrict__ cJ, int* err) {
     constexpr int NB = kFwdGroupBands;
     extern __shared__ unsigned char smem_raw[];
     Ctl* ctl;
-    uint8_t* ring = carve<kFwdBN, kFwdStages>(smem_raw, ctl);
+    constexpr int ST = TF ? 2 : kFwdStages;
+    using R = Ring<kFwdBN, ST, TF>;
+    uint8_t* ring = carve<kFwdBN, ST, TF>(smem_raw, ctl);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTM;
     const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
-    const int n_kb = c.k_pad / kBK;
+    const int n_kb = (c.k_pad + R::kBK - 1) / R::kBK;
     const int epi_threads = (int)blockDim.x - 64;
-    tc_setup<kFwdStages>(ctl, warp, epi_threads);
+    tc_setup<ST>(ctl, warp, epi_threads);
     if (warp == 0) {
-        if (lane == 0) tc_produce<kFwdBN, kFwdStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
+        if (lane == 0) tc_produce<kFwdBN, ST, TF>(ctl, ring, tm.a, tm.b, m0, n_tiles, n_kb, err, n_kb);
     } else if (warp == 1) {
-        if (lane == 0) tc_mma<kFwdBN, kFwdStages>(ctl, ring, n_tiles, n_kb, err);
+        if (lane == 0) tc_mma<kFwdBN, ST, TF>(ctl, ring, n_tiles, n_kb, err, n_kb);
     } else {
         const int e = warp - 2;
         const int q = warp & 3;                    // TMEM lane quarter this warp may access (warp id mod 4)
@@ -317,33 +354,38 @@ k_fwd_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
                 }
         }
     }
-    tc_teardown<kFwdBN, kFwdStages>(ctl, warp);
+    tc_teardown<ST>(ctl, warp);
 }
 
 // ---------------------------------------------------------------- adjoint
+template <bool TF>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
-         const __grid_constant__ Consts c, const Grid grid, int64_t n, float* __restrict__ Wbar,
-         int* err) {
+k_adj_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, const Grid grid, int64_t n,
+         float* __restrict__ Wbar, int* err) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int ST = TF ? 2 : kAdjStages;
+    using R = Ring<kAdjBN, ST, TF>;
     Ctl* ctl;
-    uint8_t* ring = carve<kAdjBN, kAdjStages>(smem_raw, ctl);
+    uint8_t* ring = carve<kAdjBN, ST, TF>(smem_raw, ctl);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTM;
     const int n_tiles = (c.K + kAdjBN - 1) / kAdjBN;
-    const int n_kb = c.lam_pad / kBK;
-    tc_setup<kAdjStages>(ctl, warp);
+    const int n_kb = (c.lam_pad + R::kBK - 1) / R::kBK;   // the last block reads zero fill
+    const int kchunk = n_kb;                                // one accumulation per tile
+    const int n_kc = (n_kb + kchunk - 1) / kchunk;
+    tc_setup<ST>(ctl, warp);
     if (warp == 0) {
-        if (lane == 0) tc_produce<kAdjBN, kAdjStages>(ctl, ring, &tA, &tB, m0, n_tiles, n_kb, err);
+        if (lane == 0) tc_produce<kAdjBN, ST, TF>(ctl, ring, tm.a, tm.b, m0, n_tiles, n_kb, err, kchunk);
     } else if (warp == 1) {
-        if (lane == 0) tc_mma<kAdjBN, kAdjStages>(ctl, ring, n_tiles, n_kb, err);
+        if (lane == 0) tc_mma<kAdjBN, ST, TF>(ctl, ring, n_tiles, n_kb, err, kchunk);
     } else {
         const int q = warp & 3;
         const int64_t row = (int64_t)m0 + 32 * q + lane;
         const bool live = row < n;
-        for (int nt = 0; nt < n_tiles; ++nt) {
-            const int buf = nt & 1;
-            const uint32_t use = (uint32_t)(nt >> 1);
+        for (int item = 0; item < n_tiles * n_kc; ++item) {
+            const int buf = item & 1;
+            const uint32_t use = (uint32_t)(item >> 1);
+            const int nt = item / n_kc, kc = item - nt * n_kc;
             if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
             tc::tc_fence_after();
             for (int cc = 0; cc < kAdjBN / 32; ++cc) {
@@ -354,7 +396,11 @@ k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int k = k0 + j;
-                        if (k < c.K) Wbar[row * c.k_pad + k] = S[j] * __ldg(grid.row_scale + k / c.n_met);
+                        if (k < c.K) {
+                            float* o = Wbar + row * c.k_pad + k;
+                            if (kc == 0) *o = TF ? S[j] : S[j] * __ldg(grid.row_scale + k / c.n_met);
+                            else *o += TF ? S[j] : S[j] * __ldg(grid.row_scale + k / c.n_met);
+                        }
                     }
                 }
             }
@@ -362,21 +408,24 @@ k_adj_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtenso
             tc::mbar_arrive(&ctl->tempty[buf]);
         }
     }
-    tc_teardown<kAdjBN, kAdjStages>(ctl, warp);
+    tc_teardown<ST>(ctl, warp);
 }
 
 }  // namespace
 
-size_t tc_fwd_smem() { return Ring<kFwdBN, kFwdStages>::kBytes + 256 + 1024; }
-size_t tc_adj_smem() { return Ring<kAdjBN, kAdjStages>::kBytes + sizeof(Ctl) + 1024; }
+size_t tc_fwd_smem(bool tf) {
+    return (tf ? Ring<kFwdBN, 2, true>::kBytes : Ring<kFwdBN, kFwdStages, false>::kBytes) + 256 + 1024;
+}
+size_t tc_adj_smem(bool tf) {
+    return (tf ? Ring<kAdjBN, 2, true>::kBytes : Ring<kAdjBN, kAdjStages, false>::kBytes) + sizeof(Ctl) + 1024;
+}
 
-cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
-                          const Grid& grid, const Galaxies& g, const float* theta,
-                          const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ, int* err,
-                          cudaStream_t s) {
+cudaError_t launch_fwd_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, const Galaxies& g,
+                          const float* theta, const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ,
+                          int* err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
-    const size_t smem = tc_fwd_smem();
+    const size_t smem = tc_fwd_smem(tf);
     const int groups = (c.n_band + kFwdGroupBands - 1) / kFwdGroupBands;   // <= 4 (B <= 32)
     const int halves = groups == 1 ? 2 : 1;
     const int threads = 64 + 32 * 4 * groups * halves;
@@ -385,24 +434,32 @@ cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Co
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (r != cudaSuccess) return r;
-        kern<<<blocks, threads, smem, s>>>(tA, tB, c, grid, g, theta, gal_idx, perm, n, halves, cJ, err);
+        kern<<<blocks, threads, smem, s>>>(tm, c, grid, g, theta, gal_idx, perm, n, halves, cJ, err);
         return cudaSuccess;
     };
-    if (threads <= 64 + 32 * 8) e = go(k_fwd_tc<64 + 32 * 8>);            // up to 16 bands
-    else if (threads <= 64 + 32 * 12) e = go(k_fwd_tc<64 + 32 * 12>);     // up to 24 bands
-    else e = go(k_fwd_tc<64 + 32 * kFwdMaxEpiWarps>);                    // up to 32 bands
+    constexpr int T8 = 64 + 32 * 8, T12 = 64 + 32 * 12, T16 = 64 + 32 * kFwdMaxEpiWarps;
+    if (threads <= T8) e = tf ? go(k_fwd_tc<T8, true>) : go(k_fwd_tc<T8, false>);            // <= 16 bands
+    else if (threads <= T12) e = tf ? go(k_fwd_tc<T12, true>) : go(k_fwd_tc<T12, false>);    // <= 24 bands
+    else e = tf ? go(k_fwd_tc<T16, true>) : go(k_fwd_tc<T16, false>);                        // <= 32 bands
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
-                          const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s) {
+cudaError_t launch_adj_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, int64_t n, float* Wbar,
+                          int* err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
-    const size_t smem = tc_adj_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_adj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_adj_tc<<<blocks, kThreadsTC, smem, s>>>(tA, tB, c, grid, n, Wbar, err);
+    const size_t smem = tc_adj_smem(tf);
+    cudaError_t e;
+    if (tf) {
+        e = cudaFuncSetAttribute(k_adj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_adj_tc<true><<<blocks, kThreadsTC, smem, s>>>(tm, c, grid, n, Wbar, err);
+    } else {
+        e = cudaFuncSetAttribute(k_adj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_adj_tc<false><<<blocks, kThreadsTC, smem, s>>>(tm, c, grid, n, Wbar, err);
+    }
     return cudaGetLastError();
 }
 

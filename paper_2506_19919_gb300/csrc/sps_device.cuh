@@ -66,6 +66,16 @@ __device__ __forceinline__ float tri_pdf(float x) {
     return (fabsf(x) <= 3.0f) ? (35.0f / 96.0f) * t * t * t : 0.0f;
 }
 
+// ---------------------------------------------------------------- 3xTF32 split
+// hi = x rounded to TF32 (10 mantissa bits, the low 13 bits zero), lo = x - hi
+// (exact in FP32): the operand halves of a 3xTF32 tensor-core product.
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    hi = __uint_as_float(r);
+    lo = x - hi;
+}
+
 // ---------------------------------------------------------------- magnitudes
 // log10 of a positive FP32 flux for the magnitude m = zp - 2.5 log10 c: with
 // x = f 2^e, f in [0.5, 1), the exponent part e log10(2) is exact in FP64 and

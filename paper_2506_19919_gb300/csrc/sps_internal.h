@@ -99,7 +99,8 @@ cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* 
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
                                  const float* theta, const int32_t* gal_idx, int64_t n,
                                  int bf16, float* W32, uint16_t* Wbf, cudaStream_t s,
-                                 const int32_t* pos_of = nullptr);   // W row of each row (or itself)
+                                 const int32_t* pos_of = nullptr,    // W row of each row (or itself)
+                                 float* W32lo = nullptr);            // with W32lo: W32 = TF32 hi, W32lo = lo
 cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
                              const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s);
@@ -112,27 +113,32 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
                               cudaStream_t s);
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
-                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s);
+                              const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s,
+                              float* V32lo = nullptr);   // with V32lo: V32 = TF32 hi, V32lo = lo
 cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int bf16,
                              const float* V32, float* Wbar, cudaStream_t s);
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
                               const float* Wbar, float* grad_out, cudaStream_t s);
 
-// Tensor-core (tcgen05) contractions; the tensor maps describe the operands.
-size_t tc_fwd_smem();
-size_t tc_adj_smem();
-cudaError_t launch_fwd_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
-                          const Grid& grid, const Galaxies& g, const float* theta,
-                          const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ, int* err,
-                          cudaStream_t s);
+// Tensor-core (tcgen05) contractions; the tensor maps describe the operands:
+// a[0], b[0] the A (rows) and B (table) operands, and for 3xTF32 (tf) a[1],
+// b[1] their low parts.
+struct TcMaps {
+    CUtensorMap a[2], b[2];
+};
+size_t tc_fwd_smem(bool tf);
+size_t tc_adj_smem(bool tf);
+cudaError_t launch_fwd_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, const Galaxies& g,
+                          const float* theta, const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ,
+                          int* err, cudaStream_t s);
+cudaError_t launch_adj_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, int64_t n, float* Wbar,
+                          int* err, cudaStream_t s);
 // Rows ordered by redshift (bucketed in log(1+z)): perm[pos] = row,
 // pos_of[row] = pos; counts is scratch of zsort_buckets() ints.
 int zsort_buckets();
 cudaError_t launch_zsort(const Galaxies& g, const int32_t* gal_idx, int64_t n, int32_t* perm,
                          int32_t* pos_of, int32_t* counts, cudaStream_t s);
-cudaError_t launch_adj_tc(const CUtensorMap& tA, const CUtensorMap& tB, const Consts& c,
-                          const Grid& grid, int64_t n, float* Wbar, int* err, cudaStream_t s);
 
 // Plain per-galaxy forward-mode path (comparison baseline).
 size_t plain_scratch_bytes_per_row(const Consts& c);

@@ -319,6 +319,28 @@ def test_full_size_sampled_rows(mode):
     ctx.close()
 
 
+@pytest.mark.parametrize("fix", ["parity64", "prod96"])
+def test_exact_tf32x3(fix, request):
+    """3xTF32 tensor-core contraction (FP32 operands split into TF32 halves).
+    Its bar follows from the arithmetic: the products are good to ~2^-21, but
+    the tensor-core FP32 accumulation over the K = 1284 terms of the
+    production grid leaves ~2.5e-5 relative in the fluxes, i.e. ~3e-5 mag;
+    the gradient inherits it through the residuals (bar 2e-3, against 1e-4
+    for the FP32 SIMT path).  parity64 also covers a wavelength grid whose
+    padded length (2016) is not a multiple of the 64-wide BF16 k-block."""
+    wl, ctx = request.getfixturevalue(fix)
+    m = ctx.photometry(wl.theta, mode="exact", prec="tf32x3").cpu().numpy()
+    ref = O.photometry(wl.theta, wl.z, wl.tables, "exact").numpy()
+    assert np.abs(m - ref).max() < 2e-4
+    mobs = ref + wl.noise
+    ev = W.prior_draw(np.random.default_rng(23), wl.n_gal)
+    llr, gr, _ = O.loglike_and_grad(ev, wl.z, wl.tables, mobs, wl.sigma, wl.mask, "exact")
+    for prec, ltol, gtol in (("tf32x3", 5e-4, 2e-3), ("bf16", 5e-3, 1e-2)):
+        ll, g = ctx.loglike_grad(ev, mobs, wl.sigma, wl.mask, mode="exact", prec=prec)
+        np.testing.assert_allclose(ll.cpu().numpy(), llr.numpy(), rtol=ltol)
+        assert _grad_rel(g.cpu().numpy(), gr.numpy()) < gtol, prec
+
+
 def test_empty_and_single_row(parity64):
     wl, ctx = parity64
     out = ctx.photometry(np.zeros((0, 12), np.float32), gal_idx=np.zeros(0, np.int32), mode="approx")
