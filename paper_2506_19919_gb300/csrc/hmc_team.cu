@@ -34,7 +34,10 @@ struct TeamWork {
     union {
         PanelScratch ps;
         float red[32][kZnReg + 1];          // qbar partials of one chain
-        struct {
+        struct {                            // per (chain, band) of the contraction
+            float F[CPW][kMaxBands];        // dust factor at lambda_eff
+            float Ah[CPW][kMaxBands], Al[CPW][kMaxBands];   // zp - m_obs - 2.5 (lgM + 9), hi + lo
+            float S[CPW][kMaxBands], gam[CPW][kMaxBands];   // flux sum, dlogL / dln c
             double tll[CPW][kMaxBands];
             float tg[CPW][kMaxBands][4];
         } t;
@@ -42,7 +45,6 @@ struct TeamWork {
     float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM], lpe[CPW][SPS_NPARAM];
     double M[CPW], lpri[CPW], ll[CPW];
     float gd[CPW][4];                       // d logL / d(lgM, A_V, delta, F_floor)
-    float S[CPW][kMaxBands], gh[CPW][kMaxBands];
     // galaxy slots
     float2 bins[kMaxAges];                  // age bins of the galaxy (centre, half-width in ln t)
     float lnT, lT10;                        // ln t_obs [Gyr], log10 t_obs [yr]
@@ -137,60 +139,120 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             age_weights(c, age_view(t, ch, et), t.th[ch], mp[ch]);
         }
     }
-    // ---- forward pass: S[ch][b] = sum_i w_i sum_j q_j C[b][i][j]
-    float qr[CPW][kZnReg], wl[CPW][4];
+    // ---- per (chain, band): dust factor and the magnitude offset
+    //      A = zp - m_obs - 2.5 (lgM + 9) as an FP32 hi + lo pair
+#pragma unroll 1
+    for (int e = lane; e < CPW * nb; e += 32) {
+        const int ch = e / nb, b = e - ch * nb;
+        const float4 dc = t.dust[b];
+        t.u.t.F[ch][b] = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]).F;
+        const double Aoff = t.zp[b] - (double)t.mobs[b] - 2.5 * ((double)t.th[ch][0] + 9.0);
+        const float ah = (float)Aoff;
+        t.u.t.Ah[ch][b] = ah;
+        t.u.t.Al[ch][b] = (float)(Aoff - (double)ah);
+    }
+    __syncwarp();
+    // ---- one pass over the galaxy's c_SSP rows, band by band, forward and adjoint:
+    //      R_i = sum_j q_j C_bij, U_j = sum_i w_i C_bij (lane partials over its rows),
+    //      S_b = sum_j q_j U_j; then with g_b = gamma_b / S_b:
+    //      wbar_i += g_b R_i, qbar_j += g_b U_j.
+    // The residual that gives gamma_b is taken in FP32: with F S = f 2^e,
+    // r = (A - 2.5 e log10 2) - 2.5 log10 f, the bracket exact in hi + lo parts
+    // (~1e-7 mag); the FP64 log likelihood is formed afterwards from S_b.
+    constexpr float kL2hi = 0.301025390625f;            // log10(2), 11 bits
+    constexpr float kL2lo = 4.6050389811952137e-6f;     // log10(2) - kL2hi
+    // Metallicity columns are taken in pairs with packed FP32x2 FMAs.
+    constexpr int kZ2 = kZnReg / 2;
+    float2 qr[CPW][kZ2], qbr[CPW][kZ2];
+    float wbl[CPW][4];
 #pragma unroll
     for (int ch = 0; ch < CPW; ++ch) {
 #pragma unroll
-        for (int j = 0; j < kZnReg; ++j) qr[ch][j] = (j < Zn) ? t.q[ch][j] : 0.0f;
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const int i = lane + 32 * tt;
-            wl[ch][tt] = (i < A) ? t.w[ch][i] : 0.0f;
+        for (int j = 0; j < kZ2; ++j) {
+            qr[ch][j] = make_float2((2 * j < Zn) ? t.q[ch][2 * j] : 0.0f, (2 * j + 1 < Zn) ? t.q[ch][2 * j + 1] : 0.0f);
+            qbr[ch][j] = make_float2(0.0f, 0.0f);
         }
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) wbl[ch][tt] = 0.0f;
     }
 #pragma unroll 1
     for (int b = 0; b < nb; ++b) {
         const float* C = t.ptr[b];
-        float sacc[CPW];
+        float2 U[CPW][kZ2];
+        float R[CPW][4];
 #pragma unroll
-        for (int ch = 0; ch < CPW; ++ch) sacc[ch] = 0.0f;
+        for (int ch = 0; ch < CPW; ++ch)
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) U[ch][j] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int tt = 0; tt < 4; ++tt) {
             const int i = lane + 32 * tt;
-            if (i < A) {
-                float cv[kZnReg];
-                load_row(C + i * Zn, Zn, cv);
+            float cs[kZnReg];
 #pragma unroll
-                for (int ch = 0; ch < CPW; ++ch) {
-                    float R = 0.0f;
+            for (int j = 0; j < kZnReg; ++j) cs[j] = 0.0f;
+            if (i < A) load_row(C + i * Zn, Zn, cs);
+            float2 cv[kZ2];
 #pragma unroll
-                    for (int j = 0; j < kZnReg; ++j) R = fmaf(qr[ch][j], cv[j], R);
-                    sacc[ch] = fmaf(wl[ch][tt], R, sacc[ch]);
+            for (int j = 0; j < kZ2; ++j) cv[j] = make_float2(cs[2 * j], cs[2 * j + 1]);
+#pragma unroll
+            for (int ch = 0; ch < CPW; ++ch) {
+                const float wi = (i < A) ? t.w[ch][i] : 0.0f;
+                const float2 w2 = make_float2(wi, wi);
+                float2 r2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int j = 0; j < kZ2; ++j) {
+                    r2 = __ffma2_rn(qr[ch][j], cv[j], r2);
+                    U[ch][j] = __ffma2_rn(w2, cv[j], U[ch][j]);
                 }
+                R[ch][tt] = r2.x + r2.y;
             }
         }
+        float sp[CPW];
 #pragma unroll
         for (int ch = 0; ch < CPW; ++ch) {
-            const float v = warp_sum(sacc[ch]);
-            if (lane == 0) t.S[ch][b] = v;
+            float2 v = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) v = __ffma2_rn(qr[ch][j], U[ch][j], v);
+            sp[ch] = v.x + v.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int ch = 0; ch < CPW; ++ch) sp[ch] += __shfl_xor_sync(kFull, sp[ch], o);
+#pragma unroll
+        for (int ch = 0; ch < CPW; ++ch) {
+            const float S = sp[ch];
+            int e2;
+            const float f = frexpf(t.u.t.F[ch][b] * S, &e2);
+            const float fe = (float)e2;
+            const float bh = t.u.t.Ah[ch][b] - 2.5f * (fe * kL2hi);
+            const float bl = t.u.t.Al[ch][b] - 2.5f * (fe * kL2lo);
+            const float r = (bh + bl) - 2.5f * log10f(f);
+            const float gam = r * t.isig2[b] * 1.0857362047581294f;     // 2.5 / ln 10
+            const float gh = __fdividef(gam, S);
+            if (lane == 0) {
+                t.u.t.S[ch][b] = S;
+                t.u.t.gam[ch][b] = gam;
+            }
+            const float2 g2 = make_float2(gh, gh);
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) qbr[ch][j] = __ffma2_rn(g2, U[ch][j], qbr[ch][j]);
+#pragma unroll
+            for (int tt = 0; tt < 4; ++tt) wbl[ch][tt] = fmaf(gh, R[ch][tt], wbl[ch][tt]);
         }
     }
     __syncwarp();
-    // ---- magnitudes, likelihood and dust / lgM gradients per (chain, band)
+    // ---- log likelihood (FP64 magnitudes) and the dust / lgM gradients per (chain, band)
 #pragma unroll 1
     for (int e = lane; e < CPW * nb; e += 32) {
         const int ch = e / nb, b = e - ch * nb;
         const float4 dc = t.dust[b];
         const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
-        const float Sv = t.S[ch][b];
-        const double lc = log10_flux(d.F * Sv) + ((double)t.th[ch][0] + 9.0);
+        const double lc = log10_flux(d.F * t.u.t.S[ch][b]) + ((double)t.th[ch][0] + 9.0);
         const double r = (t.zp[b] - 2.5 * lc) - (double)t.mobs[b];
-        const double is2 = (double)t.isig2[b];
-        t.u.t.tll[ch][b] = -0.5 * r * r * is2;
-        const float gam = (float)(r * is2 * 1.0857362047581294);   // 2.5 / ln 10
+        t.u.t.tll[ch][b] = -0.5 * r * r * (double)t.isig2[b];
+        const float gam = t.u.t.gam[ch][b];
         const float gF = __fdividef(gam, d.F);
-        t.gh[ch][b] = __fdividef(gam, Sv);
         t.u.t.tg[ch][b][0] = gam * kLn10f;
         t.u.t.tg[ch][b][1] = gF * d.dF_AV;
         t.u.t.tg[ch][b][2] = gF * d.dF_delta;
@@ -213,54 +275,23 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         t.gd[lane][2] = g2;
         t.gd[lane][3] = g3;
     }
-    __syncwarp();
-    // ---- adjoint pass, row by row: V_ij = sum_b g_b C_bij (g_b = gamma_b / S_b),
-    //      wbar_i = sum_j q_j V_ij, qbar_j = sum_i w_i V_ij
-    float qbr[CPW][kZnReg];
+    // wbar_i replaces w_i (each lane its own rows)
 #pragma unroll
-    for (int ch = 0; ch < CPW; ++ch)
+    for (int tt = 0; tt < 4; ++tt) {
+        const int i = lane + 32 * tt;
+        if (i < A)
 #pragma unroll
-        for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = 0.0f;
-#pragma unroll 1
-    for (int i = lane; i < A; i += 32) {
-        float V[CPW][kZnReg];
-#pragma unroll
-        for (int ch = 0; ch < CPW; ++ch)
-#pragma unroll
-            for (int j = 0; j < kZnReg; ++j) V[ch][j] = 0.0f;
-        float cv[kZnReg];
-#pragma unroll
-        for (int j = 0; j < kZnReg; ++j) cv[j] = 0.0f;
-        if (nb > 0) load_row(t.ptr[0] + i * Zn, Zn, cv);
-#pragma unroll 1
-        for (int b = 0; b < nb; ++b) {
-            float cn[kZnReg];
-            if (b + 1 < nb) load_row(t.ptr[b + 1] + i * Zn, Zn, cn);
-#pragma unroll
-            for (int ch = 0; ch < CPW; ++ch) {
-                const float gg = t.gh[ch][b];
-#pragma unroll
-                for (int j = 0; j < kZnReg; ++j) V[ch][j] = fmaf(gg, cv[j], V[ch][j]);
-            }
-#pragma unroll
-            for (int j = 0; j < kZnReg; ++j) cv[j] = cn[j];
-        }
-#pragma unroll
-        for (int ch = 0; ch < CPW; ++ch) {
-            float wbv = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kZnReg; ++j) wbv = fmaf((j < Zn) ? t.q[ch][j] : 0.0f, V[ch][j], wbv);
-            const float wi = t.w[ch][i];
-            t.w[ch][i] = wbv;                                   // wbar_i replaces w_i
-#pragma unroll
-            for (int j = 0; j < kZnReg; ++j) qbr[ch][j] = fmaf(wi, V[ch][j], qbr[ch][j]);
-        }
+            for (int ch = 0; ch < CPW; ++ch) t.w[ch][i] = wbl[ch][tt];
     }
+    __syncwarp();
     // qbar: sum the lanes' partials, one chain per round (two half sums)
 #pragma unroll
     for (int ch = 0; ch < CPW; ++ch) {
 #pragma unroll
-        for (int j = 0; j < kZnReg; ++j) t.u.red[lane][j] = qbr[ch][j];
+        for (int j = 0; j < kZ2; ++j) {
+            t.u.red[lane][2 * j] = qbr[ch][j].x;
+            t.u.red[lane][2 * j + 1] = qbr[ch][j].y;
+        }
         __syncwarp();
         const int j = lane & 15, h = lane >> 4;
         float s = 0.0f;
