@@ -855,7 +855,8 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
 
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
-                 cfg->seed, cfg->adapt_mass < 0 ? 0 : (cfg->adapt_mass > 2 ? 2 : cfg->adapt_mass)};
+                 cfg->seed, cfg->adapt_mass < 0 ? 0 : (cfg->adapt_mass > 2 ? 2 : cfg->adapt_mass), 1};
+    if (const char* v = std::getenv("SPS_HMC_SYNC")) hp.sync_every = std::max(1, std::atoi(v));
     if (c.n_met > 12) return fail(SPS_E_UNSUPPORTED, "HMC kernel holds at most 12 metallicity bins in registers");
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, ctx->device));
@@ -944,7 +945,8 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
                       (double)hp.eps0, (double)hp.target_accept);
         char kc[64];
         std::snprintf(kc, sizeof(kc), "%p", (void*)cmet);
-        std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw) + kc;
+        std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw) + kc + ":" +
+                         std::to_string(hp.sync_every);
         if (!ctx->graph || gk != ctx->graph_key) {
             if (ctx->graph) {
                 cudaGraphExecDestroy(ctx->graph);
@@ -1011,7 +1013,7 @@ extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_confi
     int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
-                 cfg->seed, 0};
+                 cfg->seed, 0, 1};
     // state, theta, FP64 log L, gradient, chain -> galaxy, forward-mode scratch
     const int64_t chunk = std::min<int64_t>(NC, 32768);
     CK(ctx->pst.reserve(sizeof(PlainChain) * (size_t)NC));

@@ -37,9 +37,7 @@ struct TeamWork {
         struct {                            // per (chain, band) of the contraction
             float F[CPW][kMaxBands];        // dust factor at lambda_eff
             float Ah[CPW][kMaxBands], Al[CPW][kMaxBands];   // zp - m_obs - 2.5 (lgM + 9), hi + lo
-            float S[CPW][kMaxBands], gam[CPW][kMaxBands];   // flux sum, dlogL / dln c
-            double tll[CPW][kMaxBands];
-            float tg[CPW][kMaxBands][4];
+            float res[CPW][kMaxBands], gam[CPW][kMaxBands]; // residual m - m_obs, dlogL / dln c
         } t;
     } u;
     float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM], lpe[CPW][SPS_NPARAM];
@@ -231,7 +229,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             const float gam = r * t.isig2[b] * 1.0857362047581294f;     // 2.5 / ln 10
             const float gh = __fdividef(gam, S);
             if (lane == 0) {
-                t.u.t.S[ch][b] = S;
+                t.u.t.res[ch][b] = r;
                 t.u.t.gam[ch][b] = gam;
             }
             const float2 g2 = make_float2(gh, gh);
@@ -242,38 +240,43 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         }
     }
     __syncwarp();
-    // ---- log likelihood (FP64 magnitudes) and the dust / lgM gradients per (chain, band)
-#pragma unroll 1
-    for (int e = lane; e < CPW * nb; e += 32) {
-        const int ch = e / nb, b = e - ch * nb;
-        const float4 dc = t.dust[b];
-        const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
-        const double lc = log10_flux(d.F * t.u.t.S[ch][b]) + ((double)t.th[ch][0] + 9.0);
-        const double r = (t.zp[b] - 2.5 * lc) - (double)t.mobs[b];
-        t.u.t.tll[ch][b] = -0.5 * r * r * (double)t.isig2[b];
-        const float gam = t.u.t.gam[ch][b];
-        const float gF = __fdividef(gam, d.F);
-        t.u.t.tg[ch][b][0] = gam * kLn10f;
-        t.u.t.tg[ch][b][1] = gF * d.dF_AV;
-        t.u.t.tg[ch][b][2] = gF * d.dF_delta;
-        t.u.t.tg[ch][b][3] = gF * d.dF_floor;
-    }
-    __syncwarp();
-    if (lane < CPW) {
+    // ---- log likelihood (FP64 sum of the band terms) and the dust / lgM
+    //      gradients: two chains per round, 16 lanes each, bands strided by 16
+#pragma unroll
+    for (int c0 = 0; c0 < CPW; c0 += 2) {
+        const int ch = c0 + (lane >> 4), k = lane & 15;
         double s = 0.0;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-        for (int b = 0; b < nb; ++b) {
-            s += t.u.t.tll[lane][b];
-            g0 += t.u.t.tg[lane][b][0];
-            g1 += t.u.t.tg[lane][b][1];
-            g2 += t.u.t.tg[lane][b][2];
-            g3 += t.u.t.tg[lane][b][3];
+        if (ch < CPW) {
+#pragma unroll 1
+            for (int b = k; b < nb; b += 16) {
+                const float4 dc = t.dust[b];
+                const DustTerms d = dust_eval(dc.x, dc.y, dc.z, t.th[ch][9], t.th[ch][10], t.th[ch][11]);
+                const float r = t.u.t.res[ch][b];
+                s -= 0.5 * (double)(r * r * t.isig2[b]);
+                const float gam = t.u.t.gam[ch][b];
+                const float gF = __fdividef(gam, d.F);
+                g0 = fmaf(gam, kLn10f, g0);
+                g1 = fmaf(gF, d.dF_AV, g1);
+                g2 = fmaf(gF, d.dF_delta, g2);
+                g3 = fmaf(gF, d.dF_floor, g3);
+            }
         }
-        t.ll[lane] = s;
-        t.gd[lane][0] = g0;
-        t.gd[lane][1] = g1;
-        t.gd[lane][2] = g2;
-        t.gd[lane][3] = g3;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(kFull, s, o);
+            g0 += __shfl_xor_sync(kFull, g0, o);
+            g1 += __shfl_xor_sync(kFull, g1, o);
+            g2 += __shfl_xor_sync(kFull, g2, o);
+            g3 += __shfl_xor_sync(kFull, g3, o);
+        }
+        if (k == 0 && ch < CPW) {
+            t.ll[ch] = s;
+            t.gd[ch][0] = g0;
+            t.gd[ch][1] = g1;
+            t.gd[ch][2] = g2;
+            t.gd[ch][3] = g3;
+        }
     }
     // wbar_i replaces w_i (each lane its own rows)
 #pragma unroll
@@ -733,7 +736,10 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
     bool have = false, drained = false;     // warp-uniform
     int64_t gi = 0;
     int nch = 0, nb = 0, pass = 0;
-    for (;;) {
+    const int sync_every = max(hp.sync_every, 1);
+    // every warp meets the block barrier once per sync_every of its own
+    // iterations (a warp without work iterates without evaluating)
+    for (int iter = 0;; ++iter) {
         if (!have && !drained) {
             int q = 0;
             if (lane == 0) q = atomicAdd(queue, 1);
@@ -746,7 +752,7 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
                 pass = 0;
             }
         }
-        if (!__syncthreads_or(have ? 1 : 0)) break;
+        if (iter % sync_every == 0 && !__syncthreads_or(have ? 1 : 0)) break;
         if (!have) continue;
         team_eval<CPW>(c, t, et, t.lnT, t.lT10, nb);
         if (pass == 0) {

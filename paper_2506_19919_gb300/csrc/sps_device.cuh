@@ -362,11 +362,19 @@ __device__ __forceinline__ void sfh_bins_raw(const Consts& c, const AgeView& v, 
 
 // This lane's FP64 partial of M = sum_i m_i (the cumulative mass integral);
 // warp_sum_d of it gives M.
+// The lane's (at most 4) bins are summed in FP32 with two-sum error terms, so
+// hi + lo carries their sum to ~2^-47; the FP64 accumulation starts from it.
 __device__ __forceinline__ double mass_partial(const Consts& c, const AgeView& v) {
-    double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;
 #pragma unroll 4
-    for (int i = lane_id(); i < c.n_age; i += 32) acc += (double)v.m[i];
-    return acc;
+    for (int i = lane_id(); i < c.n_age; i += 32) {
+        const float x = v.m[i];
+        const float sum = hi + x;
+        const float bp = sum - hi;
+        lo += (hi - (sum - bp)) + (x - bp);       // Knuth two-sum error term
+        hi = sum;
+    }
+    return (double)hi + (double)lo;
 }
 
 __device__ __forceinline__ double sfh_bins(const Consts& c, const AgeView& v, const float2* __restrict__ bins,

@@ -160,6 +160,7 @@ struct HmcParams {
     float target_accept, eps0;
     uint64_t seed;
     int adapt_mass;         // 0 identity, 1 windowed diagonal, 2 windowed dense metric
+    int sync_every;         // passes between the block barriers of the team kernel (>= 1)
 };
 size_t hmc_team_smem_per_warp(int cpw);
 cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm);
