@@ -132,14 +132,28 @@ def _dist():
     return ws, rank
 
 
-def _max_over_ranks(x: float, ws: int) -> float:
+def _reduce(x: float, ws: int, op: str) -> float:
+    """All-reduce of one number over the ranks ("max" or "sum"); the identity
+    for one rank.  CUDA tensors under NCCL, CPU tensors under gloo."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    return _reduce(x, ws, "max")
+
+
+def job_value(post: float, ms_step: float, ws: int):
+    """Whole-job posteriors/min: the posteriors of all ranks (each rank runs
+    its own seeded batch) over the slowest rank's step time."""
+    ms = _reduce(ms_step, ws, "max")
+    return _reduce(post, ws, "sum") / (ms / 60000.0), ms
 
 
 def _barrier(ws):
@@ -221,13 +235,13 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     kern_ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = _max_over_ranks(float(np.mean(kern_ms)), ws)
+    ms_local = float(np.mean(kern_ms))
 
     # ESS from the last step's draws (host diagnostics, outside the timed region)
     ess, rhat = pkg.diagnostics(samples, G, C)
     ess_g = ess.min(1)
     post = float(np.minimum(1.0, ess_g / ESS_TARGET).sum())
-    value = post * ws / (ms_step / 60000.0)
+    value, ms_step = job_value(post, ms_local, ws)
     nev = stats["grad_evals"].cpu().numpy()
     nb = np.array([bin(int(m)).count("1") for m in wl.mask])
     K = wl.tables.n_age * wl.tables.n_met
@@ -251,7 +265,7 @@ def run_ours(args):
                 "frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean()),
                 "accept_mean": float(stats["accept_prob"].mean()),
                 "divergences": int(stats["divergences"].sum())},
-        "grad_evals_per_s": float(nev.sum()) * ws / (ms_step / 1e3),
+        "grad_evals_per_s": _reduce(float(nev.sum()), ws, "sum") / (ms_step / 1e3),
         "roofline": {"kernel": "k_hmc_team", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": TRAFFIC["bytes"] if _kernel_sha() == TRAFFIC["sha"] else None,
@@ -265,7 +279,7 @@ def run_ours(args):
         out["loglike_grad"] = _loglike_grad_rates(ctx, dev)
     if rank == 0 and not args.skip_plain:
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
-    if rank == 0 and not args.skip_e2e:
+    if not args.skip_e2e:                       # every rank (collective timing)
         out["e2e"] = _e2e(ctx, cfg, lib, wl, mobs, x0, post, ws)
     if rank == 0 and ws == 1 and not args.skip_cpu:
         out["cpu_baseline"] = _cpu_baseline(wl, mobs.cpu().numpy(), post / G, budget_s=args.cpu_budget)
@@ -340,14 +354,15 @@ def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
     vp = lambda a: Ct.c_void_p(a.ctypes.data)
     times = []
     for _ in range(2):
+        _barrier(ws)
         t0 = time.perf_counter()
         _lib.check(lib.sps_hmc_run(ctx.h, Ct.byref(cfg), vp(x0), vp(mobs), vp(sigma), vp(mask),
                                    vp(samples), Ct.byref(st), None), "sps_hmc_run (host)")
-        times.append(time.perf_counter() - t0)
+        times.append(_reduce(time.perf_counter() - t0, ws, "max"))
     t = min(times)
     h2d = x0.nbytes + mobs.nbytes + sigma.nbytes + mask.nbytes + 4 * G
     d2h = samples.nbytes + acc.nbytes
-    return {"value": post * ws / (t / 60.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": _reduce(post, ws, "sum") / (t / 60.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "s_per_step": t}
 
 
