@@ -178,7 +178,25 @@ typedef struct {
     int32_t use_graph;      /* capture the device work in a CUDA graph             */
     int32_t autotune;       /* pick the launch shape by timing candidates          */
     int32_t adapt_mass;     /* warm-up metric: 0 identity (default), 1 diagonal, 2 dense */
+    int32_t sampler;        /* sps_sampler: SPS_HMC (default) or SPS_NUTS             */
+    int32_t max_depth;      /* NUTS tree depth limit, 1..10 (10): <= 2^depth - 1 leaves */
 } sps_hmc_config;
+
+/* Sampler of sps_hmc_run.  SPS_NUTS is the No-U-Turn Sampler the paper sets
+ * beside HMC (Sec. 4, App. D.2): multinomial NUTS with the generalised U-turn
+ * criterion (Hoffman & Gelman 2014; Betancourt 2017), identity metric; every
+ * aligned block of leaves of a new subtree is checked as it completes, a
+ * subtree is taken with probability min(1, W_subtree / W_trajectory), a leaf
+ * inside it by progressive multinomial sampling, divergence at dH > 1000.
+ * Step size by dual averaging on the mean over the leaves built of
+ * min(1, exp(-dH)).  L_min / L_max are ignored; adapt_mass must be 0.
+ * Draws: Philox-4x32-10 counters (iteration, 0..2, chain, 0) for the momentum
+ * (as HMC), (iteration, 16 + j, chain, 0) for the direction (word 0, top bit
+ * set = forward) and subtree uniform (word 1) at depth j, and
+ * (iteration, 64 + j, chain, n) word 0 for leaf n of that subtree.
+ * stats->grad_evals counts the leaves built (+1); accept_prob is the mean of
+ * that statistic over the sampling phase. */
+typedef enum { SPS_HMC = 0, SPS_NUTS = 1 } sps_sampler;
 
 sps_status sps_hmc_config_default(sps_hmc_config* cfg);
 
@@ -191,8 +209,8 @@ typedef struct {
     int32_t* status;      /* [G*C] 0 finished, 1 not finished (timeout)                   */
 } sps_hmc_stats;
 
-/* Run batched HMC for every chain of every galaxy of the current set.
- * Warm-up adapts, per chain, the step size by dual averaging (Hoffman & Gelman
+/* Run batched HMC (or NUTS, cfg->sampler) for every chain of every galaxy of
+ * the current set.  Warm-up adapts, per chain, the step size by dual averaging (Hoffman & Gelman
  * 2014) and, if adapt_mass is 1 (2), a diagonal (dense) inverse metric in
  * windows (75-iteration initial buffer, slow windows of 25, 50, 100, ...,
  * 50-iteration terminal buffer; regularised variances (covariance) of each
@@ -203,7 +221,8 @@ typedef struct {
  *  theta0_unb[G*C][12]: start points in unbounded space;
  *  samples_out[G*C][n_samp][12]: bounded (physical) draws, or NULL.
  * Random numbers: Philox-4x32-10 keyed by seed, counter (iteration, block,
- * chain, 0); a run is a pure function of its inputs. */
+ * chain, 0) (NUTS: the counters listed at sps_sampler); a run is a pure
+ * function of its inputs.  NUTS state takes 1.3 KB of device memory per chain. */
 sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
                        const float* mag_obs, const float* sigma, const uint32_t* mask,
                        float* samples_out, sps_hmc_stats* stats, void* stream);
@@ -216,7 +235,8 @@ sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* the
  * sps_loglike_grad_forward_mode whether or not its trajectory has ended.
  * Arguments, layouts and outputs as sps_hmc_run; stats->grad_evals counts the
  * evaluations performed (1 + (n_warm + n_samp) L_max per chain).
- * SPS_E_UNSUPPORTED unless cfg->adapt_mass == 0 and cfg->mode == SPS_APPROX. */
+ * SPS_E_UNSUPPORTED unless cfg->adapt_mass == 0, cfg->sampler == SPS_HMC and
+ * cfg->mode == SPS_APPROX. */
 sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
                                     const float* mag_obs, const float* sigma, const uint32_t* mask,
                                     float* samples_out, sps_hmc_stats* stats, void* stream);

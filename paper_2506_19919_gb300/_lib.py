@@ -40,7 +40,7 @@ class sps_hmc_config(C.Structure):
                 ("L_min", C.c_int32), ("L_max", C.c_int32), ("target_accept", C.c_float),
                 ("eps0", C.c_float), ("seed", C.c_uint64), ("mode", C.c_int32),
                 ("prec", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32),
-                ("adapt_mass", C.c_int32)]
+                ("adapt_mass", C.c_int32), ("sampler", C.c_int32), ("max_depth", C.c_int32)]
 
 
 class sps_hmc_stats(C.Structure):

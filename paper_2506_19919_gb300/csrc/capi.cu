@@ -256,6 +256,8 @@ sps_status sps_hmc_config_default(sps_hmc_config* cfg) {
     cfg->use_graph = 1;
     cfg->autotune = 1;
     cfg->adapt_mass = 0;
+    cfg->sampler = SPS_HMC;
+    cfg->max_depth = 10;
     return SPS_OK;
 }
 
@@ -813,7 +815,12 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
     if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
         return fail(SPS_E_SHAPE, "iteration counts");
-    if (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096) return fail(SPS_E_SHAPE, "L range");
+    const bool nuts = cfg->sampler == SPS_NUTS;
+    if (cfg->sampler != SPS_HMC && !nuts) return fail(SPS_E_INVALID_ARG, "sampler");
+    if (!nuts && (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096))
+        return fail(SPS_E_SHAPE, "L range");
+    if (nuts && (cfg->max_depth < 1 || cfg->max_depth > kNutsMaxDepth)) return fail(SPS_E_SHAPE, "max_depth in [1, 10]");
+    if (nuts && cfg->adapt_mass != 0) return fail(SPS_E_UNSUPPORTED, "NUTS runs with the identity metric");
     if (!(cfg->eps0 > 0) || !(cfg->target_accept > 0 && cfg->target_accept < 1))
         return fail(SPS_E_INVALID_ARG, "eps0 / target_accept");
     if (!theta0_unb || !mag_obs || !sigma || !mask) return fail(SPS_E_INVALID_ARG, "null input");
@@ -857,6 +864,12 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
                  cfg->seed, cfg->adapt_mass < 0 ? 0 : (cfg->adapt_mass > 2 ? 2 : cfg->adapt_mass), 1};
     if (const char* v = std::getenv("SPS_HMC_SYNC")) hp.sync_every = std::max(1, std::atoi(v));
+    if (nuts) {
+        hp.L_min = hp.L_max = 1;
+        hp.max_depth = cfg->max_depth;
+        CK(ctx->hmcn.reserve(sizeof(NutsChain) * (size_t)std::max<int64_t>(NC, 1)));
+        hp.nuts = ctx->hmcn.as<NutsChain>();
+    }
     if (c.n_met > 12) return fail(SPS_E_UNSUPPORTED, "HMC kernel holds at most 12 metallicity bins in registers");
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, ctx->device));
@@ -878,7 +891,8 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         blocks = std::max(1, per_sm) * sms;
         return cudaSuccess;
     };
-    const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max);
+    const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max) +
+                            (nuts ? ":nuts" : "");
     int cpw = cpw0, warps = cands[0].second, blocks = sms;
     auto it = ctx->tuned.find(key);
     const char* force = std::getenv("SPS_HMC_SHAPE");   // "cpw,warps": fixed launch shape
@@ -944,7 +958,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
                       hp.n_warm, hp.n_samp, hp.L_min, hp.L_max, warps, hp.adapt_mass, (unsigned long long)hp.seed,
                       (double)hp.eps0, (double)hp.target_accept);
         char kc[64];
-        std::snprintf(kc, sizeof(kc), "%p", (void*)cmet);
+        std::snprintf(kc, sizeof(kc), "%p%p%d", (void*)cmet, (void*)hp.nuts, hp.max_depth);
         std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw) + kc + ":" +
                          std::to_string(hp.sync_every);
         if (!ctx->graph || gk != ctx->graph_key) {
@@ -985,6 +999,7 @@ extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_confi
     if (cfg->mode != SPS_APPROX) return fail(SPS_E_UNSUPPORTED, "HMC runs on the approximate path");
     if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (cfg->adapt_mass != 0) return fail(SPS_E_UNSUPPORTED, "the plain sampler uses the identity metric");
+    if (cfg->sampler != SPS_HMC) return fail(SPS_E_UNSUPPORTED, "the plain sampler runs HMC");
     if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
     if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
         return fail(SPS_E_SHAPE, "iteration counts");

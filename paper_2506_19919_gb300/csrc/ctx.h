@@ -58,6 +58,7 @@ struct sps_ctx {
     DevBuf nonfinite, queue, err;
     DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
     DevBuf pst, pth, pll, pgr, pgi;   // plain lock-step HMC state and gradient buffers
+    DevBuf hmcn;                      // NUTS tree state per chain
     DevBuf zperm;                     // redshift order of the rows of a tensor-core chunk
     DevBuf Wlo, Vlo;                  // low TF32 halves of W and v (3xTF32 exact path)
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
@@ -100,7 +101,7 @@ struct sps_ctx {
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
-                         &pgi, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo};
+                         &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

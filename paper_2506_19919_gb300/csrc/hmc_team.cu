@@ -63,6 +63,11 @@ struct TeamWork {
     int wstart[CPW], wend[CPW], wwidth[CPW], wstop[CPW];
     long long nev[CPW];
     uint32_t chain[CPW];
+    // NUTS: log weights of the trajectory and of the subtree (relative to
+    // exp(-H0)), statistic sum, leaves built, subtree depth, leaf index in the
+    // subtree, direction, the subtree's acceptance uniform
+    float lw[CPW], lws[CPW], nacc[CPW], utree[CPW];
+    int nleaf[CPW], nj[CPW], nn[CPW], dir[CPW];
 };
 
 // Age and metallicity bin edges of the tables, staged once per block.
@@ -490,28 +495,15 @@ __device__ __noinline__ void dense_metric_update(ChainMetric* cm, int wn) {
     for (int e = 0; e < 78; ++e) cm->chol[e] = Lm[e];
 }
 
-// End of chain ch's trajectory: accept / reject, adaptation, sample.
+// End of iteration t.it[ch] once the chain's new state is in t.x / t.g /
+// t.lp: step-size and metric adaptation (warm-up) with statistic a, or the
+// sample (sampling phase); advances the iteration count.
 template <int CPW>
-__device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
-                                      float* __restrict__ samples) {
+__device__ __noinline__ void iter_finish(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                         float a, float* __restrict__ samples) {
     const int lane = lane_id();
     const bool dense = hp.adapt_mass == 2;
-    metric_apply(t, ch, dense);
-    const double dH = (-t.lp[ch] + kinetic(t, ch)) - t.h0[ch];
-    const bool fin = isfinite(dH);
-    const float a = fin ? fminf(1.0f, __expf(-(float)dH)) : 0.0f;
-    const bool take = fin && t.uacc[ch] < -dH;
-    if (!take && lane < SPS_NPARAM) {
-        t.x[ch][lane] = t.xs[ch][lane];
-        t.g[ch][lane] = t.gs[ch][lane];
-    }
-    __syncwarp();
     const int it = t.it[ch];
-    if (lane == 0) {
-        if (!take) t.lp[ch] = t.lps[ch];
-        if (!fin || dH > 1000.0) t.ndiv[ch] += 1;
-        t.nev[ch] += t.L[ch];
-    }
     if (it < hp.n_warm) {
         const float m = (float)(t.mda[ch] + 1);
         const float im = __frcp_rn(m + 10.0f);
@@ -587,6 +579,257 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
     __syncwarp();
     if (lane == 0) t.it[ch] = it + 1;
     __syncwarp();
+}
+
+// End of chain ch's HMC trajectory: accept / reject, then iter_finish.
+template <int CPW>
+__device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                      float* __restrict__ samples) {
+    const int lane = lane_id();
+    metric_apply(t, ch, hp.adapt_mass == 2);
+    const double dH = (-t.lp[ch] + kinetic(t, ch)) - t.h0[ch];
+    const bool fin = isfinite(dH);
+    const float a = fin ? fminf(1.0f, __expf(-(float)dH)) : 0.0f;
+    const bool take = fin && t.uacc[ch] < -dH;
+    if (!take && lane < SPS_NPARAM) {
+        t.x[ch][lane] = t.xs[ch][lane];
+        t.g[ch][lane] = t.gs[ch][lane];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (!take) t.lp[ch] = t.lps[ch];
+        if (!fin || dH > 1000.0) t.ndiv[ch] += 1;
+        t.nev[ch] += t.L[ch];
+    }
+    iter_finish<CPW>(c, t, ch, hp, a, samples);
+}
+
+// ---------------------------------------------------------------- NUTS
+// Multinomial NUTS with the generalised no-U-turn criterion (Hoffman & Gelman
+// 2014; Betancourt 2017), identity metric, the comparison sampler of Sec. 4 /
+// App. D.2.  A chain's trajectory grows by doubling: at depth j a subtree of
+// 2^j leapfrog steps is built from the trajectory's end in a drawn direction,
+// one leaf per evaluation of the team.  Leaves are weighted by exp(H0 - H);
+// a leaf replaces the subtree's proposal with probability w / (sum of the
+// subtree's weights so far), a completed subtree replaces the trajectory's
+// proposal with probability min(1, W_subtree / W_trajectory).  Every aligned
+// block of 2^k leaves of the subtree is checked for a U-turn (rho . p_first
+// <= 0 or rho . p_last <= 0) as it completes; a U-turn or a divergence
+// (H - H0 > 1000) discards the subtree and ends the iteration.  A merged
+// trajectory that U-turns, or reaches the depth limit, ends it too.  Draws:
+// Philox-4x32-10 with counter (iteration, 16 + j, chain, 0) for the
+// direction (word 0, top bit set = forward) and the subtree's uniform
+// (word 1), (iteration, 64 + j, chain, n) word 0 for leaf n of the depth-j
+// subtree; momenta as HMC.
+
+__device__ __forceinline__ float log_add(float a, float b) {
+    const float m = fmaxf(a, b);
+    return (m == -INFINITY) ? m : m + log1pf(expf(-fabsf(a - b)));
+}
+
+// Direction and acceptance uniform of the chain's subtree at depth t.nj.
+template <int CPW>
+__device__ __forceinline__ void nuts_level(TeamWork<CPW>& t, int ch, const HmcParams& hp) {
+    if (lane_id() == 0) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)t.it[ch], 16u + (uint32_t)t.nj[ch], t.chain[ch], 0u),
+                                      (uint32_t)(hp.seed & 0xffffffffu), (uint32_t)(hp.seed >> 32));
+        t.dir[ch] = (w.x >> 31) ? 1 : -1;
+        t.utree[ch] = u01_f(w.y);
+        t.nn[ch] = 0;
+        t.lws[ch] = -INFINITY;
+    }
+    __syncwarp();
+}
+
+// First half kick and drift of the next leaf, in the chain's direction.
+template <int CPW>
+__device__ __forceinline__ void nuts_advance(TeamWork<CPW>& t, int ch) {
+    const int lane = lane_id();
+    const float ve = (float)t.dir[ch] * t.eps[ch];
+    if (lane < SPS_NPARAM) {
+        const float pp = fmaf(0.5f * ve, t.g[ch][lane], t.p[ch][lane]);
+        t.p[ch][lane] = pp;
+        t.x[ch][lane] = fmaf(ve, pp, t.x[ch][lane]);
+    }
+    __syncwarp();
+}
+
+// Start of iteration t.it[ch]: momentum, H0, the one-state trajectory
+// (its ends, momentum sum and proposal), depth 0, first leaf's drift.
+template <int CPW>
+__device__ __noinline__ void nuts_start(TeamWork<CPW>& t, int ch, const HmcParams& hp) {
+    const int lane = lane_id();
+    float z[SPS_NPARAM];
+    double u;
+    int L;
+    team_draws(hp.seed, t.chain[ch], (uint32_t)t.it[ch], 1, 1, z, u, L);
+    NutsChain* ns = hp.nuts + t.chain[ch];
+    float pl = 0.0f;
+    if (lane < SPS_NPARAM) {
+        pl = z[0];
+#pragma unroll
+        for (int k = 1; k < SPS_NPARAM; ++k)
+            if (lane == k) pl = z[k];
+        const float xl = t.x[ch][lane], gl = t.g[ch][lane];
+        t.p[ch][lane] = pl;
+        t.xs[ch][lane] = xl;
+        t.gs[ch][lane] = gl;
+        ns->xe[0][lane] = xl;
+        ns->xe[1][lane] = xl;
+        ns->pe[0][lane] = pl;
+        ns->pe[1][lane] = pl;
+        ns->ge[0][lane] = gl;
+        ns->ge[1][lane] = gl;
+        ns->rho[lane] = pl;
+    }
+    const double h0 = -t.lp[ch] + 0.5 * (double)warp_sum(pl * pl);
+    if (lane == 0) {
+        t.h0[ch] = h0;
+        t.lps[ch] = t.lp[ch];
+        t.lw[ch] = 0.0f;
+        t.nacc[ch] = 0.0f;
+        t.nleaf[ch] = 0;
+        t.nj[ch] = 0;
+    }
+    __syncwarp();
+    nuts_level(t, ch, hp);
+    nuts_advance(t, ch);
+}
+
+// Chain ch after the evaluation at its newest leaf: second half kick, the
+// leaf's weight, proposal and U-turn checks; then either the next leaf's
+// drift, the next subtree, or the end of the iteration (new state, adaptation,
+// sample) and the start of the next.
+template <int CPW>
+__device__ __noinline__ void nuts_leaf(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                       float* __restrict__ samples) {
+    const int lane = lane_id();
+    NutsChain* ns = hp.nuts + t.chain[ch];
+    const float ve = (float)t.dir[ch] * t.eps[ch];
+    float pl = 0.0f;
+    if (lane < SPS_NPARAM) {
+        pl = fmaf(0.5f * ve, t.g[ch][lane], t.p[ch][lane]);
+        t.p[ch][lane] = pl;
+    }
+    const double dh = (-t.lp[ch] + 0.5 * (double)warp_sum(pl * pl)) - t.h0[ch];
+    const int j = t.nj[ch], n = t.nn[ch];
+    bool stop = false;
+    if (!isfinite(dh) || dh > 1000.0) {
+        stop = true;
+        if (lane == 0) {
+            t.ndiv[ch] += 1;
+            t.nleaf[ch] += 1;
+        }
+    } else {
+        const float mdh = -(float)dh;
+        const float lws = log_add(t.lws[ch], mdh);
+        float ul = 0.0f;
+        if (lane == 0) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)t.it[ch], 64u + (uint32_t)j, t.chain[ch], (uint32_t)n),
+                                          (uint32_t)(hp.seed & 0xffffffffu), (uint32_t)(hp.seed >> 32));
+            ul = u01_f(w.x);
+        }
+        ul = __shfl_sync(kFull, ul, 0);
+        if (n == 0 || ul < expf(mdh - lws)) {           // u01_f can round to 1
+            if (lane < SPS_NPARAM) {
+                ns->xq[lane] = t.x[ch][lane];
+                ns->gq[lane] = t.g[ch][lane];
+            }
+            if (lane == 0) ns->lpq = t.lp[ch];
+        }
+        // running sums of the aligned blocks holding this leaf; check the
+        // blocks it completes
+#pragma unroll 1
+        for (int k = 1; k <= j; ++k) {
+            const int m = (1 << k) - 1;
+            float r = pl, f = pl;
+            if (lane < SPS_NPARAM) {
+                if (n & m) {
+                    r = ns->rk[k - 1][lane] + pl;
+                    f = ns->pk[k - 1][lane];
+                } else {
+                    ns->pk[k - 1][lane] = pl;
+                }
+                ns->rk[k - 1][lane] = r;
+            }
+            if (((n + 1) & m) == 0) {
+                const float d0 = warp_sum(lane < SPS_NPARAM ? r * f : 0.0f);
+                const float d1 = warp_sum(lane < SPS_NPARAM ? r * pl : 0.0f);
+                stop = stop || d0 <= 0.0f || d1 <= 0.0f;
+            }
+        }
+        if (lane == 0) {
+            t.nacc[ch] += fminf(1.0f, __expf(mdh));
+            t.nleaf[ch] += 1;
+            t.lws[ch] = lws;
+        }
+        __syncwarp();
+        if (!stop && n + 1 == (1 << j)) {
+            // subtree complete: merge it into the trajectory
+            const bool take = lws >= t.lw[ch] || t.utree[ch] < expf(lws - t.lw[ch]);
+            const int e = t.dir[ch] > 0 ? 1 : 0;
+            float d0 = 0.0f, d1 = 0.0f;
+            if (lane < SPS_NPARAM) {
+                if (take) {
+                    t.xs[ch][lane] = ns->xq[lane];
+                    t.gs[ch][lane] = ns->gq[lane];
+                }
+                const float rho = ns->rho[lane] + (j == 0 ? pl : ns->rk[j - 1][lane]);
+                ns->rho[lane] = rho;
+                ns->xe[e][lane] = t.x[ch][lane];
+                ns->pe[e][lane] = pl;
+                ns->ge[e][lane] = t.g[ch][lane];
+                d0 = rho * (e == 0 ? pl : ns->pe[0][lane]);
+                d1 = rho * (e == 1 ? pl : ns->pe[1][lane]);
+            }
+            d0 = warp_sum(d0);
+            d1 = warp_sum(d1);
+            if (lane == 0) {
+                if (take) t.lps[ch] = ns->lpq;
+                t.lw[ch] = log_add(t.lw[ch], lws);
+                t.nj[ch] = j + 1;
+            }
+            __syncwarp();
+            if (d0 <= 0.0f || d1 <= 0.0f || j + 1 >= hp.max_depth) {
+                stop = true;
+            } else {
+                nuts_level(t, ch, hp);
+                const int e2 = t.dir[ch] > 0 ? 1 : 0;
+                if (lane < SPS_NPARAM) {
+                    t.x[ch][lane] = ns->xe[e2][lane];
+                    t.p[ch][lane] = ns->pe[e2][lane];
+                    t.g[ch][lane] = ns->ge[e2][lane];
+                }
+                __syncwarp();
+                nuts_advance(t, ch);
+                return;
+            }
+        } else if (!stop) {
+            if (lane == 0) t.nn[ch] = n + 1;
+            __syncwarp();
+            nuts_advance(t, ch);
+            return;
+        }
+    }
+    // end of the iteration: the trajectory's proposal becomes the state
+    if (lane < SPS_NPARAM) {
+        t.x[ch][lane] = t.xs[ch][lane];
+        t.g[ch][lane] = t.gs[ch][lane];
+    }
+    __syncwarp();
+    const float a = t.nacc[ch] / (float)t.nleaf[ch];
+    if (lane == 0) {
+        t.lp[ch] = t.lps[ch];
+        t.nev[ch] += t.nleaf[ch];
+    }
+    __syncwarp();
+    iter_finish<CPW>(c, t, ch, hp, a, samples);
+    if (t.it[ch] >= hp.n_warm + hp.n_samp) {
+        if (lane == 0) t.done[ch] = 1;
+        __syncwarp();
+    } else {
+        nuts_start<CPW>(t, ch, hp);
+    }
 }
 
 // Take work item q (a galaxy and a group of CPW of its chains) into the
@@ -686,6 +929,12 @@ __device__ __forceinline__ void team_step(const Consts& c, TeamWork<CPW>& t, con
                                           float* __restrict__ samples) {
     const int lane = lane_id();
     const int n_it = hp.n_warm + hp.n_samp;
+    if (hp.nuts) {
+#pragma unroll 1
+        for (int ch = 0; ch < CPW; ++ch)
+            if (!t.done[ch]) nuts_leaf<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
+        return;
+    }
 #pragma unroll 1
     for (int ch = 0; ch < CPW; ++ch) {
         if (t.done[ch]) continue;
@@ -758,7 +1007,12 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
         if (pass == 0) {
 #pragma unroll 1
             for (int ch = 0; ch < CPW; ++ch)
-                if (!t.done[ch]) start_traj<CPW>(t, ch, hp);
+                if (!t.done[ch]) {
+                    if (hp.nuts)
+                        nuts_start<CPW>(t, ch, hp);
+                    else
+                        start_traj<CPW>(t, ch, hp);
+                }
         } else {
             team_step<CPW>(c, t, hp, nch, samples);
         }

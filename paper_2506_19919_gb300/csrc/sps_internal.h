@@ -66,6 +66,20 @@ struct ChainMetric {
     float wcov[78];                              // window co-moments (dense)
 };
 
+// Tree state of one NUTS chain (hmc_team.cu), kept in global memory: the
+// trajectory's two ends, the subtree's proposal, the merged trajectory's
+// momentum sum and, per level k = 1..kNutsMaxDepth-1 of the subtree being
+// built, the running momentum sum of its current aligned block of 2^k leaves
+// and that block's first momentum.
+constexpr int kNutsMaxDepth = 10;
+struct NutsChain {
+    float xe[2][SPS_NPARAM], pe[2][SPS_NPARAM], ge[2][SPS_NPARAM];   // [0] backward end, [1] forward end
+    float xq[SPS_NPARAM], gq[SPS_NPARAM];                            // subtree proposal
+    float rho[SPS_NPARAM];                                           // momentum sum of the trajectory
+    float rk[kNutsMaxDepth - 1][SPS_NPARAM], pk[kNutsMaxDepth - 1][SPS_NPARAM];
+    double lpq;                                                      // log density of the subtree proposal
+};
+
 // State of one chain of the plain lock-step HMC (hmc_plain.cu).
 struct PlainChain {
     float x[SPS_NPARAM], p[SPS_NPARAM], g[SPS_NPARAM], xs[SPS_NPARAM], gs[SPS_NPARAM];
@@ -161,6 +175,8 @@ struct HmcParams {
     uint64_t seed;
     int adapt_mass;         // 0 identity, 1 windowed diagonal, 2 windowed dense metric
     int sync_every;         // passes between the block barriers of the team kernel (>= 1)
+    int max_depth;          // NUTS tree depth limit (1..kNutsMaxDepth)
+    NutsChain* nuts;        // per-chain NUTS state; null runs HMC
 };
 size_t hmc_team_smem_per_warp(int cpw);
 cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm);

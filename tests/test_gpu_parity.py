@@ -11,6 +11,7 @@ import torch
 
 import sps_workloads as W
 from oracle import hmc as OH
+from oracle import nuts as ON
 from oracle import sps as O
 
 pytestmark = pytest.mark.gpu
@@ -295,6 +296,75 @@ def test_hmc_prior_only_is_uniform(parity64):
     u = (s - W.PRIOR_LO) / (W.PRIOR_HI - W.PRIOR_LO)
     for k in range(12):
         assert stats.kstest(u[::13, k], "uniform").pvalue > 1e-4
+
+
+def test_nuts_prior_only_matches_oracle_draws(parity64):
+    """NUTS in the persistent kernel: at a fixed step size every chain follows
+    the oracle's NUTS draw by draw (same keyed Philox draws: momentum,
+    directions, subtree and leaf uniforms), with the same number of leaves
+    built, up to FP32 rounding of the energies and U-turn dot products."""
+    wl, ctx = parity64
+    C = 2
+    x0 = np.random.default_rng(3).normal(0, 1.5, size=(64 * C, 12)).astype(np.float32)
+    out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32), chains_per_gal=C,
+                      n_warm=0, n_samp=20, seed=17, eps0=0.7, sampler="nuts", max_depth=6)
+    s = out["samples"].cpu().numpy()
+    ref = ON.run_nuts(_Prior(), x0.astype(np.float64), np.zeros(64 * C, int), seed=17, n_warm=0, n_samp=20,
+                      eps0=0.7, max_depth=6)
+    span = W.PRIOR_HI - W.PRIOR_LO
+    d = np.abs((s - ref["samples"]) / span).max(axis=(1, 2))
+    same = d < 1e-4
+    assert same.mean() > 0.9
+    nev = out["grad_evals"].cpu().numpy()
+    assert (nev[same] == ref["grad_evals"][same]).all()
+    np.testing.assert_allclose(out["accept_prob"].cpu().numpy()[same], ref["accept_prob"][same], atol=1e-4)
+    assert (out["divergences"].cpu().numpy() == ref["divergences"]).mean() > 0.9
+
+
+def test_nuts_with_likelihood_matches_oracle_draws(prod96):
+    """NUTS with the photometric likelihood on (4 chains of a galaxy in lock
+    step on one warp, each with its own tree): draws follow the oracle's."""
+    wl, ctx = prod96
+    G, C = 3, 4
+    th_true = torch.as_tensor(wl.theta_true[:G], dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z[:G], wl.tables, "approx").numpy() + wl.noise[:G]
+    mobs_all = np.full((wl.n_gal, 6), 30.0)
+    mobs_all[:G] = mobs
+    mask = np.zeros(wl.n_gal, np.uint32)
+    mask[:G] = wl.mask[:G]
+    x0 = np.repeat(W.unbounded_of(wl.theta_true[:G]), C, axis=0)
+    x0 = (x0 + np.random.default_rng(6).normal(0, 0.02, x0.shape)).astype(np.float32)
+    x0_all = np.zeros((wl.n_gal * C, 12), np.float32)
+    x0_all[:G * C] = x0
+    out = ctx.hmc_run(x0_all, mobs_all, wl.sigma, mask, chains_per_gal=C, n_warm=0, n_samp=3, seed=23,
+                      eps0=1e-2, autotune=False, sampler="nuts", max_depth=5)
+    s = out["samples"].cpu().numpy()[:G * C]
+    tgt = OH.ApproxTarget(wl.tables, wl.z[:G], mobs, wl.sigma[:G], wl.mask[:G], W.PRIOR_LO, W.PRIOR_HI)
+    ref = ON.run_nuts(tgt, x0.astype(np.float64), np.repeat(np.arange(G), C), seed=23, n_warm=0, n_samp=3,
+                      eps0=1e-2, max_depth=5)
+    span = W.PRIOR_HI - W.PRIOR_LO
+    d = np.abs((s - ref["samples"]) / span).max(axis=(1, 2))
+    assert (d < 2e-5).mean() >= 11 / 12
+    assert (out["grad_evals"].cpu().numpy()[:G * C] == ref["grad_evals"]).mean() >= 11 / 12
+
+
+def test_nuts_adaptation_matches_oracle_statistically(parity64):
+    """NUTS warm-up (dual averaging on the mean leaf statistic) on the
+    prior-only target: adapted step sizes, sampling statistic and leaves per
+    iteration agree with the oracle's in distribution; samples are uniform."""
+    from scipy import stats
+    wl, ctx = parity64
+    x0 = np.random.default_rng(4).normal(0, 1.5, size=(64, 12)).astype(np.float32)
+    out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32), chains_per_gal=1,
+                      n_warm=120, n_samp=60, seed=29, sampler="nuts")
+    ref = ON.run_nuts(_Prior(), x0.astype(np.float64), np.zeros(64, int), seed=29, n_warm=120, n_samp=60)
+    assert np.median(out["step_size"].cpu().numpy()) == pytest.approx(np.median(ref["eps"]), rel=0.15)
+    assert out["accept_prob"].cpu().numpy().mean() == pytest.approx(ref["accept_prob"].mean(), abs=0.05)
+    ng, nr = out["grad_evals"].cpu().numpy(), ref["grad_evals"]
+    assert ng.mean() == pytest.approx(nr.mean(), rel=0.15)
+    u = (out["samples"].cpu().numpy().reshape(-1, 12) - W.PRIOR_LO) / (W.PRIOR_HI - W.PRIOR_LO)
+    for k in range(12):
+        assert stats.kstest(u[::3, k], "uniform").pvalue > 1e-4
 
 
 @pytest.mark.parametrize("mode", ["approx", "exact"])
