@@ -13,7 +13,8 @@ value = sum_g min(1, ESS_g / 100) / (minutes per step), ESS_g the minimum over
 the 12 parameters of the multi-chain ESS of galaxy g.
 
 Also reported: the same sampler run as the plain lock-step forward-mode
-baseline (posteriors/min at equal ESS), log-likelihood + gradient
+baseline (posteriors/min at equal ESS), NUTS in the same kernel on the same
+galaxies (100 + 100 iterations, its own ESS), log-likelihood + gradient
 evaluations per second on 100,000 (galaxy, chain) pairs (approximate FP32,
 exact FP32, exact BF16), the
 roofline of the dominant kernel, the clocks seen during the timed region,
@@ -279,6 +280,8 @@ def run_ours(args):
         out["loglike_grad"] = _loglike_grad_rates(ctx, dev)
     if rank == 0 and not args.skip_plain:
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
+    if rank == 0 and not args.skip_nuts:
+        out["nuts"] = _nuts(ctx, wl, x0, mobs, value, float(nev.sum()) / (ms_local / 1e3))
     if not args.skip_e2e:                       # every rank (collective timing)
         out["e2e"] = _e2e(ctx, cfg, lib, wl, mobs, x0, post, ws)
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -334,6 +337,39 @@ def _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, full):
                     "own_posteriors_per_min": own / (s_run / 60.0),
                     "own_frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean())})
     return res
+
+
+def _nuts(ctx, wl, x0, mobs, hmc_value, hmc_evals_per_s):
+    """NUTS (multinomial, generalised U-turn, depth limit 10, identity metric)
+    in the same persistent kernel on the same galaxies and start points, run
+    for 100 warm-up + 100 sampling iterations (a full 500 + 500 run takes
+    about 100 s), and scored by the same metric with its own ESS."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    G, C = wl.n_gal, wl.chains
+    nw = ns = 100
+    kw = dict(chains_per_gal=C, seed=2506199190, sampler="nuts", max_depth=10)
+    ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=2, n_samp=2, samples=False, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o = ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=nw, n_samp=ns, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    s_run = e0.elapsed_time(e1) / 1e3
+    ess, rhat = pkg.diagnostics(o["samples"], G, C)
+    ess_g = ess.min(1)
+    post = float(np.minimum(1.0, ess_g / ESS_TARGET).sum())
+    nev = o["grad_evals"].cpu().numpy().astype(np.float64)
+    eps = float(nev.sum()) / s_run
+    return {"sampler": "NUTS, multinomial, generalised U-turn, max depth 10, identity metric",
+            "n_warm": nw, "n_samp": ns, "s": s_run, "posteriors_per_min": post / (s_run / 60.0),
+            "vs_hmc_posteriors_per_min": post / (s_run / 60.0) / hmc_value,
+            "median_ess": float(np.median(ess_g)), "frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean()),
+            "leaves_per_iteration": float((nev - 1.0).mean() / (nw + ns)),
+            "grad_evals_per_s": eps, "vs_hmc_grad_evals_per_s": eps / hmc_evals_per_s,
+            "accept_mean": float(o["accept_prob"].mean()), "divergences": int(o["divergences"].sum())}
 
 
 def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
@@ -569,6 +605,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-nuts", action="store_true")
     ap.add_argument("--plain-full", action="store_true",
                     help="run the whole lock-step baseline HMC (minutes) and report its own ESS")
     # profiling captures only (not bench values): smaller galaxy count / iterations

@@ -68,6 +68,8 @@ struct TeamWork {
     // subtree, direction, the subtree's acceptance uniform
     float lw[CPW], lws[CPW], nacc[CPW], utree[CPW];
     int nleaf[CPW], nj[CPW], nn[CPW], dir[CPW];
+    float nS[CPW][SPS_NPARAM];              // momentum prefix sum of the subtree
+    float nu[CPW][32];                      // uniforms of the subtree's next 32 leaves
 };
 
 // Age and metallicity bin edges of the tables, staged once per block.
@@ -620,17 +622,30 @@ __device__ __noinline__ void end_traj(const Consts& c, TeamWork<CPW>& t, int ch,
 // Philox-4x32-10 with counter (iteration, 16 + j, chain, 0) for the
 // direction (word 0, top bit set = forward) and the subtree's uniform
 // (word 1), (iteration, 64 + j, chain, n) word 0 for leaf n of the depth-j
-// subtree; momenta as HMC.
+// subtree (drawn 32 leaves at a time, one per lane); momenta as HMC.
 
 __device__ __forceinline__ float log_add(float a, float b) {
     const float m = fmaxf(a, b);
     return (m == -INFINITY) ? m : m + log1pf(expf(-fabsf(a - b)));
 }
 
-// Direction and acceptance uniform of the chain's subtree at depth t.nj.
+// Uniforms of leaves n .. n+31 of the chain's current subtree (n = t.nn[ch]).
+template <int CPW>
+__device__ __forceinline__ void nuts_fill(TeamWork<CPW>& t, int ch, const HmcParams& hp) {
+    const int lane = lane_id();
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)t.it[ch], 64u + (uint32_t)t.nj[ch], t.chain[ch],
+                                             (uint32_t)(t.nn[ch] + lane)),
+                                  (uint32_t)(hp.seed & 0xffffffffu), (uint32_t)(hp.seed >> 32));
+    t.nu[ch][lane] = u01_f(w.x);
+    __syncwarp();
+}
+
+// New subtree at depth t.nj[ch]: direction, acceptance uniform, empty
+// weight and momentum sum, its first 32 leaf uniforms.
 template <int CPW>
 __device__ __forceinline__ void nuts_level(TeamWork<CPW>& t, int ch, const HmcParams& hp) {
-    if (lane_id() == 0) {
+    const int lane = lane_id();
+    if (lane == 0) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)t.it[ch], 16u + (uint32_t)t.nj[ch], t.chain[ch], 0u),
                                       (uint32_t)(hp.seed & 0xffffffffu), (uint32_t)(hp.seed >> 32));
         t.dir[ch] = (w.x >> 31) ? 1 : -1;
@@ -638,7 +653,9 @@ __device__ __forceinline__ void nuts_level(TeamWork<CPW>& t, int ch, const HmcPa
         t.nn[ch] = 0;
         t.lws[ch] = -INFINITY;
     }
+    if (lane < SPS_NPARAM) t.nS[ch][lane] = 0.0f;
     __syncwarp();
+    nuts_fill(t, ch, hp);
 }
 
 // First half kick and drift of the next leaf, in the chain's direction.
@@ -696,122 +713,12 @@ __device__ __noinline__ void nuts_start(TeamWork<CPW>& t, int ch, const HmcParam
     nuts_advance(t, ch);
 }
 
-// Chain ch after the evaluation at its newest leaf: second half kick, the
-// leaf's weight, proposal and U-turn checks; then either the next leaf's
-// drift, the next subtree, or the end of the iteration (new state, adaptation,
-// sample) and the start of the next.
+// End of the iteration: the trajectory's proposal becomes the state; step
+// size adaptation or sample; the next iteration starts (or the chain is done).
 template <int CPW>
-__device__ __noinline__ void nuts_leaf(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
-                                       float* __restrict__ samples) {
+__device__ __noinline__ void nuts_end_iter(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                           float* __restrict__ samples) {
     const int lane = lane_id();
-    NutsChain* ns = hp.nuts + t.chain[ch];
-    const float ve = (float)t.dir[ch] * t.eps[ch];
-    float pl = 0.0f;
-    if (lane < SPS_NPARAM) {
-        pl = fmaf(0.5f * ve, t.g[ch][lane], t.p[ch][lane]);
-        t.p[ch][lane] = pl;
-    }
-    const double dh = (-t.lp[ch] + 0.5 * (double)warp_sum(pl * pl)) - t.h0[ch];
-    const int j = t.nj[ch], n = t.nn[ch];
-    bool stop = false;
-    if (!isfinite(dh) || dh > 1000.0) {
-        stop = true;
-        if (lane == 0) {
-            t.ndiv[ch] += 1;
-            t.nleaf[ch] += 1;
-        }
-    } else {
-        const float mdh = -(float)dh;
-        const float lws = log_add(t.lws[ch], mdh);
-        float ul = 0.0f;
-        if (lane == 0) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)t.it[ch], 64u + (uint32_t)j, t.chain[ch], (uint32_t)n),
-                                          (uint32_t)(hp.seed & 0xffffffffu), (uint32_t)(hp.seed >> 32));
-            ul = u01_f(w.x);
-        }
-        ul = __shfl_sync(kFull, ul, 0);
-        if (n == 0 || ul < expf(mdh - lws)) {           // u01_f can round to 1
-            if (lane < SPS_NPARAM) {
-                ns->xq[lane] = t.x[ch][lane];
-                ns->gq[lane] = t.g[ch][lane];
-            }
-            if (lane == 0) ns->lpq = t.lp[ch];
-        }
-        // running sums of the aligned blocks holding this leaf; check the
-        // blocks it completes
-#pragma unroll 1
-        for (int k = 1; k <= j; ++k) {
-            const int m = (1 << k) - 1;
-            float r = pl, f = pl;
-            if (lane < SPS_NPARAM) {
-                if (n & m) {
-                    r = ns->rk[k - 1][lane] + pl;
-                    f = ns->pk[k - 1][lane];
-                } else {
-                    ns->pk[k - 1][lane] = pl;
-                }
-                ns->rk[k - 1][lane] = r;
-            }
-            if (((n + 1) & m) == 0) {
-                const float d0 = warp_sum(lane < SPS_NPARAM ? r * f : 0.0f);
-                const float d1 = warp_sum(lane < SPS_NPARAM ? r * pl : 0.0f);
-                stop = stop || d0 <= 0.0f || d1 <= 0.0f;
-            }
-        }
-        if (lane == 0) {
-            t.nacc[ch] += fminf(1.0f, __expf(mdh));
-            t.nleaf[ch] += 1;
-            t.lws[ch] = lws;
-        }
-        __syncwarp();
-        if (!stop && n + 1 == (1 << j)) {
-            // subtree complete: merge it into the trajectory
-            const bool take = lws >= t.lw[ch] || t.utree[ch] < expf(lws - t.lw[ch]);
-            const int e = t.dir[ch] > 0 ? 1 : 0;
-            float d0 = 0.0f, d1 = 0.0f;
-            if (lane < SPS_NPARAM) {
-                if (take) {
-                    t.xs[ch][lane] = ns->xq[lane];
-                    t.gs[ch][lane] = ns->gq[lane];
-                }
-                const float rho = ns->rho[lane] + (j == 0 ? pl : ns->rk[j - 1][lane]);
-                ns->rho[lane] = rho;
-                ns->xe[e][lane] = t.x[ch][lane];
-                ns->pe[e][lane] = pl;
-                ns->ge[e][lane] = t.g[ch][lane];
-                d0 = rho * (e == 0 ? pl : ns->pe[0][lane]);
-                d1 = rho * (e == 1 ? pl : ns->pe[1][lane]);
-            }
-            d0 = warp_sum(d0);
-            d1 = warp_sum(d1);
-            if (lane == 0) {
-                if (take) t.lps[ch] = ns->lpq;
-                t.lw[ch] = log_add(t.lw[ch], lws);
-                t.nj[ch] = j + 1;
-            }
-            __syncwarp();
-            if (d0 <= 0.0f || d1 <= 0.0f || j + 1 >= hp.max_depth) {
-                stop = true;
-            } else {
-                nuts_level(t, ch, hp);
-                const int e2 = t.dir[ch] > 0 ? 1 : 0;
-                if (lane < SPS_NPARAM) {
-                    t.x[ch][lane] = ns->xe[e2][lane];
-                    t.p[ch][lane] = ns->pe[e2][lane];
-                    t.g[ch][lane] = ns->ge[e2][lane];
-                }
-                __syncwarp();
-                nuts_advance(t, ch);
-                return;
-            }
-        } else if (!stop) {
-            if (lane == 0) t.nn[ch] = n + 1;
-            __syncwarp();
-            nuts_advance(t, ch);
-            return;
-        }
-    }
-    // end of the iteration: the trajectory's proposal becomes the state
     if (lane < SPS_NPARAM) {
         t.x[ch][lane] = t.xs[ch][lane];
         t.g[ch][lane] = t.gs[ch][lane];
@@ -829,6 +736,137 @@ __device__ __noinline__ void nuts_leaf(const Consts& c, TeamWork<CPW>& t, int ch
         __syncwarp();
     } else {
         nuts_start<CPW>(t, ch, hp);
+    }
+}
+
+// The subtree at depth t.nj[ch] is complete and free of U-turns: merge it
+// (proposal, weight, momentum sum, end), then check the whole trajectory and
+// either end the iteration or start the next subtree from the drawn end.
+template <int CPW>
+__device__ __noinline__ void nuts_merge(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                        float* __restrict__ samples) {
+    const int lane = lane_id();
+    NutsChain* ns = hp.nuts + t.chain[ch];
+    const int j = t.nj[ch];
+    const float lws = t.lws[ch];
+    const bool take = lws >= t.lw[ch] || t.utree[ch] < expf(lws - t.lw[ch]);
+    const int e = t.dir[ch] > 0 ? 1 : 0;
+    float d0 = 0.0f, d1 = 0.0f;
+    if (lane < SPS_NPARAM) {
+        if (take) {
+            t.xs[ch][lane] = ns->xq[lane];
+            t.gs[ch][lane] = ns->gq[lane];
+        }
+        const float pl = t.p[ch][lane];
+        const float rho = ns->rho[lane] + t.nS[ch][lane];
+        ns->rho[lane] = rho;
+        ns->xe[e][lane] = t.x[ch][lane];
+        ns->pe[e][lane] = pl;
+        ns->ge[e][lane] = t.g[ch][lane];
+        d0 = rho * (e == 0 ? pl : ns->pe[0][lane]);
+        d1 = rho * (e == 1 ? pl : ns->pe[1][lane]);
+    }
+    d0 = warp_sum(d0);
+    d1 = warp_sum(d1);
+    if (lane == 0) {
+        if (take) t.lps[ch] = ns->lpq;
+        t.lw[ch] = log_add(t.lw[ch], lws);
+        t.nj[ch] = j + 1;
+    }
+    __syncwarp();
+    if (d0 <= 0.0f || d1 <= 0.0f || j + 1 >= hp.max_depth) {
+        nuts_end_iter<CPW>(c, t, ch, hp, samples);
+        return;
+    }
+    nuts_level(t, ch, hp);
+    const int e2 = t.dir[ch] > 0 ? 1 : 0;
+    if (lane < SPS_NPARAM) {
+        t.x[ch][lane] = ns->xe[e2][lane];
+        t.p[ch][lane] = ns->pe[e2][lane];
+        t.g[ch][lane] = ns->ge[e2][lane];
+    }
+    __syncwarp();
+    nuts_advance(t, ch);
+}
+
+// Chain ch after the evaluation at its newest leaf n of the depth-j subtree:
+// second half kick, the leaf's weight and proposal draw, the U-turn checks of
+// the aligned blocks it completes, then the next leaf (or merge / end).
+template <int CPW>
+__device__ __forceinline__ void nuts_leaf(const Consts& c, TeamWork<CPW>& t, int ch, const HmcParams& hp,
+                                          float* __restrict__ samples) {
+    const int lane = lane_id();
+    const float ve = (float)t.dir[ch] * t.eps[ch];
+    float pl = 0.0f;
+    if (lane < SPS_NPARAM) {
+        pl = fmaf(0.5f * ve, t.g[ch][lane], t.p[ch][lane]);
+        t.p[ch][lane] = pl;
+    }
+    const double dh = (-t.lp[ch] + 0.5 * (double)warp_sum(pl * pl)) - t.h0[ch];
+    if (!isfinite(dh) || dh > 1000.0) {                       // divergence
+        if (lane == 0) {
+            t.ndiv[ch] += 1;
+            t.nleaf[ch] += 1;
+        }
+        __syncwarp();
+        nuts_end_iter<CPW>(c, t, ch, hp, samples);
+        return;
+    }
+    NutsChain* ns = hp.nuts + t.chain[ch];
+    const int j = t.nj[ch], n = t.nn[ch];
+    const float mdh = -(float)dh;
+    const float lws = log_add(t.lws[ch], mdh);
+    if (n == 0 || t.nu[ch][n & 31] < expf(mdh - lws)) {     // u01_f can round to 1
+        if (lane < SPS_NPARAM) {
+            ns->xq[lane] = t.x[ch][lane];
+            ns->gq[lane] = t.g[ch][lane];
+        }
+        if (lane == 0) ns->lpq = t.lp[ch];
+    }
+    // momentum prefix sum of the subtree; blocks of 2^k leaves starting here
+    // record it, blocks ending here are checked (rho = prefix - recorded)
+    bool turn = false;
+    if (j > 0) {
+        const int starts = (n == 0) ? j : __ffs(n) - 1;       // levels k with n % 2^k == 0
+        const int ends = __ffs(n + 1) - 1;                     // levels k with (n + 1) % 2^k == 0
+        float sb = 0.0f, sa = 0.0f;
+        if (lane < SPS_NPARAM) {
+            sb = t.nS[ch][lane];
+            sa = sb + pl;
+            t.nS[ch][lane] = sa;
+#pragma unroll 1
+            for (int k = 1; k <= starts; ++k) {
+                ns->sk[k - 1][lane] = sb;
+                ns->pk[k - 1][lane] = pl;
+            }
+        }
+#pragma unroll 1
+        for (int k = 1; k <= ends; ++k) {
+            float r = 0.0f, f = 0.0f;
+            if (lane < SPS_NPARAM) {
+                r = sa - ns->sk[k - 1][lane];
+                f = ns->pk[k - 1][lane];
+            }
+            const float d0 = warp_sum(r * f), d1 = warp_sum(r * pl);
+            turn = turn || d0 <= 0.0f || d1 <= 0.0f;
+        }
+    } else if (lane < SPS_NPARAM) {
+        t.nS[ch][lane] = pl;
+    }
+    if (lane == 0) {
+        t.nacc[ch] += fminf(1.0f, __expf(mdh));
+        t.nleaf[ch] += 1;
+        t.lws[ch] = lws;
+        t.nn[ch] = n + 1;
+    }
+    __syncwarp();
+    if (turn) {
+        nuts_end_iter<CPW>(c, t, ch, hp, samples);
+    } else if (n + 1 == (1 << j)) {
+        nuts_merge<CPW>(c, t, ch, hp, samples);
+    } else {
+        if (((n + 1) & 31) == 0) nuts_fill(t, ch, hp);
+        nuts_advance(t, ch);
     }
 }
 

@@ -69,14 +69,15 @@ struct ChainMetric {
 // Tree state of one NUTS chain (hmc_team.cu), kept in global memory: the
 // trajectory's two ends, the subtree's proposal, the merged trajectory's
 // momentum sum and, per level k = 1..kNutsMaxDepth-1 of the subtree being
-// built, the running momentum sum of its current aligned block of 2^k leaves
-// and that block's first momentum.
+// built, the subtree's momentum prefix sum before its current aligned block
+// of 2^k leaves and that block's first momentum (a block's momentum sum is
+// the prefix sum at its last leaf minus the one before its first).
 constexpr int kNutsMaxDepth = 10;
 struct NutsChain {
     float xe[2][SPS_NPARAM], pe[2][SPS_NPARAM], ge[2][SPS_NPARAM];   // [0] backward end, [1] forward end
     float xq[SPS_NPARAM], gq[SPS_NPARAM];                            // subtree proposal
     float rho[SPS_NPARAM];                                           // momentum sum of the trajectory
-    float rk[kNutsMaxDepth - 1][SPS_NPARAM], pk[kNutsMaxDepth - 1][SPS_NPARAM];
+    float sk[kNutsMaxDepth - 1][SPS_NPARAM], pk[kNutsMaxDepth - 1][SPS_NPARAM];
     double lpq;                                                      // log density of the subtree proposal
 };
 
