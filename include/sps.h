@@ -98,10 +98,21 @@ typedef struct {
     const double* band_p1;
 } sps_tables;
 
+/* Prior on the unbounded parameters x (App. C).  SPS_PRIOR_UNIFORM: uniform in
+ * each bounded parameter theta = F_B(x), i.e. the log of the Jacobian of Eq.
+ * BoundingFunction, log s (1 - s) with s = 1 / (1 + exp(-k (x - x0))) (the
+ * constant log(k (hi - lo)) dropped).  SPS_PRIOR_SKEWNORMAL: the skew-normal
+ * of Eq. SkewNormPrior on x, log(2 / omega) + log N((x - xi) / omega)
+ * + log Phi(s (x - xi) / omega), a normalised density (the paper fits xi,
+ * omega, s to prior draws mapped through F_B^-1; paper_2506_19919_gb300.priors
+ * does that on the host). */
+typedef enum { SPS_PRIOR_UNIFORM = 0, SPS_PRIOR_SKEWNORMAL = 1 } sps_prior;
+
 /* Context configuration.  sps_config_default() fills the declared defaults:
  * flat LambdaCDM with H0 = 70 km/s/Mpc, Omega_m = 0.3 (the paper states none),
  * the package's prior bounds, device 0, Gauss-Legendre order 6 and panel width
- * 0.25 in ln t for the SFH bin integrals.  The SFH bin integrals use panels of
+ * 0.25 in ln t for the SFH bin integrals, bounding functions with k = 1,
+ * x0 = 0 and the uniform prior.  The SFH bin integrals use panels of
  * sfh_panel * 10 / kappa in ln t, kappa = max(alpha + beta, beta + 1), clamped
  * to [1, 8] x sfh_panel, with the sfh_gl_order rule on each; a bin that fits in
  * one panel and is narrow against 1 / kappa takes a 2- or 3-node rule (never
@@ -114,6 +125,12 @@ typedef struct {
     int32_t device;
     int32_t sfh_gl_order; /* 2..16 */
     double sfh_panel;     /* panel width in ln t at kappa = 10, (0, 2] */
+    double sigmoid_k[SPS_NPARAM];   /* Eq. BoundingFunction k per parameter, > 0 (1)   */
+    double sigmoid_x0[SPS_NPARAM];  /* Eq. BoundingFunction x0 per parameter (0)       */
+    int32_t prior;                  /* sps_prior (SPS_PRIOR_UNIFORM)                   */
+    double skew_xi[SPS_NPARAM];     /* Eq. SkewNormPrior location per parameter (0)    */
+    double skew_omega[SPS_NPARAM];  /* Eq. SkewNormPrior scale per parameter, > 0 (1)  */
+    double skew_s[SPS_NPARAM];      /* Eq. SkewNormPrior shape per parameter (0)       */
 } sps_config;
 
 sps_status sps_config_default(sps_config* cfg);

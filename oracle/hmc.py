@@ -109,7 +109,7 @@ class ApproxTarget:
     per-galaxy redshift-dependent pieces (c_SSP, lambda_eff, N_b, distance
     factor) computed once, as Sec. 3 allows when z is known."""
 
-    def __init__(self, tables, z, mag_obs, sigma, mask, lo, hi):
+    def __init__(self, tables, z, mag_obs, sigma, mask, lo, hi, k=1.0, x0=0.0, skew=None):
         z = O._t(z)
         self.tables = tables
         self.cssp = O.c_ssp(tables, z)                      # [G, B, K]
@@ -121,6 +121,7 @@ class ApproxTarget:
         self.mag_obs, self.sigma = O._t(mag_obs), O._t(sigma)
         self.mask = np.asarray(mask)
         self.lo, self.hi = O._t(lo), O._t(hi)
+        self.k, self.x0, self.skew = k, x0, skew      # Eq. BoundingFunction / SkewNormPrior
 
     def mags(self, theta, rows):
         W, _, _, _ = O.ssp_weights(theta, self.tables, self.t_obs[rows])
@@ -130,10 +131,10 @@ class ApproxTarget:
 
     def __call__(self, x, rows):
         x = O._t(x).clone().requires_grad_(True)
-        th = O.bound(x, self.lo, self.hi)
+        th = O.bound(x, self.lo, self.hi, self.k, self.x0)
         mag = self.mags(th, rows)
         lp = O.loglike(mag, self.mag_obs[rows], self.sigma[rows], self.mask[rows]) \
-            + O.log_prior_unbounded(x)
+            + O.log_prior_unbounded(x, self.k, self.x0, self.skew)
         (g,) = torch.autograd.grad(lp.sum(), x)
         return lp.detach().numpy(), g.detach().numpy()
 
@@ -266,7 +267,8 @@ def run_hmc(target, x0, gal_of_chain, seed, n_warm, n_samp, L_min=8, L_max=64,
                         m_da = 0
         else:
             s = it - n_warm
-            th = O.bound(torch.as_tensor(x), target.lo, target.hi).numpy()
+            th = O.bound(torch.as_tensor(x), target.lo, target.hi, getattr(target, "k", 1.0),
+                         getattr(target, "x0", 0.0)).numpy()
             samples[:, s] = th
             acc_sum += a
     return dict(samples=samples, accept_prob=acc_sum / max(n_samp, 1), eps=eps, minv=minv, chol=chol,

@@ -182,7 +182,8 @@ def run_nuts(target, x0, gal_of_chain, seed, n_warm, n_samp, eps0=0.1, target_ac
                 depth_sum[c] += dep
         if it >= n_warm:
             samples_x[:, it - n_warm] = x
-            samples[:, it - n_warm] = O.bound(torch.as_tensor(x), target.lo, target.hi).numpy()
+            samples[:, it - n_warm] = O.bound(torch.as_tensor(x), target.lo, target.hi, getattr(target, "k", 1.0),
+                                              getattr(target, "x0", 0.0)).numpy()
     ns = max(n_samp, 1)
     return dict(samples=samples, samples_x=samples_x, accept_prob=acc_sum / ns, eps=eps, divergences=div,
                 grad_evals=nevals, depth=depth_sum / ns)

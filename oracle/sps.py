@@ -418,25 +418,37 @@ def loglike_and_grad(theta, z, tables, mag_obs, sigma, mask_bits, mode="exact"):
 
 
 # ---------------------------------------------------------------- bounding + prior
-def bound(theta_unb, lo, hi):
-    """Eq. BoundingFunction with k = 1, x0 = 0 (App. C)."""
-    return _t(lo) + (_t(hi) - _t(lo)) * torch.sigmoid(theta_unb)
+def bound(theta_unb, lo, hi, k=1.0, x0=0.0):
+    """Eq. BoundingFunction (App. C): theta = lo + (hi - lo) / (1 + exp(-k (x - x0))),
+    per parameter; k = 1, x0 = 0 unless tuned."""
+    return _t(lo) + (_t(hi) - _t(lo)) * torch.sigmoid(_t(k) * (theta_unb - _t(x0)))
 
 
-def log_prior_unbounded(theta_unb):
-    """log density in unbounded space of a prior uniform in the bounded
-    parameter: log of the Jacobian sigma(x)(1 - sigma(x)) of Eq.
-    BoundingFunction (constants dropped)."""
-    return (torch.nn.functional.logsigmoid(theta_unb)
-            + torch.nn.functional.logsigmoid(-theta_unb)).sum(-1)
+def log_prior_unbounded(theta_unb, k=1.0, x0=0.0, skew=None):
+    """log prior density in unbounded space, summed over the parameters.
+
+    skew None: the prior uniform in the bounded parameter, i.e. the log of
+    the Jacobian of Eq. BoundingFunction, log sigma(y) (1 - sigma(y)) with
+    y = k (x - x0) (constant log(k (hi - lo)) dropped).
+    skew = (xi, omega, s): the skew-normal of Eq. SkewNormPrior on x itself,
+    log(2 / omega) + log N(u) + log Phi(s u), u = (x - xi) / omega, with the
+    normal density's constant kept (a normalised density)."""
+    x = _t(theta_unb)
+    if skew is None:
+        y = _t(k) * (x - _t(x0))
+        return (torch.nn.functional.logsigmoid(y) + torch.nn.functional.logsigmoid(-y)).sum(-1)
+    xi, om, sk = (_t(v) for v in skew)
+    u = (x - xi) / om
+    return (math.log(2.0) - torch.log(om) - 0.5 * math.log(2.0 * math.pi) - 0.5 * u * u
+            + torch.special.log_ndtr(sk * u)).sum(-1)
 
 
 def logpost_and_grad_unbounded(theta_unb, z, tables, mag_obs, sigma, mask_bits, lo, hi,
-                               mode="approx"):
+                               mode="approx", k=1.0, x0=0.0, skew=None):
     """log posterior in unbounded space and its gradient (HMC target)."""
     x = _t(theta_unb).clone().requires_grad_(True)
-    th = bound(x, lo, hi)
+    th = bound(x, lo, hi, k, x0)
     mag = photometry(th, _t(z), tables, mode)
-    lp = loglike(mag, mag_obs, sigma, mask_bits) + log_prior_unbounded(x)
+    lp = loglike(mag, mag_obs, sigma, mask_bits) + log_prior_unbounded(x, k, x0, skew)
     (g,) = torch.autograd.grad(lp.sum(), x)
     return lp.detach(), g.detach()

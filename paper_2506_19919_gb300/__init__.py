@@ -45,7 +45,13 @@ class Context:
     """One library context: tables on one device plus the current galaxy set."""
 
     def __init__(self, tables, device: int = 0, h0: float = 70.0, omega_m: float = 0.3,
-                 prior_lo=None, prior_hi=None, gl_order: int = 6, panel: float = 0.25):
+                 prior_lo=None, prior_hi=None, gl_order: int = 6, panel: float = 0.25,
+                 sigmoid_k=None, sigmoid_x0=None, skew=None):
+        """skew = (xi, omega, s), each of 12 values, selects the skew-normal
+        prior of Eq. SkewNormPrior on the unbounded parameters (see
+        priors.fit_skew_normal); otherwise the prior is uniform in the bounded
+        parameters.  sigmoid_k / sigmoid_x0 are the Eq. BoundingFunction
+        hyper-parameters (see priors.tune_sigmoid); default 1 and 0."""
         lib = load()
         self._lib = lib
         cfg = sps_config()
@@ -59,6 +65,15 @@ class Context:
             for k in range(_lib.NPARAM):
                 cfg.prior_lo[k] = float(prior_lo[k])
                 cfg.prior_hi[k] = float(prior_hi[k])
+        for k in range(_lib.NPARAM):
+            if sigmoid_k is not None:
+                cfg.sigmoid_k[k] = float(sigmoid_k[k])
+            if sigmoid_x0 is not None:
+                cfg.sigmoid_x0[k] = float(sigmoid_x0[k])
+        if skew is not None:
+            cfg.prior = 1
+            for k in range(_lib.NPARAM):
+                cfg.skew_xi[k], cfg.skew_omega[k], cfg.skew_s[k] = (float(v[k]) for v in skew)
         self._keep = [np.ascontiguousarray(tables.age_yr, dtype=np.float64),
                       np.ascontiguousarray(tables.lgZ, dtype=np.float64),
                       np.ascontiguousarray(tables.lam_ang, dtype=np.float64),

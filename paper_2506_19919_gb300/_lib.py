@@ -32,7 +32,10 @@ class sps_tables(C.Structure):
 class sps_config(C.Structure):
     _fields_ = [("h0_kms_mpc", C.c_double), ("omega_m", C.c_double),
                 ("prior_lo", C.c_double * NPARAM), ("prior_hi", C.c_double * NPARAM),
-                ("device", C.c_int32), ("sfh_gl_order", C.c_int32), ("sfh_panel", C.c_double)]
+                ("device", C.c_int32), ("sfh_gl_order", C.c_int32), ("sfh_panel", C.c_double),
+                ("sigmoid_k", C.c_double * NPARAM), ("sigmoid_x0", C.c_double * NPARAM), ("prior", C.c_int32),
+                ("skew_xi", C.c_double * NPARAM), ("skew_omega", C.c_double * NPARAM),
+                ("skew_s", C.c_double * NPARAM)]
 
 
 class sps_hmc_config(C.Structure):

@@ -51,10 +51,7 @@ k_approx_rows(const __grid_constant__ Consts c, const Galaxies g, const float* _
 #pragma unroll
             for (int k = 0; k < SPS_NPARAM; ++k) {
                 float v = gr[k];
-                if (unbounded) {
-                    float x = theta[row * SPS_NPARAM + k];
-                    v = v * p.dth[k] + (1.0f - 2.0f * sigmoidf_(x));
-                }
+                if (unbounded) v = v * p.dth[k] + p.dlp[k];
                 bad = bad || !isfinite(v);
                 grad_out[row * SPS_NPARAM + k] = v;
             }

@@ -238,6 +238,14 @@ sps_status sps_config_default(sps_config* cfg) {
     cfg->device = 0;
     cfg->sfh_gl_order = 6;
     cfg->sfh_panel = 0.25;
+    for (int k = 0; k < SPS_NPARAM; ++k) {
+        cfg->sigmoid_k[k] = 1.0;
+        cfg->sigmoid_x0[k] = 0.0;
+        cfg->skew_xi[k] = 0.0;
+        cfg->skew_omega[k] = 1.0;
+        cfg->skew_s[k] = 0.0;
+    }
+    cfg->prior = SPS_PRIOR_UNIFORM;
     return SPS_OK;
 }
 
@@ -298,8 +306,17 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
     if (!(cfg.sfh_panel > 0 && cfg.sfh_panel <= 2.0)) return fail(SPS_E_INVALID_ARG, "sfh_panel in (0, 2]");
     if (!(cfg.h0_kms_mpc > 0) || !(cfg.omega_m > 0 && cfg.omega_m < 1))
         return fail(SPS_E_INVALID_ARG, "cosmology out of range");
-    for (int k = 0; k < SPS_NPARAM; ++k)
+    for (int k = 0; k < SPS_NPARAM; ++k) {
         if (!(cfg.prior_hi[k] > cfg.prior_lo[k])) return fail(SPS_E_INVALID_ARG, "prior_hi must exceed prior_lo");
+        if (!(cfg.sigmoid_k[k] > 0) || !std::isfinite(cfg.sigmoid_k[k]) || !std::isfinite(cfg.sigmoid_x0[k]))
+            return fail(SPS_E_INVALID_ARG, "sigmoid_k must be finite and > 0, sigmoid_x0 finite");
+        if (cfg.prior == SPS_PRIOR_SKEWNORMAL &&
+            (!(cfg.skew_omega[k] > 0) || !std::isfinite(cfg.skew_omega[k]) || !std::isfinite(cfg.skew_xi[k]) ||
+             !std::isfinite(cfg.skew_s[k])))
+            return fail(SPS_E_INVALID_ARG, "skew-normal prior needs finite xi, s and omega > 0");
+    }
+    if (cfg.prior != SPS_PRIOR_UNIFORM && cfg.prior != SPS_PRIOR_SKEWNORMAL)
+        return fail(SPS_E_INVALID_ARG, "prior");
     // Worst-case SFH panel count per row: every bin one panel plus the log-time
     // range down to the truncation point (at most ~45 in ln t) in panels.
     const int max_panels = A + (int)std::ceil(48.0 / cfg.sfh_panel) + 2;
@@ -361,7 +378,14 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
     for (int k = 0; k < SPS_NPARAM; ++k) {
         c.prior_lo[k] = (float)cfg.prior_lo[k];
         c.prior_span[k] = (float)(cfg.prior_hi[k] - cfg.prior_lo[k]);
+        c.sig_k[k] = (float)cfg.sigmoid_k[k];
+        c.sig_x0[k] = (float)cfg.sigmoid_x0[k];
+        c.sn_xi[k] = (float)cfg.skew_xi[k];
+        c.sn_iom[k] = (float)(1.0 / cfg.skew_omega[k]);
+        c.sn_s[k] = (float)cfg.skew_s[k];
+        c.sn_c[k] = (float)(std::log(2.0 / cfg.skew_omega[k]) - 0.5 * std::log(2.0 * M_PI));
     }
+    c.prior_kind = cfg.prior;
     for (int b = 0; b < B; ++b) c.band_kind[b] = t->band_kind[b];
     ctx->band_p0.assign(t->band_p0, t->band_p0 + B);
     ctx->band_p1.assign(t->band_p1, t->band_p1 + B);

@@ -35,10 +35,7 @@ __device__ __forceinline__ double logp_grad(const ChainCtx& cc, const float* x, 
     float gr[SPS_NPARAM];
     double ll = eval_row(*cc.c, *cc.ww, cc.bins, cc.lnT, cc.lT10, p, cc.nb, true, true, gr);
 #pragma unroll
-    for (int k = 0; k < SPS_NPARAM; ++k) {
-        float sg = sigmoidf_(x[k]);
-        g[k] = gr[k] * p.dth[k] + (1.0f - 2.0f * sg);
-    }
+    for (int k = 0; k < SPS_NPARAM; ++k) g[k] = gr[k] * p.dth[k] + p.dlp[k];
     return ll + p.logprior;
 }
 

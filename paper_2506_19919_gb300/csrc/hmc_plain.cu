@@ -16,31 +16,16 @@
 #include <math.h>
 
 #include "philox.cuh"
-#include "sps_internal.h"
+#include "sps_device.cuh"
 
 namespace sps {
 
 namespace {
 
-__device__ __forceinline__ void bound_param(const Consts& c, int k, float x, float& th, float& dth,
-                                            float& lpe, float& dlp) {
-    const float ex = __expf(-fabsf(x));
-    const float r = __frcp_rn(1.0f + ex);
-    const float sg = (x >= 0.0f) ? r : ex * r;        // 1 / (1 + e^-x)
-    th = c.prior_lo[k] + c.prior_span[k] * sg;
-    dth = c.prior_span[k] * sg * (1.0f - sg);
-    lpe = -fabsf(x) - 2.0f * __logf(1.0f + ex);       // log sg (1 - sg)
-    dlp = 1.0f - 2.0f * sg;
-}
-
 // theta = F_B(x) for the next gradient evaluation.
 __device__ __forceinline__ void write_theta(const Consts& c, const PlainChain& s, float* __restrict__ th) {
 #pragma unroll
-    for (int k = 0; k < SPS_NPARAM; ++k) {
-        float t, d, l, q;
-        bound_param(c, k, s.x[k], t, d, l, q);
-        th[k] = t;
-    }
+    for (int k = 0; k < SPS_NPARAM; ++k) th[k] = bound_theta(c, k, s.x[k]);
 }
 
 // log posterior and its gradient in unbounded space from the physical-space
@@ -50,7 +35,7 @@ __device__ __forceinline__ void absorb(const Consts& c, PlainChain& s, double ll
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) {
         float t, d, l, q;
-        bound_param(c, k, s.x[k], t, d, l, q);
+        bound_prior(c, k, s.x[k], t, d, l, q);
         lpri += (double)l;
         s.g[k] = gth[k] * d + q;
     }
@@ -198,7 +183,7 @@ __global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams h
             float* o = samples + ((size_t)i * hp.n_samp + (it - hp.n_warm)) * SPS_NPARAM;
 #pragma unroll
             for (int k = 0; k < SPS_NPARAM; ++k)
-                o[k] = c.prior_lo[k] + c.prior_span[k] / (1.0f + __expf(-s.x[k]));
+                o[k] = bound_theta(c, k, s.x[k]);
         }
     }
     s.it = it + 1;

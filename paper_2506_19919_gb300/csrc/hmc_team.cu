@@ -40,7 +40,8 @@ struct TeamWork {
             float res[CPW][kMaxBands], gam[CPW][kMaxBands]; // residual m - m_obs, dlogL / dln c
         } t;
     } u;
-    float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM], lpe[CPW][SPS_NPARAM];
+    float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM];
+    float lpe[CPW][SPS_NPARAM];             // log prior terms, then their x-derivatives
     double M[CPW], lpri[CPW], ll[CPW];
     float gd[CPW][4];                       // d logL / d(lgM, A_V, delta, F_floor)
     // galaxy slots
@@ -105,16 +106,14 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
                                           float lnT, float lT10, int nb) {
     const int lane = lane_id();
     const int A = c.n_age, Zn = c.n_met;
-#pragma unroll 1
-    for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
-        const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
-        const float x = t.x[ch][k];
-        const float ex = __expf(-fabsf(x));
-        const float r = __frcp_rn(1.0f + ex);
-        const float sg = (x >= 0.0f) ? r : ex * r;          // 1 / (1 + e^-x)
-        t.th[ch][k] = c.prior_lo[k] + c.prior_span[k] * sg;
-        t.dth[ch][k] = c.prior_span[k] * sg * (1.0f - sg);
-        t.lpe[ch][k] = -fabsf(x) - 2.0f * __logf(1.0f + ex);   // log sg (1 - sg)
+    float dlp[(CPW * SPS_NPARAM + 31) / 32];
+#pragma unroll
+    for (int r = 0; r < (CPW * SPS_NPARAM + 31) / 32; ++r) {
+        const int e = lane + 32 * r;
+        if (e < CPW * SPS_NPARAM) {
+            const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
+            bound_prior(c, k, t.x[ch][k], t.th[ch][k], t.dth[ch][k], t.lpe[ch][k], dlp[r]);
+        }
     }
     __syncwarp();
     // log prior, FP64: two chains per round, 16 lanes each
@@ -125,6 +124,12 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (k == 0 && ch < CPW) t.lpri[ch] = s;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < (CPW * SPS_NPARAM + 31) / 32; ++r) {     // lpe now holds d log prior / dx
+        const int e = lane + 32 * r;
+        if (e < CPW * SPS_NPARAM) t.lpe[e / SPS_NPARAM][e % SPS_NPARAM] = dlp[r];
     }
 #pragma unroll 1
     for (int ch = 0; ch < CPW; ++ch) age_met_parts(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
@@ -329,8 +334,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
 #pragma unroll
             for (int k = 1; k < SPS_NPARAM; ++k)
                 if (lane == k) v = gr[k];
-            const float sg = __frcp_rn(1.0f + __expf(-t.x[ch][lane]));
-            t.g[ch][lane] = v * t.dth[ch][lane] + (1.0f - 2.0f * sg);
+            t.g[ch][lane] = v * t.dth[ch][lane] + t.lpe[ch][lane];
         }
         if (lane == 0) t.lp[ch] = t.ll[ch] + t.lpri[ch];
     }
@@ -576,7 +580,7 @@ __device__ __noinline__ void iter_finish(const Consts& c, TeamWork<CPW>& t, int 
         if (lane == 0) t.acc[ch] += a;
         if (samples && lane < SPS_NPARAM)
             samples[((size_t)t.chain[ch] * hp.n_samp + (it - hp.n_warm)) * SPS_NPARAM + lane] =
-                c.prior_lo[lane] + c.prior_span[lane] / (1.0f + __expf(-t.x[ch][lane]));
+                bound_theta(c, lane, t.x[ch][lane]);
     }
     __syncwarp();
     if (lane == 0) t.it[ch] = it + 1;

@@ -473,11 +473,53 @@ __device__ __forceinline__ float phi_(float y) {
 // theta = lo + span / (1 + exp(-x))  (Eq. BoundingFunction, k = 1, x0 = 0).
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
+// Eq. BoundingFunction for parameter k: theta = lo + span / (1 + exp(-k_s (x - x0))).
+__device__ __forceinline__ float bound_theta(const Consts& c, int k, float x) {
+    return c.prior_lo[k] + c.prior_span[k] * sigmoidf_(c.sig_k[k] * (x - c.sig_x0[k]));
+}
+
+// Eq. BoundingFunction for parameter k with its derivative, and the log prior
+// density of x with its derivative: uniform in theta (log of the Jacobian,
+// log s (1 - s), constant log(k_s span) dropped), or the skew-normal of Eq.
+// SkewNormPrior on x, log(2/omega) + log N(u) + log Phi(s u), u = (x - xi) /
+// omega.  log Phi(z) and phi(z) / Phi(z) for z < 0 through the scaled
+// complementary error function: Phi(z) = erfcx(-z/sqrt2) e^{-z^2/2} / 2.
+__device__ __forceinline__ void bound_prior(const Consts& c, int k, float x, float& th, float& dth, float& lpe,
+                                            float& dlpe) {
+    const float ks = c.sig_k[k];
+    const float y = ks * (x - c.sig_x0[k]);
+    const float ey = __expf(-fabsf(y));
+    const float r = __frcp_rn(1.0f + ey);
+    const float sg = (y >= 0.0f) ? r : ey * r;              // 1 / (1 + e^-y)
+    th = c.prior_lo[k] + c.prior_span[k] * sg;
+    dth = c.prior_span[k] * ks * sg * (1.0f - sg);
+    if (c.prior_kind == SPS_PRIOR_SKEWNORMAL) {
+        const float u = (x - c.sn_xi[k]) * c.sn_iom[k];
+        const float z = c.sn_s[k] * u;
+        float lphi, ratio;
+        if (z < 0.0f) {
+            const float e = erfcxf(-z * 0.70710678f);
+            lphi = __logf(0.5f * e) - 0.5f * z * z;
+            ratio = 0.79788456f / e;                             // sqrt(2 / pi) / erfcx
+        } else {
+            const float q = 0.5f * erfcf(z * 0.70710678f);      // 1 - Phi(z)
+            lphi = log1pf(-q);
+            ratio = 0.39894228f * __expf(-0.5f * z * z) / (1.0f - q);
+        }
+        lpe = c.sn_c[k] - 0.5f * u * u + lphi;
+        dlpe = (c.sn_s[k] * ratio - u) * c.sn_iom[k];
+    } else {
+        lpe = -fabsf(y) - 2.0f * log1pf(ey);
+        dlpe = ks * (1.0f - 2.0f * sg);
+    }
+}
+
 // Parameters of one row held uniformly by the warp.
 struct RowParams {
     float th[SPS_NPARAM];
     float dth[SPS_NPARAM];   // d theta / d x (unbounded input) or 1
-    double logprior;         // log Jacobian of the bounding map (unbounded input) or 0
+    float dlp[SPS_NPARAM];   // d log prior / d x (unbounded input) or 0
+    double logprior;         // log prior density of x (unbounded input) or 0
     bool finite;
 };
 
@@ -490,14 +532,13 @@ __device__ __forceinline__ void load_params(const Consts& c, const float* __rest
         float x = src[k];
         p.finite = p.finite && isfinite(x);
         if (unbounded) {
-            float sg = sigmoidf_(x);
-            p.th[k] = c.prior_lo[k] + c.prior_span[k] * sg;
-            p.dth[k] = c.prior_span[k] * sg * (1.0f - sg);
-            float ax = fabsf(x);
-            p.logprior += (double)(-ax - 2.0f * log1pf(__expf(-ax)));
+            float lpe;
+            bound_prior(c, k, x, p.th[k], p.dth[k], lpe, p.dlp[k]);
+            p.logprior += (double)lpe;
         } else {
             p.th[k] = x;
             p.dth[k] = 1.0f;
+            p.dlp[k] = 0.0f;
         }
     }
 }

@@ -29,6 +29,10 @@ struct Consts {
     float log_age_edge[kMaxAges + 1];     // log10 age-bin edges [yr]; [0] = -100 stand-in
     float lgz_edge[kMaxMets + 1];         // metallicity-bin edges; outer +-inf
     float prior_lo[SPS_NPARAM], prior_span[SPS_NPARAM];
+    float sig_k[SPS_NPARAM], sig_x0[SPS_NPARAM];   // Eq. BoundingFunction slope and centre
+    int prior_kind;                                // sps_prior
+    float sn_xi[SPS_NPARAM], sn_iom[SPS_NPARAM];   // Eq. SkewNormPrior: xi, 1 / omega,
+    float sn_s[SPS_NPARAM], sn_c[SPS_NPARAM];      // s, log(2 / omega) - log(2 pi) / 2
     int band_kind[kMaxBands];
 };
 

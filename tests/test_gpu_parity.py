@@ -367,6 +367,98 @@ def test_nuts_adaptation_matches_oracle_statistically(parity64):
         assert stats.kstest(u[::3, k], "uniform").pvalue > 1e-4
 
 
+def _tuned_prior(seed):
+    """Tuned sigmoids (expected range: the middle 40-70% of each bound) and a
+    skew-normal prior fitted, per the paper's recipe, to Gaussian draws of
+    theta mapped through F_B^-1."""
+    from paper_2506_19919_gb300 import priors as P
+    lo, hi = W.PRIOR_LO, W.PRIOR_HI
+    k, x0 = P.tune_sigmoid(lo, hi, lo + 0.4 * (hi - lo), lo + 0.7 * (hi - lo))
+    rng = np.random.default_rng(seed)
+    th = np.clip(rng.normal(lo + 0.55 * (hi - lo), 0.12 * (hi - lo), (20_000, 12)), lo + 1e-4 * (hi - lo),
+                 hi - 1e-4 * (hi - lo))
+    return k, x0, P.skew_normal_prior(th, lo, hi, k, x0)
+
+
+def test_tuned_sigmoid_and_skew_prior_leapfrog(prod96):
+    """Eq. BoundingFunction with tuned (k, x0) and the skew-normal prior of
+    Eq. SkewNormPrior: leapfrog trajectories with the likelihood on follow the
+    oracle's (log posterior, positions, momenta)."""
+    import paper_2506_19919_gb300 as pkg
+    wl, _ = prod96
+    k, x0s, skew = _tuned_prior(1)
+    ctx = pkg.Context(wl.tables, device=0, sigmoid_k=k, sigmoid_x0=x0s, skew=skew)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    n = 12
+    th_true = torch.as_tensor(wl.theta_true[:n], dtype=torch.float64)
+    mobs = O.photometry(th_true, wl.z[:n], wl.tables, "approx").numpy() + wl.noise[:n]
+    from paper_2506_19919_gb300 import priors as P
+    x0 = P.unbound(wl.theta_true[:n], W.PRIOR_LO, W.PRIOR_HI, k, x0s).astype(np.float32).astype(np.float64)
+    p0 = np.random.default_rng(4).normal(size=(n, 12)).astype(np.float32).astype(np.float64)
+    eps = np.full(n, 2e-3, np.float32)
+    L = np.full(n, 8, np.int32)
+    xg, pg, lg = ctx.leapfrog(x0, p0, eps, L, mobs, wl.sigma[:n], wl.mask[:n], gal_idx=np.arange(n, dtype=np.int32))
+    tgt = OH.ApproxTarget(wl.tables, wl.z[:n], mobs, wl.sigma[:n], wl.mask[:n], W.PRIOR_LO, W.PRIOR_HI,
+                          k=k, x0=x0s, skew=skew)
+    rows = np.arange(n)
+    _, g0 = tgt(x0, rows)
+    xr, pr, _, lr = OH.leapfrog(tgt, rows, x0, p0, g0, eps.astype(np.float64), L)
+    np.testing.assert_allclose(xg.cpu().numpy(), xr, rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(pg.cpu().numpy(), pr, rtol=1e-3, atol=1e-3 * np.abs(pr).max())
+    np.testing.assert_allclose(lg.cpu().numpy(), lr, rtol=1e-5, atol=1e-3)
+    ctx.close()
+
+
+@pytest.mark.parametrize("path,sampler", [("fused", "hmc"), ("plain", "hmc"), ("fused", "nuts")])
+def test_skew_prior_samplers_match_oracle_draws(parity64, path, sampler):
+    """Prior-only target under the tuned sigmoid and skew-normal prior: the
+    fused HMC, the lock-step baseline and NUTS follow the oracle's chains draw
+    by draw at a fixed step size, and the draws follow the skew-normal."""
+    import paper_2506_19919_gb300 as pkg
+    from scipy import stats
+    wl, _ = parity64
+    k, x0s, skew = _tuned_prior(2)
+    ctx = pkg.Context(wl.tables, device=0, sigmoid_k=k, sigmoid_x0=x0s, skew=skew)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    C = 2
+    x0 = np.random.default_rng(6).normal(0, 1.0, size=(64 * C, 12)).astype(np.float32)
+    kw = dict(chains_per_gal=C, n_warm=0, n_samp=30, seed=31, eps0=0.3)
+    if sampler == "nuts":
+        out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32), sampler="nuts",
+                          max_depth=6, **kw)
+    else:
+        out = ctx.hmc_run(x0, np.zeros((64, 6)), np.ones((64, 6)), np.zeros(64, np.uint32), L_min=4, L_max=12,
+                          path=path, **kw)
+    s = out["samples"].cpu().numpy()
+
+    class _Skew:
+        lo, hi = torch.as_tensor(W.PRIOR_LO), torch.as_tensor(W.PRIOR_HI)
+
+        def __init__(self):
+            self.k, self.x0 = k, x0s
+
+        def __call__(self, x, rows):
+            xt = torch.as_tensor(np.asarray(x)).clone().requires_grad_(True)
+            lp = O.log_prior_unbounded(xt, k, x0s, skew)
+            (g,) = torch.autograd.grad(lp.sum(), xt)
+            return lp.detach().numpy(), g.numpy()
+
+    if sampler == "nuts":
+        ref = ON.run_nuts(_Skew(), x0.astype(np.float64), np.zeros(64 * C, int), seed=31, n_warm=0, n_samp=30,
+                          eps0=0.3, max_depth=6)
+    else:
+        ref = OH.run_hmc(_Skew(), x0.astype(np.float64), np.zeros(64 * C, int), seed=31, n_warm=0, n_samp=30,
+                         L_min=4, L_max=12, eps0=0.3)
+    span = W.PRIOR_HI - W.PRIOR_LO
+    d = np.abs((s - ref["samples"]) / span).max(axis=(1, 2))
+    assert (d < 1e-4).mean() > 0.9
+    from paper_2506_19919_gb300 import priors as P
+    x = P.unbound(s[:, 10:].reshape(-1, 12).astype(np.float64), W.PRIOR_LO, W.PRIOR_HI, k, x0s)
+    for j in range(12):
+        assert stats.kstest(x[::7, j], stats.skewnorm(skew[2][j], loc=skew[0][j], scale=skew[1][j]).cdf).pvalue > 1e-4
+    ctx.close()
+
+
 @pytest.mark.parametrize("mode", ["approx", "exact"])
 def test_full_size_sampled_rows(mode):
     """100,000 galaxies on the production grid in one call (the benchmark's
