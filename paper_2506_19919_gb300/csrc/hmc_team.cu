@@ -132,7 +132,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         if (e < CPW * SPS_NPARAM) t.lpe[e / SPS_NPARAM][e % SPS_NPARAM] = dlp[r];
     }
 #pragma unroll 1
-    for (int ch = 0; ch < CPW; ++ch) age_met_parts(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
+    for (int ch = 0; ch < CPW; ++ch) age_met_parts<true>(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
     __syncwarp();
     // M = sum_i m_i in FP64, the chains' reductions interleaved
     {

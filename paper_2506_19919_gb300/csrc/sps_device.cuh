@@ -170,62 +170,85 @@ __device__ __forceinline__ int panel_count(float f) {
 //   u < 0:  hh = e^{(beta+1)u} r,  r = 1 / (1 + e^{(alpha+beta)u}),  hh P = 1 - r, hh Q = r
 //   u >= 0: hh = e^{(1-alpha)u} r, r = 1 / (1 + e^{-(alpha+beta)u}), hh P = r,     hh Q = 1 - r
 // so that dhh/dalpha = -u hh (hh P), dhh/dbeta = u hh (hh Q) and
-// alpha P - beta Q = (alpha hhP - beta hhQ) / hh.
-template <int N>
+// alpha P - beta Q = (alpha hhP - beta hhQ) / hh.  kPack takes the nodes in pairs
+// with packed FP32x2 arithmetic (faster in the HMC team kernel, slower in the
+// one-row-per-warp kernels, which keep the scalar loop).
+template <int N, bool kPack = false>
 __device__ __forceinline__ void gl_panel(const float* __restrict__ gx, const float* __restrict__ gw,
                                          float hp, float xc, float alpha, float beta, bool grad,
                                          float& v0, float& v1, float& v2, float& v3) {
     const float kL2E = 1.4426950408889634f;
     const float cneg = (beta + 1.0f) * kL2E, cpos = (1.0f - alpha) * kL2E, cs = -(alpha + beta) * kL2E;
-    // nodes in pairs with packed FP32x2 arithmetic (MUFU per element)
-    const float2 hp2 = make_float2(hp, hp), xc2 = make_float2(xc, xc);
-    const float2 one2 = make_float2(1.0f, 1.0f);
-    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    if constexpr (kPack) {
+        // nodes in pairs with packed FP32x2 arithmetic (MUFU per element)
+        const float2 hp2 = make_float2(hp, hp), xc2 = make_float2(xc, xc);
+        const float2 one2 = make_float2(1.0f, 1.0f);
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
 #pragma unroll
-    for (int q = 0; q + 1 < N; q += 2) {
-        const float2 uu = __ffma2_rn(hp2, make_float2(gx[q], gx[q + 1]), xc2);
-        const bool px = uu.x >= 0.0f, py = uu.y >= 0.0f;
-        const float2 Ea = __fmul2_rn(uu, make_float2(px ? cpos : cneg, py ? cpos : cneg));
-        const float2 Ra = __fmul2_rn(make_float2(fabsf(uu.x), fabsf(uu.y)), make_float2(cs, cs));
-        const float2 E = make_float2(exp2f(Ea.x), exp2f(Ea.y));
-        const float2 R = make_float2(exp2f(Ra.x), exp2f(Ra.y));
-        const float2 d = __fadd2_rn(one2, R);
-        const float2 r = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
-        const float2 wh = __fmul2_rn(__fmul2_rn(make_float2(gw[q], gw[q + 1]), hp2), __fmul2_rn(E, r));
-        a0 = __fadd2_rn(a0, wh);
-        if (grad) {
-            const float2 hP = make_float2(px ? r.x : 1.0f - r.x, py ? r.y : 1.0f - r.y);   // hh P
-            const float2 hQ = __fadd2_rn(one2, make_float2(-hP.x, -hP.y));              // hh Q
-            const float2 tt = __ffma2_rn(make_float2(alpha, alpha), hP, __fmul2_rn(make_float2(-beta, -beta), hQ));
-            a1 = __ffma2_rn(wh, tt, a1);
-            const float2 whu = __fmul2_rn(wh, uu);
-            a2 = __ffma2_rn(make_float2(-whu.x, -whu.y), hP, a2);
-            a3 = __ffma2_rn(whu, hQ, a3);
+        for (int q = 0; q + 1 < N; q += 2) {
+            const float2 uu = __ffma2_rn(hp2, make_float2(gx[q], gx[q + 1]), xc2);
+            const bool px = uu.x >= 0.0f, py = uu.y >= 0.0f;
+            const float2 Ea = __fmul2_rn(uu, make_float2(px ? cpos : cneg, py ? cpos : cneg));
+            const float2 Ra = __fmul2_rn(make_float2(fabsf(uu.x), fabsf(uu.y)), make_float2(cs, cs));
+            const float2 E = make_float2(exp2f(Ea.x), exp2f(Ea.y));
+            const float2 R = make_float2(exp2f(Ra.x), exp2f(Ra.y));
+            const float2 d = __fadd2_rn(one2, R);
+            const float2 r = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
+            const float2 wh = __fmul2_rn(__fmul2_rn(make_float2(gw[q], gw[q + 1]), hp2), __fmul2_rn(E, r));
+            a0 = __fadd2_rn(a0, wh);
+            if (grad) {
+                const float2 hP = make_float2(px ? r.x : 1.0f - r.x, py ? r.y : 1.0f - r.y);   // hh P
+                const float2 hQ = __fadd2_rn(one2, make_float2(-hP.x, -hP.y));              // hh Q
+                const float2 tt = __ffma2_rn(make_float2(alpha, alpha), hP, __fmul2_rn(make_float2(-beta, -beta), hQ));
+                a1 = __ffma2_rn(wh, tt, a1);
+                const float2 whu = __fmul2_rn(wh, uu);
+                a2 = __ffma2_rn(make_float2(-whu.x, -whu.y), hP, a2);
+                a3 = __ffma2_rn(whu, hQ, a3);
+            }
         }
-    }
-    if (N & 1) {
-        const int q = N - 1;
-        const float uu = fmaf(hp, gx[q], xc);
-        const bool pos = uu >= 0.0f;
-        const float E = exp2f(uu * (pos ? cpos : cneg));
-        const float R = exp2f(fabsf(uu) * cs);
-        const float r = __fdividef(1.0f, 1.0f + R);
-        const float wh = gw[q] * hp * E * r;
-        a0.x += wh;
-        if (grad) {
-            const float hP = pos ? r : 1.0f - r;
-            const float hQ = 1.0f - hP;
-            a1.x = fmaf(wh, alpha * hP - beta * hQ, a1.x);
-            const float whu = wh * uu;
-            a2.x = fmaf(-whu, hP, a2.x);
-            a3.x = fmaf(whu, hQ, a3.x);
+        if (N & 1) {
+            const int q = N - 1;
+            const float uu = fmaf(hp, gx[q], xc);
+            const bool pos = uu >= 0.0f;
+            const float E = exp2f(uu * (pos ? cpos : cneg));
+            const float R = exp2f(fabsf(uu) * cs);
+            const float r = __fdividef(1.0f, 1.0f + R);
+            const float wh = gw[q] * hp * E * r;
+            a0.x += wh;
+            if (grad) {
+                const float hP = pos ? r : 1.0f - r;
+                const float hQ = 1.0f - hP;
+                a1.x = fmaf(wh, alpha * hP - beta * hQ, a1.x);
+                const float whu = wh * uu;
+                a2.x = fmaf(-whu, hP, a2.x);
+                a3.x = fmaf(whu, hQ, a3.x);
+            }
         }
-    }
-    v0 += a0.x + a0.y;
-    if (grad) {
-        v1 += a1.x + a1.y;
-        v2 += a2.x + a2.y;
-        v3 += a3.x + a3.y;
+        v0 += a0.x + a0.y;
+        if (grad) {
+            v1 += a1.x + a1.y;
+            v2 += a2.x + a2.y;
+            v3 += a3.x + a3.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const float uu = fmaf(hp, gx[q], xc);
+            const bool pos = uu >= 0.0f;
+            const float E = exp2f(uu * (pos ? cpos : cneg));
+            const float R = exp2f(fabsf(uu) * cs);
+            const float r = __fdividef(1.0f, 1.0f + R);
+            const float wh = gw[q] * hp * E * r;                      // w hh
+            v0 += wh;
+            if (grad) {
+                const float hP = pos ? r : 1.0f - r;                  // hh P
+                const float hQ = 1.0f - hP;                           // hh Q
+                v1 = fmaf(wh, alpha * hP - beta * hQ, v1);
+                const float whu = wh * uu;
+                v2 = fmaf(-whu, hP, v2);
+                v3 = fmaf(whu, hQ, v3);
+            }
+        }
     }
 }
 __device__ __forceinline__ void gl_panel_any(int n, const float* __restrict__ gx,
@@ -249,6 +272,7 @@ __device__ __forceinline__ void gl_panel_any(int n, const float* __restrict__ gx
 // ln tau + min(ln t_obs - ln tau, 0) - 22 / (beta + 1) the integrand is below
 // e^-22 of its value at the peak or at t_obs, and the remaining mass (< 1e-9
 // of the total) is dropped.
+template <bool kPack = false>
 __device__ __forceinline__ void sfh_bins_raw(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
                                              float lnT, float tau, float alpha, float beta, bool grad) {
     PanelScratch& ps = *v.ps;
@@ -303,11 +327,11 @@ __device__ __forceinline__ void sfh_bins_raw(const Consts& c, const AgeView& v, 
         if (oc > 0 && ord > 0) {
             const float xc = x0 - lntau;
             if (oc <= 2)
-                gl_panel<2>(c.gl2_x, c.gl2_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+                gl_panel<2, kPack>(c.gl2_x, c.gl2_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
             else if (oc == 3)
-                gl_panel<3>(c.gl3_x, c.gl3_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+                gl_panel<3, kPack>(c.gl3_x, c.gl3_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
             else if (oc == 6)
-                gl_panel<6>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+                gl_panel<6, kPack>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
             else
                 gl_panel_any(G, c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
         }
@@ -364,7 +388,7 @@ __device__ __forceinline__ void sfh_bins_raw(const Consts& c, const AgeView& v, 
             const float hp = inf.y;
             const float xc = inf.x + 2.0f * (float)(p - __float_as_int(inf.z)) * hp - lntau;
             if (G == 6)
-                gl_panel<6>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
+                gl_panel<6, kPack>(c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
             else
                 gl_panel_any(G, c.gl_x, c.gl_w, hp, xc, alpha, beta, grad, v0, v1, v2, v3);
         }
@@ -545,9 +569,10 @@ __device__ __forceinline__ void load_params(const Consts& c, const float* __rest
 
 // ---------------------------------------------------------------- weights stage
 // Bin integrals, burst and metallicity weights (everything but M and w).
+template <bool kPack = false>
 __device__ __forceinline__ void age_met_parts(const Consts& c, const AgeView& v, const float2* __restrict__ bins,
                                               float lnT, float lT10, const float* th, bool grad) {
-    sfh_bins_raw(c, v, bins, lnT, th[1], th[2], th[3], grad);
+    sfh_bins_raw<kPack>(c, v, bins, lnT, th[1], th[2], th[3], grad);
     burst_weights(c, v, lT10, th[5], th[6] * (1.0f / 3.0f));
     met_weights(c, v, th[7], th[8]);
 }
