@@ -77,7 +77,7 @@ typedef enum { SPS_EXACT = 0, SPS_APPROX = 1 } sps_mode;
  *             the tensor cores (~3e-5 mag, gradients ~1e-3: the tensor-core
  *             accumulation over the 1284-term contraction limits it). */
 typedef enum { SPS_FP32 = 0, SPS_BF16 = 1, SPS_TF32X3 = 2 } sps_prec;
-typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1 } sps_band_kind;
+typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1, SPS_BAND_TABLE = 2 } sps_band_kind;
 
 /* Model grids, SSP table and filters (host memory, float64; copied in).
  *  age_yr[n_age]  strictly increasing SSP ages [yr]
@@ -86,7 +86,14 @@ typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1 } sps_band_kind;
  *  ssp[n_age*n_met*n_lam] L_SSP[i][j][n] in L_sun/Hz per solar mass formed
  *  band_kind[n_band], band_p0, band_p1: observed-frame filters;
  *    TOPHAT: transmission 1 on [p0, p1) Angstrom;
- *    GAUSS:  transmission exp(-(l - p0)^2 / (2 s^2)), s = p1 / (2 sqrt(2 ln 2)) (p1 = FWHM). */
+ *    GAUSS:  transmission exp(-(l - p0)^2 / (2 s^2)), s = p1 / (2 sqrt(2 ln 2)) (p1 = FWHM);
+ *    TABLE:  a measured throughput curve (Sec. 5 uses LSST's): band_tab_n[b] >= 2
+ *            samples T_m >= 0 at l = p0 + m p1 Angstrom (p0 > 0, p1 > 0), the
+ *            transmission their linear interpolant, zero outside the samples.
+ *  band_tab_n[n_band]: samples per TABLE band (ignored for the others; the
+ *    pointer may be NULL when no band is tabulated); band_tab_T: the TABLE
+ *    bands' samples, concatenated in band order.  Resample curves with uneven
+ *    steps onto a uniform grid first (paper_2506_19919_gb300.loaders does). */
 typedef struct {
     int32_t n_age, n_met, n_lam, n_band;
     const double* age_yr;
@@ -96,6 +103,8 @@ typedef struct {
     const int32_t* band_kind;
     const double* band_p0;
     const double* band_p1;
+    const int32_t* band_tab_n;
+    const double* band_tab_T;
 } sps_tables;
 
 /* Prior on the unbounded parameters x (App. C).  SPS_PRIOR_UNIFORM: uniform in

@@ -293,15 +293,30 @@ def trapezoid_weights(lam_ang):
 
 def transmission(tables, lam_obs):
     """T_b at observed-frame wavelengths lam_obs [..., Lam] -> [..., B, Lam].
-    Top-hat: 1 on [lo, hi); Gaussian: peak 1, given FWHM."""
+    Top-hat: 1 on [lo, hi); Gaussian: peak 1, given FWHM; tabulated (a
+    supplied throughput curve, e.g. a survey's filter files): the linear
+    interpolant of samples T_m at lam_start + m * step, m = 0..n-1, zero
+    outside [lam_start, lam_start + (n-1) step] (reading: the paper uses
+    measured LSST curves without saying how they are interpolated)."""
     out = []
+    off = 0
     for b in range(tables.n_band):
         p0, p1 = float(tables.band_p0[b]), float(tables.band_p1[b])
-        if int(tables.band_kind[b]) == 0:
+        kind = int(tables.band_kind[b])
+        if kind == 0:
             out.append(((lam_obs >= p0) & (lam_obs < p1)).to(DT))
-        else:
+        elif kind == 1:
             s = p1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
             out.append(torch.exp(-0.5 * ((lam_obs - p0) / s) ** 2))
+        else:
+            n = int(tables.band_tab_n[b])
+            Tm = torch.as_tensor(np.asarray(tables.band_tab_T[off:off + n], dtype=np.float64))
+            off += n
+            u = (lam_obs - p0) / p1                                  # sample coordinate
+            inside = (u >= 0.0) & (u <= n - 1)
+            m = torch.clamp(torch.floor(u), 0, n - 2).long()
+            f = u - m.to(DT)
+            out.append(torch.where(inside, (1.0 - f) * Tm[m] + f * Tm[m + 1], torch.zeros_like(u)))
     return torch.stack(out, dim=-2)
 
 

@@ -82,9 +82,15 @@ class Context:
                       np.ascontiguousarray(tables.band_p0, dtype=np.float64),
                       np.ascontiguousarray(tables.band_p1, dtype=np.float64)]
         a, z, l, s, k, p0, p1 = self._keep
+        tab_n = getattr(tables, "band_tab_n", None)
+        tab_T = getattr(tables, "band_tab_T", None)
+        if tab_n is not None:
+            self._keep += [np.ascontiguousarray(tab_n, dtype=np.int32),
+                           np.ascontiguousarray(tab_T, dtype=np.float64)]
         t = sps_tables(len(a), len(z), len(l), len(k), a.ctypes.data, z.ctypes.data,
                        l.ctypes.data, s.ctypes.data, k.ctypes.data, p0.ctypes.data,
-                       p1.ctypes.data)
+                       p1.ctypes.data, self._keep[7].ctypes.data if tab_n is not None else None,
+                       self._keep[8].ctypes.data if tab_n is not None else None)
         h = C.c_void_p()
         check(lib.sps_create(C.byref(h), C.byref(t), C.byref(cfg)), "sps_create")
         self.h = h

@@ -291,13 +291,25 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
     for (int n = 0; n < L; ++n)
         if (!(t->lam_ang[n] > 0) || (n && !(t->lam_ang[n] > t->lam_ang[n - 1])))
             return fail(SPS_E_INVALID_ARG, "wavelength grid must be positive and increasing");
+    int64_t n_tab = 0;                        // tabulated samples in all
     for (int b = 0; b < B; ++b) {
         int k = t->band_kind[b];
-        if (k != SPS_BAND_TOPHAT && k != SPS_BAND_GAUSS) return fail(SPS_E_INVALID_ARG, "bad band kind");
+        if (k != SPS_BAND_TOPHAT && k != SPS_BAND_GAUSS && k != SPS_BAND_TABLE)
+            return fail(SPS_E_INVALID_ARG, "bad band kind");
         if (k == SPS_BAND_TOPHAT && !(t->band_p1[b] > t->band_p0[b] && t->band_p0[b] > 0))
             return fail(SPS_E_INVALID_ARG, "top-hat band needs 0 < p0 < p1");
         if (k == SPS_BAND_GAUSS && !(t->band_p1[b] > 0 && t->band_p0[b] > 0))
             return fail(SPS_E_INVALID_ARG, "Gaussian band needs positive centre and FWHM");
+        if (k == SPS_BAND_TABLE) {
+            if (!t->band_tab_n || !t->band_tab_T) return fail(SPS_E_INVALID_ARG, "tabulated band without samples");
+            if (!(t->band_p0[b] > 0 && t->band_p1[b] > 0) || t->band_tab_n[b] < 2 || t->band_tab_n[b] > (1 << 20))
+                return fail(SPS_E_INVALID_ARG, "tabulated band needs start > 0, step > 0 and 2..2^20 samples");
+            for (int m = 0; m < t->band_tab_n[b]; ++m) {
+                const double v = t->band_tab_T[n_tab + m];
+                if (!std::isfinite(v) || v < 0) return fail(SPS_E_INVALID_ARG, "tabulated transmission must be finite and >= 0");
+            }
+            n_tab += t->band_tab_n[b];
+        }
     }
     const size_t K = (size_t)A * Zn;
     for (size_t e = 0; e < K * L; ++e)
@@ -386,7 +398,18 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         c.sn_c[k] = (float)(std::log(2.0 / cfg.skew_omega[k]) - 0.5 * std::log(2.0 * M_PI));
     }
     c.prior_kind = cfg.prior;
-    for (int b = 0; b < B; ++b) c.band_kind[b] = t->band_kind[b];
+    std::vector<double> tab64;
+    for (int b = 0; b < B; ++b) {
+        c.band_kind[b] = t->band_kind[b];
+        c.tab_off[b] = (int)tab64.size();
+        c.tab_n[b] = 0;
+        if (t->band_kind[b] == SPS_BAND_TABLE) {
+            c.tab_n[b] = t->band_tab_n[b];
+            tab64.insert(tab64.end(), t->band_tab_T + c.tab_off[b], t->band_tab_T + c.tab_off[b] + c.tab_n[b]);
+        }
+    }
+    if (tab64.empty()) tab64.push_back(0.0);
+    std::vector<float> tab32(tab64.begin(), tab64.end());
     ctx->band_p0.assign(t->band_p0, t->band_p0 + B);
     ctx->band_p1.assign(t->band_p1, t->band_p1 + B);
 
@@ -437,6 +460,8 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         (e = upload(ctx->age_edges, edges.data(), edges.size() * 8)) != cudaSuccess ||
         (e = upload(ctx->bp0, t->band_p0, sizeof(double) * B)) != cudaSuccess ||
         (e = upload(ctx->bp1, t->band_p1, sizeof(double) * B)) != cudaSuccess ||
+        (e = upload(ctx->tabT, tab32.data(), sizeof(float) * tab32.size())) != cudaSuccess ||
+        (e = upload(ctx->tabT64, tab64.data(), sizeof(double) * tab64.size())) != cudaSuccess ||
         (e = ctx->lam32.reserve(sizeof(float) * L)) != cudaSuccess ||
         (e = ctx->lamc.reserve(sizeof(float4) * L)) != cudaSuccess ||
         (e = ctx->nonfinite.reserve(64)) != cudaSuccess || (e = ctx->queue.reserve(64)) != cudaSuccess ||
@@ -497,7 +522,8 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
             return fail(SPS_E_NOMEM, "c_SSP table does not fit in device memory");
         }
         ctx->has_approx = true;
-        CK(launch_cssp(c, ctx->grid(), ctx->gal(), ctx->bp0.as<double>(), ctx->gcssp.as<float>(), s));
+        CK(launch_cssp(c, ctx->grid(), ctx->gal(), ctx->bp0.as<double>(), ctx->bp1.as<double>(),
+                       ctx->gcssp.as<float>(), s));
     }
     CK(cudaStreamSynchronize(s));
     return SPS_OK;

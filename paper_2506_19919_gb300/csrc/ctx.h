@@ -50,6 +50,7 @@ struct sps_ctx {
     // tables
     DevBuf lam64, lam32, lamc, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, age_edges, bp0, bp1;
     DevBuf ssp_hi, ssp_lo, ssp_t_hi, ssp_t_lo;   // 3xTF32 halves of the FP32 tables
+    DevBuf tabT, tabT64;                         // tabulated transmission samples
     // galaxies
     int64_t n_gal = 0;
     bool has_approx = false;
@@ -78,6 +79,8 @@ struct sps_ctx {
         g.ssp_bf = ssp_bf.as<uint16_t>();
         g.ssp_t_bf = ssp_t_bf.as<uint16_t>();
         g.row_scale = row_scale.as<float>();
+        g.band_T = tabT.as<float>();
+        g.band_T64 = tabT64.as<double>();
         return g;
     }
     Galaxies gal() const {
@@ -101,7 +104,7 @@ struct sps_ctx {
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
-                         &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo};
+                         &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo, &tabT, &tabT64};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

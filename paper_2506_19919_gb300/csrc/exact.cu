@@ -11,6 +11,7 @@
 // This file holds the SIMT contraction kernels.
 #include <cuda_bf16.h>
 
+#include "band_tab.cuh"
 #include "sps_device.cuh"
 
 namespace sps {
@@ -172,7 +173,9 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
         }
         __syncthreads();
         for (int b = 0; b < B; ++b) {
-            const bool top = c.band_kind[b] == 0;
+            const int kind = c.band_kind[b];
+            const float* tabT = grid.band_T + c.tab_off[b];
+            const int tabn = c.tab_n[b];
             float v[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -187,9 +190,11 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
                     if (nn >= sp.x && nn < sp.y) {
                         const float4 L4 = lc[nl];
                         float wb = L4.x;
-                        if (!top) {
+                        if (kind == 1) {
                             float u = (lamt[nl] - gg.x) * gg.y;
                             wb *= __expf(-0.5f * u * u);
+                        } else if (kind == 2) {
+                            wb *= tab_T32(tabT, tabn, (lamt[nl] - gg.x) * -gg.y);
                         }
                         float pw = __expf(rd.y * L4.z);
                         float base = L4.y * pw + rd.w * L4.w;
@@ -323,9 +328,11 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
             for (int b = 0; b < B; ++b) {
                 if (gb[b] != 0.0f && nn >= sp[b].x && nn < sp[b].y) {
                     float wb = L4.x;
-                    if (c.band_kind[b] != 0) {
+                    if (c.band_kind[b] == 1) {
                         float u = (lam - gg[b].x) * gg[b].y;
                         wb *= __expf(-0.5f * u * u);
+                    } else if (c.band_kind[b] == 2) {
+                        wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (lam - gg[b].x) * -gg[b].y);
                     }
                     sum = fmaf(gb[b], wb, sum);
                 }

@@ -19,6 +19,7 @@
 // is released.
 #include <cuda.h>
 
+#include "band_tab.cuh"
 #include "sps_device.cuh"
 #include "tc_ptx.cuh"
 
@@ -288,7 +289,7 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             }
             sxy[k] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
             gc[k] = ga.x;
-            gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 marks a top-hat
+            gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 top-hat, > 0 Gaussian, < 0 table
             acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
         }
         for (int nt = 0; nt < n_tiles; ++nt) {
@@ -319,9 +320,13 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                             const float E = exp2f(cA * base);
                             const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
                             float w = L4.x;
-                            if (gs[k] != 0.0f) {
+                            if (gs[k] > 0.0f) {
                                 const float u = (__ldg(grid.lam + nn) - gc[k]) * gs[k];
                                 w *= __expf(-0.5f * u * u);
+                            } else if (gs[k] < 0.0f) {
+                                const int b = b0 + k;
+                                w *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b],
+                                             (__ldg(grid.lam + nn) - gc[k]) * -gs[k]);
                             }
                             const float Sw = S[j] * w;
                             const float es = Sw * E;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "band_tab.cuh"
 #include "sps_internal.h"
 
 namespace sps {
@@ -68,7 +69,8 @@ __global__ void k_lambda_consts(const double* __restrict__ lam, int L, float4* _
 __global__ void __launch_bounds__(kPrepThreads)
 k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
           const double* __restrict__ band_p0, const double* __restrict__ band_p1,
-          const double* __restrict__ age_edges_yr, const float* __restrict__ zin, int64_t G,
+          const double* __restrict__ tabT, const double* __restrict__ age_edges_yr,
+          const float* __restrict__ zin, int64_t G,
           double h0, double om, float* __restrict__ lnT_out, float* __restrict__ lT10_out,
           float2* __restrict__ bins, double* __restrict__ zp, int2* __restrict__ support,
           float2* __restrict__ gauss, float4* __restrict__ dust_eff) {
@@ -125,7 +127,7 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
     const int L = c.n_lam;
     for (int b = 0; b < c.n_band; ++b) {
         const double p0 = band_p0[b], p1 = band_p1[b];
-        const bool top = c.band_kind[b] == 0;
+        const int kind = c.band_kind[b];
         const double sg = p1 * kFwhmToSigma;
         if (threadIdx.x == 0) {
             shmin = L;
@@ -139,13 +141,17 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
             const double lo_ = opz * l;                             // observed wavelength
             double T;
             bool in;
-            if (top) {
+            if (kind == 0) {
                 in = (lo_ >= p0) && (lo_ < p1);
                 T = in ? 1.0 : 0.0;
-            } else {
+            } else if (kind == 1) {
                 double u = (lo_ - p0) / sg;
                 in = fabs(u) < 9.0;
                 T = in ? exp(-0.5 * u * u) : 0.0;
+            } else {
+                const double u = (lo_ - p0) / p1;
+                in = u >= 0.0 && u <= (double)(c.tab_n[b] - 1);
+                T = tab_T64(tabT + c.tab_off[b], c.tab_n[b], u);
             }
             if (in) {
                 double q = (n == 0) ? 0.5 * (lam[1] - lam[0])
@@ -168,7 +174,9 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
             const double K = opz * kLsun / (4.0 * M_PI * dl_cm * dl_cm * kAbZp * sN);
             zp[gb] = -2.5 * log10(K);
             support[gb] = (shmax >= 0) ? make_int2(shmin, shmax + 1) : make_int2(0, 0);
-            gauss[gb] = make_float2((float)(p0 / opz), (float)(opz / sg));
+            // (rest centre, (1+z)/s) of a Gaussian; (rest start, -(1+z)/step) of a table
+            gauss[gb] = (kind == 2) ? make_float2((float)(p0 / opz), (float)(-opz / p1))
+                                    : make_float2((float)(p0 / opz), (float)(opz / sg));
             const double le = sQTL / sQT;                           // rest-frame lambda_eff
             const double lum = le * 1e-4;
             dust_eff[gb] = make_float4((float)calzetti_k0(lum), (float)log(le / 5500.0),
@@ -187,7 +195,7 @@ constexpr int kCsspK = 128;
 constexpr int kCsspChunk = 256;
 __global__ void __launch_bounds__(kCsspK)
 k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
-       const double* __restrict__ band_p0, float* __restrict__ out) {
+       const double* __restrict__ band_p0, const double* __restrict__ band_p1, float* __restrict__ out) {
     __shared__ float wsh[kCsspChunk];
     const int64_t g = blockIdx.x;
     const int k = blockIdx.y * kCsspK + threadIdx.x;
@@ -197,7 +205,7 @@ k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
         const int2 sup = gal.support[gb];
         const double crest = band_p0[b] / opz;
         const double inv = (double)gal.gauss[gb].y;
-        const bool top = c.band_kind[b] == 0;
+        const int kind = c.band_kind[b];
         double acc = 0.0;
         for (int n0 = sup.x; n0 < sup.y; n0 += kCsspChunk) {
             __syncthreads();
@@ -206,11 +214,14 @@ k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
                 float w = 0.0f;
                 if (n < sup.y) {
                     float4 lc = grid.lamc[n];
-                    if (top) {
+                    if (kind == 0) {
                         w = lc.x;
-                    } else {
+                    } else if (kind == 1) {
                         float u = (float)((grid.lam64[n] - crest) * inv);
                         w = lc.x * expf(-0.5f * u * u);
+                    } else {
+                        const double u = (opz * grid.lam64[n] - band_p0[b]) / band_p1[b];
+                        w = (float)((double)lc.x * tab_T64(grid.band_T64 + c.tab_off[b], c.tab_n[b], u));
                     }
                 }
                 wsh[t] = w;
@@ -245,19 +256,18 @@ cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const dou
                                     double h0, double om, float* lnT, float* lT10, float2* bins,
                                     double* zp, int2* support, float2* gauss, float4* dust_eff,
                                     cudaStream_t s) {
-    (void)grid;
     if (n_gal <= 0) return cudaSuccess;
-    k_prepare<<<(unsigned)n_gal, kPrepThreads, 0, s>>>(c, lam64, band_p0, band_p1, age_edges_yr, z,
-                                                       n_gal, h0, om, lnT, lT10, bins, zp, support,
+    k_prepare<<<(unsigned)n_gal, kPrepThreads, 0, s>>>(c, lam64, band_p0, band_p1, grid.band_T64, age_edges_yr,
+                                                       z, n_gal, h0, om, lnT, lT10, bins, zp, support,
                                                        gauss, dust_eff);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cssp(const Consts& c, const Grid& grid, const Galaxies& g,
-                        const double* band_p0, float* cssp, cudaStream_t s) {
+                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
     dim3 grd((unsigned)g.n, (c.K + kCsspK - 1) / kCsspK);
-    k_cssp<<<grd, kCsspK, 0, s>>>(c, grid, g, band_p0, cssp);
+    k_cssp<<<grd, kCsspK, 0, s>>>(c, grid, g, band_p0, band_p1, cssp);
     return cudaGetLastError();
 }
 

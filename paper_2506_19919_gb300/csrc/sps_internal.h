@@ -34,6 +34,7 @@ struct Consts {
     float sn_xi[SPS_NPARAM], sn_iom[SPS_NPARAM];   // Eq. SkewNormPrior: xi, 1 / omega,
     float sn_s[SPS_NPARAM], sn_c[SPS_NPARAM];      // s, log(2 / omega) - log(2 pi) / 2
     int band_kind[kMaxBands];
+    int tab_off[kMaxBands], tab_n[kMaxBands];      // TABLE bands: offset and count in Grid::band_T
 };
 
 // Per-galaxy tables built by sps_set_galaxies (device, structure of arrays).
@@ -60,6 +61,8 @@ struct Grid {
     const uint16_t* ssp_bf;  // [k_pad][lam_pad] SSP table, BF16 bits, row-scaled by 2^-e_i
     const uint16_t* ssp_t_bf;// [lam_pad][k_pad] transposed BF16 row-scaled
     const float* row_scale;  // [A] 2^e_i
+    const float* band_T;     // tabulated transmission samples, all TABLE bands (FP32)
+    const double* band_T64;  // the same in FP64 (per-galaxy set-up kernels)
 };
 
 // Metric-adaptation state of one HMC chain, kept in global memory (read at
@@ -105,7 +108,7 @@ cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const dou
                                     double* zp, int2* support, float2* gauss, float4* dust_eff,
                                     cudaStream_t s);
 cudaError_t launch_cssp(const Consts& c, const Grid& grid, const Galaxies& g,
-                        const double* band_p0, float* cssp, cudaStream_t s);
+                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s);
 
 // Row evaluation of the approximate path (photometry / log-likelihood + gradient).
 cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* theta,

@@ -59,6 +59,7 @@ PRIOR_HI = np.array([2.5, 12.0, 5.0, 5.0, 0.2, 8.5, 1.5, 0.2, 0.5, 3.0, 0.4, 0.5
 
 BAND_TOPHAT = 0
 BAND_GAUSS = 1
+BAND_TABLE = 2
 
 
 @dataclass
@@ -68,9 +69,11 @@ class Tables:
     lgZ: np.ndarray           # [Zn] increasing, log10(Z/Z_sun)
     lam_ang: np.ndarray       # [Lam] rest-frame wavelength, increasing
     ssp: np.ndarray           # [A, Zn, Lam] L_sun/Hz per M_sun formed
-    band_kind: np.ndarray     # [B] int32: BAND_TOPHAT or BAND_GAUSS
-    band_p0: np.ndarray       # [B] top-hat lower edge or Gaussian centre (A, observed)
-    band_p1: np.ndarray       # [B] top-hat upper edge or Gaussian FWHM (A, observed)
+    band_kind: np.ndarray     # [B] int32: BAND_TOPHAT, BAND_GAUSS or BAND_TABLE
+    band_p0: np.ndarray       # [B] top-hat lower edge, Gaussian centre or table start (A, observed)
+    band_p1: np.ndarray       # [B] top-hat upper edge, Gaussian FWHM or table step (A, observed)
+    band_tab_n: np.ndarray = None   # [B] int32 samples per tabulated band (0 otherwise)
+    band_tab_T: np.ndarray = None   # [sum n] the tabulated bands' samples, band after band
 
     @property
     def n_age(self) -> int:
@@ -105,6 +108,41 @@ class Workload:
     @property
     def n_gal(self) -> int:
         return self.z.shape[0]
+
+
+def tabulated_bands(rng: np.random.Generator, edges_nm, step_ang: float = 10.0):
+    """Synthetic broad-band throughput curves sampled every step_ang (A) on
+    the observed frame, one band per [lo, hi) pair of edges_nm: a smooth
+    flat-topped profile (product of two logistic edges of width ~2% of the
+    band centre) with a seeded ripple of a few per cent and a peak between
+    0.5 and 0.9.  Returns (kind, start, step, n, T) in the Tables layout.
+    (Input synthesis only.)"""
+    kind, p0, p1, ns, Ts = [], [], [], [], []
+    for lo_nm, hi_nm in zip(edges_nm[:-1], edges_nm[1:]):
+        lo, hi = 10.0 * lo_nm, 10.0 * hi_nm
+        w = 0.02 * 0.5 * (lo + hi)
+        start = step_ang * np.floor((lo - 8 * w) / step_ang)
+        n = int(np.ceil((hi + 8 * w - start) / step_ang)) + 1
+        lam = start + step_ang * np.arange(n)
+        prof = 1.0 / (1.0 + np.exp(-(lam - lo) / w)) / (1.0 + np.exp((lam - hi) / w))
+        ph, amp, per = rng.uniform(0, 2 * np.pi), rng.uniform(0.01, 0.04), rng.uniform(200.0, 600.0)
+        T = rng.uniform(0.5, 0.9) * prof * (1.0 + amp * np.sin(2 * np.pi * lam / per + ph))
+        T[0] = T[-1] = 0.0
+        kind.append(BAND_TABLE)
+        p0.append(start)
+        p1.append(step_ang)
+        ns.append(n)
+        Ts.append(T)
+    return (np.array(kind, np.int32), np.array(p0), np.array(p1), np.array(ns, np.int32),
+            np.concatenate(Ts))
+
+
+def with_bands(tables: Tables, kind, p0, p1, tab_n=None, tab_T=None) -> Tables:
+    """The same SSP grid with another filter set."""
+    return Tables(tables.age_yr, tables.lgZ, tables.lam_ang, tables.ssp, np.asarray(kind, np.int32),
+                  np.asarray(p0, np.float64), np.asarray(p1, np.float64),
+                  None if tab_n is None else np.asarray(tab_n, np.int32),
+                  None if tab_T is None else np.asarray(tab_T, np.float64))
 
 
 def _f32(x):
@@ -241,6 +279,6 @@ def tiny_tables(rng=None, n_age=5, n_met=3, n_lam=400, lam_lo=1000.0, lam_hi=120
 
 __all__ = [
     "SEED_BASE", "PARAM_NAMES", "N_PARAM", "PRIOR_LO", "PRIOR_HI", "BAND_TOPHAT",
-    "BAND_GAUSS", "Tables", "Workload", "config", "prior_draw", "unbounded_of",
+    "BAND_GAUSS", "BAND_TABLE", "tabulated_bands", "with_bands", "Tables", "Workload", "config", "prior_draw", "unbounded_of",
     "tiny_tables", "make_tables", "ssp_table", "CONFIG_NAMES",
 ]

@@ -94,6 +94,27 @@ def test_bad_tables_rejected_on_host(lib):
     assert lib.sps_create(C.byref(h), C.byref(tab2), None) == 1
 
 
+def test_bad_tabulated_bands_rejected_on_host(lib):
+    """sps_create checks tabulated filter curves before any device work: too
+    few samples, a negative throughput."""
+    from paper_2506_19919_gb300 import _lib
+    import sps_workloads as W
+    t = W.tiny_tables()
+    kind = np.array([2, 0, 0, 0], np.int32)
+    p0 = np.array([4000.0, 4500, 6000, 8000])
+    p1 = np.array([10.0, 6000, 8000, 9000])
+
+    def create(tab_n, tab_T):
+        keep = [np.ascontiguousarray(x) for x in (t.age_yr, t.lgZ, t.lam_ang, t.ssp, kind, p0, p1,
+                                                  np.asarray(tab_n, np.int32), np.asarray(tab_T, np.float64))]
+        tab = _lib.sps_tables(len(t.age_yr), len(t.lgZ), len(t.lam_ang), 4, *[k.ctypes.data for k in keep])
+        h = C.c_void_p()
+        return lib.sps_create(C.byref(h), C.byref(tab), None)
+
+    assert create([1, 0, 0, 0], [0.5]) == 1
+    assert create([2, 0, 0, 0], [-0.1, 0.2]) == 1
+
+
 def test_host_diagnostics_match_oracle(lib):
     from oracle import diagnostics as D
     import paper_2506_19919_gb300 as pkg
