@@ -216,28 +216,39 @@ def burst_weights(theta, age_yr, t_obs):
     return raw / norm[:, None]
 
 
-def met_weights(theta, lgZ):
+def met_weights(theta, lgZ, age_offset=None):
     """Lognormal metallicity distribution (App. A.2): weight of grid value j
     is the Gaussian (in log10 Z; mean lgZ, sd sigma_lgZ) mass between the
     midpoints to its neighbours, the outer edges open.  Reading: 'lognormal
-    MDF' with free mean and width."""
+    MDF' with free mean and width.  Returns [N, Zn].
+
+    age_offset [A] (optional): the non-separable variant Sec. 2 mentions,
+    where the MDF follows the time evolution of the mass-metallicity
+    relation.  Reading: the mean of the MDF of stars in age bin i is
+    lgZ + age_offset[i] (the offsets supplied with the age grid), the width
+    shared.  Returns [N, A, Zn]."""
     mu, sd = theta[:, 7], theta[:, 8]
+    if age_offset is not None:
+        mu = mu[:, None] + torch.as_tensor(np.asarray(age_offset, dtype=np.float64))[None, :]   # [N, A]
+        sd = sd[:, None]
     g = np.asarray(lgZ, dtype=np.float64)
     e = torch.as_tensor(0.5 * (g[1:] + g[:-1]), dtype=DT)                    # interior edges
-    y = (e[None, :] - mu[:, None]) / sd[:, None]
+    y = (e - mu[..., None]) / sd[..., None]
     lower = torch.special.ndtr(y)                                             # P(X < e)
     upper = torch.special.ndtr(-y)                                            # P(X > e)
-    first = lower[:, :1]
-    last = upper[:, -1:]
-    mid = lower[:, 1:] - lower[:, :-1]
-    return torch.cat([first, mid, last], dim=1)
+    first = lower[..., :1]
+    last = upper[..., -1:]
+    mid = lower[..., 1:] - lower[..., :-1]
+    return torch.cat([first, mid, last], dim=-1)
 
 
 def ssp_weights(theta, tables, t_obs):
     """W_ij = M_star * P_SFH(tau_i) * P_met(Z_j) (Eq. galSED_decomposed with
     Eq. composite_age_weights), with M_star the total mass formed by t_obs
     (Eq. totalMstarFormed) and P_smooth = bin mass / M_star (Eq. smoothPsfh).
-    Returns (W [N, A, Zn], M_star [N], P_SFH [N, A], P_met [N, Zn])."""
+    With tables.mdf_offset set, P_met depends on the age bin (met_weights)
+    and W_ij = M_star P_SFH(tau_i) P_met(Z_j | tau_i).
+    Returns (W [N, A, Zn], M_star [N], P_SFH [N, A], P_met [N, Zn] or [N, A, Zn])."""
     t_lo, t_hi = cosmic_time_bins(tables.age_yr, t_obs)
     m = smooth_bin_masses(theta, t_lo, t_hi)
     mstar = m.sum(1)
@@ -245,8 +256,10 @@ def ssp_weights(theta, tables, t_obs):
     fb = theta[:, 4]
     p_burst = burst_weights(theta, tables.age_yr, t_obs)
     p_sfh = (1.0 - fb)[:, None] * p_smooth + fb[:, None] * p_burst
-    p_met = met_weights(theta, tables.lgZ)
-    W = mstar[:, None, None] * p_sfh[:, :, None] * p_met[:, None, :]
+    off = getattr(tables, "mdf_offset", None)
+    p_met = met_weights(theta, tables.lgZ, off)
+    pm = p_met if off is not None else p_met[:, None, :]
+    W = mstar[:, None, None] * p_sfh[:, :, None] * pm
     return W, mstar, p_sfh, p_met
 
 

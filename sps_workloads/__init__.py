@@ -74,6 +74,7 @@ class Tables:
     band_p1: np.ndarray       # [B] top-hat upper edge, Gaussian FWHM or table step (A, observed)
     band_tab_n: np.ndarray = None   # [B] int32 samples per tabulated band (0 otherwise)
     band_tab_T: np.ndarray = None   # [sum n] the tabulated bands' samples, band after band
+    mdf_offset: np.ndarray = None   # [A] age-dependent shift of the MDF mean (None: separable)
 
     @property
     def n_age(self) -> int:
@@ -142,7 +143,22 @@ def with_bands(tables: Tables, kind, p0, p1, tab_n=None, tab_T=None) -> Tables:
     return Tables(tables.age_yr, tables.lgZ, tables.lam_ang, tables.ssp, np.asarray(kind, np.int32),
                   np.asarray(p0, np.float64), np.asarray(p1, np.float64),
                   None if tab_n is None else np.asarray(tab_n, np.int32),
-                  None if tab_T is None else np.asarray(tab_T, np.float64))
+                  None if tab_T is None else np.asarray(tab_T, np.float64), tables.mdf_offset)
+
+
+def mzr_offsets(age_yr, slope: float = 0.25, t_ref_gyr: float = 1.0) -> np.ndarray:
+    """An age-dependent shift of the MDF mean of the kind an evolving
+    mass-metallicity relation produces: older stars formed earlier from less
+    enriched gas, dlgZ_i = -slope * log10(1 + age_i / t_ref) (input synthesis
+    only; any [A] vector may be supplied)."""
+    return -slope * np.log10(1.0 + np.asarray(age_yr, dtype=np.float64) / (t_ref_gyr * 1e9))
+
+
+def with_mdf_offset(tables: Tables, offset) -> Tables:
+    """The same tables with an age-dependent MDF mean (non-separable W)."""
+    return Tables(tables.age_yr, tables.lgZ, tables.lam_ang, tables.ssp, tables.band_kind, tables.band_p0,
+                  tables.band_p1, tables.band_tab_n, tables.band_tab_T,
+                  None if offset is None else np.asarray(offset, np.float64))
 
 
 def _f32(x):
@@ -279,6 +295,6 @@ def tiny_tables(rng=None, n_age=5, n_met=3, n_lam=400, lam_lo=1000.0, lam_hi=120
 
 __all__ = [
     "SEED_BASE", "PARAM_NAMES", "N_PARAM", "PRIOR_LO", "PRIOR_HI", "BAND_TOPHAT",
-    "BAND_GAUSS", "BAND_TABLE", "tabulated_bands", "with_bands", "Tables", "Workload", "config", "prior_draw", "unbounded_of",
+    "BAND_GAUSS", "BAND_TABLE", "tabulated_bands", "with_bands", "mzr_offsets", "with_mdf_offset", "Tables", "Workload", "config", "prior_draw", "unbounded_of",
     "tiny_tables", "make_tables", "ssp_table", "CONFIG_NAMES",
 ]
