@@ -93,7 +93,13 @@ typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1, SPS_BAND_TABLE = 2 } sps
  *  band_tab_n[n_band]: samples per TABLE band (ignored for the others; the
  *    pointer may be NULL when no band is tabulated); band_tab_T: the TABLE
  *    bands' samples, concatenated in band order.  Resample curves with uneven
- *    steps onto a uniform grid first (paper_2506_19919_gb300.loaders does). */
+ *    steps onto a uniform grid first (paper_2506_19919_gb300.loaders does).
+ *  mdf_offset[n_age] or NULL: a non-separable SSP weighting (Sec. 2: the MDF
+ *    following the time evolution of the mass-metallicity relation): the
+ *    metallicity distribution of stars in age bin i has mean lgZ +
+ *    mdf_offset[i] (width sigma_lgZ shared), so W_ij = M_star P_SFH,i
+ *    P_met,ij is a general [n_age x n_met] matrix.  NULL: the separable model.
+ *    The forward-mode comparison baselines support only the separable model. */
 typedef struct {
     int32_t n_age, n_met, n_lam, n_band;
     const double* age_yr;
@@ -105,6 +111,7 @@ typedef struct {
     const double* band_p1;
     const int32_t* band_tab_n;
     const double* band_tab_T;
+    const double* mdf_offset;
 } sps_tables;
 
 /* Prior on the unbounded parameters x (App. C).  SPS_PRIOR_UNIFORM: uniform in

@@ -87,10 +87,13 @@ class Context:
         if tab_n is not None:
             self._keep += [np.ascontiguousarray(tab_n, dtype=np.int32),
                            np.ascontiguousarray(tab_T, dtype=np.float64)]
+        off = getattr(tables, "mdf_offset", None)
+        self._mdf = None if off is None else np.ascontiguousarray(off, dtype=np.float64)
         t = sps_tables(len(a), len(z), len(l), len(k), a.ctypes.data, z.ctypes.data,
                        l.ctypes.data, s.ctypes.data, k.ctypes.data, p0.ctypes.data,
                        p1.ctypes.data, self._keep[7].ctypes.data if tab_n is not None else None,
-                       self._keep[8].ctypes.data if tab_n is not None else None)
+                       self._keep[8].ctypes.data if tab_n is not None else None,
+                       self._mdf.ctypes.data if self._mdf is not None else None)
         h = C.c_void_p()
         check(lib.sps_create(C.byref(h), C.byref(t), C.byref(cfg)), "sps_create")
         self.h = h

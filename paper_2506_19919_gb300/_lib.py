@@ -27,7 +27,7 @@ class sps_tables(C.Structure):
                 ("n_band", C.c_int32), ("age_yr", C.c_void_p), ("lgZ", C.c_void_p),
                 ("lam_ang", C.c_void_p), ("ssp", C.c_void_p), ("band_kind", C.c_void_p),
                 ("band_p0", C.c_void_p), ("band_p1", C.c_void_p), ("band_tab_n", C.c_void_p),
-                ("band_tab_T", C.c_void_p)]
+                ("band_tab_T", C.c_void_p), ("mdf_offset", C.c_void_p)]
 
 
 class sps_config(C.Structure):

@@ -83,9 +83,11 @@ k_weights_rows(const __grid_constant__ Consts c, const Galaxies g, const float* 
         const double scale = 1e9 * exp10((double)p.th[0]);
         if (mstar_out && lane == 0) mstar_out[row] = scale * M;
         if (W_out) {
+            if (c.mdf_age) mdf_rows_fill(c, c.lgz_edge, p.th[7], p.th[8], s.u.kbuf);
             for (int k = lane; k < c.K; k += 32) {
                 int i = k / c.n_met, j = k % c.n_met;
-                W_out[row * c.K + k] = (float)(scale * (double)s.w[i] * (double)s.q[j]);
+                const float q = c.mdf_age ? s.u.kbuf[k] : s.q[j];
+                W_out[row * c.K + k] = (float)(scale * (double)s.w[i] * (double)q);
             }
         }
         __syncwarp();

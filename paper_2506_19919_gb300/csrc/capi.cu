@@ -291,6 +291,10 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
     for (int n = 0; n < L; ++n)
         if (!(t->lam_ang[n] > 0) || (n && !(t->lam_ang[n] > t->lam_ang[n - 1])))
             return fail(SPS_E_INVALID_ARG, "wavelength grid must be positive and increasing");
+    if (t->mdf_offset)
+        for (int i = 0; i < A; ++i)
+            if (!std::isfinite(t->mdf_offset[i]) || std::fabs(t->mdf_offset[i]) > 10.0)
+                return fail(SPS_E_INVALID_ARG, "mdf_offset must be finite, |offset| <= 10 dex");
     int64_t n_tab = 0;                        // tabulated samples in all
     for (int b = 0; b < B; ++b) {
         int k = t->band_kind[b];
@@ -398,6 +402,8 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         c.sn_c[k] = (float)(std::log(2.0 / cfg.skew_omega[k]) - 0.5 * std::log(2.0 * M_PI));
     }
     c.prior_kind = cfg.prior;
+    c.mdf_age = t->mdf_offset ? 1 : 0;
+    for (int i = 0; i < kMaxAges; ++i) c.mdf_off[i] = (t->mdf_offset && i < A) ? (float)t->mdf_offset[i] : 0.0f;
     std::vector<double> tab64;
     for (int b = 0; b < B; ++b) {
         c.band_kind[b] = t->band_kind[b];
@@ -711,6 +717,7 @@ sps_status sps_loglike_grad_forward_mode(sps_ctx* ctx, const float* theta, const
     sps_status st0 = check_rows(ctx, theta, gal_idx, n);
     if (st0 != SPS_OK) return st0;
     if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (ctx->c.mdf_age) return fail(SPS_E_UNSUPPORTED, "the forward-mode baseline supports the separable model only");
     if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
         return fail(SPS_E_INVALID_ARG, "null data or output pointer");
     if (n == 0) return SPS_OK;
@@ -930,24 +937,30 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     // grid is persistent (occupancy x SMs) and pulls (galaxy, chain group)
     // items from the queue
     // first candidate = default; another replaces it only if >3% faster in the probe
+    // an age-dependent MDF (general W) runs the row-evaluation variant, one chain per warp
+    const bool rows = ctx->c.mdf_age != 0;
     std::vector<std::pair<int, int>> cands = {{1, 8}, {1, 16}};
-    if (C >= 2) cands.insert(cands.begin(), {{2, 4}, {2, 8}, {2, 16}});
-    if (C >= 4) cands.push_back({4, 8});
+    if (rows) {
+        cands = {{1, 4}, {1, 2}, {1, 8}};
+    } else {
+        if (C >= 2) cands.insert(cands.begin(), {{2, 4}, {2, 8}, {2, 16}});
+        if (C >= 4) cands.push_back({4, 8});
+    }
     const int cpw0 = cands[0].first;
     auto blocks_for = [&](int cpw, int warps, int& blocks) -> cudaError_t {
         int per_sm = 0;
-        cudaError_t e = hmc_team_occupancy(cpw, warps, &per_sm);
+        cudaError_t e = hmc_team_occupancy(cpw, rows, warps, &per_sm);
         if (e != cudaSuccess) return e;
         blocks = std::max(1, per_sm) * sms;
         return cudaSuccess;
     };
     const std::string key = std::to_string(G) + ":" + std::to_string(C) + ":" + std::to_string(nb_max) +
-                            (nuts ? ":nuts" : "");
+                            (nuts ? ":nuts" : "") + (rows ? ":rows" : "");
     int cpw = cpw0, warps = cands[0].second, blocks = sms;
     auto it = ctx->tuned.find(key);
     const char* force = std::getenv("SPS_HMC_SHAPE");   // "cpw,warps": fixed launch shape
     int fc = 0, fw = 0;
-    if (force && std::sscanf(force, "%d,%d", &fc, &fw) == 2 && (fc == 1 || fc == 2 || fc == 4) &&
+    if (force && std::sscanf(force, "%d,%d", &fc, &fw) == 2 && (fc == 1 || (!rows && (fc == 2 || fc == 4))) &&
         fc <= std::max(C, 1) && fw >= 1 && fw <= 16) {
         cpw = fc;
         warps = fw;
@@ -973,7 +986,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
             gsub.n = std::min<int64_t>(G, ((int64_t)b * cw.second * 2 + groups - 1) / groups);
             CK(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s));
             CK(cudaEventRecord(e0, s));
-            CK(launch_hmc_team(cw.first, c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr,
+            CK(launch_hmc_team(cw.first, rows, c, gsub, tp, x0, mo, sg, mk, ord, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr, ctx->queue.as<int>(), cmet, b, cw.second, s));
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
@@ -997,7 +1010,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        return launch_hmc_team(cpw, c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+        return launch_hmc_team(cpw, rows, c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
                                ctx->queue.as<int>(), cmet, blocks, warps, s);
     };
     if (cfg->use_graph) {
@@ -1050,6 +1063,7 @@ extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_confi
     if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (cfg->adapt_mass != 0) return fail(SPS_E_UNSUPPORTED, "the plain sampler uses the identity metric");
     if (cfg->sampler != SPS_HMC) return fail(SPS_E_UNSUPPORTED, "the plain sampler runs HMC");
+    if (ctx->c.mdf_age) return fail(SPS_E_UNSUPPORTED, "the plain sampler supports the separable model only");
     if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
     if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
         return fail(SPS_E_SHAPE, "iteration counts");

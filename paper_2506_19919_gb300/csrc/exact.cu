@@ -55,12 +55,14 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
             __syncwarp();
         }
         const int64_t wr = pos_of ? (int64_t)pos_of[row] : row;
+        const bool nonsep = c.mdf_age != 0 && p.finite;
+        if (nonsep) mdf_rows_fill(c, c.lgz_edge, p.th[7], p.th[8], s.u.kbuf);
         for (int k = lane; k < c.k_pad; k += 32) {
             float v = 0.0f;
             int i = 0;
             if (k < c.K) {
                 i = k / c.n_met;
-                v = s.w[i] * s.q[k % c.n_met];
+                v = s.w[i] * (nonsep ? s.u.kbuf[k] : s.q[k % c.n_met]);
             }
             if (bf16) {
                 Wbf[wr * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
@@ -404,20 +406,24 @@ k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __
         const double M = age_met_weights(c, s, g.bins + (size_t)gi * A, g.lnT[gi], g.lT10[gi], p, true);
         for (int k = lane; k < K; k += 32) s.u.kbuf[k] = Wbar[row * c.k_pad + k];
         __syncwarp();
-        for (int i = lane; i < A; i += 32) {
-            float a = 0.0f;
-            for (int j = 0; j < Zn; ++j) a = fmaf(s.u.kbuf[i * Zn + j], s.q[j], a);
-            s.wb[i] = a;
-        }
-        if (lane < Zn) {
-            float a = 0.0f;
-            for (int i = 0; i < A; ++i) a = fmaf(s.u.kbuf[i * Zn + lane], s.w[i], a);
-            s.qb[lane] = a;
-        }
-        __syncwarp();
         float gr[SPS_NPARAM];
 #pragma unroll
         for (int k = 0; k < SPS_NPARAM; ++k) gr[k] = 0.0f;
+        if (c.mdf_age) {
+            mdf_rows_adjoint(c, s.view(c), s.u.kbuf, p.th[7], p.th[8], gr);
+        } else {
+            for (int i = lane; i < A; i += 32) {
+                float a = 0.0f;
+                for (int j = 0; j < Zn; ++j) a = fmaf(s.u.kbuf[i * Zn + j], s.q[j], a);
+                s.wb[i] = a;
+            }
+            if (lane < Zn) {
+                float a = 0.0f;
+                for (int i = 0; i < A; ++i) a = fmaf(s.u.kbuf[i * Zn + lane], s.w[i], a);
+                s.qb[lane] = a;
+            }
+            __syncwarp();
+        }
         gr[0] = rowinfo[row * 4 + 0];
         gr[9] = rowinfo[row * 4 + 1];
         gr[10] = rowinfo[row * 4 + 2];

@@ -17,7 +17,7 @@
 // energy accept, dual-averaged step size and windowed diagonal metric in the
 // warm-up, Philox-4x32-10 draws with counter (iteration, block, chain, 0).
 #include "philox.cuh"
-#include "sps_device.cuh"
+#include "sps_eval.cuh"
 
 namespace sps {
 
@@ -882,7 +882,8 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
                                           TeamWork<CPW>& t, int q, const float* __restrict__ theta0,
                                           const float* __restrict__ mag_obs, const float* __restrict__ sigma,
                                           const uint32_t* __restrict__ mask, const int32_t* __restrict__ gal_order,
-                                          ChainMetric* __restrict__ metric, int* nch_out, int* nb_out) {
+                                          ChainMetric* __restrict__ metric, int* nch_out, int* nb_out,
+                                          WarpWork* ww) {
     const int lane = lane_id();
     const int B = c.n_band, K = c.K;
     const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
@@ -960,6 +961,7 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
         t.wstop[ch] = nw - term_b;
     }
     __syncwarp();
+    if (ww) fill_slots(c, g, ww->d, gi, bits, mag_obs, sigma, g.cssp + (size_t)gi * B * K, false);
     *nch_out = nch;
     *nb_out = __popc(bits);
     return gi;
@@ -1003,11 +1005,44 @@ __device__ __forceinline__ void team_step(const Consts& c, TeamWork<CPW>& t, con
     }
 }
 
+// log posterior and gradient of the team's single chain through the general
+// row evaluation (eval_row: W = w_i q_ij held whole, c_SSP contracted per
+// band), for models whose weights do not factor into age x metallicity (an
+// age-dependent MDF); the sampler around it is the same.
+template <int CPW>
+__device__ __forceinline__ void rows_eval(const Consts& c, TeamWork<CPW>& t, WarpWork& ww, int nb) {
+    static_assert(CPW == 1, "the row evaluation takes one chain per warp");
+    const int lane = lane_id();
+    RowParams p;
+    load_params(c, t.x[0], true, p);
+    float gr[SPS_NPARAM];
+    const double ll = eval_row(c, ww, t.bins, t.lnT, t.lT10, p, nb, true, true, gr);
+    if (lane < SPS_NPARAM) {
+        float v = gr[0], d = p.dth[0], q = p.dlp[0];
+#pragma unroll
+        for (int k = 1; k < SPS_NPARAM; ++k)
+            if (lane == k) {
+                v = gr[k];
+                d = p.dth[k];
+                q = p.dlp[k];
+            }
+        t.g[0][lane] = v * d + q;
+    }
+    if (lane == 0) t.lp[0] = ll + p.logprior;
+    __syncwarp();
+}
+
+// Shared memory of one warp: the team state, and with kRows the row scratch.
+template <int CPW, bool kRows>
+__host__ __device__ constexpr size_t team_stride() {
+    return kRows ? sizeof(TeamWork<CPW>) + sizeof(WarpWork) : sizeof(TeamWork<CPW>);
+}
+
 // Persistent kernel: each warp is a team working through the queue of
 // (galaxy, chain group) items; the warps of a block advance one evaluation per
 // pass together (one block barrier per pass), so that they run the same code
 // at the same time and share the instruction cache.
-template <int CPW>
+template <int CPW, bool kRows>
 __global__ void __launch_bounds__(512, 1)
 k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
            const float* __restrict__ theta0, const float* __restrict__ mag_obs,
@@ -1017,7 +1052,9 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
            ChainMetric* __restrict__ metric) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ EdgeTables et;
-    TeamWork<CPW>& t = reinterpret_cast<TeamWork<CPW>*>(smem)[threadIdx.x >> 5];
+    unsigned char* mine = smem + (size_t)(threadIdx.x >> 5) * team_stride<CPW, kRows>();
+    TeamWork<CPW>& t = *reinterpret_cast<TeamWork<CPW>*>(mine);
+    WarpWork* ww = kRows ? reinterpret_cast<WarpWork*>(mine + sizeof(TeamWork<CPW>)) : nullptr;
     const int lane = lane_id();
     const int C = hp.chains_per_gal;
     for (int i = threadIdx.x; i <= c.n_age; i += blockDim.x) et.age[i] = c.log_age_edge[i];
@@ -1038,14 +1075,18 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
             if ((int64_t)q >= g.n * groups) {
                 drained = true;
             } else {
-                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb);
+                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb,
+                                    ww);
                 have = true;
                 pass = 0;
             }
         }
         if (iter % sync_every == 0 && !__syncthreads_or(have ? 1 : 0)) break;
         if (!have) continue;
-        team_eval<CPW>(c, t, et, t.lnT, t.lT10, nb);
+        if constexpr (kRows)
+            rows_eval<CPW>(c, t, *ww, nb);
+        else
+            team_eval<CPW>(c, t, et, t.lnT, t.lT10, nb);
         if (pass == 0) {
 #pragma unroll 1
             for (int ch = 0; ch < CPW; ++ch)
@@ -1078,60 +1119,61 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
 
 }  // namespace
 
-size_t hmc_team_smem_per_warp(int cpw) {
+size_t hmc_team_smem_per_warp(int cpw, bool rows) {
+    if (rows) return team_stride<1, true>();
     return cpw >= 4 ? sizeof(TeamWork<4>) : cpw == 2 ? sizeof(TeamWork<2>) : sizeof(TeamWork<1>);
 }
 
-template <int CPW>
+template <int CPW, bool kRows>
 static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcParams& hp,
                                const float* theta0, const float* mag_obs, const float* sigma,
                                const uint32_t* mask, const int32_t* gal_order, float* samples,
                                float* acc, float* eps_out, int32_t* div, int64_t* nevals,
                                int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                                cudaStream_t s) {
-    const size_t smem = sizeof(TeamWork<CPW>) * warps;
-    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = team_stride<CPW, kRows>() * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_hmc_team<CPW><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask,
-                                                     gal_order, samples, acc, eps_out, div,
-                                                     nevals, status, queue, metric);
+    k_hmc_team<CPW, kRows><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order,
+                                                            samples, acc, eps_out, div, nevals, status, queue,
+                                                            metric);
     return cudaGetLastError();
 }
 
-cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm) {
-    const size_t smem = hmc_team_smem_per_warp(cpw) * warps;
-    cudaError_t e;
-    if (cpw >= 4) {
-        e = cudaFuncSetAttribute(k_hmc_team<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<4>, warps * 32, smem);
-    } else if (cpw == 2) {
-        e = cudaFuncSetAttribute(k_hmc_team<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<2>, warps * 32, smem);
-    } else {
-        e = cudaFuncSetAttribute(k_hmc_team<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<1>, warps * 32, smem);
-    }
-    return e;
+template <int CPW, bool kRows>
+static cudaError_t team_occupancy(int warps, int* blocks_per_sm) {
+    const size_t smem = team_stride<CPW, kRows>() * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<CPW, kRows>, warps * 32, smem);
 }
 
-cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const HmcParams& hp,
+cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm) {
+    if (rows) return team_occupancy<1, true>(warps, blocks_per_sm);
+    if (cpw >= 4) return team_occupancy<4, false>(warps, blocks_per_sm);
+    if (cpw == 2) return team_occupancy<2, false>(warps, blocks_per_sm);
+    return team_occupancy<1, false>(warps, blocks_per_sm);
+}
+
+cudaError_t launch_hmc_team(int cpw, bool rows, const Consts& c, const Galaxies& g, const HmcParams& hp,
                             const float* theta0, const float* mag_obs, const float* sigma,
                             const uint32_t* mask, const int32_t* gal_order, float* samples,
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
                             int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                             cudaStream_t s) {
+    if (rows)
+        return team_launch<1, true>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                                    div, nevals, status, queue, metric, blocks, warps, s);
     if (cpw >= 4)
-        return team_launch<4>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                              eps_out, div, nevals, status, queue, metric, blocks, warps, s);
+        return team_launch<4, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                                     eps_out, div, nevals, status, queue, metric, blocks, warps, s);
     if (cpw == 2)
-        return team_launch<2>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                              eps_out, div, nevals, status, queue, metric, blocks, warps, s);
-    return team_launch<1>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
-                          div, nevals, status, queue, metric, blocks, warps, s);
+        return team_launch<2, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                                     eps_out, div, nevals, status, queue, metric, blocks, warps, s);
+    return team_launch<1, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                                 div, nevals, status, queue, metric, blocks, warps, s);
 }
 
 }  // namespace sps

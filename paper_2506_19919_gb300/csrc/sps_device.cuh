@@ -486,6 +486,88 @@ __device__ __forceinline__ void met_weights(const Consts& c, const AgeView& v, f
     if (e < Zn) v.q[e] = pos ? (T - Th) : (ph ? (1.0f - Th) - T : Th - T);
 }
 
+// ---------------------------------------------------------------- non-separable MDF
+// With c.mdf_age the MDF of age bin i has mean mu_i = lgZ + c.mdf_off[i] and
+// the common width sigma: q_ij = Phi(y_{i,j+1}) - Phi(y_ij), y = (edge - mu_i)
+// / sigma, so W_ij = w_i q_ij is a general [A x Zn] matrix.  One lane takes
+// one age row and walks its edges, each cell from the smaller tails at its two
+// edges (as met_weights).
+__device__ __forceinline__ void mdf_edge(const float* __restrict__ lgz_edge, int e, float mu, float isd,
+                                         float& y, float& T, bool& pos) {
+    y = (lgz_edge[e] - mu) * isd;
+    T = 0.5f * erfcf(fabsf(y) * 0.70710678118654752f);
+    pos = y >= 0.0f;
+}
+__device__ __forceinline__ float mdf_cell(float Tl, bool pl, float Th, bool ph) {
+    return pl ? (Tl - Th) : (ph ? (1.0f - Th) - Tl : Th - Tl);
+}
+
+// qm[i * Zn + j] = q_ij for every age row (lanes over rows).
+__device__ __forceinline__ void mdf_rows_fill(const Consts& c, const float* __restrict__ lgz_edge, float mz,
+                                              float sz, float* __restrict__ qm) {
+    const int Zn = c.n_met;
+    const float isd = 1.0f / sz;
+    for (int i = lane_id(); i < c.n_age; i += 32) {
+        const float mu = mz + c.mdf_off[i];
+        float y, Tl, Th;
+        bool pl, ph;
+        mdf_edge(lgz_edge, 0, mu, isd, y, Tl, pl);
+#pragma unroll 1
+        for (int j = 0; j < Zn; ++j) {
+            mdf_edge(lgz_edge, j + 1, mu, isd, y, Th, ph);
+            qm[i * Zn + j] = mdf_cell(Tl, pl, Th, ph);
+            Tl = Th;
+            pl = ph;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ float phi_(float y);
+__device__ __forceinline__ float phi_y(float y);
+
+// Adjoint through the non-separable MDF.  vbuf[i * Zn + j] holds dlogL/dW'_ij
+// for W'_ij = w_i q_ij: writes wb_i = sum_j v_ij q_ij and adds
+// dlogL/d(lgZ, sigma) = sum_i (1/sigma) sum_e (phi_e, y_e phi_e)(qb_ie - qb_i,e-1),
+// qb_ij = w_i v_ij, into g[7], g[8] (warp-uniform).  The MDF part of
+// age_met_adjoint must then see qb = 0.
+__device__ __forceinline__ void mdf_rows_adjoint(const Consts& c, const AgeView& v, const float* __restrict__ vbuf,
+                                                 float mz, float sz, float* g) {
+    const int Zn = c.n_met;
+    const float isd = 1.0f / sz;
+    float gz = 0.0f, gs = 0.0f;
+    for (int i = lane_id(); i < c.n_age; i += 32) {
+        const float mu = mz + c.mdf_off[i];
+        const float wi = v.w[i];
+        const float* vr = vbuf + i * Zn;
+        float y, Tl, Th;
+        bool pl, ph;
+        mdf_edge(v.lgz_edge, 0, mu, isd, y, Tl, pl);
+        float a = 0.0f, vprev = 0.0f;
+#pragma unroll 1
+        for (int e = 0; e <= Zn; ++e) {
+            if (e > 0) mdf_edge(v.lgz_edge, e, mu, isd, y, Th, ph);
+            const float ve = (e < Zn) ? vr[e] : 0.0f;
+            if (e > 0) {
+                a = fmaf(vprev, mdf_cell(Tl, pl, Th, ph), a);
+                Tl = Th;
+                pl = ph;
+            }
+            const float d = wi * (ve - vprev);
+            gz = fmaf(phi_(y), d, gz);
+            gs = fmaf(phi_y(y), d, gs);
+            vprev = ve;
+        }
+        v.wb[i] = a;
+    }
+    gz = warp_sum(gz);
+    gs = warp_sum(gs);
+    if (lane_id() < Zn) v.qb[lane_id()] = 0.0f;
+    __syncwarp();
+    g[7] += gz * isd;
+    g[8] += gs * isd;
+}
+
 __device__ __forceinline__ float phi_y(float y) {  // y phi(y), 0 at +-inf
     return isinf(y) ? 0.0f : y * kInvSqrt2Pi * __expf(-0.5f * y * y);
 }

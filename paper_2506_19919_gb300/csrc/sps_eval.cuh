@@ -61,13 +61,17 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
     const int K = c.K, Zn = c.n_met, A = c.n_age;
     const double M = age_met_weights(c, s, bins, lnT, lT10, p, grad);
 
-    // W_ij / (1e9 10^lgM) = w_i q_j, one register tile per lane (k = lane + 32 t)
+    // W_ij / (1e9 10^lgM) = w_i q_j, one register tile per lane (k = lane + 32 t);
+    // with an age-dependent MDF, w_i q_ij with q_ij staged in kbuf
+    const bool nonsep = c.mdf_age != 0;
+    if (nonsep) mdf_rows_fill(c, c.lgz_edge, p.th[7], p.th[8], s.u.kbuf);
     float wreg[kKTileMax];
 #pragma unroll
     for (int t = 0; t < kKTileMax; ++t) {
         int k = lane + 32 * t;
-        wreg[t] = (k < K) ? s.w[k / Zn] * s.q[k % Zn] : 0.0f;
+        wreg[t] = (k < K) ? s.w[k / Zn] * (nonsep ? s.u.kbuf[k] : s.q[k % Zn]) : 0.0f;
     }
+    __syncwarp();
     for (int sl = 0; sl < nb; ++sl) {
         const float* C = d.ptr[sl];
         float a = 0.0f;
@@ -125,18 +129,6 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
         }
     }
     __syncwarp();
-    for (int i = lane; i < A; i += 32) {
-        float a = 0.0f;
-        const float* vr = s.u.kbuf + i * Zn;
-        for (int j = 0; j < Zn; ++j) a = fmaf(vr[j], s.q[j], a);
-        s.wb[i] = a;
-    }
-    if (lane < Zn) {
-        float a = 0.0f;
-        for (int i = 0; i < A; ++i) a = fmaf(s.u.kbuf[i * Zn + lane], s.w[i], a);
-        s.qb[lane] = a;
-    }
-    __syncwarp();
     float g[SPS_NPARAM];
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) g[k] = 0.0f;
@@ -144,6 +136,22 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
     g[9] = gAV;
     g[10] = gdl;
     g[11] = gff;
+    if (nonsep) {
+        mdf_rows_adjoint(c, s.view(c), s.u.kbuf, p.th[7], p.th[8], g);
+    } else {
+        for (int i = lane; i < A; i += 32) {
+            float a = 0.0f;
+            const float* vr = s.u.kbuf + i * Zn;
+            for (int j = 0; j < Zn; ++j) a = fmaf(vr[j], s.q[j], a);
+            s.wb[i] = a;
+        }
+        if (lane < Zn) {
+            float a = 0.0f;
+            for (int i = 0; i < A; ++i) a = fmaf(s.u.kbuf[i * Zn + lane], s.w[i], a);
+            s.qb[lane] = a;
+        }
+        __syncwarp();
+    }
     age_met_adjoint(c, s, lT10, M, p, g);
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) gout[k] = g[k];

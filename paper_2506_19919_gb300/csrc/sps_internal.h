@@ -35,6 +35,8 @@ struct Consts {
     float sn_s[SPS_NPARAM], sn_c[SPS_NPARAM];      // s, log(2 / omega) - log(2 pi) / 2
     int band_kind[kMaxBands];
     int tab_off[kMaxBands], tab_n[kMaxBands];      // TABLE bands: offset and count in Grid::band_T
+    int mdf_age;                                   // 1: MDF mean shifted per age bin (non-separable W)
+    float mdf_off[kMaxAges];                       // the shift of age bin i
 };
 
 // Per-galaxy tables built by sps_set_galaxies (device, structure of arrays).
@@ -186,9 +188,10 @@ struct HmcParams {
     int max_depth;          // NUTS tree depth limit (1..kNutsMaxDepth)
     NutsChain* nuts;        // per-chain NUTS state; null runs HMC
 };
-size_t hmc_team_smem_per_warp(int cpw);
-cudaError_t hmc_team_occupancy(int cpw, int warps, int* blocks_per_sm);
-cudaError_t launch_hmc_team(int cpw, const Consts& c, const Galaxies& g, const HmcParams& hp,
+// rows: the row-evaluation variant (one chain per warp, general W); see hmc_team.cu
+size_t hmc_team_smem_per_warp(int cpw, bool rows);
+cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm);
+cudaError_t launch_hmc_team(int cpw, bool rows, const Consts& c, const Galaxies& g, const HmcParams& hp,
                             const float* theta0, const float* mag_obs, const float* sigma,
                             const uint32_t* mask, const int32_t* gal_order, float* samples,
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
