@@ -14,7 +14,8 @@ the 12 parameters of the multi-chain ESS of galaxy g.
 
 Also reported: the same sampler run as the plain lock-step forward-mode
 baseline (posteriors/min at equal ESS), NUTS in the same kernel on the same
-galaxies (100 + 100 iterations, its own ESS), log-likelihood + gradient
+galaxies (100 + 100 iterations, its own ESS), the cost of the model
+extensions (skew-normal prior, age-dependent MDF, tabulated filter curves), log-likelihood + gradient
 evaluations per second on 100,000 (galaxy, chain) pairs (approximate FP32,
 exact FP32, exact BF16), the
 roofline of the dominant kernel, the clocks seen during the timed region,
@@ -47,7 +48,7 @@ UNIT = "posteriors/min"
 # dram__bytes_write.sum, mean of five full-size launches in one ncu capture,
 # profiles/k_hmc_team_hmc4096gal_x4_launches.md), valid only while the
 # kernel's sources hash to the recorded value; otherwise reported as null.
-KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_internal.h", "philox.cuh")
+KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_eval.cuh", "sps_internal.h", "philox.cuh")
 TRAFFIC = {"sha": "e46332faaa20406d", "bytes": 182.743e9 + 7.673e9}
 
 
@@ -282,6 +283,8 @@ def run_ours(args):
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
     if rank == 0 and not args.skip_nuts:
         out["nuts"] = _nuts(ctx, wl, x0, mobs, value, float(nev.sum()) / (ms_local / 1e3))
+    if rank == 0 and not args.skip_models:
+        out["models"] = _models(wl, dev)
     if not args.skip_e2e:                       # every rank (collective timing)
         out["e2e"] = _e2e(ctx, cfg, lib, wl, mobs, x0, post, ws)
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -370,6 +373,77 @@ def _nuts(ctx, wl, x0, mobs, hmc_value, hmc_evals_per_s):
             "leaves_per_iteration": float((nev - 1.0).mean() / (nw + ns)),
             "grad_evals_per_s": eps, "vs_hmc_grad_evals_per_s": eps / hmc_evals_per_s,
             "accept_mean": float(o["accept_prob"].mean()), "divergences": int(o["divergences"].sum())}
+
+
+def _models(wl, dev):
+    """Cost of the model extensions against the base model on the same
+    workloads: HMC (100 + 100 iterations on the bench galaxies and start
+    points) with the skew-normal prior, and with an age-dependent MDF mean
+    (general W; the row-evaluation variant of the kernel); log L + gradient on
+    100,000 pairs (the loglike workload) with the age-dependent MDF and with a
+    tabulated filter set (synthetic measured-style curves, one sample per 10 A)
+    in place of the Gaussian bands."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    from paper_2506_19919_gb300 import priors as P
+
+    def hmc_time(tables, **ctx_kw):
+        ctx = pkg.Context(tables, device=dev.index, **ctx_kw)
+        ctx.set_galaxies(wl.z, build_approx=True)
+        mt = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev), mode="approx")
+        mo = (mt + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)).contiguous()
+        x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
+        kw = dict(chains_per_gal=wl.chains, seed=2506199190, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"],
+                  samples=False)
+        ctx.hmc_run(x0, mo, wl.sigma, wl.mask, n_warm=2, n_samp=2, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = ctx.hmc_run(x0, mo, wl.sigma, wl.mask, n_warm=100, n_samp=100, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        s_run = e0.elapsed_time(e1) / 1e3
+        nev = float(o["grad_evals"].sum())
+        ctx.close()
+        return {"s": s_run, "grad_evals_per_s": nev / s_run}
+
+    def ll_times(tables):
+        w2 = W.config(2)
+        ctx = pkg.Context(tables, device=dev.index)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_galaxies(w2.z, build_approx=True)
+        torch.cuda.synchronize()
+        res = {"set_galaxies_s": time.perf_counter() - t0}
+        th = torch.as_tensor(w2.theta, dtype=torch.float32, device=dev)
+        mobs = ctx.photometry(torch.as_tensor(w2.theta_true, dtype=torch.float32, device=dev),
+                              mode="approx") + torch.as_tensor(w2.noise, dtype=torch.float32, device=dev)
+        for mode, prec, reps in (("approx", "fp32", 10), ("exact", "bf16", 3)):
+            ctx.loglike_grad(th, mobs, w2.sigma, w2.mask, mode=mode, prec=prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ctx.loglike_grad(th, mobs, w2.sigma, w2.mask, mode=mode, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            res[f"{mode}_{prec}_ms"] = e0.elapsed_time(e1) / reps
+        ctx.close()
+        return res
+
+    base2 = W.config(2).tables
+    off = W.mzr_offsets(wl.tables.age_yr, slope=0.25)
+    tab = W.tabulated_bands(np.random.default_rng(7), [360, 482, 604, 726, 848, 970, 1092])
+    res = {"workloads": "HMC: the bench galaxies, 100 + 100 iterations; log L + gradient: "
+                        + W.CONFIG_NAMES[2],
+           "hmc_base": hmc_time(wl.tables),
+           "hmc_skew_prior": hmc_time(wl.tables, skew=P.skew_normal_prior(wl.theta_true, W.PRIOR_LO, W.PRIOR_HI)),
+           "hmc_age_dependent_mdf": hmc_time(W.with_mdf_offset(wl.tables, off)),
+           "loglike_base": ll_times(base2),
+           "loglike_age_dependent_mdf": ll_times(W.with_mdf_offset(base2, W.mzr_offsets(base2.age_yr, 0.25))),
+           "loglike_tabulated_bands": ll_times(W.with_bands(base2, *tab))}
+    return res
 
 
 def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
@@ -606,6 +680,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-nuts", action="store_true")
+    ap.add_argument("--skip-models", action="store_true")
     ap.add_argument("--plain-full", action="store_true",
                     help="run the whole lock-step baseline HMC (minutes) and report its own ESS")
     # profiling captures only (not bench values): smaller galaxy count / iterations

@@ -19,6 +19,8 @@
 // is released.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "band_tab.cuh"
 #include "sps_device.cuh"
 #include "tc_ptx.cuh"
@@ -292,6 +294,9 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 top-hat, > 0 Gaussian, < 0 table
             acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
         }
+        bool has_tab = false;                      // a tabulated band in this warp's group
+#pragma unroll
+        for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < B && c.band_kind[b0 + k] == 2);
         for (int nt = 0; nt < n_tiles; ++nt) {
             const int buf = nt & 1;
             const uint32_t use = (uint32_t)(nt >> 1);
@@ -304,43 +309,54 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                 float S[32];
                 tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
                                   (uint32_t)(buf * kFwdBN + half * ncol + cc * 32), S);
+                // 32 columns x this warp's bands; the tabulated-curve form is a
+                // separate copy of the loop, run only by groups holding a
+                // tabulated band, so that the Gaussian / top-hat loop keeps
+                // its instruction footprint
+                auto columns = [&](auto tab_tag) {
+                    constexpr bool kTab = decltype(tab_tag)::value;
 #pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
-                    const bool ov = lo < nb0 + 32 && hi > nb0;
-                    if (!__any_sync(0xffffffffu, ov)) continue;
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    for (int k = 0; k < NB; ++k) {
+                        const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+                        const bool ov = lo < nb0 + 32 && hi > nb0;
+                        if (!__any_sync(0xffffffffu, ov)) continue;
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int nn = nb0 + j;
-                        if (nn >= lo && nn < hi) {
-                            const float4 L4 = __ldg(grid.lamc + nn);
-                            const float pw = __expf(dl * L4.z);
-                            const float base = L4.y * pw + eb * L4.w;
-                            const float E = exp2f(cA * base);
-                            const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
-                            float w = L4.x;
-                            if (gs[k] > 0.0f) {
-                                const float u = (__ldg(grid.lam + nn) - gc[k]) * gs[k];
-                                w *= __expf(-0.5f * u * u);
-                            } else if (gs[k] < 0.0f) {
-                                const int b = b0 + k;
-                                w *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b],
-                                             (__ldg(grid.lam + nn) - gc[k]) * -gs[k]);
+                        for (int j = 0; j < 32; ++j) {
+                            const int nn = nb0 + j;
+                            if (nn >= lo && nn < hi) {
+                                const float4 L4 = __ldg(grid.lamc + nn);
+                                const float pw = __expf(dl * L4.z);
+                                const float base = L4.y * pw + eb * L4.w;
+                                const float E = exp2f(cA * base);
+                                const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
+                                float w = L4.x;
+                                if (kTab && gs[k] < 0.0f) {
+                                    const int b = b0 + k;
+                                    w *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b],
+                                                 (__ldg(grid.lam + nn) - gc[k]) * -gs[k]);
+                                } else if (gs[k] != 0.0f) {
+                                    const float u = (__ldg(grid.lam + nn) - gc[k]) * gs[k];
+                                    w *= __expf(-0.5f * u * u);
+                                }
+                                const float Sw = S[j] * w;
+                                const float es = Sw * E;
+                                a0 += Sw;
+                                a1 += es;
+                                a2 = fmaf(es, base, a2);
+                                a3 = fmaf(es, dterm, a3);
                             }
-                            const float Sw = S[j] * w;
-                            const float es = Sw * E;
-                            a0 += Sw;
-                            a1 += es;
-                            a2 = fmaf(es, base, a2);
-                            a3 = fmaf(es, dterm, a3);
                         }
+                        acc[k][0] += a0;
+                        acc[k][1] += a1;
+                        acc[k][2] += a2;
+                        acc[k][3] += a3;
                     }
-                    acc[k][0] += a0;
-                    acc[k][1] += a1;
-                    acc[k][2] += a2;
-                    acc[k][3] += a3;
-                }
+                };
+                if (has_tab)
+                    columns(std::true_type{});
+                else
+                    columns(std::false_type{});
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&ctl->tempty[buf]);
