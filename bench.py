@@ -45,11 +45,11 @@ METRIC = "posteriors/min at fixed ESS"
 UNIT = "posteriors/min"
 
 # DRAM traffic of one k_hmc_team launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of five full-size launches in one ncu capture,
+# dram__bytes_write.sum, mean of the five full-size launches in one ncu capture,
 # profiles/k_hmc_team_hmc4096gal_x4_launches.md), valid only while the
 # kernel's sources hash to the recorded value; otherwise reported as null.
 KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_eval.cuh", "sps_internal.h", "philox.cuh")
-TRAFFIC = {"sha": "e46332faaa20406d", "bytes": 182.743e9 + 7.673e9}
+TRAFFIC = {"sha": "0c2800f58a560367", "bytes": 213.252e9 + 10.552e9}
 
 
 def _kernel_sha():
