@@ -182,6 +182,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = _hmc_workload(rank, args.gal, (args.warm, args.samp) if args.warm is not None else None)
+    if args.mdf_age:
+        wl.tables = W.with_mdf_offset(wl.tables, W.mzr_offsets(wl.tables.age_yr, slope=0.25))
     G, C = wl.n_gal, wl.chains
     n_warm, n_samp = wl.extra["n_warm"], wl.extra["n_samp"]
     ctx = pkg.Context(wl.tables, device=local)
@@ -205,6 +207,7 @@ def run_ours(args):
     cfg.L_min, cfg.L_max = wl.extra["L_min"], wl.extra["L_max"]
     cfg.seed = 2506199190 + rank
     cfg.use_graph, cfg.autotune = 1, 1
+    cfg.sampler = 1 if args.sampler == "nuts" else 0
     import ctypes as Ct
     st = _lib.sps_hmc_stats(*(Ct.c_void_p(stats[k].data_ptr()) for k in
                               ("accept_prob", "step_size", "divergences", "grad_evals", "status")))
@@ -259,7 +262,8 @@ def run_ours(args):
         "config": {"workload": W.CONFIG_NAMES[3], "galaxies": G, "chains_per_gal": C,
                    "n_warm": n_warm, "n_samp": n_samp, "L": [cfg.L_min, cfg.L_max],
                    "ssp_grid": [wl.tables.n_age, wl.tables.n_met, wl.tables.n_lam],
-                   "bands": wl.tables.n_band, "photometry": "approx",
+                   "bands": wl.tables.n_band, "photometry": "approx", "sampler": args.sampler,
+                   "mdf": "age-dependent" if args.mdf_age else "separable",
                    "l2": "flushed (256 MB write) between timed steps; working set > L2",
                    "parallelism": f"replicas{ws}"},
         "ess": {"target": ESS_TARGET, "galaxies_at_target": int((ess_g >= ESS_TARGET).sum()),
@@ -687,6 +691,10 @@ def main():
     ap.add_argument("--gal", type=int, default=None)
     ap.add_argument("--warm", type=int, default=None)
     ap.add_argument("--samp", type=int, default=None)
+    ap.add_argument("--sampler", default="hmc", choices=["hmc", "nuts"],
+                    help="sampler of the timed step (profiling captures; the bench line is HMC)")
+    ap.add_argument("--mdf-age", action="store_true",
+                    help="age-dependent MDF (row-evaluation kernel variant; profiling captures)")
     ap.add_argument("--survey", action="store_true",
                     help="throughput on the 1,000,000-galaxy survey batch (not the bench line)")
     ap.add_argument("--loglike-only", default=None,
