@@ -700,7 +700,10 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
-    if (mode == SPS_APPROX) {
+    if (mode == SPS_APPROX && !ctx->c.mdf_age && ctx->c.n_met <= 12 && !std::getenv("SPS_LIKE_ROWS")) {
+        // separable model: the team evaluation, one row per warp
+        CK(launch_like_team(ctx->c, ctx->gal(), th, gi, n, mo, sg, mk, llo, gro, ctx->nonfinite.as<int>(), s));
+    } else if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, mo, sg, mk, nullptr, llo, gro, nullptr,
                               ctx->nonfinite.as<int>(), s));
     } else {

@@ -16,6 +16,8 @@
 // leapfrog (half kick, drift x += eps minv p, gradient, half kick), FP64
 // energy accept, dual-averaged step size and windowed diagonal metric in the
 // warm-up, Philox-4x32-10 draws with counter (iteration, block, chain, 0).
+#include <algorithm>
+
 #include "philox.cuh"
 #include "sps_eval.cuh"
 
@@ -101,7 +103,7 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, int Zn, fl
 
 // log posterior (unbounded space) and its gradient for every chain of the
 // team at t.x; writes t.lp and t.g.
-template <int CPW>
+template <int CPW, bool kPhys = false>
 __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, const EdgeTables& et,
                                           float lnT, float lT10, int nb) {
     const int lane = lane_id();
@@ -112,7 +114,14 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         const int e = lane + 32 * r;
         if (e < CPW * SPS_NPARAM) {
             const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
-            bound_prior(c, k, t.x[ch][k], t.th[ch][k], t.dth[ch][k], t.lpe[ch][k], dlp[r]);
+            if (kPhys) {                                     // physical parameters, no prior
+                t.th[ch][k] = t.x[ch][k];
+                t.dth[ch][k] = 1.0f;
+                t.lpe[ch][k] = 0.0f;
+                dlp[r] = 0.0f;
+            } else {
+                bound_prior(c, k, t.x[ch][k], t.th[ch][k], t.dth[ch][k], t.lpe[ch][k], dlp[r]);
+            }
         }
     }
     __syncwarp();
@@ -874,6 +883,32 @@ __device__ __forceinline__ void nuts_leaf(const Consts& c, TeamWork<CPW>& t, int
     }
 }
 
+// The galaxy's age bins, ln t_obs and, for the observed bands in `bits`, the
+// slot table (c_SSP row pointer, dust constants, zero point, data).
+template <int CPW>
+__device__ __forceinline__ void team_galaxy(const Consts& c, const Galaxies& g, TeamWork<CPW>& t, int64_t gi,
+                                            uint32_t bits, const float* __restrict__ mag_obs,
+                                            const float* __restrict__ sigma) {
+    const int lane = lane_id();
+    const int B = c.n_band, K = c.K;
+    for (int i = lane; i < c.n_age; i += 32) t.bins[i] = g.bins[(size_t)gi * c.n_age + i];
+    if (lane == 0) {
+        t.lnT = g.lnT[gi];
+        t.lT10 = g.lT10[gi];
+    }
+    if (lane < B && ((bits >> lane) & 1u)) {
+        const int slot = __popc(bits & ((1u << lane) - 1u));
+        const size_t gb = (size_t)gi * B + lane;
+        t.ptr[slot] = g.cssp + gb * K;
+        t.dust[slot] = g.dust_eff[gb];
+        t.zp[slot] = g.zp[gb];
+        t.mobs[slot] = mag_obs[gb];
+        const float sg = sigma[gb];
+        t.isig2[slot] = 1.0f / (sg * sg);
+    }
+    __syncwarp();
+}
+
 // Take work item q (a galaxy and a group of CPW of its chains) into the
 // team: the galaxy's observed-band slots and the chains' initial state.
 // Returns the galaxy index; *nch / *nb get the live chains and observed bands.
@@ -894,21 +929,7 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
     const int c0 = (q % groups) * CPW;
     const int nch = min(CPW, C - c0);
     const uint32_t bits = mask[gi] & all;
-    for (int i = lane; i < c.n_age; i += 32) t.bins[i] = g.bins[(size_t)gi * c.n_age + i];
-    if (lane == 0) {
-        t.lnT = g.lnT[gi];
-        t.lT10 = g.lT10[gi];
-    }
-    if (lane < B && ((bits >> lane) & 1u)) {
-        const int slot = __popc(bits & ((1u << lane) - 1u));
-        const size_t gb = (size_t)gi * B + lane;
-        t.ptr[slot] = g.cssp + gb * K;
-        t.dust[slot] = g.dust_eff[gb];
-        t.zp[slot] = g.zp[gb];
-        t.mobs[slot] = mag_obs[gb];
-        const float sg = sigma[gb];
-        t.isig2[slot] = 1.0f / (sg * sg);
-    }
+    team_galaxy<CPW>(c, g, t, gi, bits, mag_obs, sigma);
     // chain state; unused chain slots mirror the first chain and never write
     for (int e = lane; e < CPW * SPS_NPARAM; e += 32) {
         const int ch = e / SPS_NPARAM, k = e - ch * SPS_NPARAM;
@@ -1117,7 +1138,79 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
     }
 }
 
+// log L and its gradient (physical parameters) for n independent rows, one
+// row per warp through the team evaluation (the fused single-pass contraction
+// and lane-parallel reductions of the sampler); every warp of a block takes
+// its next row after one block barrier, so the block's warps stay in phase.
+// Non-finite parameters or a galaxy index out of range give NaN outputs;
+// any non-finite output raises *nonfinite.
+__global__ void __launch_bounds__(512, 1)
+k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
+            const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ mag_obs,
+            const float* __restrict__ sigma, const uint32_t* __restrict__ mask, float* __restrict__ ll_out,
+            float* __restrict__ grad_out, int* __restrict__ nonfinite) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ EdgeTables et;
+    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    TeamWork<1>& t = reinterpret_cast<TeamWork<1>*>(smem)[warp];
+    const int lane = lane_id();
+    const int B = c.n_band;
+    const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
+    for (int i = threadIdx.x; i <= c.n_age; i += blockDim.x) et.age[i] = c.log_age_edge[i];
+    for (int i = threadIdx.x; i <= c.n_met; i += blockDim.x) et.lgz[i] = c.lgz_edge[i];
+    const int64_t per_round = (int64_t)gridDim.x * warps;
+    const int64_t rounds = (n + per_round - 1) / per_round;
+    for (int64_t r = 0; r < rounds; ++r) {
+        __syncthreads();
+        const int64_t row = (r * gridDim.x + blockIdx.x) * warps + warp;
+        if (row >= n) continue;
+        const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+        float xk = (lane < SPS_NPARAM) ? theta[row * SPS_NPARAM + lane] : 0.0f;
+        const bool ok = __all_sync(kFull, isfinite(xk)) && gi >= 0 && gi < g.n;
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(nonfinite, 1);
+                ll_out[row] = __int_as_float(0x7fc00000);
+            }
+            if (grad_out && lane < SPS_NPARAM) grad_out[row * SPS_NPARAM + lane] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const uint32_t bits = mask[gi] & all;
+        team_galaxy<1>(c, g, t, gi, bits, mag_obs, sigma);
+        if (lane < SPS_NPARAM) t.x[0][lane] = xk;
+        __syncwarp();
+        team_eval<1, true>(c, t, et, t.lnT, t.lT10, __popc(bits));
+        const double ll = t.ll[0];
+        const float gk = (lane < SPS_NPARAM) ? t.g[0][lane] : 0.0f;
+        if (lane == 0) ll_out[row] = (float)ll;
+        if (grad_out && lane < SPS_NPARAM) grad_out[row * SPS_NPARAM + lane] = gk;
+        const bool bad = __any_sync(kFull, !isfinite(gk)) || !isfinite(ll);
+        if (bad && lane == 0) atomicOr(nonfinite, 1);
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_like_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
+                             int64_t n, const float* mag_obs, const float* sigma, const uint32_t* mask,
+                             float* ll_out, float* grad_out, int* nonfinite, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    constexpr int kWarps = 8;
+    const size_t smem = sizeof(TeamWork<1>) * kWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_like_team, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_like_team, 32 * kWarps, smem)) != cudaSuccess)
+        return e;
+    const int64_t need = (n + kWarps - 1) / kWarps;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * sms);
+    k_like_team<<<blocks, 32 * kWarps, smem, s>>>(c, g, theta, gal_idx, n, mag_obs, sigma, mask, ll_out, grad_out,
+                                                  nonfinite);
+    return cudaGetLastError();
+}
 
 size_t hmc_team_smem_per_warp(int cpw, bool rows) {
     if (rows) return team_stride<1, true>();
