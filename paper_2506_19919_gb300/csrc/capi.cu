@@ -700,8 +700,8 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
     if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
-    if (mode == SPS_APPROX && !ctx->c.mdf_age && ctx->c.n_met <= 12 && !std::getenv("SPS_LIKE_ROWS")) {
-        // separable model: the team evaluation, one row per warp
+    if (mode == SPS_APPROX && ctx->c.n_met <= 12 && !std::getenv("SPS_LIKE_ROWS")) {
+        // the team evaluation, one row per warp
         CK(launch_like_team(ctx->c, ctx->gal(), th, gi, n, mo, sg, mk, llo, gro, ctx->nonfinite.as<int>(), s));
     } else if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, mo, sg, mk, nullptr, llo, gro, nullptr,
@@ -940,11 +940,17 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     // grid is persistent (occupancy x SMs) and pulls (galaxy, chain group)
     // items from the queue
     // first candidate = default; another replaces it only if >3% faster in the probe
-    // an age-dependent MDF (general W) runs the row-evaluation variant, one chain per warp
+    // an age-dependent MDF runs the one-chain-per-warp variant with the per-age q matrix
     const bool rows = ctx->c.mdf_age != 0;
     std::vector<std::pair<int, int>> cands = {{1, 8}, {1, 16}};
     if (rows) {
         cands = {{1, 4}, {1, 2}, {1, 8}};
+    } else if (nuts) {
+        // NUTS: the 8-iteration probe from the start points does not rank the
+        // shapes reliably (tree depths change over the warm-up); one chain per
+        // warp measured best on full runs, two per warp within 1%
+        cands = {{1, 8}};
+        if (C >= 2) cands.push_back({2, 8});
     } else {
         if (C >= 2) cands.insert(cands.begin(), {{2, 4}, {2, 8}, {2, 16}});
         if (C >= 4) cands.push_back({4, 8});

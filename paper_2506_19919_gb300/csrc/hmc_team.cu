@@ -19,7 +19,7 @@
 #include <algorithm>
 
 #include "philox.cuh"
-#include "sps_eval.cuh"
+#include "sps_device.cuh"
 
 namespace sps {
 
@@ -40,6 +40,7 @@ struct TeamWork {
             float F[CPW][kMaxBands];        // dust factor at lambda_eff
             float Ah[CPW][kMaxBands], Al[CPW][kMaxBands];   // zp - m_obs - 2.5 (lgM + 9), hi + lo
             float res[CPW][kMaxBands], gam[CPW][kMaxBands]; // residual m - m_obs, dlogL / dln c
+            float gh[CPW][kMaxBands];                       // gamma_b / S_b (age-dependent MDF pass)
         } t;
     } u;
     float th[CPW][SPS_NPARAM], dth[CPW][SPS_NPARAM];
@@ -103,9 +104,15 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, int Zn, fl
 
 // log posterior (unbounded space) and its gradient for every chain of the
 // team at t.x; writes t.lp and t.g.
-template <int CPW, bool kPhys = false>
+// kNonsep (one chain per warp): the MDF mean depends on the age bin, so q is
+// a matrix qm[i * Zn + j] (shared memory, filled here); the forward takes
+// R_i = sum_j q_ij C_bij and S_b = sum_i w_i R_i, and a second pass over the
+// c_SSP rows forms V_ij = sum_b g_b C_bij for the MDF gradient (qbar_ij =
+// w_i V_ij through the edge pdfs of each row).
+template <int CPW, bool kPhys = false, bool kNonsep = false>
 __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, const EdgeTables& et,
-                                          float lnT, float lT10, int nb) {
+                                          float lnT, float lT10, int nb, float* __restrict__ qm = nullptr) {
+    static_assert(!kNonsep || CPW == 1, "the age-dependent MDF takes one chain per warp");
     const int lane = lane_id();
     const int A = c.n_age, Zn = c.n_met;
     float dlp[(CPW * SPS_NPARAM + 31) / 32];
@@ -143,6 +150,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
 #pragma unroll 1
     for (int ch = 0; ch < CPW; ++ch) age_met_parts<true>(c, age_view(t, ch, et), t.bins, lnT, lT10, t.th[ch], true);
     __syncwarp();
+    if constexpr (kNonsep) mdf_rows_fill(c, et.lgz, t.th[0][7], t.th[0][8], qm);
     // M = sum_i m_i in FP64, the chains' reductions interleaved
     {
         double mp[CPW];
@@ -199,6 +207,7 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         const float* C = t.ptr[b];
         float2 U[CPW][kZ2];
         float R[CPW][4];
+        float spn = 0.0f;                                   // kNonsep: lane partial of S_b
 #pragma unroll
         for (int ch = 0; ch < CPW; ++ch)
 #pragma unroll
@@ -213,26 +222,44 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             float2 cv[kZ2];
 #pragma unroll
             for (int j = 0; j < kZ2; ++j) cv[j] = make_float2(cs[2 * j], cs[2 * j + 1]);
-#pragma unroll
-            for (int ch = 0; ch < CPW; ++ch) {
-                const float wi = (i < A) ? t.w[ch][i] : 0.0f;
-                const float2 w2 = make_float2(wi, wi);
+            if constexpr (kNonsep) {
+                const float wi = (i < A) ? t.w[0][i] : 0.0f;
                 float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int j = 0; j < kZ2; ++j) {
-                    r2 = __ffma2_rn(qr[ch][j], cv[j], r2);
-                    U[ch][j] = __ffma2_rn(w2, cv[j], U[ch][j]);
+                    const float2 q2 = (i < A) ? make_float2((2 * j < Zn) ? qm[i * Zn + 2 * j] : 0.0f,
+                                                            (2 * j + 1 < Zn) ? qm[i * Zn + 2 * j + 1] : 0.0f)
+                                              : make_float2(0.0f, 0.0f);
+                    r2 = __ffma2_rn(q2, cv[j], r2);
                 }
-                R[ch][tt] = r2.x + r2.y;
+                R[0][tt] = r2.x + r2.y;
+                spn = fmaf(wi, R[0][tt], spn);
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < CPW; ++ch) {
+                    const float wi = (i < A) ? t.w[ch][i] : 0.0f;
+                    const float2 w2 = make_float2(wi, wi);
+                    float2 r2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int j = 0; j < kZ2; ++j) {
+                        r2 = __ffma2_rn(qr[ch][j], cv[j], r2);
+                        U[ch][j] = __ffma2_rn(w2, cv[j], U[ch][j]);
+                    }
+                    R[ch][tt] = r2.x + r2.y;
+                }
             }
         }
         float sp[CPW];
 #pragma unroll
         for (int ch = 0; ch < CPW; ++ch) {
-            float2 v = make_float2(0.0f, 0.0f);
+            if constexpr (kNonsep) {
+                sp[ch] = spn;
+            } else {
+                float2 v = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < kZ2; ++j) v = __ffma2_rn(qr[ch][j], U[ch][j], v);
-            sp[ch] = v.x + v.y;
+                for (int j = 0; j < kZ2; ++j) v = __ffma2_rn(qr[ch][j], U[ch][j], v);
+                sp[ch] = v.x + v.y;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
@@ -252,15 +279,54 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             if (lane == 0) {
                 t.u.t.res[ch][b] = r;
                 t.u.t.gam[ch][b] = gam;
+                if (kNonsep) t.u.t.gh[ch][b] = gh;
             }
-            const float2 g2 = make_float2(gh, gh);
+            if constexpr (!kNonsep) {
+                const float2 g2 = make_float2(gh, gh);
 #pragma unroll
-            for (int j = 0; j < kZ2; ++j) qbr[ch][j] = __ffma2_rn(g2, U[ch][j], qbr[ch][j]);
+                for (int j = 0; j < kZ2; ++j) qbr[ch][j] = __ffma2_rn(g2, U[ch][j], qbr[ch][j]);
+            }
 #pragma unroll
             for (int tt = 0; tt < 4; ++tt) wbl[ch][tt] = fmaf(gh, R[ch][tt], wbl[ch][tt]);
         }
     }
     __syncwarp();
+    // kNonsep: V_ij = sum_b g_b C_bij row by row, and the MDF gradient
+    // sum_ij w_i V_ij dq_ij/d(lgZ, sigma) edge by edge (q_ij = Phi(y_i,j+1) - Phi(y_ij))
+    float mdf_gz = 0.0f, mdf_gs = 0.0f;
+    if constexpr (kNonsep) {
+        const float isd = 1.0f / t.th[0][8], mz = t.th[0][7];
+#pragma unroll 1
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            if (i >= A) break;
+            float v[kZnReg];
+#pragma unroll
+            for (int j = 0; j < kZnReg; ++j) v[j] = 0.0f;
+#pragma unroll 1
+            for (int b = 0; b < nb; ++b) {
+                float cs[kZnReg];
+                load_row(t.ptr[b] + i * Zn, Zn, cs);
+                const float gb = t.u.t.gh[0][b];
+#pragma unroll
+                for (int j = 0; j < kZnReg; ++j) v[j] = fmaf(gb, cs[j], v[j]);
+            }
+            const float wi = t.w[0][i], mu = mz + c.mdf_off[i];
+            float vprev = 0.0f;
+#pragma unroll
+            for (int e = 0; e <= kZnReg; ++e) {
+                if (e > Zn) break;
+                const float ve = (e < Zn) ? v[e < kZnReg ? e : kZnReg - 1] : 0.0f;
+                const float y = (et.lgz[e] - mu) * isd;
+                const float d = wi * (ve - vprev);
+                mdf_gz = fmaf(phi_(y), d, mdf_gz);
+                mdf_gs = fmaf(phi_y(y), d, mdf_gs);
+                vprev = ve;
+            }
+        }
+        mdf_gz = warp_sum(mdf_gz) * isd;
+        mdf_gs = warp_sum(mdf_gs) * isd;
+    }
     // ---- log likelihood (FP64 sum of the band terms) and the dust / lgM
     //      gradients: two chains per round, 16 lanes each, bands strided by 16
 #pragma unroll
@@ -308,9 +374,15 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
             for (int ch = 0; ch < CPW; ++ch) t.w[ch][i] = wbl[ch][tt];
     }
     __syncwarp();
-    // qbar: sum the lanes' partials, one chain per round (two half sums)
+    // qbar: sum the lanes' partials, one chain per round (two half sums);
+    // with kNonsep the MDF gradient is already formed and qbar is zero
 #pragma unroll
     for (int ch = 0; ch < CPW; ++ch) {
+        if constexpr (kNonsep) {
+            if (lane < Zn) t.qb[ch][lane] = 0.0f;
+            __syncwarp();
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < kZ2; ++j) {
             t.u.red[lane][2 * j] = qbr[ch][j].x;
@@ -338,6 +410,10 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
         gr[10] = t.gd[ch][2];
         gr[11] = t.gd[ch][3];
         age_met_adjoint(c, age_view(t, ch, et), lT10, t.M[ch], t.th[ch], gr);
+        if constexpr (kNonsep) {
+            gr[7] += mdf_gz;
+            gr[8] += mdf_gs;
+        }
         if (lane < SPS_NPARAM) {
             float v = gr[0];
 #pragma unroll
@@ -917,8 +993,7 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
                                           TeamWork<CPW>& t, int q, const float* __restrict__ theta0,
                                           const float* __restrict__ mag_obs, const float* __restrict__ sigma,
                                           const uint32_t* __restrict__ mask, const int32_t* __restrict__ gal_order,
-                                          ChainMetric* __restrict__ metric, int* nch_out, int* nb_out,
-                                          WarpWork* ww) {
+                                          ChainMetric* __restrict__ metric, int* nch_out, int* nb_out) {
     const int lane = lane_id();
     const int B = c.n_band, K = c.K;
     const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
@@ -982,7 +1057,6 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
         t.wstop[ch] = nw - term_b;
     }
     __syncwarp();
-    if (ww) fill_slots(c, g, ww->d, gi, bits, mag_obs, sigma, g.cssp + (size_t)gi * B * K, false);
     *nch_out = nch;
     *nb_out = __popc(bits);
     return gi;
@@ -1026,44 +1100,19 @@ __device__ __forceinline__ void team_step(const Consts& c, TeamWork<CPW>& t, con
     }
 }
 
-// log posterior and gradient of the team's single chain through the general
-// row evaluation (eval_row: W = w_i q_ij held whole, c_SSP contracted per
-// band), for models whose weights do not factor into age x metallicity (an
-// age-dependent MDF); the sampler around it is the same.
-template <int CPW>
-__device__ __forceinline__ void rows_eval(const Consts& c, TeamWork<CPW>& t, WarpWork& ww, int nb) {
-    static_assert(CPW == 1, "the row evaluation takes one chain per warp");
-    const int lane = lane_id();
-    RowParams p;
-    load_params(c, t.x[0], true, p);
-    float gr[SPS_NPARAM];
-    const double ll = eval_row(c, ww, t.bins, t.lnT, t.lT10, p, nb, true, true, gr);
-    if (lane < SPS_NPARAM) {
-        float v = gr[0], d = p.dth[0], q = p.dlp[0];
-#pragma unroll
-        for (int k = 1; k < SPS_NPARAM; ++k)
-            if (lane == k) {
-                v = gr[k];
-                d = p.dth[k];
-                q = p.dlp[k];
-            }
-        t.g[0][lane] = v * d + q;
-    }
-    if (lane == 0) t.lp[0] = ll + p.logprior;
-    __syncwarp();
-}
-
-// Shared memory of one warp: the team state, and with kRows the row scratch.
-template <int CPW, bool kRows>
+// Shared memory of one warp: the team state, and with an age-dependent MDF
+// (kNonsep, one chain per warp) the q matrix of the chain.
+constexpr int kQmFloats = kKTileMax * 32;
+template <int CPW, bool kNonsep>
 __host__ __device__ constexpr size_t team_stride() {
-    return kRows ? sizeof(TeamWork<CPW>) + sizeof(WarpWork) : sizeof(TeamWork<CPW>);
+    return kNonsep ? sizeof(TeamWork<CPW>) + sizeof(float) * kQmFloats : sizeof(TeamWork<CPW>);
 }
 
 // Persistent kernel: each warp is a team working through the queue of
 // (galaxy, chain group) items; the warps of a block advance one evaluation per
 // pass together (one block barrier per pass), so that they run the same code
 // at the same time and share the instruction cache.
-template <int CPW, bool kRows>
+template <int CPW, bool kNonsep>
 __global__ void __launch_bounds__(512, 1)
 k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
            const float* __restrict__ theta0, const float* __restrict__ mag_obs,
@@ -1073,9 +1122,9 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
            ChainMetric* __restrict__ metric) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ EdgeTables et;
-    unsigned char* mine = smem + (size_t)(threadIdx.x >> 5) * team_stride<CPW, kRows>();
+    unsigned char* mine = smem + (size_t)(threadIdx.x >> 5) * team_stride<CPW, kNonsep>();
     TeamWork<CPW>& t = *reinterpret_cast<TeamWork<CPW>*>(mine);
-    WarpWork* ww = kRows ? reinterpret_cast<WarpWork*>(mine + sizeof(TeamWork<CPW>)) : nullptr;
+    float* qm = kNonsep ? reinterpret_cast<float*>(mine + sizeof(TeamWork<CPW>)) : nullptr;
     const int lane = lane_id();
     const int C = hp.chains_per_gal;
     for (int i = threadIdx.x; i <= c.n_age; i += blockDim.x) et.age[i] = c.log_age_edge[i];
@@ -1096,18 +1145,14 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
             if ((int64_t)q >= g.n * groups) {
                 drained = true;
             } else {
-                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb,
-                                    ww);
+                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb);
                 have = true;
                 pass = 0;
             }
         }
         if (iter % sync_every == 0 && !__syncthreads_or(have ? 1 : 0)) break;
         if (!have) continue;
-        if constexpr (kRows)
-            rows_eval<CPW>(c, t, *ww, nb);
-        else
-            team_eval<CPW>(c, t, et, t.lnT, t.lT10, nb);
+        team_eval<CPW, false, kNonsep>(c, t, et, t.lnT, t.lT10, nb, qm);
         if (pass == 0) {
 #pragma unroll 1
             for (int ch = 0; ch < CPW; ++ch)
@@ -1144,6 +1189,7 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
 // its next row after one block barrier, so the block's warps stay in phase.
 // Non-finite parameters or a galaxy index out of range give NaN outputs;
 // any non-finite output raises *nonfinite.
+template <bool kNonsep>
 __global__ void __launch_bounds__(512, 1)
 k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
             const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ mag_obs,
@@ -1152,7 +1198,9 @@ k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __r
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ EdgeTables et;
     const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    TeamWork<1>& t = reinterpret_cast<TeamWork<1>*>(smem)[warp];
+    unsigned char* mine = smem + (size_t)warp * team_stride<1, kNonsep>();
+    TeamWork<1>& t = *reinterpret_cast<TeamWork<1>*>(mine);
+    float* qm = kNonsep ? reinterpret_cast<float*>(mine + sizeof(TeamWork<1>)) : nullptr;
     const int lane = lane_id();
     const int B = c.n_band;
     const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
@@ -1179,7 +1227,7 @@ k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __r
         team_galaxy<1>(c, g, t, gi, bits, mag_obs, sigma);
         if (lane < SPS_NPARAM) t.x[0][lane] = xk;
         __syncwarp();
-        team_eval<1, true>(c, t, et, t.lnT, t.lT10, __popc(bits));
+        team_eval<1, true, kNonsep>(c, t, et, t.lnT, t.lT10, __popc(bits), qm);
         const double ll = t.ll[0];
         const float gk = (lane < SPS_NPARAM) ? t.g[0][lane] : 0.0f;
         if (lane == 0) ll_out[row] = (float)ll;
@@ -1192,24 +1240,35 @@ k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __r
 
 }  // namespace
 
-cudaError_t launch_like_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
-                             int64_t n, const float* mag_obs, const float* sigma, const uint32_t* mask,
-                             float* ll_out, float* grad_out, int* nonfinite, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+template <bool kNonsep>
+static cudaError_t like_launch(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
+                               int64_t n, const float* mag_obs, const float* sigma, const uint32_t* mask,
+                               float* ll_out, float* grad_out, int* nonfinite, cudaStream_t s) {
     constexpr int kWarps = 8;
-    const size_t smem = sizeof(TeamWork<1>) * kWarps;
-    cudaError_t e = cudaFuncSetAttribute(k_like_team, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = team_stride<1, kNonsep>() * kWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_like_team<kNonsep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_like_team, 32 * kWarps, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_like_team<kNonsep>, 32 * kWarps, smem)) !=
+        cudaSuccess)
         return e;
     const int64_t need = (n + kWarps - 1) / kWarps;
     const int blocks = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * sms);
-    k_like_team<<<blocks, 32 * kWarps, smem, s>>>(c, g, theta, gal_idx, n, mag_obs, sigma, mask, ll_out, grad_out,
-                                                  nonfinite);
+    k_like_team<kNonsep><<<blocks, 32 * kWarps, smem, s>>>(c, g, theta, gal_idx, n, mag_obs, sigma, mask, ll_out,
+                                                           grad_out, nonfinite);
     return cudaGetLastError();
+}
+
+cudaError_t launch_like_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
+                             int64_t n, const float* mag_obs, const float* sigma, const uint32_t* mask,
+                             float* ll_out, float* grad_out, int* nonfinite, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (c.mdf_age)
+        return like_launch<true>(c, g, theta, gal_idx, n, mag_obs, sigma, mask, ll_out, grad_out, nonfinite, s);
+    return like_launch<false>(c, g, theta, gal_idx, n, mag_obs, sigma, mask, ll_out, grad_out, nonfinite, s);
 }
 
 size_t hmc_team_smem_per_warp(int cpw, bool rows) {
@@ -1217,30 +1276,30 @@ size_t hmc_team_smem_per_warp(int cpw, bool rows) {
     return cpw >= 4 ? sizeof(TeamWork<4>) : cpw == 2 ? sizeof(TeamWork<2>) : sizeof(TeamWork<1>);
 }
 
-template <int CPW, bool kRows>
+template <int CPW, bool kNonsep>
 static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcParams& hp,
                                const float* theta0, const float* mag_obs, const float* sigma,
                                const uint32_t* mask, const int32_t* gal_order, float* samples,
                                float* acc, float* eps_out, int32_t* div, int64_t* nevals,
                                int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                                cudaStream_t s) {
-    const size_t smem = team_stride<CPW, kRows>() * warps;
-    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = team_stride<CPW, kNonsep>() * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kNonsep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_hmc_team<CPW, kRows><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order,
+    k_hmc_team<CPW, kNonsep><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order,
                                                             samples, acc, eps_out, div, nevals, status, queue,
                                                             metric);
     return cudaGetLastError();
 }
 
-template <int CPW, bool kRows>
+template <int CPW, bool kNonsep>
 static cudaError_t team_occupancy(int warps, int* blocks_per_sm) {
-    const size_t smem = team_stride<CPW, kRows>() * warps;
-    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = team_stride<CPW, kNonsep>() * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kNonsep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<CPW, kRows>, warps * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<CPW, kNonsep>, warps * 32, smem);
 }
 
 cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm) {
