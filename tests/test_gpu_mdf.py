@@ -1,8 +1,8 @@
 """Age-dependent metallicity distribution (non-separable SSP weights) on the
 GPU: weights, photometry, log L + gradient (approximate and exact paths) and
 the samplers (the one-chain-per-warp, per-age-q variant of the persistent
-kernel), against
-the FP64 oracle on the production grid.  Tolerances as in test_gpu_parity."""
+kernel), against the FP64 oracle on the production grid.  Tolerances as in
+test_gpu_parity."""
 import numpy as np
 import pytest
 import torch
