@@ -283,6 +283,13 @@ sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const fl
                         const float* sigma, const uint32_t* mask, float* x_out, float* p_out,
                         double* logp_out, void* stream);
 
+/* Test hook for failure detection without a GPU fault: runs the bounded
+ * mbarrier wait of the tensor-core pipeline on a barrier that is completed
+ * (ready != 0) or never completed (ready == 0).  The wait polls at most
+ * spin_limit times (1 .. 2^26), then flags the timeout and the kernel returns,
+ * so the context stays usable.  Returns SPS_OK or SPS_E_TIMEOUT. */
+sps_status sps_wait_probe(sps_ctx* ctx, int32_t ready, uint32_t spin_limit, void* stream);
+
 /* The device Philox-4x32-10 generator: out[n][4] = philox(ctr[n][4], key).
  * (Salmon et al. 2011; the generator behind every HMC draw.) */
 sps_status sps_philox(sps_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out,

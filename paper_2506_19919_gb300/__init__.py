@@ -240,6 +240,11 @@ class Context:
               "sps_leapfrog")
         return xo, po, lo
 
+    def wait_probe(self, ready: bool, spin_limit: int = 1 << 16):
+        """Run the bounded device wait on a barrier that is (ready) or is never
+        completed; raises SpsError (SPS_E_TIMEOUT) when the wait gives up."""
+        check(self._lib.sps_wait_probe(self.h, int(bool(ready)), spin_limit, None), "sps_wait_probe")
+
     def philox(self, ctr, key: int):
         c = torch.as_tensor(np.asarray(ctr, dtype=np.uint32).view(np.int32)).to(self.device).contiguous()
         n = c.shape[0]

@@ -70,6 +70,7 @@ _PROTOS = {
     "sps_loglike_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, _P, _P,
                                    _P]),
     "sps_loglike_grad_forward_mode": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P]),
+    "sps_wait_probe": (C.c_int, [_P, C.c_int32, C.c_uint32, _P]),
     "sps_hmc_run": (C.c_int, [_P, C.POINTER(sps_hmc_config), _P, _P, _P, _P, _P,
                               C.POINTER(sps_hmc_stats), _P]),
     "sps_hmc_run_forward_mode": (C.c_int, [_P, C.POINTER(sps_hmc_config), _P, _P, _P, _P, _P,

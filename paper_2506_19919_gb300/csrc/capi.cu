@@ -865,6 +865,25 @@ struct HmcLaunch {
 
 }  // namespace
 
+namespace sps {
+// exact_tc.cu: the tensor-core pipeline's bounded wait on a barrier completed or not
+cudaError_t launch_wait_probe(int ready, uint32_t limit, int* err, cudaStream_t s);
+}  // namespace sps
+
+extern "C" sps_status sps_wait_probe(sps_ctx* ctx, int32_t ready, uint32_t spin_limit, void* stream) {
+    if (!ctx) return fail(SPS_E_INVALID_ARG, "null context");
+    if (spin_limit < 1 || spin_limit > (1u << 26)) return fail(SPS_E_INVALID_ARG, "spin_limit in [1, 2^26]");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int fl[2] = {0, 0};
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
+    CK(launch_wait_probe(ready != 0, spin_limit, ctx->nonfinite.as<int>() + 1, s));
+    CK(cudaMemcpyAsync(fl, ctx->nonfinite.p, sizeof(fl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fl[1]) return fail(SPS_E_TIMEOUT, "the probed wait timed out");
+    return SPS_OK;
+}
+
 extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
                                   const float* mag_obs, const float* sigma, const uint32_t* mask,
                                   float* samples_out, sps_hmc_stats* stats, void* stream) {

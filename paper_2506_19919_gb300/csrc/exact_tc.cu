@@ -61,7 +61,8 @@ struct Ctl {
     int issued;
 };
 
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err);
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err,
+                                              uint32_t limit = tc::kSpinLimit);
 
 // Warp-uniform wait: lane 0 polls, the outcome is broadcast.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
@@ -70,8 +71,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, Ctl* c
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
-    for (uint32_t i = 0; i < tc::kSpinLimit; ++i) {
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err,
+                                              uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
         if ((i & 1023) == 1023 && ctl->abort) return false;
     }
@@ -378,6 +380,24 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
     tc_teardown<ST>(ctl, warp);
 }
 
+// ---------------------------------------------------------------- wait probe
+// Exercises the pipeline's bounded wait: warp 0 waits on an mbarrier that
+// warp 1 arrives on when `ready`; otherwise nothing completes it, the wait
+// gives up after `limit` polls, sets the abort flag and raises error bit 2,
+// and the kernel returns normally.
+__global__ void __launch_bounds__(64) k_wait_probe(int ready, uint32_t limit, int* err) {
+    __shared__ Ctl ctl;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&ctl.drain, 1);
+        ctl.abort = 0;
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && ready) tc::mbar_arrive(&ctl.drain);
+    if (threadIdx.x == 0) wait_or_abort(&ctl.drain, 0u, &ctl, err, limit);
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- adjoint
 template <bool TF>
 __global__ void __launch_bounds__(kThreadsTC, 1)
@@ -481,6 +501,11 @@ cudaError_t launch_adj_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid
         if (e != cudaSuccess) return e;
         k_adj_tc<false><<<blocks, kThreadsTC, smem, s>>>(tm, c, grid, n, Wbar, err);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(int ready, uint32_t limit, int* err, cudaStream_t s) {
+    k_wait_probe<<<1, 64, 0, s>>>(ready, limit, err);
     return cudaGetLastError();
 }
 

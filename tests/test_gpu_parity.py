@@ -168,6 +168,21 @@ def test_philox_matches_oracle_bit_exact(parity64):
     np.testing.assert_array_equal(out.astype(np.uint64), ref)
 
 
+def test_bounded_wait_times_out_and_the_context_stays_usable(parity64):
+    """Failure detection without a fault: the tensor-core pipeline's bounded
+    wait on a barrier that nothing completes gives up, the call returns
+    SPS_E_TIMEOUT, and the same context then computes correct photometry."""
+    from paper_2506_19919_gb300 import SpsError, _lib
+    wl, ctx = parity64
+    ctx.wait_probe(True)
+    with pytest.raises(SpsError) as e:
+        ctx.wait_probe(False, spin_limit=1 << 14)
+    assert _lib.STATUS_NAMES[e.value.status] == "SPS_E_TIMEOUT"
+    m = ctx.photometry(wl.theta, mode="exact", prec="bf16").cpu().numpy()
+    ref = O.photometry(wl.theta, wl.z, wl.tables, "exact").numpy()
+    assert np.abs(m - ref).max() < MAG_TOL_BF16
+
+
 def test_leapfrog_trajectories_match_oracle(prod96):
     wl, ctx = prod96
     n = 12
