@@ -542,7 +542,9 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
     return {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"{n} galaxies x {wl.chains} chains x {iters} iterations of the FP64 "
                       f"oracle HMC ({dt:.2f} s/iteration), extrapolated to {it_total} iterations "
-                      f"per galaxy; ESS fraction per galaxy from the GPU run"}
+                      f"per galaxy; " + ("ESS fraction taken as 1, an upper bound for the oracle"
+                                         if post_frac == 1.0 else
+                                         f"ESS fraction per galaxy {post_frac:.3g} from the GPU run")}
 
 
 def run_loglike_only(args):
