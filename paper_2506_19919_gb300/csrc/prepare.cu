@@ -145,8 +145,10 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
                 in = (lo_ >= p0) && (lo_ < p1);
                 T = in ? 1.0 : 0.0;
             } else if (kind == 1) {
+                // Gaussian support: |u| < 6 drops 2e-9 of the band's weight, below
+                // FP32 rounding; zero point and fluxes use the same support
                 double u = (lo_ - p0) / sg;
-                in = fabs(u) < 9.0;
+                in = fabs(u) < 6.0;
                 T = in ? exp(-0.5 * u * u) : 0.0;
             } else {
                 const double u = (lo_ - p0) / p1;
