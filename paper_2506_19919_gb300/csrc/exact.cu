@@ -300,11 +300,16 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
 
 // ---------------------------------------------------------------- adjoint source
 // One block per row: v[n] = F_att(n) sum_b gbar_b wb(n), zero beyond the grid.
+// The band sum is built band by band over each band's support only (a row
+// buffer in shared memory, bands in order, so each v[n] sums its bands in
+// the same order as a per-wavelength loop would), then the dust factor is
+// applied once per wavelength.
 __global__ void __launch_bounds__(256)
 k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
              const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
              const float* __restrict__ gbar, float* __restrict__ V, uint16_t* __restrict__ Vbf,
              float* __restrict__ Vlo) {
+    extern __shared__ float ssum[];                // [lam_pad]
     __shared__ float gb[kMaxBands];
     __shared__ int2 sp[kMaxBands];
     __shared__ float2 gg[kMaxBands];
@@ -318,28 +323,34 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
         sp[threadIdx.x] = g.support[gi * B + threadIdx.x];
         gg[threadIdx.x] = g.gauss[gi * B + threadIdx.x];
     }
+    for (int nn = threadIdx.x; nn < c.lam_pad; nn += blockDim.x) ssum[nn] = 0.0f;
     __syncthreads();
+    for (int b = 0; b < B; ++b) {
+        const float gbb = gb[b];
+        if (gbb == 0.0f) continue;                 // block-uniform
+        const int kind = c.band_kind[b];
+        const int lo = sp[b].x, hi = min(sp[b].y, c.n_lam);
+        const float2 gp = gg[b];
+        for (int nn = lo + threadIdx.x; nn < hi; nn += blockDim.x) {
+            float wb = __ldg(&grid.lamc[nn].x);
+            if (kind == 1) {
+                const float u = (__ldg(grid.lam + nn) - gp.x) * gp.y;
+                wb *= __expf(-0.5f * u * u);
+            } else if (kind == 2) {
+                wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (__ldg(grid.lam + nn) - gp.x) * -gp.y);
+            }
+            ssum[nn] = fmaf(gbb, wb, ssum[nn]);
+        }
+        __syncthreads();
+    }
     const float* t = theta + row * SPS_NPARAM;
     const float AV = t[9], dl = t[10], ff = t[11];
     for (int nn = threadIdx.x; nn < c.lam_pad; nn += blockDim.x) {
+        const float sum = ssum[nn];
         float v = 0.0f;
-        if (nn < c.n_lam) {
+        if (sum != 0.0f) {
             const float4 L4 = grid.lamc[nn];
-            const float lam = grid.lam[nn];
-            float sum = 0.0f;
-            for (int b = 0; b < B; ++b) {
-                if (gb[b] != 0.0f && nn >= sp[b].x && nn < sp[b].y) {
-                    float wb = L4.x;
-                    if (c.band_kind[b] == 1) {
-                        float u = (lam - gg[b].x) * gg[b].y;
-                        wb *= __expf(-0.5f * u * u);
-                    } else if (c.band_kind[b] == 2) {
-                        wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (lam - gg[b].x) * -gg[b].y);
-                    }
-                    sum = fmaf(gb[b], wb, sum);
-                }
-            }
-            if (sum != 0.0f) v = dust_eval(L4.y, L4.z, L4.w, AV, dl, ff).F * sum;
+            v = dust_eval(L4.y, L4.z, L4.w, AV, dl, ff).F * sum;
         }
         if (Vbf) {
             Vbf[row * c.lam_pad + nn] = f_to_bf16(v);
@@ -547,7 +558,12 @@ cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies&
                               const float* theta, const int32_t* gal_idx, int64_t n,
                               const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s, float* V32lo) {
     if (n <= 0) return cudaSuccess;
-    k_exact_vgen<<<(unsigned)n, 256, 0, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32, Vbf, V32lo);
+    const size_t smem = sizeof(float) * (size_t)c.lam_pad;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_exact_vgen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_exact_vgen<<<(unsigned)n, 256, smem, s>>>(c, grid, g, theta, gal_idx, n, gbar, V32, Vbf, V32lo);
     return cudaGetLastError();
 }
 
