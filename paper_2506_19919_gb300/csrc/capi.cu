@@ -616,10 +616,10 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                 TcMaps tm;
                 const bool ok = tf ? (make_tmap_f32(&tm.a[0], ctx->V.p, c.lam_pad, m, c.lam_pad, 128) &&
                                       make_tmap_f32(&tm.a[1], ctx->Vlo.p, c.lam_pad, m, c.lam_pad, 128) &&
-                                      make_tmap_f32(&tm.b[0], ctx->ssp_hi.p, c.lam_pad, c.K, c.lam_pad, 192) &&
-                                      make_tmap_f32(&tm.b[1], ctx->ssp_lo.p, c.lam_pad, c.K, c.lam_pad, 192))
+                                      make_tmap_f32(&tm.b[0], ctx->ssp_hi.p, c.lam_pad, c.K, c.lam_pad, 224) &&
+                                      make_tmap_f32(&tm.b[1], ctx->ssp_lo.p, c.lam_pad, c.K, c.lam_pad, 224))
                                    : (make_tmap_bf16(&tm.a[0], ctx->V.p, c.lam_pad, m, c.lam_pad, 128) &&
-                                      make_tmap_bf16(&tm.b[0], ctx->ssp_bf.p, c.lam_pad, c.K, c.lam_pad, 192));
+                                      make_tmap_bf16(&tm.b[0], ctx->ssp_bf.p, c.lam_pad, c.K, c.lam_pad, 224));
                 if (!ok) return fail(SPS_E_CUDA, "tensor map encoding failed");
                 if (!tf) tm.a[1] = tm.a[0], tm.b[1] = tm.b[0];
                 CK(launch_adj_tc(tm, tf, c, grid, m, ctx->Wbar.as<float>(), terr, s));

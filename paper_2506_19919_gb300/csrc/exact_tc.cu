@@ -36,7 +36,7 @@ constexpr int kFwdGroupBands = 8; // forward: bands per epilogue warp
 constexpr int kFwdMaxEpiWarps = 16;
 constexpr int kFwdBN = 256;
 constexpr int kFwdStages = 4;    // BF16 ring depth (TF32: 2; four tiles per stage)
-constexpr int kAdjBN = 192;
+constexpr int kAdjBN = 224;      // K = 1344 = 6 x 224: each 128-row block streams V six times
 constexpr int kAdjStages = 5;    // BF16 ring depth (TF32: 2)
 constexpr uint32_t kTmemCols = 512;
 
