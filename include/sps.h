@@ -86,7 +86,8 @@ typedef enum { SPS_BAND_TOPHAT = 0, SPS_BAND_GAUSS = 1, SPS_BAND_TABLE = 2 } sps
  *  ssp[n_age*n_met*n_lam] L_SSP[i][j][n] in L_sun/Hz per solar mass formed
  *  band_kind[n_band], band_p0, band_p1: observed-frame filters;
  *    TOPHAT: transmission 1 on [p0, p1) Angstrom;
- *    GAUSS:  transmission exp(-(l - p0)^2 / (2 s^2)), s = p1 / (2 sqrt(2 ln 2)) (p1 = FWHM);
+ *    GAUSS:  transmission exp(-(l - p0)^2 / (2 s^2)), s = p1 / (2 sqrt(2 ln 2)) (p1 = FWHM),
+ *            integrated over |l - p0| < 6 s (the rest is 2e-9 of the band's weight);
  *    TABLE:  a measured throughput curve (Sec. 5 uses LSST's): band_tab_n[b] >= 2
  *            samples T_m >= 0 at l = p0 + m p1 Angstrom (p0 > 0, p1 > 0), the
  *            transmission their linear interpolant, zero outside the samples.
