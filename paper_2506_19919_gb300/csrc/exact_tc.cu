@@ -8,7 +8,7 @@
 // Forward: S[r][n] = sum_k W[r][k] L[k][n] for a 128-row tile and 256-wide
 // wavelength tiles, with the dust x filter reduction over n fused into the
 // epilogue (the SED never reaches HBM).  Adjoint: Wbar[r][k] = sum_n v[r][n]
-// L[k][n] for 128 x 192 tiles.
+// L[k][n] for 128 x 224 tiles.
 //
 // Block of 6 warps, one block per SM: warp 0 issues TMA loads of A and B
 // k-blocks (128-byte rows, 128-byte swizzle) into a ring of stages; one lane
@@ -434,13 +434,31 @@ k_adj_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                 tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kAdjBN + cc * 32), S);
                 const int k0 = nt * kAdjBN + cc * 32;
                 if (live) {
+                    // 16-byte stores (k_pad is a multiple of 64, k0 of 32): a lane
+                    // owns one row, so each store covers half a sector, not an eighth
+                    float* orow = Wbar + row * c.k_pad;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 32; j += 4) {
                         const int k = k0 + j;
-                        if (k < c.K) {
-                            float* o = Wbar + row * c.k_pad + k;
-                            if (kc == 0) *o = TF ? S[j] : S[j] * __ldg(grid.row_scale + k / c.n_met);
-                            else *o += TF ? S[j] : S[j] * __ldg(grid.row_scale + k / c.n_met);
+                        float v[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            v[t] = (TF || k + t >= c.K) ? S[j + t] : S[j + t] * __ldg(grid.row_scale + (k + t) / c.n_met);
+                        if (k + 3 < c.K) {
+                            float4* o = reinterpret_cast<float4*>(orow + k);
+                            if (kc == 0) {
+                                *o = make_float4(v[0], v[1], v[2], v[3]);
+                            } else {
+                                float4 p = *o;
+                                *o = make_float4(p.x + v[0], p.y + v[1], p.z + v[2], p.w + v[3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t)
+                                if (k + t < c.K) {
+                                    if (kc == 0) orow[k + t] = v[t];
+                                    else orow[k + t] += v[t];
+                                }
                         }
                     }
                 }
