@@ -497,13 +497,8 @@ def _loglike_grad_rates(ctx_hmc, dev):
     sg = torch.as_tensor(wl.sigma, dtype=torch.float32, device=dev)
     mk = torch.as_tensor(wl.mask.view(np.int32), device=dev)
     res = {"pairs": wl.n_gal, "workload": W.CONFIG_NAMES[2], "inputs": "device-resident"}
-    for mode, prec, reps in (("approx", "fp32", 10), ("plain", "fp32", 3), ("exact", "fp32", 2),
-                             ("exact", "bf16", 3), ("exact", "tf32x3", 3)):
-        def call():
-            if mode == "plain":
-                ctx.loglike_grad_forward_mode(th, mobs, sg, mk)
-            else:
-                ctx.loglike_grad(th, mobs, sg, mk, mode=mode, prec=prec)
+
+    def timed(call, reps):
         call()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -512,10 +507,42 @@ def _loglike_grad_rates(ctx_hmc, dev):
             call()
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        res[f"{mode}_{prec}"] = {"evals_per_s": wl.n_gal / (ms / 1e3), "ms": ms}
+        return e0.elapsed_time(e1) / reps
+
+    # tensor-core throughput of the exact path: 2 K Lambda FLOP per row and
+    # contraction (the unpadded grid), one contraction for photometry and two
+    # (forward and adjoint) for log L + gradient; BF16 against the measured
+    # BF16 peak, 3xTF32 (three TF32 products per FLOP) against that peak times
+    # the nominal TF32 / BF16 ratio 1.1 / 2.25
+    peaks, src = _peaks()
+    flop_row = 2.0 * wl.tables.n_age * wl.tables.n_met * wl.tables.n_lam
+
+    def tensor(ms, n_gemm, prec):
+        if prec not in ("bf16", "tf32x3"):
+            return {}
+        tf = n_gemm * flop_row * wl.n_gal / (ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else 1.1 / 2.25)
+        return {"tensor_tflops": tf, "tensor_frac": tf * (3.0 if prec == "tf32x3" else 1.0) / peak,
+                "tensor_peak_tflops": peak, "peak_source": src}
+
+    for mode, prec, reps in (("approx", "fp32", 10), ("plain", "fp32", 3), ("exact", "fp32", 2),
+                             ("exact", "bf16", 3), ("exact", "tf32x3", 3)):
+        def call():
+            if mode == "plain":
+                ctx.loglike_grad_forward_mode(th, mobs, sg, mk)
+            else:
+                ctx.loglike_grad(th, mobs, sg, mk, mode=mode, prec=prec)
+        ms = timed(call, reps)
+        res[f"{mode}_{prec}"] = {"evals_per_s": wl.n_gal / (ms / 1e3), "ms": ms, **tensor(ms, 2, prec)}
     res["fused_adjoint_vs_plain_forward_mode"] = (res["approx_fp32"]["evals_per_s"]
                                                   / res["plain_fp32"]["evals_per_s"])
+    # production photometry (magnitudes only) on the same 100,000 galaxies
+    phot = {"galaxies": wl.n_gal}
+    for mode, prec, reps in (("approx", "fp32", 10), ("exact", "fp32", 2), ("exact", "bf16", 5),
+                             ("exact", "tf32x3", 3)):
+        ms = timed(lambda: ctx.photometry(th, mode=mode, prec=prec), reps)
+        phot[f"{mode}_{prec}"] = {"galaxies_per_s": wl.n_gal / (ms / 1e3), "ms": ms, **tensor(ms, 1, prec)}
+    res["photometry"] = phot
     ctx.close()
     return res
 
