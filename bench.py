@@ -453,19 +453,30 @@ def _models(wl, dev):
 
 
 def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
-    """Same metric through the C ABI with host buffers: the call stages the
-    inputs to the device and copies the draws back inside the timed region."""
+    """Same metric through the C ABI with pinned host buffers: the call stages
+    the inputs to the device and copies the draws back inside the timed region."""
     import ctypes as Ct
 
     from paper_2506_19919_gb300 import _lib
+    import torch
     G, C = wl.n_gal, wl.chains
     NC = G * C
-    x0 = np.ascontiguousarray(x0_dev.cpu().numpy())
-    mobs = np.ascontiguousarray(mobs_dev.cpu().numpy())
-    sigma = np.ascontiguousarray(wl.sigma.astype(np.float32))
-    mask = np.ascontiguousarray(wl.mask)
-    samples = np.empty((NC, cfg.n_samp, 12), np.float32)
-    acc = np.empty(NC, np.float32)
+    keep = []                                     # the pinned tensors behind the arrays
+
+    def pinned(shape, dtype, src=None):
+        t = torch.empty(shape, dtype=dtype, pin_memory=True)
+        keep.append(t)
+        a = t.numpy()
+        if src is not None:
+            a[...] = src
+        return a
+
+    x0 = pinned(tuple(x0_dev.shape), torch.float32, x0_dev.cpu().numpy())
+    mobs = pinned(tuple(mobs_dev.shape), torch.float32, mobs_dev.cpu().numpy())
+    sigma = pinned(wl.sigma.shape, torch.float32, wl.sigma)
+    mask = pinned(wl.mask.shape, torch.int32, wl.mask.view(np.int32)).view(np.uint32)
+    samples = pinned((NC, cfg.n_samp, 12), torch.float32)
+    acc = pinned((NC,), torch.float32)
     st = _lib.sps_hmc_stats(acc.ctypes.data, None, None, None, None)
     vp = lambda a: Ct.c_void_p(a.ctypes.data)
     times = []
