@@ -154,7 +154,28 @@ sps_status sps_config_default(sps_config* cfg);
 
 /* Create a context on cfg->device: validates and uploads the tables (FP32,
  * BF16 row-scaled and per-wavelength dust constants).  On success *out owns
- * device memory until sps_destroy.  Sec. 2 (fixed SSP library), App. A.3. */
+ * device memory until sps_destroy.  Sec. 2 (fixed SSP library), App. A.3.
+ * cfg may be NULL (the defaults).  The tables are read, not kept.
+ * Errors (*out stays NULL; sps_last_error_message() names the failed check).
+ * Every table and config check runs on the host before any device work:
+ *   SPS_E_SHAPE       n_age outside [2, 128], n_met outside [1, 32],
+ *                     n_lam < 2, n_band outside [1, 32], n_age * n_met > 1312;
+ *   SPS_E_INVALID_ARG a NULL pointer; a grid that is not positive and
+ *                     increasing (ages, wavelengths) or not increasing (lgZ);
+ *                     an SSP value that is negative or not finite; a bad band
+ *                     (unknown kind, top-hat without 0 < p0 < p1, Gaussian
+ *                     without positive centre and FWHM, tabulated without
+ *                     start > 0, step > 0, 2..2^20 finite samples >= 0);
+ *                     an mdf_offset that is not finite or exceeds 10 dex;
+ *                     a config field out of range (sfh_gl_order, sfh_panel or
+ *                     a panel too small for the panel budget, H0 <= 0,
+ *                     Omega_m outside (0, 1), prior_hi <= prior_lo,
+ *                     sigmoid_k <= 0 or not finite, sigmoid_x0 not finite,
+ *                     an unknown prior, and for the skew-normal prior
+ *                     omega <= 0 or a parameter that is not finite);
+ *   SPS_E_UNSUPPORTED no CUDA device, or one older than sm_100;
+ *   SPS_E_INVALID_ARG a device ordinal out of range;
+ *   SPS_E_CUDA / SPS_E_NOMEM a failed device call or allocation. */
 sps_status sps_create(sps_ctx** out, const sps_tables* tables, const sps_config* cfg);
 sps_status sps_destroy(sps_ctx* ctx);
 
