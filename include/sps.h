@@ -329,6 +329,23 @@ sps_status sps_weights(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
 sps_status sps_diagnostics(const float* samples, int64_t n_gal, int32_t chains_per_gal,
                            int32_t n_draws, int32_t n_param, double* ess_out, double* rhat_out);
 
+/* Host-side split of a galaxy catalogue over n_parts processes (one per GPU).
+ * Galaxies are independent units (Sec. 4 fits them in parallel with no
+ * exchange), so the split is into contiguous blocks; a galaxy weighs
+ * base_weight plus its observed bands (the set bits of mask[g]), the part of
+ * an evaluation's cost that varies between galaxies, and the heaviest block is
+ * made as light as possible (exact for these integer weights).  While
+ * n_gal >= n_parts every block holds at least one galaxy; with fewer galaxies
+ * each has its own block and the trailing blocks are empty.  If every weight
+ * is 0 the counts are balanced.
+ *   mask        host [n_gal] band bitmasks, or NULL (weights base_weight)
+ *   starts_out  host [n_parts + 1]: block p is galaxies [starts_out[p],
+ *               starts_out[p + 1]); starts_out[0] = 0, starts_out[n_parts] = n_gal
+ * Errors: SPS_E_INVALID_ARG (starts_out NULL, base_weight < 0), SPS_E_SHAPE
+ * (n_gal < 0, n_parts < 1).  No device work. */
+sps_status sps_partition_galaxies(const uint32_t* mask, int64_t n_gal, int32_t base_weight, int32_t n_parts,
+                                  int64_t* starts_out);
+
 /* Sizes and a few derived quantities of a context (host integers). */
 typedef struct {
     int32_t n_age, n_met, n_lam, n_band, k_pad;

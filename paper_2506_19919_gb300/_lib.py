@@ -79,6 +79,7 @@ _PROTOS = {
     "sps_philox": (C.c_int, [_P, _P, C.c_int64, C.c_uint64, _P, _P]),
     "sps_weights": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "sps_diagnostics": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
+    "sps_partition_galaxies": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "sps_get_info": (C.c_int, [_P, C.POINTER(sps_info)]),
     "sps_gl_rule": (C.c_int, [_P, _P, _P]),
     "sps_photometry_exact_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P]),
