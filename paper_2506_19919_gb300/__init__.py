@@ -36,9 +36,20 @@ def _stream(t):
     return None
 
 
-def _f32(x, device):
+def _f32(x, device=None):
+    """x as a contiguous float32 tensor on `device` (a tensor's own device when
+    None); a tensor that already is one is returned as it is, without a copy."""
     t = torch.as_tensor(x)
-    return t.to(device=device, dtype=torch.float32).contiguous()
+    return t.to(device=t.device if device is None else device, dtype=torch.float32).contiguous()
+
+
+def _mask32(mask, device):
+    """Band bitmasks as a contiguous int32 tensor holding the uint32 bits."""
+    if isinstance(mask, torch.Tensor):
+        if mask.dtype != torch.int32:
+            mask = torch.as_tensor(np.asarray(mask.cpu().numpy(), dtype=np.int64).astype(np.uint32).view(np.int32))
+        return mask.to(device).contiguous()
+    return torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(device).contiguous()
 
 
 class Context:
@@ -133,7 +144,7 @@ class Context:
 
     # ------------------------------------------------------------------ compute
     def photometry(self, theta, gal_idx=None, mode="exact", prec="fp32", out=None):
-        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        th = _f32(theta, None if isinstance(theta, torch.Tensor) else self.device)
         n = th.shape[0]
         if out is None:
             out = torch.empty((n, self.n_band), dtype=torch.float32, device=th.device)
@@ -145,13 +156,12 @@ class Context:
 
     def loglike_grad(self, theta, mag_obs, sigma, mask, gal_idx=None, mode="approx",
                      prec="fp32", grad=True):
-        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        th = _f32(theta, None if isinstance(theta, torch.Tensor) else self.device)
         dev = th.device
         n = th.shape[0]
         mo = _f32(mag_obs, dev)
         sg = _f32(sigma, dev)
-        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
-            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        mk = _mask32(mask, dev)
         gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
                                                              device=dev).contiguous()
         ll = torch.empty(n, dtype=torch.float32, device=dev)
@@ -163,13 +173,12 @@ class Context:
 
     def loglike_grad_forward_mode(self, theta, mag_obs, sigma, mask, gal_idx=None):
         """The plain forward-mode comparison path (approximate photometry)."""
-        th = theta if isinstance(theta, torch.Tensor) else _f32(theta, self.device)
+        th = _f32(theta, None if isinstance(theta, torch.Tensor) else self.device)
         dev = th.device
         n = th.shape[0]
         mo = _f32(mag_obs, dev)
         sg = _f32(sigma, dev)
-        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
-            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        mk = _mask32(mask, dev)
         gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
                                                              device=dev).contiguous()
         ll = torch.empty(n, dtype=torch.float32, device=dev)
@@ -188,12 +197,11 @@ class Context:
         path="fused" runs the persistent sampler (sps_hmc_run); path="plain"
         the lock-step forward-mode comparison baseline (sps_hmc_run_forward_mode,
         HMC with the identity metric only)."""
-        x0 = theta0_unb if isinstance(theta0_unb, torch.Tensor) else _f32(theta0_unb, self.device)
+        x0 = _f32(theta0_unb, None if isinstance(theta0_unb, torch.Tensor) else self.device)
         dev = x0.device
         mo = _f32(mag_obs, dev)
         sg = _f32(sigma, dev)
-        mk = torch.as_tensor(np.asarray(mask, dtype=np.uint32).view(np.int32)).to(dev).contiguous() \
-            if not isinstance(mask, torch.Tensor) else mask.to(dev).contiguous()
+        mk = _mask32(mask, dev)
         nc = x0.shape[0]
         cfg = sps_hmc_config()
         check(self._lib.sps_hmc_config_default(C.byref(cfg)), "sps_hmc_config_default")
