@@ -572,6 +572,7 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
     x0 = wl.extra["theta0_unb"][: n * wl.chains]
     it_total = wl.extra["n_warm"] + wl.extra["n_samp"]
     t0 = time.perf_counter()
+    c0 = time.process_time()
     iters = 0
     while True:
         OH.run_hmc(tgt, x0, np.repeat(np.arange(n), wl.chains), seed=1, n_warm=1, n_samp=0,
@@ -579,10 +580,13 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
         iters += 1
         if time.perf_counter() - t0 > budget_s or iters >= 50:
             break
-    dt = (time.perf_counter() - t0) / iters          # s per iteration for n galaxies
+    wall = time.perf_counter() - t0
+    cores_used = (time.process_time() - c0) / wall   # CPU seconds per wall second of the sample
+    dt = wall / iters                                 # s per iteration for n galaxies
     s_per_gal = dt * it_total / n
     value = post_frac * 60.0 / s_per_gal
-    return {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": round(cores_used, 2),
+            "threads_available": torch.get_num_threads(), "kind": "oracle",
             "sample": f"{n} galaxies x {wl.chains} chains x {iters} iterations of the FP64 "
                       f"oracle HMC ({dt:.2f} s/iteration), extrapolated to {it_total} iterations "
                       f"per galaxy; " + ("ESS fraction taken as 1, an upper bound for the oracle"
