@@ -171,6 +171,17 @@ def _hmc_workload(rank: int, n_gal: int | None = None, iters=None):
     return wl
 
 
+def _config(tables, G, C, n_warm, n_samp, L, sampler, mdf_age, ws):
+    """The workload description of the bench line (both arms)."""
+    return {"workload": W.CONFIG_NAMES[3], "galaxies": G, "chains_per_gal": C,
+            "n_warm": n_warm, "n_samp": n_samp, "L": list(L),
+            "ssp_grid": [tables.n_age, tables.n_met, tables.n_lam],
+            "bands": tables.n_band, "photometry": "approx", "sampler": sampler,
+            "mdf": "age-dependent" if mdf_age else "separable",
+            "l2": "flushed (256 MB write) between timed steps; working set > L2",
+            "parallelism": f"replicas{ws}"}
+
+
 def run_ours(args):
     import torch
 
@@ -259,13 +270,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": W.CONFIG_NAMES[3], "galaxies": G, "chains_per_gal": C,
-                   "n_warm": n_warm, "n_samp": n_samp, "L": [cfg.L_min, cfg.L_max],
-                   "ssp_grid": [wl.tables.n_age, wl.tables.n_met, wl.tables.n_lam],
-                   "bands": wl.tables.n_band, "photometry": "approx", "sampler": args.sampler,
-                   "mdf": "age-dependent" if args.mdf_age else "separable",
-                   "l2": "flushed (256 MB write) between timed steps; working set > L2",
-                   "parallelism": f"replicas{ws}"},
+        "config": _config(wl.tables, G, C, n_warm, n_samp, (cfg.L_min, cfg.L_max), args.sampler,
+                          args.mdf_age, ws),
         "ess": {"target": ESS_TARGET, "galaxies_at_target": int((ess_g >= ESS_TARGET).sum()),
                 "median_ess": float(np.median(ess_g)), "median_rhat_max": float(np.median(rhat.max(1))),
                 "frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean()),
@@ -700,6 +706,7 @@ def run_reference(args):
         return
     import torch
     wl = _hmc_workload(0, n_gal=2)
+    full = _hmc_workload(0)                  # the workload the sample stands for (its description only)
     from oracle import sps as O
     mobs = O.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float64), wl.z, wl.tables,
                         "approx").numpy() + wl.noise
@@ -714,8 +721,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": W.CONFIG_NAMES[3], "photometry": "approx",
-                      "note": "ESS fraction assumed 1 per galaxy (upper bound for the oracle)"},
+           "config": _config(full.tables, full.n_gal, full.chains, full.extra["n_warm"], full.extra["n_samp"],
+                             (full.extra["L_min"], full.extra["L_max"]), "hmc", False, ws),
+           "note": "ESS fraction assumed 1 per galaxy (upper bound for the oracle)",
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
