@@ -211,11 +211,22 @@ def test_dust_identities_and_normalisation():
     for av, dl, ff in ((0.0, -0.5, 0.2), (2.0, 0.3, 1.0)):
         F = O.attenuation(lam, av * one, dl * one, ff * one)
         torch.testing.assert_close(F, torch.ones_like(F), rtol=0, atol=0)
-    # the Calzetti curve is normalised so that A(V) ~= A_V (k'(V) = R_V)
+    # the Calzetti curve is normalised so that A(V) ~= A_V, with Calzetti et
+    # al.'s (2000) published R_V = 4.05 (k'(V) = R_V)
     k_v = float(O.calzetti_k0(torch.tensor(0.55, dtype=DT)))
-    assert k_v == pytest.approx(O.RV_CALZ, abs=0.01)
+    assert k_v == pytest.approx(4.05, abs=0.01)
     F = O.attenuation(torch.tensor([[5500.0]], dtype=DT), 1.0 * one, 0.0 * one, 0.0 * one)
     assert float(-2.5 * torch.log10(F)) == pytest.approx(1.0, abs=0.01)
+    # its two fitted branches (UV-optical below 0.63 um, red above) meet at
+    # 0.63 um to within 1%, and the curve is small but positive at 2.2 um,
+    # the red end of the fit
+    kb, kr = O.calzetti_k0(torch.tensor([0.63 - 1e-9, 0.63], dtype=DT)).tolist()
+    assert abs(kb - kr) < 0.05
+    assert 0.0 < float(O.calzetti_k0(torch.tensor(2.2, dtype=DT))) < 0.5
+    # the slope change (lambda / lambda_V)^delta pivots at V: A(V) ~= A_V for any delta
+    for dl in (-0.8, -0.3, 0.3, 0.4):
+        F = O.attenuation(torch.tensor([[5500.0]], dtype=DT), 1.0 * one, dl * one, 0.0 * one)
+        assert float(-2.5 * torch.log10(F)) == pytest.approx(1.0, abs=0.005)
     # attenuation decreases with wavelength over the fitted range
     k = O.calzetti_k0(torch.as_tensor(np.geomspace(0.12, 2.2, 200), dtype=DT))
     assert (k[1:] < k[:-1]).all()
