@@ -16,6 +16,21 @@ from oracle import sps as O
 DT = torch.float64
 
 
+# ---------------------------------------------------------------- constants
+def test_physical_constants_against_independent_sources():
+    """The oracle's unit constants, against SciPy's CODATA / IAU values and
+    the published definitions they follow (the pins below reuse them)."""
+    from scipy import constants as K
+    assert O.C_KMS == K.c / 1e3                                   # exact by definition
+    assert O.MPC_KM == pytest.approx(K.parsec * 1e6 / 1e3, rel=1e-12)
+    assert O.MPC_CM == pytest.approx(K.parsec * 1e6 * 1e2, rel=1e-12)
+    assert O.GYR_S == pytest.approx(1e9 * K.Julian_year, rel=1e-15)
+    assert O.AB_ZP_CGS == pytest.approx(3631 * 1e-26 * 1e3, rel=1e-15)   # 3631 Jy; 1 Jy = 1e-26 W/m^2/Hz
+    assert O.L_SUN_ERG_S == pytest.approx(3.828e26 * 1e7, rel=1e-15)      # IAU 2015 B3 nominal, W -> erg/s
+    # the Hubble time 977.8 / H0 Gyr (H0 in km/s/Mpc)
+    assert O.hubble_time_gyr() == pytest.approx(977.792 / 70.0, rel=1e-5)
+
+
 # ---------------------------------------------------------------- cosmology
 def test_cosmic_age_matches_time_integral():
     th = O.hubble_time_gyr()
