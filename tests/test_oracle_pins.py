@@ -249,9 +249,10 @@ def test_dust_identities_and_normalisation():
     d = O.drude_shape(torch.as_tensor(np.linspace(0.15, 0.3, 300001), dtype=DT))
     lam_um = np.linspace(0.15, 0.3, 300001)
     assert float(d.max()) == pytest.approx(1.0, abs=1e-9)
-    assert lam_um[int(d.argmax())] == pytest.approx(O.DRUDE_L0_UM, abs=1e-6)
+    # the 2175 A bump of the cited dust literature: centre 2175 A, width 350 A
+    assert lam_um[int(d.argmax())] == pytest.approx(0.2175, abs=1e-6)
     above = lam_um[(d >= 0.5).numpy()]
-    assert above[-1] - above[0] == pytest.approx(O.DRUDE_DL_UM, rel=0.01)
+    assert above[-1] - above[0] == pytest.approx(0.035, rel=0.01)
 
 
 # ---------------------------------------------------------------- filter integrals
