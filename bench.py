@@ -729,7 +729,7 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def main():
+def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -756,7 +756,11 @@ def main():
                     help="throughput on the 1,000,000-galaxy survey batch (not the bench line)")
     ap.add_argument("--loglike-only", default=None,
                     help="comma list of mode_prec (e.g. exact_bf16,approx_fp32)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = _parser().parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.warm is not None and args.samp is None:
