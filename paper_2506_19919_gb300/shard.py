@@ -20,11 +20,9 @@ def partition_galaxies(mask, n_parts: int, base_weight: int = 0) -> np.ndarray:
     starts[p]:starts[p + 1].  A galaxy weighs base_weight (the fixed part of
     its cost, in units of one observed band's share) plus its observed bands;
     the heaviest block is made as light as possible.  mask: [n_gal] uint32
-    band bitmasks, or None to weigh every galaxy base_weight (counts are
-    balanced when every weight is 0)."""
+    band bitmasks (all zero: every galaxy weighs base_weight, and the counts
+    are balanced when every weight is 0)."""
     lib = load()
-    if mask is None:
-        raise ValueError("mask is required (use np.zeros(n_gal, np.uint32) to balance the counts)")
     m = np.ascontiguousarray(np.asarray(mask), dtype=np.uint32)
     starts = np.zeros(int(n_parts) + 1 if n_parts >= 1 else 1, np.int64)
     check(lib.sps_partition_galaxies(C.c_void_p(m.ctypes.data), m.shape[0], int(base_weight),
@@ -43,12 +41,13 @@ def gather_blocks(local, dst: int = 0, group=None):
     """Host-side gather of per-galaxy results: every process passes its
     block's array (leading axis = its galaxies, any trailing shape); process
     dst receives the blocks concatenated in rank order, i.e. in catalogue
-    order, the others None.  Uses torch.distributed's object gather, so with
-    the NCCL backend each process must have selected its device first."""
+    order, the others None.  dst is a global rank (a member of group).  Uses
+    torch.distributed's object gather, so with the NCCL backend each process
+    must have selected its device first."""
     import torch.distributed as dist
     arr = np.asarray(local)
     world = dist.get_world_size(group)
-    rank = dist.get_rank(group)
+    rank = dist.get_rank()
     parts = [None] * world if rank == dst else None
     dist.gather_object(arr, parts, dst=dst, group=group)
     if rank != dst:
