@@ -57,7 +57,9 @@ def philox4x32_10(ctr, key):
     ctr: [..., 4] integers < 2^32, key: [..., 2].  Each round multiplies
     words 0 and 2 by M0, M1 (64-bit products), mixes the high halves with
     words 1, 3 and the key, and the key is bumped by the Weyl constants
-    between rounds.  Returns [..., 4] uint64 holding 32-bit words."""
+    between rounds.  Returns [..., 4] uint64 holding 32-bit words.  Pinned
+    word for word to an independent implementation of the generator (Triton's,
+    run on the CPU) and its Weyl constants to their definitions."""
     c = [np.asarray(ctr[..., i], dtype=np.uint64) & _MASK32 for i in range(4)]
     k0 = np.asarray(key[..., 0], dtype=np.uint64) & _MASK32
     k1 = np.asarray(key[..., 1], dtype=np.uint64) & _MASK32

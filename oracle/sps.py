@@ -23,7 +23,13 @@ M_star; burst and metallicity weights summing to one; F_burst limits; A_V = 0
 and F_floor = 1 identities; single-age single-Z magnitudes equal to the
 directly filter-integrated SSP; flat-f_nu sources giving the AB zero point;
 approximate photometry converging to exact as the bands narrow; gradient
-against central differences.
+against central differences; lambda_eff equal to the band centre over (1+z)
+for a Gaussian band at R = 3.4 and the mid-point for a top-hat (rejecting the
+photon-weighted variant); the Calzetti curve's k'(V) = R_V, k'(B) - k'(V) = 1
+and the signed 0.025 mismatch of its published branches at 0.63 um; the
+bump strength read back out of the attenuation curve at 2175 A as
+0.85 - 1.9 delta.  Each of the last three also fails on a mistake planted in
+this module.
 """
 from __future__ import annotations
 
@@ -49,8 +55,13 @@ AB_ZP_CGS = 3631e-23          # 3631 Jy in erg/s/cm^2/Hz
 # cited literature: Calzetti et al. 2000, Kriek & Conroy 2013 bump-slope).
 LAMBDA_V_UM = 0.55
 RV_CALZ = 4.05
+CALZ_SCALE = 2.659
+CALZ_BLUE = (-2.156, 1.509, -0.198, 0.011)   # coefficients of 1, 1/lam, 1/lam^2, 1/lam^3
+CALZ_RED = (-1.857, 1.040)                    # coefficients of 1, 1/lam
+CALZ_SPLIT_UM = 0.63
 DRUDE_L0_UM = 0.2175
 DRUDE_DL_UM = 0.035
+BUMP_E0, BUMP_E1 = 0.85, -1.9                 # E_b = E0 + E1 delta (Kriek & Conroy 2013)
 
 
 def _t(x):
@@ -268,9 +279,11 @@ def calzetti_k0(lam_um):
     """Calzetti et al. (2000) starburst curve k'(lambda) with R_V = 4.05,
     both branches extrapolated outside 0.12-2.2 um and clamped at zero."""
     lam = _t(lam_um)
-    blue = 2.659 * (-2.156 + 1.509 / lam - 0.198 / lam ** 2 + 0.011 / lam ** 3) + RV_CALZ
-    red = 2.659 * (-1.857 + 1.040 / lam) + RV_CALZ
-    return torch.clamp(torch.where(lam < 0.63, blue, red), min=0.0)
+    b0, b1, b2, b3 = CALZ_BLUE
+    r0, r1 = CALZ_RED
+    blue = CALZ_SCALE * (b0 + b1 / lam + b2 / lam ** 2 + b3 / lam ** 3) + RV_CALZ
+    red = CALZ_SCALE * (r0 + r1 / lam) + RV_CALZ
+    return torch.clamp(torch.where(lam < CALZ_SPLIT_UM, blue, red), min=0.0)
 
 
 def drude_shape(lam_um):
@@ -278,6 +291,13 @@ def drude_shape(lam_um):
     lam = _t(lam_um)
     x = (lam * DRUDE_DL_UM) ** 2
     return x / ((lam ** 2 - DRUDE_L0_UM ** 2) ** 2 + x)
+
+
+def bump_strength(delta):
+    """UV-bump amplitude tied to the slope tilt, E_b = 0.85 - 1.9 delta
+    (Kriek & Conroy 2013), clamped at zero (App. A.3 names the Drude bump
+    without its strength: a declared convention)."""
+    return torch.clamp(BUMP_E0 + BUMP_E1 * delta, min=0.0)
 
 
 def attenuation(lam_ang, A_V, delta, F_floor):
@@ -288,7 +308,7 @@ def attenuation(lam_ang, A_V, delta, F_floor):
     lam_ang broadcasts against the parameter tensors."""
     lam_um = lam_ang * 1e-4
     k0 = calzetti_k0(lam_um)
-    eb = torch.clamp(0.85 - 1.9 * delta, min=0.0)
+    eb = bump_strength(delta)
     A = (A_V / RV_CALZ) * (k0 * (lam_um / LAMBDA_V_UM) ** delta + eb * drude_shape(lam_um))
     return F_floor + (1.0 - F_floor) * 10.0 ** (-0.4 * A)
 

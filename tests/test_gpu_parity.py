@@ -161,11 +161,15 @@ def test_philox_matches_oracle_bit_exact(parity64):
     _, ctx = parity64
     rng = np.random.default_rng(0)
     ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
-    key = 0x1234_5678_9ABC_DEF0
-    out = ctx.philox(ctr, key)
-    ref = OH.philox4x32_10(ctr.astype(np.uint64), np.tile(
-        np.array([key & 0xFFFFFFFF, key >> 32], np.uint64), (4096, 1)))
-    np.testing.assert_array_equal(out.astype(np.uint64), ref)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    # the all-zero and all-ones counter and key, and random ones (the
+    # oracle's generator is itself held to an independent implementation)
+    for key in (0, 0xFFFF_FFFF_FFFF_FFFF, 0x1234_5678_9ABC_DEF0):
+        out = ctx.philox(ctr, key)
+        ref = OH.philox4x32_10(ctr.astype(np.uint64), np.tile(
+            np.array([key & 0xFFFFFFFF, key >> 32], np.uint64), (4096, 1)))
+        np.testing.assert_array_equal(out.astype(np.uint64), ref)
 
 
 def test_bounded_wait_times_out_and_the_context_stays_usable(parity64):

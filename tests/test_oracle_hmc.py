@@ -32,6 +32,65 @@ def test_philox_words_are_uniform_and_decorrelated():
     assert abs(flips.mean() - 64.0) < 0.5
 
 
+def _triton_philox(keys, ctrs):
+    """Philox-4x32-10 words from Triton's implementation of the generator,
+    run by its CPU interpreter in a child process (see philox_triton_ref)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    pytest.importorskip("triton")
+    here = os.path.dirname(os.path.abspath(__file__))
+    job = json.dumps({"keys": [[int(a) for a in k] for k in keys],
+                      "ctrs": [[int(a) for a in c] for c in ctrs]})
+    r = subprocess.run([sys.executable, os.path.join(here, "philox_triton_ref.py")],
+                       input=job, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return np.asarray(json.loads(r.stdout), dtype=np.uint64).reshape(len(keys), len(ctrs), 4)
+
+
+def _philox_disagreement(keys, ctrs, ref):
+    out = np.stack([H.philox4x32_10(np.asarray(ctrs, np.uint64),
+                                    np.tile(np.asarray(k, np.uint64), (len(ctrs), 1)))
+                    for k in keys])
+    return int((out != ref).sum())
+
+
+def test_philox_matches_an_independent_implementation(monkeypatch):
+    """The oracle's Philox-4x32-10 equals, word for word, the generator as
+    Triton implements it (run on the CPU by Triton's interpreter), on the
+    all-zero and all-ones counter and key and on 256 random counters under
+    four random keys.  A wrong multiplier, Weyl key increment or output
+    word order, planted in the oracle, changes the words."""
+    rng = np.random.default_rng(20110101)
+    M = 0xFFFFFFFF
+    ctrs = np.concatenate([[[0, 0, 0, 0], [M, M, M, M]],
+                           rng.integers(0, 2 ** 32, (254, 4), dtype=np.uint64)])
+    keys = np.concatenate([[[0, 0], [M, M]], rng.integers(0, 2 ** 32, (4, 2), dtype=np.uint64)])
+    ref = _triton_philox(keys, ctrs)
+    assert _philox_disagreement(keys, ctrs, ref) == 0
+    for name, val in (("PHILOX_M0", H.PHILOX_M0 ^ 4), ("PHILOX_M1", H.PHILOX_M1 + 2),
+                      ("PHILOX_W0", H.PHILOX_W0 + 1), ("PHILOX_W1", H.PHILOX_W1 ^ 0x100)):
+        with monkeypatch.context() as m:
+            m.setattr(H, name, val)
+            assert _philox_disagreement(keys, ctrs, ref) > 0.9 * ref.size
+    swapped = H.philox4x32_10
+    with monkeypatch.context() as m:
+        m.setattr(H, "philox4x32_10", lambda c, k: swapped(c, k)[..., [1, 0, 3, 2]])
+        assert _philox_disagreement(keys, ctrs, ref) > 0.9 * ref.size
+
+
+def test_philox_weyl_increments_from_their_definition():
+    """Salmon et al. (2011) bump the Philox key by the golden ratio and by
+    sqrt(3) - 1, each as a 32-bit fixed-point fraction."""
+    import decimal
+    decimal.getcontext().prec = 60
+    phi = (1 + decimal.Decimal(5).sqrt()) / 2
+    s3 = decimal.Decimal(3).sqrt()
+    assert H.PHILOX_W0 == int((phi - 1) * (1 << 32))
+    assert H.PHILOX_W1 == int((s3 - 1) * (1 << 32))
+
+
 def test_momentum_and_length_draws():
     p, u, L = H.draws(99, np.arange(4000), 3, 8, 64)
     assert p.shape == (4000, 12)

@@ -255,6 +255,91 @@ def test_dust_identities_and_normalisation():
     assert above[-1] - above[0] == pytest.approx(0.035, rel=0.01)
 
 
+def _calzetti_join_gap():
+    """k' just below minus k' at the 0.63 um join of the two fitted branches."""
+    kb, kr = O.calzetti_k0(torch.tensor([0.63 - 1e-12, 0.63], dtype=DT)).tolist()
+    return kb - kr
+
+
+def _calzetti_colour_normalisation():
+    """k'(B) - k'(V), which is 1 by the definition k' = A / E(B - V) at the
+    B (4400 A) and V (5500 A) points of the fit."""
+    kB, kV = O.calzetti_k0(torch.tensor([0.44, 0.55], dtype=DT)).tolist()
+    return kB - kV
+
+
+def test_calzetti_branches_against_their_defining_properties(monkeypatch):
+    """Calzetti et al. (2000) give k'(lambda) as two fitted branches that
+    meet at 0.63 um, normalised so that k'(V) = R_V = 4.05 and
+    k'(B) - k'(V) = 1 (k' = A / E(B - V)).  With the published, rounded
+    coefficients the red branch starts 0.025 above the blue one at the join;
+    the red branch is pinned by that signed mismatch, which moves by 0.044-
+    0.049 for a 1% change of either red coefficient and by 0.0055 for a 1%
+    change of the common 2.659 factor on the red branch alone.  The red
+    branch is linear in 1/lambda and reaches zero beyond the fitted 2.2 um."""
+    assert -0.028 < _calzetti_join_gap() < -0.022
+    assert _calzetti_colour_normalisation() == pytest.approx(1.0, abs=0.02)
+    assert float(O.calzetti_k0(torch.tensor(0.55, dtype=DT))) == pytest.approx(4.05, abs=0.01)
+    inv = np.linspace(1 / 2.2, 1 / 0.63, 7)
+    k = O.calzetti_k0(torch.as_tensor(1 / inv, dtype=DT)).numpy()
+    fit = np.polyfit(inv, k, 1)
+    assert np.abs(np.polyval(fit, inv) - k).max() < 1e-12
+    assert fit[0] / -fit[1] > 2.2                    # k' = 0 past the fitted range (in um)
+    # planted mistakes in the oracle's coefficients fail the same pins
+    for red in ((-1.857 * 1.01, 1.040), (-1.857 * 0.99, 1.040),
+                (-1.857, 1.040 * 1.01), (-1.857, 1.040 * 0.99)):
+        with monkeypatch.context() as m:
+            m.setattr(O, "CALZ_RED", red)
+            assert not -0.028 < _calzetti_join_gap() < -0.022
+    with monkeypatch.context() as m:
+        m.setattr(O, "RV_CALZ", 4.05 * 1.01)
+        assert abs(float(O.calzetti_k0(torch.tensor(0.55, dtype=DT))) - 4.05) > 0.01
+
+
+def _bump_fit(delta):
+    """Read the UV-bump strength out of the oracle's attenuation curve as a
+    black box.  Eq. DustAtt gives, at the Drude centre lambda_0 = 2175 A
+    where the unit profile is 1, A(lambda_0) / (A_V / 4.05) =
+    K r^delta + E_b(delta), r = lambda_0 / lambda_V and K = k_0(lambda_0)
+    unknown; with E_b = e0 + e1 delta, a least-squares fit over several delta
+    recovers (K, e0, e1) and the residual of the model."""
+    one = torch.ones(len(delta), 1, dtype=DT)
+    d = torch.as_tensor(delta, dtype=DT)[:, None]
+    F = O.attenuation(torch.tensor([[2175.0]], dtype=DT), 4.05 * one, d, 0.0 * one)
+    y = (-2.5 * torch.log10(F))[:, 0].numpy()
+    r = 0.2175 / 0.55
+    X = np.stack([r ** np.asarray(delta), np.ones(len(delta)), np.asarray(delta)], 1)
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    return coef, np.abs(X @ coef - y).max()
+
+
+def _bump_pin_holds(delta):
+    (K, e0, e1), res = _bump_fit(delta)
+    return (res < 1e-12 and abs(e0 - 0.85) < 1e-9 and abs(e1 + 1.9) < 1e-9
+            and abs(K / float(O.calzetti_k0(torch.tensor(0.2175, dtype=DT))) - 1) < 1e-9)
+
+
+def test_bump_strength_follows_kriek_conroy(monkeypatch):
+    """The bump the oracle's curve carries at 2175 A has the strength of
+    Kriek & Conroy (2013): E_b = 0.85 at the Calzetti slope (delta = 0),
+    falling by 1.9 per unit delta, and no bump once that reaches zero
+    (delta > 0.447).  A sign error, a wrong intercept or the bump moved
+    inside the power-law tilt fails the fit."""
+    dl = np.linspace(-1.0, 0.4, 8)
+    assert _bump_pin_holds(dl)
+    hi = np.linspace(0.45, 1.0, 5)                  # clamp: the continuum alone
+    (_, e0h, e1h), resh = _bump_fit(hi)
+    assert resh < 1e-12 and abs(e0h) < 1e-9 and abs(e1h) < 1e-9
+    for name, val in (("BUMP_E1", 1.9), ("BUMP_E1", -1.9 * 1.01), ("BUMP_E0", 0.85 * 1.01)):
+        with monkeypatch.context() as m:
+            m.setattr(O, name, val)
+            assert not _bump_pin_holds(dl)
+    with monkeypatch.context() as m:               # bump inside the tilt
+        m.setattr(O, "bump_strength", lambda d: (0.85 - 1.9 * d).clamp(min=0)
+                  * (0.2175 / 0.55) ** d)
+        assert not _bump_pin_holds(dl)
+
+
 # ---------------------------------------------------------------- filter integrals
 def test_flat_fnu_source_gives_ab_zero_point():
     tabs = W.config(1, n_gal=1).tables
@@ -320,6 +405,44 @@ def test_redshift_moves_band_to_bluer_rest_wavelength():
     z = torch.tensor([0.0, 0.6, 2.0], dtype=DT)
     le = O.lambda_eff(tabs, z)[:, 0]
     torch.testing.assert_close(le, 8000.0 / (1 + z), rtol=1e-4, atol=0)
+
+
+def _lambda_eff_photon_weighted(tables, z):
+    """A plausible misreading of Eq. lambda_eff, kept here only to show that
+    the pin below tells it apart: the photon-counting 1/lambda weight of the
+    band integrals carried into the effective wavelength."""
+    lam = torch.as_tensor(tables.lam_ang, dtype=DT)
+    q = O.trapezoid_weights(tables.lam_ang)
+    T = O.transmission(tables, (1.0 + z)[:, None] * lam[None, :])
+    return (T * q[None, None, :]).sum(-1) / (T * (q / lam)[None, None, :]).sum(-1)
+
+
+def _lambda_eff_pin(tabs, z):
+    """Largest relative deviation of the oracle's lambda_eff from c / (1+z)
+    (Gaussian band, centre c) and (lo + hi) / 2 / (1+z) (top-hat)."""
+    ref = torch.stack([3600.0 / (1 + z), 6500.0 / (1 + z)], dim=1)
+    rel = ((O.lambda_eff(tabs, z) - ref) / ref).abs()
+    return float(rel[:, 0].max()), float(rel[:, 1].max()), float(rel.min())
+
+
+def test_lambda_eff_is_the_unweighted_band_mean_at_low_resolution(monkeypatch):
+    """Eq. lambda_eff weighs wavelength by the transmission alone.  For a
+    Gaussian band of observed centre c, substituting lambda_obs = (1+z)
+    lambda makes the ratio of integrals exactly c / (1+z) at any width; for
+    a top-hat [lo, hi] it is (lo + hi) / 2 / (1+z).  At the paper's lowest
+    resolution R = 3.4 (App. B) the photon-weighted variant lies 1.6% below
+    (Gaussian) and 1.8% (top-hat), so planting it in the oracle fails."""
+    lam = np.geomspace(91.0, 25000.0, 20000)
+    tabs = W.Tables(np.array([1e7, 5e9]), np.array([-1.0, 0.0]), lam,
+                    np.ones((2, 2, lam.size)), np.array([1, 0], np.int32),
+                    np.array([3600.0, 5000.0]), np.array([3600.0 / 3.4, 8000.0]))
+    z = torch.tensor([0.0, 0.7, 2.1], dtype=DT)
+    gauss_err, hat_err, _ = _lambda_eff_pin(tabs, z)
+    assert gauss_err < 1e-6        # trapezoid on a smooth band: O(h^2)
+    assert hat_err < 1e-3          # discontinuous edges: O(h / width)
+    with monkeypatch.context() as m:
+        m.setattr(O, "lambda_eff", _lambda_eff_photon_weighted)
+        assert _lambda_eff_pin(tabs, z)[2] > 0.01
 
 
 # ---------------------------------------------------------------- approximation (Sec. 3)
