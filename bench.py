@@ -591,8 +591,8 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
     dt = wall / iters                                 # s per iteration for n galaxies
     s_per_gal = dt * it_total / n
     value = post_frac * 60.0 / s_per_gal
-    return {"value": value, "unit": UNIT, "cores": round(cores_used, 2),
-            "threads_available": torch.get_num_threads(), "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
+            "cpu_busy": round(cores_used, 2), "nproc": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} galaxies x {wl.chains} chains x {iters} iterations of the FP64 "
                       f"oracle HMC ({dt:.2f} s/iteration), extrapolated to {it_total} iterations "
                       f"per galaxy; " + ("ESS fraction taken as 1, an upper bound for the oracle"
@@ -759,8 +759,29 @@ def _parser():
     return ap
 
 
+def _launch_ranks(args):
+    """--gpus N outside a launcher: start N ranks of this script on this node
+    with torch.distributed.run (one process per GPU, rendezvous on 127.0.0.1),
+    as the launcher would, and return its exit status."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__),
+           *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     args = _parser().parse_args()
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus < 1:
+        sys.exit("--gpus must be >= 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(_launch_ranks(args))
+    if "WORLD_SIZE" in os.environ and ws != args.gpus:
+        sys.exit(f"--gpus {args.gpus} does not match the launcher's WORLD_SIZE {ws}")
     if args.warmup < 3:
         args.warmup = 3
     if args.warm is not None and args.samp is None:

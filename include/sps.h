@@ -29,7 +29,10 @@
  *    row == galaxy (then n must equal the galaxy count).
  *  - Every array argument may be a host pointer or a device pointer of the
  *    context's device; the library detects which (cudaPointerGetAttributes)
- *    and stages host arrays through its own device buffers.  With device
+ *    and stages host arrays through its own device buffers.  An array in the
+ *    memory of another device gives SPS_E_INVALID_ARG.  Each call makes the
+ *    context's device current and restores the caller's current device before
+ *    it returns.  With device
  *    pointers the call is asynchronous on `stream` (a cudaStream_t, NULL =
  *    legacy default stream); with any host pointer it synchronises `stream`
  *    before returning.  The caller keeps ownership of every array.
@@ -270,9 +273,12 @@ typedef struct {
  * windows (75-iteration initial buffer, slow windows of 25, 50, 100, ...,
  * 50-iteration terminal buffer; regularised variances (covariance) of each
  * window's positions; a dense metric M^-1 = L L^T gives momenta L^-T z).
- * The target is log L (App. D.1) plus the log-Jacobian of the bounding map
- * theta = lo + (hi - lo) / (1 + exp(-x)) (Eq. BoundingFunction, k = 1, x0 = 0),
- * i.e. a prior uniform in each bounded parameter; sampling is in x.
+ * The target is log L (App. D.1) plus the log prior the context's sps_config
+ * selects on the unbounded parameters x, where theta = lo + (hi - lo) /
+ * (1 + exp(-k (x - x0))) (Eq. BoundingFunction with the config's per-parameter
+ * sigmoid_k and sigmoid_x0): by default the log-Jacobian of that map, i.e. a
+ * prior uniform in each bounded parameter, else the skew-normal of
+ * Eq. SkewNormPrior (sps_prior); sampling is in x.
  *  theta0_unb[G*C][12]: start points in unbounded space;
  *  samples_out[G*C][n_samp][12]: bounded (physical) draws, or NULL.
  * Random numbers: Philox-4x32-10 keyed by seed, counter (iteration, block,
@@ -374,10 +380,11 @@ sps_status sps_gl_rule(const sps_ctx* ctx, double* nodes, double* weights);
  * with a message.  theta, gal_idx and mag_out must be device pointers (host
  * arrays would need staging buffers): SPS_E_INVALID_ARG otherwise.  The first
  * call on a device looks the array's device address up (cudaGetSymbolAddress)
- * and should come before any stream capture.  All calls share the array;
+ * and should come before any stream capture (it looks it up again if the
+ * device's context has been reset since).  All calls share the array;
  * calls that overlap on the GPU race.  The call synchronises `stream` to
- * report SPS_E_NONFINITE.  The paper has no counterpart: this is a deployment
- * variant of Eq. photo_integral_exact's evaluation. */
+ * report SPS_E_NONFINITE, and restores the caller's current device.  The
+ * paper has no counterpart. */
 sps_status sps_photometry_exact_noalloc(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
                                         int64_t n, float* mag_out, void* stream);
 

@@ -44,15 +44,21 @@ sps_status cuda_fail(cudaError_t e, const char* where) {
         if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
     } while (0)
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+}  // namespace
+
+int sps::pointer_location(const void* p, int device) {
+    if (!p) return 0;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? 1 : -1;
+    return 0;
 }
+
+namespace {
 
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, double* x, double* w) {
@@ -158,10 +164,19 @@ struct Stager {
     };
     std::vector<Back> back;
     cudaError_t err = cudaSuccess;
+    bool foreign = false;    // an argument lives in another device's memory
 
+    // 1: use p as it is; 0: stage it; -1: reject it
+    int where(const void* p, size_t count) {
+        if (!p || count == 0) return 1;
+        const int w = pointer_location(p, ctx->device);
+        if (w < 0) foreign = true;
+        return w;
+    }
     template <typename T>
     const T* in(const T* p, size_t count) {
-        if (!p || count == 0 || is_device_ptr(p)) return p;
+        const int w = where(p, count);
+        if (w != 0) return w > 0 ? p : nullptr;
         any_host = true;
         DevBuf& b = ctx->stage[slot++];
         if ((err = b.reserve(count * sizeof(T))) != cudaSuccess) return nullptr;
@@ -171,12 +186,20 @@ struct Stager {
     }
     template <typename T>
     T* out(T* p, size_t count) {
-        if (!p || count == 0 || is_device_ptr(p)) return p;
+        const int w = where(p, count);
+        if (w != 0) return w > 0 ? p : nullptr;
         any_host = true;
         DevBuf& b = ctx->stage[slot++];
         if ((err = b.reserve(count * sizeof(T))) != cudaSuccess) return nullptr;
         back.push_back({p, b.p, count * sizeof(T)});
         return b.as<T>();
+    }
+    sps_status check() const {
+        if (foreign)
+            return fail(SPS_E_INVALID_ARG, "an array argument lives in the memory of another device "
+                                           "than the context's");
+        if (err != cudaSuccess) return cuda_fail(err, "staging");
+        return SPS_OK;
     }
     cudaError_t finish() {
         for (auto& bk : back) {
@@ -196,7 +219,9 @@ sps_status check_rows(const sps_ctx* ctx, const float* theta, const int32_t* gal
     if (!theta) return fail(SPS_E_INVALID_ARG, "theta is NULL");
     if (!gal_idx && n != ctx->n_gal)
         return fail(SPS_E_SHAPE, "gal_idx is NULL but n differs from the galaxy count");
-    if (gal_idx && n > 0 && !is_device_ptr(gal_idx)) {
+    const int gw = gal_idx && n > 0 ? pointer_location(gal_idx, ctx->device) : 1;
+    if (gw < 0) return fail(SPS_E_INVALID_ARG, "gal_idx lives in the memory of another device");
+    if (gw == 0) {
         for (int64_t i = 0; i < n; ++i)
             if (gal_idx[i] < 0 || gal_idx[i] >= ctx->n_gal)
                 return fail(SPS_E_SHAPE, "gal_idx out of range at row " + std::to_string(i));
@@ -344,7 +369,8 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         return fail(SPS_E_UNSUPPORTED, "no CUDA device");
     }
     if (cfg.device < 0 || cfg.device >= ndev) return fail(SPS_E_INVALID_ARG, "bad device ordinal");
-    CK(cudaSetDevice(cfg.device));
+    DeviceGuard dg(cfg.device);
+    CK(dg.err);
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, cfg.device));
     if (prop.major < 10) return fail(SPS_E_UNSUPPORTED, "needs a Blackwell (sm_100+) device");
@@ -496,10 +522,11 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
                             void* stream) {
     if (!ctx || (!z && n_gal > 0)) return fail(SPS_E_INVALID_ARG, "null argument");
     if (n_gal <= 0 || n_gal > (int64_t)1 << 31) return fail(SPS_E_SHAPE, "n_gal out of range");
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<float> zh((size_t)n_gal);
-    if (is_device_ptr(z)) CK(cudaMemcpy(zh.data(), z, n_gal * 4, cudaMemcpyDeviceToHost));
+    if (pointer_location(z, ctx->device) != 0) CK(cudaMemcpy(zh.data(), z, n_gal * 4, cudaMemcpyDeviceToHost));
     else std::memcpy(zh.data(), z, n_gal * 4);
     for (int64_t i = 0; i < n_gal; ++i)
         if (!(zh[i] > 0.0f && zh[i] < 20.0f)) return fail(SPS_E_INVALID_ARG, "redshift must be in (0, 20)");
@@ -655,13 +682,14 @@ sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_i
     if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (n > 0 && !mag_out) return fail(SPS_E_INVALID_ARG, "mag_out is NULL");
     if (n == 0) return SPS_OK;
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     Stager st{ctx, s};
     const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
     const int32_t* gi = st.in(gal_idx, (size_t)n);
     float* mo = st.out(mag_out, (size_t)n * ctx->c.n_band);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, nullptr, nullptr, nullptr, mo, nullptr,
@@ -687,7 +715,8 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
         return fail(SPS_E_INVALID_ARG, "null data or output pointer");
     if (n == 0) return SPS_OK;
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t GB = (size_t)ctx->n_gal * ctx->c.n_band;
     Stager st{ctx, s};
@@ -698,7 +727,7 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
     const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
     float* llo = st.out(loglike_out, (size_t)n);
     float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     if (mode == SPS_APPROX && ctx->c.n_met <= 12 && !std::getenv("SPS_LIKE_ROWS")) {
         // the team evaluation, one row per warp
@@ -724,7 +753,8 @@ sps_status sps_loglike_grad_forward_mode(sps_ctx* ctx, const float* theta, const
     if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out))
         return fail(SPS_E_INVALID_ARG, "null data or output pointer");
     if (n == 0) return SPS_OK;
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     const Consts& c = ctx->c;
     const size_t GB = (size_t)ctx->n_gal * c.n_band;
@@ -736,7 +766,7 @@ sps_status sps_loglike_grad_forward_mode(sps_ctx* ctx, const float* theta, const
     const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
     float* llo = st.out(loglike_out, (size_t)n);
     float* gro = st.out(grad_out, (size_t)n * SPS_NPARAM);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     const int64_t chunk = 32768;
     const int64_t rows = std::min<int64_t>(n, chunk);
@@ -772,10 +802,11 @@ sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const fl
     if (n > 0 && (!p0 || !eps || !L || !mag_obs || !sigma || !mask || !x_out || !p_out || !logp_out))
         return fail(SPS_E_INVALID_ARG, "null argument");
     if (n == 0) return SPS_OK;
-    if (!is_device_ptr(L))
+    if (pointer_location(L, ctx->device) == 0)
         for (int64_t i = 0; i < n; ++i)
             if (L[i] < 0 || L[i] > 100000) return fail(SPS_E_SHAPE, "L out of range");
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t GB = (size_t)ctx->n_gal * ctx->c.n_band;
     Stager st{ctx, s};
@@ -790,7 +821,7 @@ sps_status sps_leapfrog(sps_ctx* ctx, const float* x0, const float* p0, const fl
     float* xo = st.out(x_out, (size_t)n * SPS_NPARAM);
     float* po = st.out(p_out, (size_t)n * SPS_NPARAM);
     double* lo = st.out(logp_out, (size_t)n);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(launch_leapfrog(ctx->c, ctx->gal(), x, p, e, l, gi, n, mo, sg, mk, xo, po, lo, s));
     CK(st.finish());
     return SPS_OK;
@@ -800,12 +831,13 @@ sps_status sps_philox(sps_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key
                       void* stream) {
     if (!ctx || (n > 0 && (!ctr || !out))) return fail(SPS_E_INVALID_ARG, "null argument");
     if (n <= 0) return SPS_OK;
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     Stager st{ctx, s};
     const uint32_t* c = st.in(ctr, (size_t)n * 4);
     uint32_t* o = st.out(out, (size_t)n * 4);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(launch_philox(c, n, key, o, s));
     CK(st.finish());
     return SPS_OK;
@@ -816,14 +848,15 @@ sps_status sps_weights(sps_ctx* ctx, const float* theta, const int32_t* gal_idx,
     sps_status st0 = check_rows(ctx, theta, gal_idx, n);
     if (st0 != SPS_OK) return st0;
     if (n == 0) return SPS_OK;
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     Stager st{ctx, s};
     const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
     const int32_t* gi = st.in(gal_idx, (size_t)n);
     float* w = st.out(W_out, (size_t)n * ctx->c.K);
     double* m = st.out(mstar_out, (size_t)n);
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(launch_weights_rows(ctx->c, ctx->gal(), th, gi, n, w, m, s));
     CK(st.finish());
     return SPS_OK;
@@ -873,7 +906,8 @@ cudaError_t launch_wait_probe(int ready, uint32_t limit, int* err, cudaStream_t 
 extern "C" sps_status sps_wait_probe(sps_ctx* ctx, int32_t ready, uint32_t spin_limit, void* stream) {
     if (!ctx) return fail(SPS_E_INVALID_ARG, "null context");
     if (spin_limit < 1 || spin_limit > (1u << 26)) return fail(SPS_E_INVALID_ARG, "spin_limit in [1, 2^26]");
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     int fl[2] = {0, 0};
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
@@ -907,13 +941,14 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     const int C = cfg->chains_per_gal;
     const int64_t NC = G * C;
     if (NC > ((int64_t)1 << 31)) return fail(SPS_E_SHAPE, "too many chains");
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     const Consts& c = ctx->c;
     const size_t GB = (size_t)G * c.n_band;
     // maximum observed band count decides the shared table size
     std::vector<uint32_t> mh((size_t)G);
-    if (is_device_ptr(mask)) CK(cudaMemcpy(mh.data(), mask, G * 4, cudaMemcpyDeviceToHost));
+    if (pointer_location(mask, ctx->device) != 0) CK(cudaMemcpy(mh.data(), mask, G * 4, cudaMemcpyDeviceToHost));
     else std::memcpy(mh.data(), mask, G * 4);
     const uint32_t all = (c.n_band >= 32) ? 0xffffffffu : ((1u << c.n_band) - 1u);
     int nb_max = 0;
@@ -938,7 +973,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     int32_t* dv = stats ? st.out(stats->divergences, (size_t)NC) : nullptr;
     int64_t* nev = stats ? st.out(stats->grad_evals, (size_t)NC) : nullptr;
     int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
 
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
                  cfg->seed, cfg->adapt_mass < 0 ? 0 : (cfg->adapt_mass > 2 ? 2 : cfg->adapt_mass), 1};
@@ -1103,7 +1138,8 @@ extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_confi
     const int C = cfg->chains_per_gal;
     const int64_t NC = G * C;
     if (NC > ((int64_t)1 << 31)) return fail(SPS_E_SHAPE, "too many chains");
-    CK(cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
     cudaStream_t s = (cudaStream_t)stream;
     const Consts& c = ctx->c;
     const size_t GB = (size_t)G * c.n_band;
@@ -1118,7 +1154,7 @@ extern "C" sps_status sps_hmc_run_forward_mode(sps_ctx* ctx, const sps_hmc_confi
     int32_t* dv = stats ? st.out(stats->divergences, (size_t)NC) : nullptr;
     int64_t* nev = stats ? st.out(stats->grad_evals, (size_t)NC) : nullptr;
     int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
-    if (st.err != cudaSuccess) return cuda_fail(st.err, "staging");
+    if (sps_status r = st.check(); r != SPS_OK) return r;
     HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
                  cfg->seed, 0, 1};
     // state, theta, FP64 log L, gradient, chain -> galaxy, forward-mode scratch

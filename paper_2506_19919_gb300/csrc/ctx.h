@@ -13,6 +13,27 @@
 
 namespace sps {
 
+// Makes `dev` the current device for the guard's lifetime and gives the
+// caller's current device back on destruction, so an entry point never
+// leaves a different device current behind.
+struct DeviceGuard {
+    int prev = -1;
+    int dev;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int d) : dev(d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Grow-only device buffer.
 struct DevBuf {
     void* p = nullptr;
@@ -98,7 +119,7 @@ struct sps_ctx {
         return g;
     }
     ~sps_ctx() {
-        cudaSetDevice(device);
+        sps::DeviceGuard dg(device);
         if (graph) cudaGraphExecDestroy(graph);
         DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,

@@ -101,6 +101,9 @@ struct PlainChain {
 
 // Records the message returned by sps_last_error_message() on this thread.
 void set_last_error(const char* msg);
+// Where an array argument lives: 1 in the memory of `device` (or managed
+// memory), 0 in host memory, -1 in the memory of another device.
+int pointer_location(const void* p, int device);
 
 // Launchers (defined in the .cu files); all return cudaError_t of the launch.
 cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const double* lam64,

@@ -4,9 +4,10 @@ It serves callers that cannot allocate device memory while running (a fixed
 device-memory budget reserved at start-up, a host allocator that owns the
 device memory, or loops where cudaMalloc would synchronise or fail): its
 scratch is a fixed array compiled into the library.  Its magnitudes must
-equal those of the ordinary sps_photometry entry point (exact, FP32) within
-the magnitude tolerance the parity tests use, on two calls in a row that share
-the static scratch.  This file is collected last on purpose."""
+equal those of the ordinary sps_photometry entry point (exact, FP32) and
+those of the FP64 oracle within the magnitude tolerance the parity tests
+use, on two calls in a row that share the static scratch.  This file is
+collected last on purpose."""
 import ctypes as C
 
 import numpy as np
@@ -14,6 +15,7 @@ import pytest
 import torch
 
 import sps_workloads as W
+from oracle import sps as O
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +46,9 @@ def test_noalloc_matches_photometry_on_two_calls():
         assert st == 0, lib.sps_last_error_message()
         assert torch.isfinite(out).all()
         assert (out - ref).abs().max().item() < MAG_TOL
+        rows = gidx.cpu().numpy() if use_idx else np.arange(64)
+        mo = O.photometry(th.cpu().numpy().astype(np.float64), wl.z[rows], wl.tables, "exact")
+        assert np.abs(out.cpu().numpy() - mo.numpy()).max() < MAG_TOL
     # sizes beyond the static scratch and host arrays are refused with a message
     big = torch.zeros(40000, dtype=torch.int32, device="cuda")
     thb = torch.zeros((40000, 12), dtype=torch.float32, device="cuda")
@@ -53,4 +58,8 @@ def test_noalloc_matches_photometry_on_two_calls():
     host = np.zeros((64, 12), np.float32)
     assert lib.sps_photometry_exact_noalloc(ctx.h, C.c_void_p(host.ctypes.data), None, 64,
                                             _vp(out), stream) == 1
+    assert b"device pointers" in lib.sps_last_error_message()
+    assert lib.sps_photometry_exact_noalloc(None, _vp(thb), None, 64, _vp(out), stream) == 1
+    assert b"null context" in lib.sps_last_error_message()
+    assert torch.cuda.current_device() == 0
     ctx.close()
