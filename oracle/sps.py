@@ -100,6 +100,33 @@ def lum_dist_mpc(z, h0=H0_KMS_MPC, om=OMEGA_M):
     return torch.as_tensor(out, dtype=DT)
 
 
+def hubble_e(z, om=OMEGA_M):
+    """E(z) = H(z) / H0 of flat LambdaCDM."""
+    return torch.sqrt(om * (1.0 + _t(z)) ** 3 + (1.0 - om))
+
+
+class _LumDist(torch.autograd.Function):
+    """d_L(z) in Mpc as a differentiable function of z: the value from the
+    adaptive quadrature of lum_dist_mpc, the derivative from differentiating
+    its defining integral, d d_L / dz = d_L / (1+z) + (1+z) (c / H0) / E(z)."""
+
+    @staticmethod
+    def forward(ctx, z):
+        dl = lum_dist_mpc(z.detach().numpy()).reshape(z.shape)
+        ctx.save_for_backward(z, dl)
+        return dl
+
+    @staticmethod
+    def backward(ctx, g):
+        z, dl = ctx.saved_tensors
+        return g * (dl / (1.0 + z) + (1.0 + z) * (C_KMS / H0_KMS_MPC) / hubble_e(z))
+
+
+def lum_dist_mpc_t(z):
+    """lum_dist_mpc on a float64 tensor z, differentiable in z."""
+    return _LumDist.apply(_t(z))
+
+
 # ---------------------------------------------------------------- age bins
 def age_bin_edges_yr(age_yr):
     """Age-bin edges: geometric midpoints between grid ages, 0 below the
@@ -430,7 +457,7 @@ def magnitudes(flux, nb, z):
     """AB apparent magnitudes m_b = -2.5 log10[(1+z) L_sun c_b /
     (4 pi d_L^2 3631 Jy N_b)] (App. B reports apparent magnitudes; the AB
     convention and the (1+z) bandwidth factor are the declared reading)."""
-    dl_cm = lum_dist_mpc(z.detach().numpy()) * MPC_CM
+    dl_cm = lum_dist_mpc_t(z) * MPC_CM
     fac = (1.0 + z) * L_SUN_ERG_S / (4.0 * math.pi * dl_cm ** 2 * AB_ZP_CGS)
     return -2.5 * torch.log10(fac[:, None] * flux / nb)
 
@@ -455,14 +482,26 @@ def loglike(mag, mag_obs, sigma, mask_bits):
     return -0.5 * (m * r * r).sum(1)
 
 
-def loglike_and_grad(theta, z, tables, mag_obs, sigma, mask_bits, mode="exact"):
+def loglike_and_grad(theta, z, tables, mag_obs, sigma, mask_bits, mode="exact", wrt_z=False):
     """log L and d log L / d theta (12 physical parameters, z held fixed),
-    the gradient by reverse-mode autodiff of this FP64 definition."""
+    the gradient by reverse-mode autodiff of this FP64 definition.
+
+    wrt_z: the gradient has a 13th column, d log L / dz of each row's own
+    redshift (the observed-frame filter T((1+z) lambda), the band
+    normalisation N_b(z), d_L(z), the (1+z) bandwidth factor, and t_obs(z)
+    through the age bins, M_star and the burst clipping).  It is defined for
+    Gaussian and tabulated bands; a top-hat band's rest-grid sum is piecewise
+    constant in z, so its z-derivative is not represented (reading: the
+    redshift gradient is given for bands with a continuous transmission)."""
     th = _t(theta).clone().requires_grad_(True)
-    mag = photometry(th, _t(z), tables, mode)
+    zt = _t(z).clone().requires_grad_(wrt_z)
+    mag = photometry(th, zt, tables, mode)
     ll = loglike(mag, mag_obs, sigma, mask_bits)
-    (g,) = torch.autograd.grad(ll.sum(), th)
-    return ll.detach(), g.detach(), mag.detach()
+    if not wrt_z:
+        (g,) = torch.autograd.grad(ll.sum(), th)
+        return ll.detach(), g.detach(), mag.detach()
+    g, gz = torch.autograd.grad(ll.sum(), (th, zt))
+    return ll.detach(), torch.cat([g, gz[:, None]], 1).detach(), mag.detach()
 
 
 # ---------------------------------------------------------------- bounding + prior
