@@ -289,6 +289,10 @@ def run_ours(args):
     }
     if rank == 0 and not args.skip_extra:
         out["loglike_grad"] = _loglike_grad_rates(ctx, dev)
+    if rank == 0 and not args.skip_errors:
+        out["error"] = _errors(dev)
+    if rank == 0 and not args.skip_survey:
+        out["survey"] = _survey(dev)
     if rank == 0 and not args.skip_plain:
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
     if rank == 0 and not args.skip_nuts:
@@ -499,6 +503,54 @@ def _e2e(ctx, cfg, lib, wl, mobs_dev, x0_dev, post, ws):
             "d2h_bytes_per_step": int(d2h), "s_per_step": t}
 
 
+def _errors(dev):
+    """Error of every path and precision against the FP64 oracle on sampled
+    rows of the workloads: magnitudes (|dm| in mag), log L (relative) and the
+    13-column gradient (12 parameters and z; per row the max-component error
+    over the largest component), max and median over the rows.  The oracle's
+    values were stored by tests/golden/make_bench_reference.py; the GPU side
+    runs the library's public calls on the same rows (no oracle is run here)."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    with open(os.path.join(ROOT, "tests", "golden", "bench_error_reference.json")) as f:
+        ref = json.load(f)
+    tables = {W.CONFIG_NAMES[2]: W.config(2, n_gal=1).tables, W.CONFIG_NAMES[3]: W.config(3, n_gal=1).tables}
+    stat = lambda v: {"max": float(np.max(v)), "median": float(np.median(v))}
+    out = {"reference": "FP64 oracle on the sampled rows (tests/golden/bench_error_reference.json)",
+           "gradient_measure": "per row max_k |g_k - g_ref,k| / max_k |g_ref,k| over 12 parameters and z"}
+    for name, r in ref.items():
+        z = np.asarray(r["z"])
+        th = np.asarray(r["theta"], np.float32)
+        mobs = np.asarray(r["mag_obs"], np.float32)
+        sg = np.asarray(r["sigma"], np.float32)
+        mk = np.asarray(r["mask"], np.int64).astype(np.uint32)
+        ctx = pkg.Context(tables[name], device=dev.index)
+        ctx.set_galaxies(z, build_approx=True)
+        res = {"rows": len(z)}
+        modes = [("approx", "fp32")] + ([("exact", "fp32"), ("exact", "bf16"), ("exact", "tf32x3")]
+                                        if "mag_exact" in r else [])
+        for mode, prec in modes:
+            m = ctx.photometry(th, mode=mode, prec=prec).cpu().numpy().astype(np.float64)
+            dm = np.abs(m - np.asarray(r[f"mag_{mode}"]))
+            ll, g = ctx.loglike_grad_z(th, mobs, sg, mk, mode=mode, prec=prec)
+            gref = np.asarray(r[f"grad_{mode}"])
+            gg = g.cpu().numpy().astype(np.float64)
+            grel = np.abs(gg - gref).max(1) / np.abs(gref).max(1)
+            lref = np.asarray(r[f"loglike_{mode}"])
+            lrel = np.abs(ll.cpu().numpy().astype(np.float64) - lref) / np.abs(lref)
+            res[f"{mode}_{prec}"] = {"mag_abs": stat(dm), "loglike_rel": stat(lrel), "gradient_rel": stat(grel)}
+            if mode == "approx":       # the 12-column team evaluation the samplers use
+                _, g12 = ctx.loglike_grad(th, mobs, sg, mk, mode="approx")
+                g12 = g12.cpu().numpy().astype(np.float64)
+                res["approx_fp32_team12"] = {"gradient_rel": stat(
+                    np.abs(g12 - gref[:, :12]).max(1) / np.abs(gref[:, :12]).max(1))}
+        ctx.close()
+        out[name] = res
+    torch.cuda.synchronize()
+    return out
+
+
 def _loglike_grad_rates(ctx_hmc, dev):
     """loglike + gradient evaluations per second on 100,000 pairs."""
     import torch
@@ -636,6 +688,11 @@ def run_loglike_only(args):
 
 
 def run_survey(args):
+    import torch
+    print(json.dumps(_survey(torch.device("cuda", 0))))
+
+
+def _survey(dev):
     """Throughput on the large bursty survey batch (1,000,000 galaxies x 2
     chains, 20 bands, 6-20 observed, burst on, 300 + 300 iterations): table
     build, log L + gradient on all 2,000,000 (galaxy, chain) pairs (FP32
@@ -646,8 +703,7 @@ def run_survey(args):
     import paper_2506_19919_gb300 as pkg
     wl = W.config(4)
     G, C = wl.n_gal, wl.chains
-    dev = torch.device("cuda", 0)
-    ctx = pkg.Context(wl.tables, device=0)
+    ctx = pkg.Context(wl.tables, device=dev.index)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx.set_galaxies(wl.z, build_approx=True)
@@ -695,7 +751,7 @@ def run_survey(args):
                   "projected_s_for_300_plus_300": runs[4][0] + per_it * (n_it - 4),
                   "note": "warm-up iterations from prior draws; cost per iteration from the 12-4 difference"}
     ctx.close()
-    print(json.dumps(out))
+    return out
 
 
 def run_reference(args):
@@ -742,6 +798,8 @@ def _parser():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-nuts", action="store_true")
     ap.add_argument("--skip-models", action="store_true")
+    ap.add_argument("--skip-errors", action="store_true")
+    ap.add_argument("--skip-survey", action="store_true")
     ap.add_argument("--plain-full", action="store_true",
                     help="run the whole lock-step baseline HMC (minutes) and report its own ESS")
     # profiling captures only (not bench values): smaller galaxy count / iterations

@@ -211,6 +211,24 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
                             sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
                             void* stream);
 
+/* sps_loglike_grad with a 13th gradient column: the derivative of each row's
+ * log L with respect to its galaxy's redshift z, for fits that free z (the
+ * SPS redshift parameter; Sec. 3 T(lambda | z) and c_SSP(z), App. A.1
+ * t_obs(z)).  grad_out[n][13]: columns 0-11 as sps_loglike_grad, column 12
+ * d log L / dz through the observed-frame filters T((1+z) lambda), the band
+ * normalisation N_b(z), d_L(z), the (1+z) bandwidth factor, lambda_eff(z) and
+ * c_SSP(z) (approximate path), and t_obs(z) (age bins, mass formed, burst
+ * clipping).  Needs a filter set without top-hat bands (the rest-grid filter
+ * sum of a top-hat is piecewise constant in z): SPS_E_UNSUPPORTED otherwise.
+ * The approximate path builds, on its first call after sps_set_galaxies, a
+ * d c_SSP / dz table the size of c_SSP (SPS_E_NOMEM if it does not fit).
+ * Arguments, precisions and errors otherwise as sps_loglike_grad; grad_out
+ * must not be NULL. */
+sps_status sps_loglike_grad_z(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                              const float* mag_obs, const float* sigma, const uint32_t* mask,
+                              sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
+                              void* stream);
+
 /* Comparison baseline, not a product path: the same approximate-path log L and
  * gradient as sps_loglike_grad (SPS_APPROX), computed the plain way a direct
  * GPU port would: unfused kernels with their intermediates in HBM and the

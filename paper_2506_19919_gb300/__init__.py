@@ -171,6 +171,24 @@ class Context:
               "sps_loglike_grad")
         return ll, g
 
+    def loglike_grad_z(self, theta, mag_obs, sigma, mask, gal_idx=None, mode="approx", prec="fp32"):
+        """log L and its gradient with respect to the 12 parameters and the
+        galaxy's redshift: returns (loglike [n], grad [n, 13]), column 12 = d/dz."""
+        th = _f32(theta, None if isinstance(theta, torch.Tensor) else self.device)
+        dev = th.device
+        n = th.shape[0]
+        mo = _f32(mag_obs, dev)
+        sg = _f32(sigma, dev)
+        mk = _mask32(mask, dev)
+        gi = None if gal_idx is None else torch.as_tensor(gal_idx, dtype=torch.int32,
+                                                             device=dev).contiguous()
+        ll = torch.empty(n, dtype=torch.float32, device=dev)
+        g = torch.empty((n, _lib.NPARAM + 1), dtype=torch.float32, device=dev)
+        check(self._lib.sps_loglike_grad_z(self.h, _vp(th), _vp(gi), n, _vp(mo), _vp(sg), _vp(mk),
+                                           MODES[mode], PRECS[prec], _vp(ll), _vp(g), _stream(th)),
+              "sps_loglike_grad_z")
+        return ll, g
+
     def loglike_grad_forward_mode(self, theta, mag_obs, sigma, mask, gal_idx=None):
         """The plain forward-mode comparison path (approximate photometry)."""
         th = _f32(theta, None if isinstance(theta, torch.Tensor) else self.device)

@@ -69,6 +69,8 @@ _PROTOS = {
     "sps_photometry": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_int, _P, _P]),
     "sps_loglike_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, _P, _P,
                                    _P]),
+    "sps_loglike_grad_z": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, C.c_int, C.c_int, _P, _P,
+                                   _P]),
     "sps_loglike_grad_forward_mode": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P]),
     "sps_wait_probe": (C.c_int, [_P, C.c_int32, C.c_uint32, _P]),
     "sps_hmc_run": (C.c_int, [_P, C.POINTER(sps_hmc_config), _P, _P, _P, _P, _P,

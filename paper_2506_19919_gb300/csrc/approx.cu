@@ -63,6 +63,52 @@ k_approx_rows(const __grid_constant__ Consts c, const Galaxies g, const float* _
     }
 }
 
+// log L and d log L / d(theta, z) of the approximate path, one warp per row:
+// grad_out[row][13], the last column the derivative in the galaxy's redshift.
+__global__ void __launch_bounds__(32 * kWarpsApprox)
+k_approx_rows_z(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
+                const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ mag_obs,
+                const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
+                float* __restrict__ ll_out, float* __restrict__ grad_out, int* __restrict__ nonfinite) {
+    __shared__ WarpWork work[kWarpsApprox];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    WarpWork& ww = work[warp];
+    const int B = c.n_band;
+    constexpr int NG = SPS_NPARAM + 1;
+    const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
+    for (int64_t row = (int64_t)blockIdx.x * kWarpsApprox + warp; row < n;
+         row += (int64_t)gridDim.x * kWarpsApprox) {
+        const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+        RowParams p;
+        load_params(c, theta + row * SPS_NPARAM, false, p);
+        if (gi < 0 || gi >= g.n) p.finite = false;
+        if (!p.finite) {
+            if (lane == 0) atomicOr(nonfinite, 1);
+            if (lane == 0) ll_out[row] = __int_as_float(0x7fc00000);
+            if (lane < NG) grad_out[row * NG + lane] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const size_t gb0 = (size_t)gi * B;
+        const int nb = fill_slots(c, g, ww.d, gi, mask[gi] & all, mag_obs, sigma, g.cssp + gb0 * c.K, false);
+        const ZRow zr{g.dcssp + gb0 * c.K, g.dzp + gb0, g.ddust + gb0, g.dtdz[gi]};
+        float gr[NG];
+        const double ll = eval_row<true>(c, ww, g.bins + (size_t)gi * c.n_age, g.lnT[gi], g.lT10[gi], p,
+                                         nb, true, true, gr, &zr);
+        if (lane == 0) {
+            ll_out[row] = (float)ll;
+            bool bad = !isfinite(ll);
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                bad = bad || !isfinite(gr[k]);
+                grad_out[row * NG + k] = gr[k];
+            }
+            if (bad) atomicOr(nonfinite, 1);
+        }
+        __syncwarp();
+    }
+}
+
 // W[row][i*Zn + j] = M_star P_SFH,i P_met,j and M_star (test hook).
 __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_weights_rows(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
@@ -124,6 +170,16 @@ cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* 
     k_approx_rows<<<blocks_for(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(
         c, g, theta, theta_unbounded, gal_idx, n, mag_obs, sigma, mask, mag_out, loglike_out,
         grad_out, logp_out, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_approx_rows_z(const Consts& c, const Galaxies& g, const float* theta,
+                                 const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                                 const float* sigma, const uint32_t* mask, float* loglike_out,
+                                 float* grad_out, int* nonfinite, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_approx_rows_z<<<blocks_for(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(
+        c, g, theta, gal_idx, n, mag_obs, sigma, mask, loglike_out, grad_out, nonfinite);
     return cudaGetLastError();
 }
 

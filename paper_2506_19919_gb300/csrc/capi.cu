@@ -540,14 +540,19 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
     CK(ctx->gsup.reserve(G * B * sizeof(int2)));
     CK(ctx->ggauss.reserve(G * B * sizeof(float2)));
     CK(ctx->gdust.reserve(G * B * sizeof(float4)));
+    CK(ctx->gdtdz.reserve(G * 4));
+    CK(ctx->gdzp.reserve(G * B * 4));
+    CK(ctx->gddust.reserve(G * B * sizeof(float4)));
     CK(cudaMemcpyAsync(ctx->gz.p, zh.data(), G * 4, cudaMemcpyHostToDevice, s));
     ctx->n_gal = n_gal;
     ctx->has_approx = false;
+    ctx->has_dcssp = false;
     CK(launch_prepare_galaxies(c, ctx->grid(), ctx->lam64.as<double>(), ctx->bp0.as<double>(),
                                ctx->bp1.as<double>(), ctx->age_edges.as<double>(), ctx->gz.as<float>(),
                                n_gal, ctx->h0, ctx->om, ctx->glnT.as<float>(), ctx->glT10.as<float>(),
                                ctx->gbins.as<float2>(), ctx->gzp.as<double>(), ctx->gsup.as<int2>(),
-                               ctx->ggauss.as<float2>(), ctx->gdust.as<float4>(), s));
+                               ctx->ggauss.as<float2>(), ctx->gdust.as<float4>(), ctx->gdtdz.as<float>(),
+                               ctx->gdzp.as<float>(), ctx->gddust.as<float4>(), s));
     if (build_approx) {
         cudaError_t e = ctx->gcssp.reserve(G * B * c.K * sizeof(float));
         if (e != cudaSuccess) {
@@ -562,10 +567,13 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
     return SPS_OK;
 }
 
+// want_z: grad_out has 13 columns, d log L / dz last.
 static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gidx, int64_t n,
                             const float* mobs, const float* sigma, const uint32_t* mask, sps_prec prec,
-                            float* mag_out, float* ll_out, float* grad_out, cudaStream_t s) {
+                            float* mag_out, float* ll_out, float* grad_out, cudaStream_t s,
+                            bool want_z = false) {
     const Consts& c = ctx->c;
+    const int NG = want_z ? SPS_NPARAM + 1 : SPS_NPARAM;
     // tcgen05 for BF16 operands (SIMT when disabled) and for 3xTF32; FP32 is SIMT
     if (prec == SPS_TF32X3 && !ctx->use_tc) return fail(SPS_E_UNSUPPORTED, "3xTF32 needs the tensor cores");
     const int bf16 = prec == SPS_BF16 ? 1 : 0;
@@ -587,6 +595,12 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
         CK(ctx->Wbar.reserve((size_t)rows * c.k_pad * 4));
         if (tf) CK(ctx->Vlo.reserve((size_t)rows * c.lam_pad * 4));
     }
+    if (want_z) {
+        CK(ctx->cJz.reserve((size_t)rows * c.n_band * 2 * 4));
+        CK(ctx->rowz.reserve((size_t)rows * 4));
+    }
+    float* cJz = want_z ? ctx->cJz.as<float>() : nullptr;
+    float* rowz = want_z ? ctx->rowz.as<float>() : nullptr;
     const Grid grid = ctx->grid();
     const Galaxies gal = ctx->gal();
     int* nf = ctx->nonfinite.as<int>();
@@ -609,6 +623,8 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
             gv.bins += r0 * c.n_age; gv.zp += r0 * c.n_band; gv.support += r0 * c.n_band;
             gv.gauss += r0 * c.n_band; gv.dust_eff += r0 * c.n_band;
             if (gv.cssp) gv.cssp += r0 * c.n_band * c.K;
+            gv.dtdz += r0; gv.dzp += r0 * c.n_band; gv.ddust += r0 * c.n_band;
+            if (gv.dcssp) gv.dcssp += r0 * c.n_band * c.K;
             gv.n = m;
         }
         if (tc) CK(launch_zsort(gv, gi, m, perm, pos_of, zcounts, s));
@@ -624,14 +640,14 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                                   make_tmap_bf16(&tm.b[0], ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256));
             if (!ok) return fail(SPS_E_CUDA, "tensor map encoding failed");
             if (!tf) tm.a[1] = tm.a[0], tm.b[1] = tm.b[0];
-            CK(launch_fwd_tc(tm, tf, c, grid, gv, th, gi, perm, m, ctx->cJ.as<float>(), terr, s));
+            CK(launch_fwd_tc(tm, tf, c, grid, gv, th, gi, perm, m, ctx->cJ.as<float>(), terr, s, cJz));
         } else {
             CK(launch_exact_fwd(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(),
-                                ctx->cJ.as<float>(), s));
+                                ctx->cJ.as<float>(), s, cJz));
         }
         CK(launch_exact_like(c, gv, th, gi, m, ctx->cJ.as<float>(), ctx->rowinfo.as<float>(), mo, sg,
                              mk, mag_out ? mag_out + r0 * c.n_band : nullptr,
-                             ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s));
+                             ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s, cJz, rowz));
         if (grad_out) {
             if (tc) {
                 if (tf)
@@ -656,7 +672,7 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                 CK(launch_exact_adj(c, grid, m, bf16, ctx->V.as<float>(), ctx->Wbar.as<float>(), s));
             }
             CK(launch_exact_grad(c, gv, th, gi, m, ctx->rowinfo.as<float>(), ctx->Wbar.as<float>(),
-                                 grad_out + r0 * SPS_NPARAM, s));
+                                 grad_out + r0 * NG, s, rowz));
         }
     }
     return SPS_OK;
@@ -737,6 +753,58 @@ sps_status sps_loglike_grad(sps_ctx* ctx, const float* theta, const int32_t* gal
                               ctx->nonfinite.as<int>(), s));
     } else {
         sps_status r = run_exact(ctx, th, gi, n, mo, sg, mk, prec, nullptr, llo, gro, s);
+        if (r != SPS_OK) return r;
+    }
+    return finish_call(ctx, st, s);
+}
+
+sps_status sps_loglike_grad_z(sps_ctx* ctx, const float* theta, const int32_t* gal_idx, int64_t n,
+                              const float* mag_obs, const float* sigma, const uint32_t* mask,
+                              sps_mode mode, sps_prec prec, float* loglike_out, float* grad_out,
+                              void* stream) {
+    sps_status st0 = check_rows(ctx, theta, gal_idx, n);
+    if (st0 != SPS_OK) return st0;
+    if (mode != SPS_EXACT && mode != SPS_APPROX) return fail(SPS_E_INVALID_ARG, "bad mode");
+    if (prec != SPS_FP32 && prec != SPS_BF16 && prec != SPS_TF32X3) return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (mode == SPS_APPROX && prec != SPS_FP32) return fail(SPS_E_UNSUPPORTED, "approximate path is FP32");
+    if (mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    for (int b = 0; b < ctx->c.n_band; ++b)
+        if (ctx->c.band_kind[b] == SPS_BAND_TOPHAT)
+            return fail(SPS_E_UNSUPPORTED, "the redshift derivative needs bands with a continuous "
+                                           "transmission (Gaussian or tabulated); band " + std::to_string(b) +
+                                           " is a top-hat");
+    if (n > 0 && (!mag_obs || !sigma || !mask || !loglike_out || !grad_out))
+        return fail(SPS_E_INVALID_ARG, "null data or output pointer");
+    if (n == 0) return SPS_OK;
+    DeviceGuard dg(ctx->device);
+    CK(dg.err);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Consts& c = ctx->c;
+    if (mode == SPS_APPROX && !ctx->has_dcssp) {          // d c_SSP / dz, once per galaxy set
+        cudaError_t e = ctx->gdcssp.reserve((size_t)ctx->n_gal * c.n_band * c.K * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPS_E_NOMEM, "the d c_SSP / dz table does not fit in device memory");
+        }
+        CK(launch_cssp(c, ctx->grid(), ctx->gal(), ctx->bp0.as<double>(), ctx->bp1.as<double>(),
+                       ctx->gdcssp.as<float>(), s, 1));
+        ctx->has_dcssp = true;
+    }
+    const size_t GB = (size_t)ctx->n_gal * c.n_band;
+    Stager st{ctx, s};
+    const float* th = st.in(theta, (size_t)n * SPS_NPARAM);
+    const int32_t* gi = st.in(gal_idx, (size_t)n);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)ctx->n_gal);
+    float* llo = st.out(loglike_out, (size_t)n);
+    float* gro = st.out(grad_out, (size_t)n * (SPS_NPARAM + 1));
+    if (sps_status r = st.check(); r != SPS_OK) return r;
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
+    if (mode == SPS_APPROX) {
+        CK(launch_approx_rows_z(c, ctx->gal(), th, gi, n, mo, sg, mk, llo, gro, ctx->nonfinite.as<int>(), s));
+    } else {
+        sps_status r = run_exact(ctx, th, gi, n, mo, sg, mk, prec, nullptr, llo, gro, s, true);
         if (r != SPS_OK) return r;
     }
     return finish_call(ctx, st, s);

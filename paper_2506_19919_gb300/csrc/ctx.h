@@ -76,6 +76,10 @@ struct sps_ctx {
     int64_t n_gal = 0;
     bool has_approx = false;
     DevBuf gz, glnT, glT10, gbins, gzp, gsup, ggauss, gcssp, gdust;
+    DevBuf gdtdz, gdzp, gddust;       // redshift derivatives of the per-galaxy set-up
+    DevBuf gdcssp;                    // d c_SSP / dz, built on the first request
+    bool has_dcssp = false;
+    DevBuf cJz, rowz;                 // exact path: the z accumulators and explicit z term
     // scratch
     DevBuf nonfinite, queue, err;
     DevBuf W, V, Wbar, cJ, gbar, rowinfo, tcerr, plainT, plainC, hmcm;
@@ -116,6 +120,10 @@ struct sps_ctx {
         g.gauss = ggauss.as<float2>();
         g.cssp = has_approx ? gcssp.as<float>() : nullptr;
         g.dust_eff = gdust.as<float4>();
+        g.dtdz = gdtdz.as<float>();
+        g.dzp = gdzp.as<float>();
+        g.ddust = gddust.as<float4>();
+        g.dcssp = has_dcssp ? gdcssp.as<float>() : nullptr;
         return g;
     }
     ~sps_ctx() {
@@ -123,7 +131,7 @@ struct sps_ctx {
         if (graph) cudaGraphExecDestroy(graph);
         DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
-                         &gcssp, &gdust, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
+                         &gcssp, &gdust, &gdtdz, &gdzp, &gddust, &gdcssp, &cJz, &rowz, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
                          &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo, &tabT, &tabT64};
         for (DevBuf* b : all) b->release();

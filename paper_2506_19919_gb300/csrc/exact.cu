@@ -124,12 +124,15 @@ __device__ __forceinline__ void tile_contract(const TA* __restrict__ A, int64_t 
 
 // ---------------------------------------------------------------- forward + epilogue
 // One block per 64 rows, looping over every wavelength tile; the epilogue
-// folds each tile into A[r][b][4] in shared memory (fixed order).
-template <typename T>
+// folds each tile into A[r][b][4] in shared memory (fixed order).  KZ also
+// folds the redshift derivative of the band weights, wb' = d wb / dz =
+// q_n T'((1+z) l_n), into Az[r][b][2] = sum_n wb' S (1, E).
+template <typename T, bool KZ = false>
 __global__ void __launch_bounds__(kThreads)
 k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
             const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
-            const T* __restrict__ W, const T* __restrict__ Ltab, float* __restrict__ cJ) {
+            const T* __restrict__ W, const T* __restrict__ Ltab, float* __restrict__ cJ,
+            float* __restrict__ cJz) {
     __shared__ float As[kBK][kBM + 4];
     __shared__ float Bs[kBK][kBN];
     __shared__ float4 lc[kBN];
@@ -140,9 +143,13 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
     float* accsm = dyn;                                              // [kBM][B][4]
     int2* sup = reinterpret_cast<int2*>(dyn + kBM * B * 4);          // [kBM][B]
     float2* ga = reinterpret_cast<float2*>(sup + kBM * B);           // [kBM][B]
+    float* accz = reinterpret_cast<float*>(ga + kBM * B);            // KZ: [kBM][B][2]
+    float* gzf = accz + kBM * B * 2;                                 // KZ: [kBM][B] 1/sigma or 1/step
     const int64_t m0 = (int64_t)blockIdx.x * kBM;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int e = tid; e < kBM * B * 4; e += kThreads) accsm[e] = 0.0f;
+    if (KZ)
+        for (int e = tid; e < kBM * B * 2; e += kThreads) accz[e] = 0.0f;
     for (int e = tid; e < kBM * B; e += kThreads) {
         int r = e / B, b = e % B;
         int64_t row = m0 + r;
@@ -150,9 +157,11 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
         if (gi >= 0 && gi < g.n) {
             sup[e] = g.support[gi * B + b];
             ga[e] = g.gauss[gi * B + b];
+            if (KZ) gzf[e] = fabsf(ga[e].y) / (1.0f + g.z[gi]);   // (1+z)/s / (1+z)
         } else {
             sup[e] = make_int2(0, 0);
             ga[e] = make_float2(0.f, 0.f);
+            if (KZ) gzf[e] = 0.0f;
         }
     }
     for (int r = tid; r < kBM; r += kThreads) {
@@ -179,24 +188,31 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
             const float* tabT = grid.band_T + c.tab_off[b];
             const int tabn = c.tab_n[b];
             float v[4][4];
+            float vz[4][2];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.0f;
+                vz[i][0] = vz[i][1] = 0.0f;
                 const int r = ty * 4 + i;
                 const int2 sp = sup[r * B + b];
                 const float2 gg = ga[r * B + b];
                 const float4 rd = rdust[r];
+                const float fz = KZ ? gzf[r * B + b] : 0.0f;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int nl = tx * 8 + j, nn = n0 + nl;
                     if (nn >= sp.x && nn < sp.y) {
                         const float4 L4 = lc[nl];
                         float wb = L4.x;
+                        float wz = 0.0f;
                         if (kind == 1) {
                             float u = (lamt[nl] - gg.x) * gg.y;
                             wb *= __expf(-0.5f * u * u);
+                            if (KZ) wz = -wb * lamt[nl] * u * fz;       // q T' with T' = -u T / s
                         } else if (kind == 2) {
-                            wb *= tab_T32(tabT, tabn, (lamt[nl] - gg.x) * -gg.y);
+                            const float ut = (lamt[nl] - gg.x) * -gg.y;
+                            wb *= tab_T32(tabT, tabn, ut);
+                            if (KZ) wz = L4.x * lamt[nl] * tab_dT32(tabT, tabn, ut) * fz;
                         }
                         float pw = __expf(rd.y * L4.z);
                         float base = L4.y * pw + rd.w * L4.w;
@@ -208,11 +224,16 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
                         v[i][1] += es;
                         v[i][2] += es * base;
                         v[i][3] += es * dterm;
+                        if (KZ) {
+                            const float Sz = acc[i][j] * wz;
+                            vz[i][0] += Sz;
+                            vz[i][1] += Sz * E;
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float x = v[i][q];
@@ -222,11 +243,28 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
                     x += __shfl_xor_sync(kFull, x, 1);
                     v[i][q] = x;
                 }
+                if (KZ) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        float x = vz[i][q];
+                        x += __shfl_xor_sync(kFull, x, 8);
+                        x += __shfl_xor_sync(kFull, x, 4);
+                        x += __shfl_xor_sync(kFull, x, 2);
+                        x += __shfl_xor_sync(kFull, x, 1);
+                        vz[i][q] = x;
+                    }
+                }
+            }
             if (tx == 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) accsm[((ty * 4 + i) * B + b) * 4 + q] += v[i][q];
+                    if (KZ) {
+                        accz[((ty * 4 + i) * B + b) * 2 + 0] += vz[i][0];
+                        accz[((ty * 4 + i) * B + b) * 2 + 1] += vz[i][1];
+                    }
+                }
             }
         }
         __syncthreads();
@@ -235,6 +273,11 @@ k_exact_fwd(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
         int64_t row = m0 + e / (B * 4);
         if (row < n) cJ[m0 * B * 4 + e] = accsm[e];
     }
+    if (KZ)
+        for (int e = tid; e < kBM * B * 2; e += kThreads) {
+            int64_t row = m0 + e / (B * 2);
+            if (row < n) cJz[m0 * B * 2 + e] = accz[e];
+        }
 }
 
 // ---------------------------------------------------------------- likelihood
@@ -246,13 +289,15 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
                              const float* __restrict__ mag_obs, const float* __restrict__ sigma,
                              const uint32_t* __restrict__ mask, float* __restrict__ mag_out,
                              float* __restrict__ ll_out, float* __restrict__ gbar,
-                             float* __restrict__ rowinfo, int* __restrict__ nonfinite) {
+                             float* __restrict__ rowinfo, int* __restrict__ nonfinite,
+                             const float* __restrict__ cJz, float* __restrict__ rowz) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const int B = c.n_band;
     const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
     if (gi < 0 || gi >= g.n) {
         atomicOr(nonfinite, 1);
+        if (rowz) rowz[row] = 0.0f;
         if (ll_out) ll_out[row] = __int_as_float(0x7fc00000);
         for (int b = 0; b < B; ++b) {
             if (mag_out) mag_out[row * B + b] = __int_as_float(0x7fc00000);
@@ -267,6 +312,7 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
     const uint32_t bits = mask ? mask[gi] : 0u;
     double ll = 0.0;
     float g0 = 0.f, gAV = 0.f, gdl = 0.f, gff = 0.f;
+    float gz = 0.f;     // explicit d log L / dz (zero point, band weights; weights W fixed)
     bool bad = false;
     for (int b = 0; b < B; ++b) {
         const float* a = cJ + (row * B + b) * 4;
@@ -285,9 +331,14 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
             gAV += gb * (1.0f - ff) * (-0.4f * kLn10f / 4.05f) * a[2];
             gdl += gb * (1.0f - ff) * (-0.4f * kLn10f) * (AV / 4.05f) * a[3];
             gff += gb * (a[0] - a[1]);
+            if (cJz) {
+                const float* az = cJz + (row * B + b) * 2;
+                gz += (float)(-r * is2) * g.dzp[gi * B + b] + gb * (ff * az[0] + (1.0f - ff) * az[1]);
+            }
         }
         if (gbar) gbar[row * B + b] = gb;
     }
+    if (rowz) rowz[row] = gz;
     if (ll_out) ll_out[row] = (float)ll;
     if (rowinfo) {
         rowinfo[row * 4 + 0] = g0;
@@ -399,11 +450,12 @@ k_exact_adj(const __grid_constant__ Consts c, const Grid grid, int64_t n,
 __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
              const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ rowinfo,
-             const float* __restrict__ Wbar, float* __restrict__ grad_out) {
+             const float* __restrict__ Wbar, float* __restrict__ grad_out, const float* __restrict__ rowz) {
     __shared__ RowScratch scratch[kWarpsApprox];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     RowScratch& s = scratch[warp];
     const int A = c.n_age, Zn = c.n_met, K = c.K;
+    const int NG = rowz ? SPS_NPARAM + 1 : SPS_NPARAM;       // with rowz: d/dz last
     for (int64_t row = (int64_t)blockIdx.x * kWarpsApprox + warp; row < n;
          row += (int64_t)gridDim.x * kWarpsApprox) {
         const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
@@ -411,7 +463,7 @@ k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __
         load_params(c, theta + row * SPS_NPARAM, false, p);
         if (gi < 0 || gi >= g.n) p.finite = false;
         if (!p.finite) {
-            if (lane < SPS_NPARAM) grad_out[row * SPS_NPARAM + lane] = __int_as_float(0x7fc00000);
+            if (lane < NG) grad_out[row * NG + lane] = __int_as_float(0x7fc00000);
             continue;
         }
         const double M = age_met_weights(c, s, g.bins + (size_t)gi * A, g.lnT[gi], g.lT10[gi], p, true);
@@ -440,9 +492,14 @@ k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __
         gr[10] = rowinfo[row * 4 + 2];
         gr[11] = rowinfo[row * 4 + 3];
         age_met_adjoint(c, s, g.lT10[gi], M, p, gr);
+        float gzt = 0.0f;          // d log L / dz through t_obs (age bins, M, burst clipping)
+        if (rowz)
+            gzt = rowz[row] + g.dtdz[gi] * tobs_adjoint(c, s.view(c), g.bins + (size_t)gi * A, g.lnT[gi],
+                                                         g.lT10[gi], M, p.th);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < SPS_NPARAM; ++k) grad_out[row * SPS_NPARAM + k] = gr[k];
+            for (int k = 0; k < SPS_NPARAM; ++k) grad_out[row * NG + k] = gr[k];
+            if (rowz) grad_out[row * NG + SPS_NPARAM] = gzt;
         }
         __syncwarp();
     }
@@ -526,19 +583,21 @@ cudaError_t launch_zsort(const Galaxies& g, const int32_t* gal_idx, int64_t n, i
 
 cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
-                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s) {
+                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s,
+                             float* cJz) {
     if (n <= 0) return cudaSuccess;
-    const size_t dyn = (size_t)kBM * c.n_band * (4 * sizeof(float) + sizeof(int2) + sizeof(float2));
+    const bool kz = cJz != nullptr;
+    const size_t dyn = (size_t)kBM * c.n_band *
+                       (4 * sizeof(float) + sizeof(int2) + sizeof(float2) + (kz ? 3 * sizeof(float) : 0));
     const unsigned grid_m = (unsigned)((n + kBM - 1) / kBM);
-    if (bf16) {
-        cudaFuncSetAttribute(k_exact_fwd<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        k_exact_fwd<uint16_t><<<grid_m, kThreads, dyn, s>>>(c, grid, g, theta, gal_idx, n, Wbf,
-                                                            grid.ssp_bf, cJ);
-    } else {
-        cudaFuncSetAttribute(k_exact_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        k_exact_fwd<float><<<grid_m, kThreads, dyn, s>>>(c, grid, g, theta, gal_idx, n, W32,
-                                                         grid.ssp, cJ);
-    }
+    auto go = [&](auto kern, const auto* Wp, const auto* Lp) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        kern<<<grid_m, kThreads, dyn, s>>>(c, grid, g, theta, gal_idx, n, Wp, Lp, cJ, cJz);
+    };
+    if (bf16)
+        kz ? go(k_exact_fwd<uint16_t, true>, Wbf, grid.ssp_bf) : go(k_exact_fwd<uint16_t, false>, Wbf, grid.ssp_bf);
+    else
+        kz ? go(k_exact_fwd<float, true>, W32, grid.ssp) : go(k_exact_fwd<float, false>, W32, grid.ssp);
     return cudaGetLastError();
 }
 
@@ -546,11 +605,11 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
                               const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
                               const float* mag_obs, const float* sigma, const uint32_t* mask,
                               float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
-                              cudaStream_t s) {
+                              cudaStream_t s, const float* cJz, float* rowz) {
     if (n <= 0) return cudaSuccess;
     k_exact_like<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, g, theta, gal_idx, n, cJ, mag_obs,
                                                              sigma, mask, mag_out, loglike_out, gbar,
-                                                             rowinfo, nonfinite);
+                                                             rowinfo, nonfinite, cJz, rowz);
     return cudaGetLastError();
 }
 
@@ -580,10 +639,10 @@ cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int b
 
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
-                              const float* Wbar, float* grad_out, cudaStream_t s) {
+                              const float* Wbar, float* grad_out, cudaStream_t s, const float* rowz) {
     if (n <= 0) return cudaSuccess;
     k_exact_grad<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, g, theta, gal_idx, n,
-                                                                            rowinfo, Wbar, grad_out);
+                                                                            rowinfo, Wbar, grad_out, rowz);
     return cudaGetLastError();
 }
 

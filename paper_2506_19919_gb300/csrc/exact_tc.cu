@@ -17,368 +17,11 @@
 // wait is bounded: a timeout sets the block's abort flag and the global error
 // word, the roles unwind, in-flight copies are waited for (bounded) and TMEM
 // is released.
-#include <cuda.h>
-
-#include <type_traits>
-
-#include "band_tab.cuh"
-#include "sps_device.cuh"
-#include "tc_ptx.cuh"
+#include "exact_tc.cuh"
 
 namespace sps {
 
 namespace {
-
-constexpr int kTM = 128;       // rows per tile (MMA M)
-constexpr int kRowBytes = 128; // one k-block row: 64 BF16 or 32 FP32 (128-byte swizzle)
-constexpr int kThreadsTC = 192;   // adjoint: TMA warp, MMA warp, 4 epilogue warps
-constexpr int kFwdGroupBands = 8; // forward: bands per epilogue warp
-constexpr int kFwdMaxEpiWarps = 16;
-constexpr int kFwdBN = 256;
-constexpr int kFwdStages = 4;    // BF16 ring depth (TF32: 2; four tiles per stage)
-constexpr int kAdjBN = 224;      // K = 1344 = 6 x 224: each 128-row block streams V six times
-constexpr int kAdjStages = 5;    // BF16 ring depth (TF32: 2)
-constexpr uint32_t kTmemCols = 512;
-
-// Ring of STAGES stages; a stage holds an A tile (kTM rows) and a B tile (BN
-// rows) of one k-block, twice (hi and lo parts) for 3xTF32.
-template <int BN, int STAGES, bool TF>
-struct Ring {
-    static constexpr int kBK = TF ? 32 : 64;          // k per block row
-    static constexpr int kParts = TF ? 2 : 1;
-    static constexpr int kA = kTM * kRowBytes;
-    static constexpr int kB = BN * kRowBytes;
-    static constexpr int kStage = kParts * (kA + kB);
-    static constexpr int kBytes = STAGES * kStage;
-};
-
-struct Ctl {
-    uint64_t full[8], empty[8];
-    uint64_t tfull[2], tempty[2];
-    uint64_t drain;
-    uint32_t tmem_base;
-    volatile int abort;
-    int issued;
-};
-
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err,
-                                              uint32_t limit = tc::kSpinLimit);
-
-// Warp-uniform wait: lane 0 polls, the outcome is broadcast.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, ctl, err) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err,
-                                              uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023) == 1023 && ctl->abort) return false;
-    }
-    ctl->abort = 1;
-    atomicOr(err, 2);
-    return false;
-}
-
-// Shared prologue: barriers and TMEM allocation.  Returns the ring base.
-template <int STAGES>
-__device__ __forceinline__ void tc_setup(Ctl* ctl, int warp, int epi_threads = 4 * 32) {
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            tc::mbar_init(&ctl->full[s], 1);
-            tc::mbar_init(&ctl->empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&ctl->tfull[b], 1);
-            tc::mbar_init(&ctl->tempty[b], epi_threads);
-        }
-        tc::mbar_init(&ctl->drain, 1);
-        ctl->abort = 0;
-        ctl->issued = 0;
-        tc::fence_mbar_init();
-    }
-    if (warp == 1) {
-        tc::tmem_alloc(&ctl->tmem_base, kTmemCols);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-}
-
-// Producer (one lane): k-blocks of A (rows m0..) and B (rows of the n tile).
-// Stage layout: A_hi, B_hi, then (3xTF32) A_lo, B_lo.  tA[1], tB[1] are the
-// lo-part maps (unused for BF16).
-// Work items: (output tile nt, k chunk kc) for nt < n_tiles, kc < ceil(n_kb / kchunk);
-// an item accumulates k-blocks [kc kchunk, min((kc + 1) kchunk, n_kb)) from zero.
-template <int BN, int STAGES, bool TF>
-__device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtensorMap* tA,
-                                           const CUtensorMap* tB, int m0, int n_tiles, int n_kb,
-                                           int* err, int kchunk) {
-    using R = Ring<BN, STAGES, TF>;
-    int it = 0;
-    const int n_items = n_tiles * ((n_kb + kchunk - 1) / kchunk);
-    const int n_kc = (n_kb + kchunk - 1) / kchunk;
-    for (int item = 0; item < n_items && !ctl->abort; ++item) {
-        const int nt = item / n_kc, kc = item - nt * n_kc;
-        const int kb_end = min((kc + 1) * kchunk, n_kb);
-        for (int kb = kc * kchunk; kb < kb_end; ++kb, ++it) {
-            const int s = it % STAGES;
-            const uint32_t round = (uint32_t)(it / STAGES);
-            if (!wait_or_abort(&ctl->empty[s], (round & 1u) ^ 1u, ctl, err)) return;
-            uint8_t* a = ring + s * R::kStage;
-            uint8_t* b = a + R::kA;
-            tc::mbar_expect_tx(&ctl->full[s], R::kStage);
-            tc::tma_load_2d(a, &tA[0], kb * R::kBK, m0, &ctl->full[s]);
-            tc::tma_load_2d(b, &tB[0], kb * R::kBK, nt * BN, &ctl->full[s]);
-            if (TF) {
-                tc::tma_load_2d(b + R::kB, &tA[1], kb * R::kBK, m0, &ctl->full[s]);
-                tc::tma_load_2d(b + R::kB + R::kA, &tB[1], kb * R::kBK, nt * BN, &ctl->full[s]);
-            }
-            ctl->issued = it + 1;
-        }
-    }
-}
-
-// MMA issuer (one lane).
-template <int BN, int STAGES, bool TF>
-__device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int n_kb, int* err,
-                                       int kchunk) {
-    using R = Ring<BN, STAGES, TF>;
-    constexpr uint32_t idesc = TF ? tc::idesc_tf32(kTM, BN) : tc::idesc_bf16(kTM, BN);
-    int it = 0;
-    const int n_kc = (n_kb + kchunk - 1) / kchunk;
-    const int n_items = n_tiles * n_kc;
-    for (int item = 0; item < n_items; ++item) {
-        const int buf = item & 1;
-        const uint32_t use = (uint32_t)(item >> 1);
-        const int kc = item % n_kc;
-        const int kb0 = kc * kchunk, kb_end = min(kb0 + kchunk, n_kb);
-        if (!wait_or_abort(&ctl->tempty[buf], (use & 1u) ^ 1u, ctl, err)) break;
-        tc::tc_fence_after();
-        const uint32_t d = ctl->tmem_base + (uint32_t)(buf * BN);
-        bool ok = true;
-        for (int kb = kb0; kb < kb_end; ++kb, ++it) {
-            const int s = it % STAGES;
-            const uint32_t round = (uint32_t)(it / STAGES);
-            if (!wait_or_abort(&ctl->full[s], round & 1u, ctl, err)) {
-                ok = false;
-                break;
-            }
-            tc::tc_fence_after();
-            uint8_t* a = ring + s * R::kStage;
-            uint8_t* b = a + R::kA;
-            const uint64_t da = tc::sw128_desc(a), db = tc::sw128_desc(b);
-            if (TF) {
-                const uint64_t dal = tc::sw128_desc(b + R::kB), dbl = tc::sw128_desc(b + R::kB + R::kA);
-                // four k-steps of 8 FP32 (32 bytes) per 128-byte row
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    tc::mma_tf32(d, da + 2 * k, dbl + 2 * k, idesc, ((kb - kb0) | k) != 0);   // hi lo
-                    tc::mma_tf32(d, dal + 2 * k, db + 2 * k, idesc, 1);              // lo hi
-                    tc::mma_tf32(d, da + 2 * k, db + 2 * k, idesc, 1);               // hi hi
-                }
-            } else {
-                // four k-steps of 16 BF16 (32 bytes) per 128-byte row
-#pragma unroll
-                for (int k = 0; k < 4; ++k) tc::mma_bf16(d, da + 2 * k, db + 2 * k, idesc, ((kb - kb0) | k) != 0);
-            }
-            tc::mma_commit(&ctl->empty[s]);
-        }
-        if (!ok) break;
-        tc::mma_commit(&ctl->tfull[buf]);
-    }
-    // all issued MMAs complete before TMEM is released
-    tc::mma_commit(&ctl->drain);
-    for (uint32_t i = 0; i < tc::kSpinLimit; ++i)
-        if (tc::mbar_try_wait(&ctl->drain, 0)) break;
-}
-
-// Teardown: wait (bounded) for the producer's copies still in flight, then
-// free TMEM from the allocating warp.
-template <int STAGES>
-__device__ __forceinline__ void tc_teardown(Ctl* ctl, int warp) {
-    __syncwarp();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int issued = ctl->issued;
-        for (int it = max(0, issued - STAGES); it < issued; ++it) {
-            const int s = it % STAGES;
-            const uint32_t round = (uint32_t)(it / STAGES);
-            for (uint32_t i = 0; i < tc::kSpinLimit; ++i)
-                if (tc::mbar_try_wait(&ctl->full[s], round & 1u)) break;
-        }
-    }
-    __syncthreads();
-    if (warp == 1) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(ctl->tmem_base, kTmemCols);
-    }
-}
-
-static_assert(sizeof(Ctl) <= 256, "control block must fit before the staging area");
-
-template <int BN, int STAGES, bool TF>
-__device__ __forceinline__ uint8_t* carve(unsigned char* raw, Ctl*& ctl) {
-    uintptr_t p = reinterpret_cast<uintptr_t>(raw);
-    p = (p + 1023) & ~uintptr_t(1023);
-    uint8_t* ring = reinterpret_cast<uint8_t*>(p);
-    ctl = reinterpret_cast<Ctl*>(ring + Ring<BN, STAGES, TF>::kBytes);
-    return ring;
-}
-
-// ---------------------------------------------------------------- forward
-// Epilogue layout: 4 x n_groups x n_halves warps.  A warp reads the TMEM lane
-// quarter q = (warp id mod 4) (32 rows) of each tile, for the bands of its group (<= 8, held in
-// registers) and, when one group covers all bands, for one half of the tile's
-// columns.  Rows arrive sorted by redshift (perm), so the 32 rows of a warp see
-// nearly the same band supports: a band is visited in a 32-column chunk only if
-// it overlaps the chunk in some lane.
-template <int MAXT, bool TF>
-__global__ void __launch_bounds__(MAXT, 1)
-k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
-         const float* __restrict__ theta, const int32_t* __restrict__ gal_idx,
-         const int32_t* __restrict__ perm, int64_t n, int n_halves, float* __restrict__ cJ, int* err) {
-    constexpr int NB = kFwdGroupBands;
-    extern __shared__ unsigned char smem_raw[];
-    Ctl* ctl;
-    constexpr int ST = TF ? 2 : kFwdStages;
-    using R = Ring<kFwdBN, ST, TF>;
-    uint8_t* ring = carve<kFwdBN, ST, TF>(smem_raw, ctl);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kTM;
-    const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
-    const int n_kb = (c.k_pad + R::kBK - 1) / R::kBK;
-    const int epi_threads = (int)blockDim.x - 64;
-    tc_setup<ST>(ctl, warp, epi_threads);
-    if (warp == 0) {
-        if (lane == 0) tc_produce<kFwdBN, ST, TF>(ctl, ring, tm.a, tm.b, m0, n_tiles, n_kb, err, n_kb);
-    } else if (warp == 1) {
-        if (lane == 0) tc_mma<kFwdBN, ST, TF>(ctl, ring, n_tiles, n_kb, err, n_kb);
-    } else {
-        const int e = warp - 2;
-        const int q = warp & 3;                    // TMEM lane quarter this warp may access (warp id mod 4)
-        const int half = (e >> 2) % n_halves;      // column half (one group only)
-        const int b0 = ((e >> 2) / n_halves) * NB; // first band of this warp's group
-        const int ncol = kFwdBN / n_halves;
-        const int rl = 32 * q + lane;
-        const int64_t pos = (int64_t)m0 + rl;
-        const bool live = pos < n;
-        const int64_t row = live ? (perm ? (int64_t)perm[pos] : pos) : 0;
-        const int B = c.n_band;
-        int64_t gi = live ? (gal_idx ? (int64_t)gal_idx[row] : row) : 0;
-        const bool valid = live && gi >= 0 && gi < g.n;
-        if (!valid) gi = 0;
-        float cA = 0.f, dl = 0.f, eb = 0.f;
-        if (valid) {
-            const float* t = theta + row * SPS_NPARAM;
-            cA = -0.4f * kLog2_10f * t[9] * (1.0f / 4.05f);
-            dl = t[10];
-            eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
-        }
-        uint32_t sxy[NB];                          // support [lo, hi): lo | hi << 16
-        float gc[NB], gs[NB];
-        float acc[NB][4];
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            const int b = b0 + k;
-            int2 sp = make_int2(0, 0);
-            float2 ga = make_float2(0.f, 0.f);
-            if (b < B && valid) {
-                sp = g.support[gi * B + b];
-                ga = g.gauss[gi * B + b];
-            }
-            sxy[k] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
-            gc[k] = ga.x;
-            gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 top-hat, > 0 Gaussian, < 0 table
-            acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
-        }
-        bool has_tab = false;                      // a tabulated band in this warp's group
-#pragma unroll
-        for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < B && c.band_kind[b0 + k] == 2);
-        for (int nt = 0; nt < n_tiles; ++nt) {
-            const int buf = nt & 1;
-            const uint32_t use = (uint32_t)(nt >> 1);
-            if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
-            tc::tc_fence_after();
-            const int col0 = nt * kFwdBN + half * ncol;
-            for (int cc = 0; cc < ncol / 32; ++cc) {
-                const int nb0 = col0 + cc * 32;
-                if (nb0 >= c.n_lam) break;                 // warp-uniform
-                float S[32];
-                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
-                                  (uint32_t)(buf * kFwdBN + half * ncol + cc * 32), S);
-                // 32 columns x this warp's bands; the tabulated-curve form is a
-                // separate copy of the loop, run only by groups holding a
-                // tabulated band, so that the Gaussian / top-hat loop keeps
-                // its instruction footprint
-                auto columns = [&](auto tab_tag) {
-                    constexpr bool kTab = decltype(tab_tag)::value;
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
-                        const bool ov = lo < nb0 + 32 && hi > nb0;
-                        if (!__any_sync(0xffffffffu, ov)) continue;
-                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int nn = nb0 + j;
-                            if (nn >= lo && nn < hi) {
-                                const float4 L4 = __ldg(grid.lamc + nn);
-                                const float pw = __expf(dl * L4.z);
-                                const float base = L4.y * pw + eb * L4.w;
-                                const float E = exp2f(cA * base);
-                                const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
-                                float w = L4.x;
-                                if (kTab && gs[k] < 0.0f) {
-                                    const int b = b0 + k;
-                                    w *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b],
-                                                 (__ldg(grid.lam + nn) - gc[k]) * -gs[k]);
-                                } else if (gs[k] != 0.0f) {
-                                    const float u = (__ldg(grid.lam + nn) - gc[k]) * gs[k];
-                                    w *= __expf(-0.5f * u * u);
-                                }
-                                const float Sw = S[j] * w;
-                                const float es = Sw * E;
-                                a0 += Sw;
-                                a1 += es;
-                                a2 = fmaf(es, base, a2);
-                                a3 = fmaf(es, dterm, a3);
-                            }
-                        }
-                        acc[k][0] += a0;
-                        acc[k][1] += a1;
-                        acc[k][2] += a2;
-                        acc[k][3] += a3;
-                    }
-                };
-                if (has_tab)
-                    columns(std::true_type{});
-                else
-                    columns(std::false_type{});
-            }
-            tc::tc_fence_before();
-            tc::mbar_arrive(&ctl->tempty[buf]);
-        }
-        // cJ is zeroed before the launch; a (row, band) gets one addend per
-        // column half, so the sum does not depend on their order
-        if (valid && !ctl->abort) {
-#pragma unroll
-            for (int k = 0; k < NB; ++k)
-                if (b0 + k < B) {
-                    float* o = cJ + (row * B + b0 + k) * 4;
-                    atomicAdd(o + 0, acc[k][0]);
-                    atomicAdd(o + 1, acc[k][1]);
-                    atomicAdd(o + 2, acc[k][2]);
-                    atomicAdd(o + 3, acc[k][3]);
-                }
-        }
-    }
-    tc_teardown<ST>(ctl, warp);
-}
 
 // ---------------------------------------------------------------- wait probe
 // Exercises the pipeline's bounded wait: warp 0 waits on an mbarrier that
@@ -481,27 +124,9 @@ size_t tc_adj_smem(bool tf) {
 
 cudaError_t launch_fwd_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, const Galaxies& g,
                           const float* theta, const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ,
-                          int* err, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((n + kTM - 1) / kTM);
-    const size_t smem = tc_fwd_smem(tf);
-    const int groups = (c.n_band + kFwdGroupBands - 1) / kFwdGroupBands;   // <= 4 (B <= 32)
-    const int halves = groups == 1 ? 2 : 1;
-    const int threads = 64 + 32 * 4 * groups * halves;
-    cudaError_t e = cudaMemsetAsync(cJ, 0, (size_t)n * c.n_band * 4 * sizeof(float), s);
-    if (e != cudaSuccess) return e;
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (r != cudaSuccess) return r;
-        kern<<<blocks, threads, smem, s>>>(tm, c, grid, g, theta, gal_idx, perm, n, halves, cJ, err);
-        return cudaSuccess;
-    };
-    constexpr int T8 = 64 + 32 * 8, T12 = 64 + 32 * 12, T16 = 64 + 32 * kFwdMaxEpiWarps;
-    if (threads <= T8) e = tf ? go(k_fwd_tc<T8, true>) : go(k_fwd_tc<T8, false>);            // <= 16 bands
-    else if (threads <= T12) e = tf ? go(k_fwd_tc<T12, true>) : go(k_fwd_tc<T12, false>);    // <= 24 bands
-    else e = tf ? go(k_fwd_tc<T16, true>) : go(k_fwd_tc<T16, false>);                        // <= 32 bands
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+                          int* err, cudaStream_t s, float* cJz) {
+    if (cJz) return launch_fwd_tc_z(tm, tf, c, grid, g, theta, gal_idx, perm, n, cJ, err, s, cJz);
+    return fwd_tc_launch<false>(tm, tf, c, grid, g, theta, gal_idx, perm, n, cJ, err, s, nullptr);
 }
 
 cudaError_t launch_adj_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, int64_t n, float* Wbar,

@@ -33,6 +33,22 @@ __device__ double drude_shape(double lum) {
     return x / (d * d + x);
 }
 
+// d k0 / d lambda and d D / d lambda [per um] of the two curves above.
+__device__ double calzetti_dk0(double lum) {
+    if (calzetti_k0(lum) <= 0.0) return 0.0;
+    const double i1 = 1.0 / lum, i2 = i1 * i1;
+    return (lum < 0.63) ? 2.659 * (-1.509 * i2 + 2.0 * 0.198 * i2 * i1 - 3.0 * 0.011 * i2 * i2)
+                        : 2.659 * (-1.040 * i2);
+}
+__device__ double drude_dshape(double lum) {
+    const double x = (lum * 0.035) * (lum * 0.035);
+    const double dx = 2.0 * 0.035 * 0.035 * lum;
+    const double d = lum * lum - 0.2175 * 0.2175;
+    const double dd = 2.0 * lum;
+    const double den = d * d + x;
+    return (dx * d * d - 2.0 * x * d * dd) / (den * den);
+}
+
 template <typename T>
 __device__ T block_sum(T v, T* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -73,7 +89,8 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
           const float* __restrict__ zin, int64_t G,
           double h0, double om, float* __restrict__ lnT_out, float* __restrict__ lT10_out,
           float2* __restrict__ bins, double* __restrict__ zp, int2* __restrict__ support,
-          float2* __restrict__ gauss, float4* __restrict__ dust_eff) {
+          float2* __restrict__ gauss, float4* __restrict__ dust_eff, float* __restrict__ dtdz,
+          float* __restrict__ dzp, float4* __restrict__ ddust) {
     __shared__ double shd[32];
     __shared__ int shmin, shmax;
     const int64_t g = blockIdx.x;
@@ -100,9 +117,13 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
     const double dc = block_sum(part, shd) * (kCkms / h0);    // Mpc
     const double dl_cm = opz * dc * kMpcCm;
     const double T_yr = t_obs * 1e9;
+    // redshift derivatives: dt/dz = -1 / ((1+z) H(z)); d ln d_L / dz = 1/(1+z) + (c/H0) / (E d_C)
+    const double Ez = sqrt(om * opz * opz * opz + ol);
+    const double dlnDL = 1.0 / opz + (kCkms / h0) / (Ez * dc);
     if (threadIdx.x == 0) {
         lnT_out[g] = (float)log(t_obs);
         lT10_out[g] = (float)log10(T_yr);
+        dtdz[g] = (float)(-th / (opz * Ez));
     }
     // age bins in cosmic time (Eq. smoothPsfh): ages [min(E_i,T), min(E_{i+1},T)]
     for (int i = threadIdx.x; i < c.n_age; i += blockDim.x) {
@@ -135,25 +156,29 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
         }
         __syncthreads();
         double sN = 0.0, sQT = 0.0, sQTL = 0.0;
+        double sNd = 0.0, sQTd = 0.0, sQTLd = 0.0;              // their z derivatives over lambda
         int lo = L, hi = -1;
         for (int n = threadIdx.x; n < L; n += blockDim.x) {
             const double l = lam[n];
             const double lo_ = opz * l;                             // observed wavelength
-            double T;
+            double T, Td;                                           // T and dT / d lambda_obs
             bool in;
             if (kind == 0) {
                 in = (lo_ >= p0) && (lo_ < p1);
                 T = in ? 1.0 : 0.0;
+                Td = 0.0;
             } else if (kind == 1) {
                 // Gaussian support: |u| < 6 drops 2e-9 of the band's weight, below
                 // FP32 rounding; zero point and fluxes use the same support
                 double u = (lo_ - p0) / sg;
                 in = fabs(u) < 6.0;
                 T = in ? exp(-0.5 * u * u) : 0.0;
+                Td = -u / sg * T;
             } else {
                 const double u = (lo_ - p0) / p1;
                 in = u >= 0.0 && u <= (double)(c.tab_n[b] - 1);
                 T = tab_T64(tabT + c.tab_off[b], c.tab_n[b], u);
+                Td = tab_dT64(tabT + c.tab_off[b], c.tab_n[b], u) / p1;
             }
             if (in) {
                 double q = (n == 0) ? 0.5 * (lam[1] - lam[0])
@@ -162,6 +187,10 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
                 sN += q * T / l;
                 sQT += q * T;
                 sQTL += q * T * l;
+                // d T((1+z) l) / dz = l T'
+                sNd += q * Td;
+                sQTd += q * Td * l;
+                sQTLd += q * Td * l * l;
                 lo = min(lo, n);
                 hi = max(hi, n);
             }
@@ -171,6 +200,9 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
         sN = block_sum(sN, shd);
         sQT = block_sum(sQT, shd);
         sQTL = block_sum(sQTL, shd);
+        sNd = block_sum(sNd, shd);
+        sQTd = block_sum(sQTd, shd);
+        sQTLd = block_sum(sQTLd, shd);
         if (threadIdx.x == 0) {
             const size_t gb = (size_t)g * c.n_band + b;
             const double K = opz * kLsun / (4.0 * M_PI * dl_cm * dl_cm * kAbZp * sN);
@@ -183,6 +215,11 @@ k_prepare(const __grid_constant__ Consts c, const double* __restrict__ lam,
             const double lum = le * 1e-4;
             dust_eff[gb] = make_float4((float)calzetti_k0(lum), (float)log(le / 5500.0),
                                        (float)drude_shape(lum), (float)le);
+            // zp = -2.5 log10((1+z) L_sun / (4 pi d_L^2 3631 Jy N_b))
+            dzp[gb] = (float)(-2.5 / M_LN10 * (1.0 / opz - 2.0 * dlnDL - sNd / sN));
+            const double dle = (sQTLd * sQT - sQTL * sQTd) / (sQT * sQT);   // d lambda_eff / dz
+            ddust[gb] = make_float4((float)(calzetti_dk0(lum) * 1e-4 * dle), (float)(dle / le),
+                                    (float)(drude_dshape(lum) * 1e-4 * dle), 0.0f);
         }
         __syncthreads();
     }
@@ -197,7 +234,8 @@ constexpr int kCsspK = 128;
 constexpr int kCsspChunk = 256;
 __global__ void __launch_bounds__(kCsspK)
 k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
-       const double* __restrict__ band_p0, const double* __restrict__ band_p1, float* __restrict__ out) {
+       const double* __restrict__ band_p0, const double* __restrict__ band_p1, float* __restrict__ out,
+       int deriv) {
     __shared__ float wsh[kCsspChunk];
     const int64_t g = blockIdx.x;
     const int k = blockIdx.y * kCsspK + threadIdx.x;
@@ -214,7 +252,7 @@ k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
             for (int t = threadIdx.x; t < kCsspChunk; t += blockDim.x) {
                 int n = n0 + t;
                 float w = 0.0f;
-                if (n < sup.y) {
+                if (n < sup.y && !deriv) {
                     float4 lc = grid.lamc[n];
                     if (kind == 0) {
                         w = lc.x;
@@ -224,6 +262,16 @@ k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
                     } else {
                         const double u = (opz * grid.lam64[n] - band_p0[b]) / band_p1[b];
                         w = (float)((double)lc.x * tab_T64(grid.band_T64 + c.tab_off[b], c.tab_n[b], u));
+                    }
+                } else if (n < sup.y) {
+                    // d/dz of (q_n / l_n) T((1+z) l_n) = q_n T'((1+z) l_n): zero for a top-hat
+                    const double ql = (double)grid.lamc[n].x * grid.lam64[n];
+                    if (kind == 1) {
+                        const double u = (grid.lam64[n] - crest) * inv;
+                        w = (float)(-ql * u * (inv / opz) * exp(-0.5 * u * u));
+                    } else if (kind == 2) {
+                        const double u = (opz * grid.lam64[n] - band_p0[b]) / band_p1[b];
+                        w = (float)(ql * tab_dT64(grid.band_T64 + c.tab_off[b], c.tab_n[b], u) / band_p1[b]);
                     }
                 }
                 wsh[t] = w;
@@ -257,19 +305,20 @@ cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const dou
                                     const double* age_edges_yr, const float* z, int64_t n_gal,
                                     double h0, double om, float* lnT, float* lT10, float2* bins,
                                     double* zp, int2* support, float2* gauss, float4* dust_eff,
-                                    cudaStream_t s) {
+                                    float* dtdz, float* dzp, float4* ddust, cudaStream_t s) {
     if (n_gal <= 0) return cudaSuccess;
     k_prepare<<<(unsigned)n_gal, kPrepThreads, 0, s>>>(c, lam64, band_p0, band_p1, grid.band_T64, age_edges_yr,
                                                        z, n_gal, h0, om, lnT, lT10, bins, zp, support,
-                                                       gauss, dust_eff);
+                                                       gauss, dust_eff, dtdz, dzp, ddust);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cssp(const Consts& c, const Grid& grid, const Galaxies& g,
-                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s) {
+                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s,
+                        int deriv) {
     if (g.n <= 0) return cudaSuccess;
     dim3 grd((unsigned)g.n, (c.K + kCsspK - 1) / kCsspK);
-    k_cssp<<<grd, kCsspK, 0, s>>>(c, grid, g, band_p0, band_p1, cssp);
+    k_cssp<<<grd, kCsspK, 0, s>>>(c, grid, g, band_p0, band_p1, cssp, deriv);
     return cudaGetLastError();
 }
 

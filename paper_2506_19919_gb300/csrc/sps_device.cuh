@@ -147,7 +147,7 @@ struct RowScratch {
     float qb[kMaxMets];
     int slot_band[kMaxBands];
     float slot_S[kMaxBands];
-    float slot_F[kMaxBands];
+    float slot_D[kMaxBands];    // sum_k W_k d c_SSP[b][k] / dz (redshift gradient)
     float slot_g[kMaxBands];    // gamma_b
     __device__ AgeView view(const Consts& c) {
         return AgeView{m, dm[0], dm[1], dm[2], pi, w, wb, q, qb, &u.s, c.log_age_edge, c.lgz_edge};
@@ -764,6 +764,68 @@ __device__ __forceinline__ void age_met_adjoint(const Consts& c, const AgeView& 
 __device__ inline void age_met_adjoint(const Consts& c, RowScratch& s, float lT10, double M,
                                        const RowParams& p, float* g) {
     age_met_adjoint(c, s.view(c), lT10, M, p.th, g);
+}
+
+// ---------------------------------------------------------------- redshift through t_obs
+// SFR shape of Eq. SFRsmooth at ln t (t in Gyr): [(t/tau)^alpha + (t/tau)^-beta]^-1,
+// written as exp(beta v - softplus((alpha + beta) v)), v = ln(t / tau).
+__device__ __forceinline__ float sfr_shape_ln(float lnt, float ltau, float alpha, float beta) {
+    const float v = lnt - ltau;
+    const float x = (alpha + beta) * v;
+    const float sp = fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x)));
+    return __expf(beta * v - sp);
+}
+
+// sum_i wbar_i d w_i / d t_obs (t_obs in Gyr), given s.wb (dlogL/dw_i) and the
+// weights of age_met_weights, w_i = (1 - F_b) m_i + F_b pi_i M.  The bin
+// integrals m_i run over [t_obs - E_{i+1}, t_obs - E_i], so d m_i / d t_obs is
+// the SFR shape at the upper limit minus that at the lower one (a limit pinned
+// at t = 0 does not move); M = sum m_i moves by the shape at t_obs.  The burst
+// edges are clipped at lT = log10 t_obs: with x_T = (lT - mu) / sigma and
+// D = T(x_T), d pi_i / d lT = t(x_T) / (sigma D) ([i holds t_obs] - pi_i).
+// Bins are (centre c, half-width hw) in ln t; (ln t_hi, -1) reaches t = 0;
+// (0, 0) is empty.  The youngest bins are ~1e-5 wide in ln t, so forming
+// c +- hw in FP32 would lose most of the difference of the two shapes; it is
+// taken instead around the centre, h(c + s) / h(c) = exp(a(s)) with
+// a(s) = beta s - log1p(expm1(k s) sigma(k v)), k = alpha + beta, v = c - ln tau
+// (the softplus difference written exactly), so the difference is
+// h(c) (expm1(a(hw)) - expm1(a(-hw))).  Returns the warp-uniform sum.
+__device__ __forceinline__ float tobs_adjoint(const Consts& c, const AgeView& s, const float2* __restrict__ bins,
+                                              float lnT, float lT10, double M, const float* th) {
+    const int lane = lane_id();
+    const float ltau = __logf(th[1]), al = th[2], be = th[3], fb = th[4];
+    float s_m = 0.0f, s_p = 0.0f, wT = 0.0f;
+    for (int i = lane; i < c.n_age; i += 32) {
+        const float2 b = bins[i];
+        const float wb = s.wb[i];
+        float dm = 0.0f;
+        if (b.y > 0.0f) {
+            const float kk = al + be;
+            if (kk * b.y < 20.0f) {
+                const float sg = 1.0f / (1.0f + __expf(-kk * (b.x - ltau)));
+                const float ap = be * b.y - log1pf(expm1f(kk * b.y) * sg);
+                const float am = -be * b.y - log1pf(expm1f(-kk * b.y) * sg);
+                dm = sfr_shape_ln(b.x, ltau, al, be) * (expm1f(ap) - expm1f(am));
+            } else {            // a wide bin: no cancellation in the plain difference
+                dm = sfr_shape_ln(b.x + b.y, ltau, al, be) - sfr_shape_ln(b.x - b.y, ltau, al, be);
+            }
+        } else if (b.y < 0.0f) {
+            dm = sfr_shape_ln(b.x, ltau, al, be);
+            wT = wb;
+        }
+        s_m = fmaf(wb, dm, s_m);
+        s_p = fmaf(wb, s.pi[i], s_p);
+    }
+    s_m = warp_sum(s_m);
+    s_p = warp_sum(s_p);
+    wT = warp_sum(wT);
+    const float sig = th[6] * (1.0f / 3.0f);
+    const float xT = (lT10 - th[5]) / sig;
+    const float D = tri_cdf(xT);
+    const float dlT = 1.0f / (__expf(lnT) * kLn10f);              // d lT / d t_obs
+    const float dpi = tri_pdf(xT) / (sig * D) * dlT;
+    const float shT = sfr_shape_ln(lnT, ltau, al, be);
+    return (1.0f - fb) * s_m + fb * (shT * s_p + (float)M * dpi * (wT - s_p));
 }
 
 }  // namespace sps

@@ -49,12 +49,24 @@ __device__ __forceinline__ int fill_slots(const Consts& c, const Galaxies& g, Sl
     return nb;
 }
 
+// Per-galaxy redshift derivatives for the z column (kZ): d c_SSP / dz rows,
+// d zp / dz, the dust constants' d/dz at lambda_eff, and d t_obs / dz.
+struct ZRow {
+    const float* dcssp;     // [B][K]
+    const float* dzp;       // [B]
+    const float4* ddust;    // [B]
+    float dtdz;
+};
+
 // Evaluate one row.  Returns log L (FP64, warp-uniform; 0 if !like), writes
 // d.mag[slot] (FP64) and, if grad, the physical-parameter gradient into g[12]
-// (warp-uniform).
+// (warp-uniform).  kZ (with like and grad): also d log L / dz into g[12] (13
+// entries), the explicit part (filter, zero point, lambda_eff, c_SSP(z)) plus
+// the part through t_obs(z) (age bins, M, burst clipping).
+template <bool kZ = false>
 __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* __restrict__ bins,
                            float lnT, float lT10, const RowParams& p, int nb, bool like,
-                           bool grad, float* gout) {
+                           bool grad, float* gout, const ZRow* zr = nullptr) {
     RowScratch& s = ww.r;
     SlotData& d = ww.d;
     const int lane = lane_id();
@@ -82,11 +94,23 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
         }
         a = warp_sum(a);
         if (lane == 0) s.slot_S[sl] = a;
+        if (kZ) {
+            const float* Cd = zr->dcssp + (size_t)d.band[sl] * K;
+            float b = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kKTileMax; ++t) {
+                int k = lane + 32 * t;
+                if (k < K) b = fmaf(wreg[t], Cd[k], b);
+            }
+            b = warp_sum(b);
+            if (lane == 0) s.slot_D[sl] = b;
+        }
     }
     __syncwarp();
 
     double ll = 0.0;
     float gam = 0.0f;
+    float gz = 0.0f;             // kZ: this band's explicit d log L / dz
     DustTerms dt{1.f, 0.f, 0.f, 0.f};
     float S = 1.0f;
     if (lane < nb) {
@@ -101,6 +125,19 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
             double is2 = (double)d.isig2[lane];
             ll = -0.5 * r * r * is2;
             gam = (float)(2.5 * r * is2 / 2.302585092994046);
+            if (kZ) {
+                // m = zp - 2.5 log10(F S ...): dlogL/dm = -r is2, dlogL/dln c = gam;
+                // dF/dz through the dust curve at lambda_eff(z)
+                const int band = d.band[lane];
+                const float4 dd = zr->ddust[band];
+                const float AV = p.th[9], dl = p.th[10], ff = p.th[11];
+                const float eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
+                const float pw = __expf(dl * dc.y);
+                const float E = exp2f(-0.4f * kLog2_10f * AV * (1.0f / 4.05f) * (dc.x * pw + eb * dc.z));
+                const float dA = AV * (1.0f / 4.05f) * (dd.x * pw + dc.x * pw * dl * dd.y + eb * dd.z);
+                const float dF = (1.0f - ff) * E * (-0.4f * kLn10f) * dA;
+                gz = (float)(-r * is2) * zr->dzp[band] + gam * (dF / dt.F + s.slot_D[lane] / S);
+            }
         }
     }
     ll = warp_sum_d(ll);
@@ -155,6 +192,10 @@ __device__ inline double eval_row(const Consts& c, WarpWork& ww, const float2* _
     age_met_adjoint(c, s, lT10, M, p, g);
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) gout[k] = g[k];
+    if (kZ) {
+        gz = warp_sum(gz);
+        gout[SPS_NPARAM] = gz + zr->dtdz * tobs_adjoint(c, s.view(c), bins, lnT, lT10, M, p.th);
+    }
     __syncwarp();
     return ll;
 }

@@ -51,6 +51,11 @@ struct Galaxies {
     const float2* gauss;     // [G][B] (rest centre, (1+z)/s) of a Gaussian band
     const float* cssp;       // [G][B][K] per-galaxy c_SSP (approximate path) or nullptr
     const float4* dust_eff;  // [G][B] (k0, ln(l/lV), Drude, lambda_eff) at lambda_eff
+    // redshift derivatives (the z column of sps_loglike_grad_z)
+    const float* dtdz;       // [G] d t_obs / dz [Gyr]
+    const float* dzp;        // [G][B] d zp / dz [mag]
+    const float4* ddust;     // [G][B] d(k0, ln(l/lV), Drude) / dz at lambda_eff, unused
+    const float* dcssp;      // [G][B][K] d c_SSP / dz (approximate path) or nullptr
 };
 
 // Per-wavelength constants of the rest grid (device).
@@ -111,9 +116,11 @@ cudaError_t launch_prepare_galaxies(const Consts& c, const Grid& grid, const dou
                                     const double* age_edges_yr, const float* z, int64_t n_gal,
                                     double h0, double om, float* lnT, float* lT10, float2* bins,
                                     double* zp, int2* support, float2* gauss, float4* dust_eff,
-                                    cudaStream_t s);
+                                    float* dtdz, float* dzp, float4* ddust, cudaStream_t s);
+// c_SSP (deriv = 0) or its redshift derivative d c_SSP / dz (deriv = 1)
 cudaError_t launch_cssp(const Consts& c, const Grid& grid, const Galaxies& g,
-                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s);
+                        const double* band_p0, const double* band_p1, float* cssp, cudaStream_t s,
+                        int deriv = 0);
 
 // Row evaluation of the approximate path (photometry / log-likelihood + gradient).
 cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* theta,
@@ -121,6 +128,12 @@ cudaError_t launch_approx_rows(const Consts& c, const Galaxies& g, const float* 
                                const float* mag_obs, const float* sigma, const uint32_t* mask,
                                float* mag_out, float* loglike_out, float* grad_out,
                                double* logp_out, int* nonfinite, cudaStream_t s);
+// log L and the 13-column gradient (12 parameters and the redshift) of the
+// approximate path, one row per warp; needs g.dcssp
+cudaError_t launch_approx_rows_z(const Consts& c, const Galaxies& g, const float* theta,
+                                 const int32_t* gal_idx, int64_t n, const float* mag_obs,
+                                 const float* sigma, const uint32_t* mask, float* loglike_out,
+                                 float* grad_out, int* nonfinite, cudaStream_t s);
 
 // Exact path pieces.
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
@@ -130,14 +143,17 @@ cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxi
                                  float* W32lo = nullptr);            // with W32lo: W32 = TF32 hi, W32lo = lo
 cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
-                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s);
+                             const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s,
+                             float* cJz = nullptr);   // with cJz: [r][b][2] sum_n wb' S (1, E)
 cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32,
                                  cudaStream_t s);
 cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
                               const float* mag_obs, const float* sigma, const uint32_t* mask,
                               float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
-                              cudaStream_t s);
+                              cudaStream_t s,
+                              const float* cJz = nullptr,   // with cJz: rowz[r] = the explicit
+                              float* rowz = nullptr);       // (fixed-weights) part of dlogL/dz
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
                               const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s,
@@ -146,7 +162,8 @@ cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int b
                              const float* V32, float* Wbar, cudaStream_t s);
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
-                              const float* Wbar, float* grad_out, cudaStream_t s);
+                              const float* Wbar, float* grad_out, cudaStream_t s,
+                              const float* rowz = nullptr);   // with rowz: 13 columns, z last
 
 // Tensor-core (tcgen05) contractions; the tensor maps describe the operands:
 // a[0], b[0] the A (rows) and B (table) operands, and for 3xTF32 (tf) a[1],
@@ -158,7 +175,10 @@ size_t tc_fwd_smem(bool tf);
 size_t tc_adj_smem(bool tf);
 cudaError_t launch_fwd_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, const Galaxies& g,
                           const float* theta, const int32_t* gal_idx, const int32_t* perm, int64_t n, float* cJ,
-                          int* err, cudaStream_t s);
+                          int* err, cudaStream_t s, float* cJz = nullptr);
+cudaError_t launch_fwd_tc_z(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, const Galaxies& g,
+                            const float* theta, const int32_t* gal_idx, const int32_t* perm, int64_t n,
+                            float* cJ, int* err, cudaStream_t s, float* cJz);   // exact_tc_z.cu
 cudaError_t launch_adj_tc(const TcMaps& tm, bool tf, const Consts& c, const Grid& grid, int64_t n, float* Wbar,
                           int* err, cudaStream_t s);
 // Rows ordered by redshift (bucketed in log(1+z)): perm[pos] = row,

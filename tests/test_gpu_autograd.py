@@ -45,9 +45,12 @@ def prod96():
     ctx.close()
 
 
-@pytest.mark.parametrize("mode,prec,tol", [("approx", "fp32", 1e-4), ("exact", "fp32", 1e-4),
-                                           ("exact", "tf32x3", 2e-3), ("exact", "bf16", 1e-2)])
-def test_autograd_matches_oracle_gradient(prod96, mode, prec, tol):
+# (mode, precision, log L relative tolerance, gradient tolerance): the bars of
+# the parity tests for each path
+@pytest.mark.parametrize("mode,prec,ltol,tol", [("approx", "fp32", 2e-4, 1e-4), ("exact", "fp32", 2e-4, 1e-4),
+                                                ("exact", "tf32x3", 5e-4, 2e-3),
+                                                ("exact", "bf16", 5e-3, 1e-2)])
+def test_autograd_matches_oracle_gradient(prod96, mode, prec, ltol, tol):
     from paper_2506_19919_gb300 import autograd as AG
     wl, ctx, data = prod96
     dev = torch.device("cuda", 0)
@@ -61,7 +64,7 @@ def test_autograd_matches_oracle_gradient(prod96, mode, prec, tol):
     w = torch.linspace(0.5, 2.0, wl.n_gal, device=dev)
     (gw,) = torch.autograd.grad((w * ll).sum(), theta)
     llr, gr, _ = O.loglike_and_grad(ev, wl.z, wl.tables, data[mode], wl.sigma, wl.mask, mode)
-    np.testing.assert_allclose(ll.detach().cpu().numpy(), llr.numpy(), rtol=2e-4 if prec != "bf16" else 5e-3)
+    np.testing.assert_allclose(ll.detach().cpu().numpy(), llr.numpy(), rtol=ltol)
     g = (gw / w[:, None]).cpu().numpy()
     assert _rel(g, gr.numpy()) < tol
 

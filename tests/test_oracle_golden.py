@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden")
 
 
-def _load_generator():
-    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLD, "make_golden.py"))
+def _load_generator(name="make_golden"):
+    spec = importlib.util.spec_from_file_location(name, os.path.join(GOLD, name + ".py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod
@@ -37,3 +37,20 @@ def test_oracle_reproduces_its_regression_record():
         tol = 1e-7 if key.startswith(("hmc", "nuts")) else 1e-9
         scale = np.abs(b).max() if b.size else 1.0
         np.testing.assert_allclose(a, b, rtol=tol, atol=tol * scale, err_msg=key)
+
+
+def test_bench_error_reference_is_the_oracle():
+    """bench_error_reference.json (the FP64 values bench.py reports its
+    errors against) is what the oracle gives on those rows now."""
+    with open(os.path.join(GOLD, "bench_error_reference.json")) as f:
+        ref = json.load(f)
+    got = _load_generator("make_bench_reference").compute()
+    assert set(got) == set(ref)
+    for case in ref:
+        assert set(got[case]) == set(ref[case]), case
+        for key in ref[case]:
+            a = np.asarray(got[case][key], dtype=np.float64)
+            b = np.asarray(ref[case][key], dtype=np.float64)
+            assert a.shape == b.shape, (case, key)
+            scale = np.abs(b).max() if b.size else 1.0
+            np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-9 * scale, err_msg=f"{case} {key}")
