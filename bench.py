@@ -297,6 +297,8 @@ def run_ours(args):
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
     if rank == 0 and not args.skip_nuts:
         out["nuts"] = _nuts(ctx, wl, x0, mobs, value, float(nev.sum()) / (ms_local / 1e3))
+    if rank == 0 and not args.skip_exact_hmc:
+        out["hmc_exact"] = _hmc_exact(ctx, wl, x0, mobs, ms_step / 1e3)
     if rank == 0 and not args.skip_models:
         out["models"] = _models(wl, dev)
     if not args.skip_e2e:                       # every rank (collective timing)
@@ -354,6 +356,36 @@ def _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, full):
                     "own_posteriors_per_min": own / (s_run / 60.0),
                     "own_frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean())})
     return res
+
+
+def _hmc_exact(ctx, wl, x0, mobs, hmc_s_per_step):
+    """HMC on the exact photometry (BF16 contraction on the tensor cores) on
+    the bench galaxies and start points: every round evaluates every chain's
+    gradient through the exact path and takes one trajectory-asynchronous
+    leapfrog step.  A bounded run (10 + 10 iterations) is timed and scaled to
+    the workload's 500 + 500 by its cost per round; the paper's comparison is
+    the exact-photometry run against the approximate one."""
+    import torch
+    G, C = wl.n_gal, wl.chains
+    nw = ns = 10
+    kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"], seed=2506199190,
+              mode="exact", prec="bf16", samples=False)
+    ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=1, n_samp=0, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o = ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=nw, n_samp=ns, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    s_run = e0.elapsed_time(e1) / 1e3
+    nev = float(o["grad_evals"].sum())
+    n_it = wl.extra["n_warm"] + wl.extra["n_samp"]
+    s_full = s_run * n_it / (nw + ns)
+    return {"path": "sps_hmc_run mode EXACT, BF16 tcgen05 contraction, one gradient per chain per round",
+            "iterations_timed": nw + ns, "s_timed": s_run, "grad_evals_per_s": nev / s_run,
+            "projected_s_for_500_plus_500": s_full,
+            "exact_vs_approx_step_time": s_full / hmc_s_per_step,
+            "accept_mean": float(o["accept_prob"].mean()), "divergences": int(o["divergences"].sum())}
 
 
 def _nuts(ctx, wl, x0, mobs, hmc_value, hmc_evals_per_s):
@@ -750,6 +782,23 @@ def _survey(dev):
                   "s_per_iteration": per_it, "grad_evals_per_s": (runs[12][1] - runs[4][1]) / (runs[12][0] - runs[4][0]),
                   "projected_s_for_300_plus_300": runs[4][0] + per_it * (n_it - 4),
                   "note": "warm-up iterations from prior draws; cost per iteration from the 12-4 difference"}
+    # exact-photometry HMC (BF16): the cost of one round (a gradient of all
+    # 2,000,000 chains and a leapfrog step) from runs of 1 and 3 rounds
+    # (L = 1 and 3 in one iteration), projected with the mean L of the workload
+    kx = dict(chains_per_gal=C, samples=False, mode="exact", prec="bf16", n_warm=1, n_samp=0)
+    tr = {}
+    for L in (1, 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.hmc_run(x0, mobs, sigma, mask, L_min=L, L_max=L, **kx)
+        e1.record()
+        torch.cuda.synchronize()
+        tr[L] = e0.elapsed_time(e1) / 1e3
+    per_round = (tr[3] - tr[1]) / 2.0
+    mean_L = 0.5 * (wl.extra["L_min"] + wl.extra["L_max"])
+    out["hmc_exact_bf16"] = {"s_per_round": per_round, "grad_evals_per_s": G * C / per_round,
+                             "projected_s_for_300_plus_300": per_round * mean_L * n_it,
+                             "note": "rounds of 1 and 3 leapfrog steps timed; projected with the mean trajectory length"}
     ctx.close()
     return out
 
@@ -800,6 +849,7 @@ def _parser():
     ap.add_argument("--skip-models", action="store_true")
     ap.add_argument("--skip-errors", action="store_true")
     ap.add_argument("--skip-survey", action="store_true")
+    ap.add_argument("--skip-exact-hmc", action="store_true")
     ap.add_argument("--plain-full", action="store_true",
                     help="run the whole lock-step baseline HMC (minutes) and report its own ESS")
     # profiling captures only (not bench values): smaller galaxy count / iterations

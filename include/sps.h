@@ -299,6 +299,15 @@ typedef struct {
  * Eq. SkewNormPrior (sps_prior); sampling is in x.
  *  theta0_unb[G*C][12]: start points in unbounded space;
  *  samples_out[G*C][n_samp][12]: bounded (physical) draws, or NULL.
+ * cfg->mode APPROX (Eq. photo_integral_approx) runs the persistent fused
+ * kernel (HMC or NUTS, any metric).  cfg->mode EXACT (Eq. photo_integral_exact;
+ * the paper's exact-photometry HMC, Sec. 3) runs HMC with the identity metric
+ * in rounds: each round evaluates every chain's log L and gradient through the
+ * exact path in cfg->prec (the tensor-core contractions for SPS_BF16 and
+ * SPS_TF32X3) and takes one leapfrog step of every chain, a chain whose
+ * trajectory has ended starting its next iteration at once; same draws and
+ * sampler as the approximate path's HMC.  Synchronous; SPS_E_UNSUPPORTED for
+ * NUTS or an adapted metric in this mode.
  * Random numbers: Philox-4x32-10 keyed by seed, counter (iteration, block,
  * chain, 0) (NUTS: the counters listed at sps_sampler); a run is a pure
  * function of its inputs.  NUTS state takes 1.3 KB of device memory per chain. */

@@ -141,6 +141,25 @@ class ApproxTarget:
         return lp.detach().numpy(), g.detach().numpy()
 
 
+class ExactTarget(ApproxTarget):
+    """log posterior in unbounded space on the exact photometry (Eq.
+    photo_integral_exact): the SED contracted with the SSP table and the dust
+    curve at every wavelength, then integrated through the redshifted filters
+    (the band weights of each galaxy computed once, as its z is fixed)."""
+
+    def __init__(self, tables, z, mag_obs, sigma, mask, lo, hi, k=1.0, x0=0.0, skew=None):
+        super().__init__(tables, z, mag_obs, sigma, mask, lo, hi, k, x0, skew)
+        self.w, _, _ = O.band_weights(tables, O._t(z))                 # [G, B, Lam]
+        self.lam = torch.as_tensor(tables.lam_ang, dtype=O.DT)
+
+    def mags(self, theta, rows):
+        W, _, _, _ = O.ssp_weights(theta, self.tables, self.t_obs[rows])
+        S = O.sed_rest(W, self.tables)
+        F = O.attenuation(self.lam[None, :], theta[:, 9:10], theta[:, 10:11], theta[:, 11:12])
+        c = O.band_flux(S, F, self.w[rows])
+        return -2.5 * torch.log10(self.fac[rows, None] * c / self.nb[rows])
+
+
 def warmup_windows(n_warm):
     """(end of the initial buffer, slow windows [(start, end)], start of the
     terminal buffer) of the windowed metric adaptation."""

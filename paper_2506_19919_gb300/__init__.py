@@ -209,12 +209,13 @@ class Context:
     def hmc_run(self, theta0_unb, mag_obs, sigma, mask, chains_per_gal=4, n_warm=500,
                 n_samp=500, L_min=8, L_max=64, target_accept=0.8, eps0=0.1, seed=2506199190,
                 use_graph=True, autotune=True, samples=True, mode="approx", adapt_mass=0,
-                path="fused", sampler="hmc", max_depth=10):
+                path="fused", sampler="hmc", max_depth=10, prec="bf16"):
         """Batched HMC (sampler="hmc") or NUTS (sampler="nuts", identity metric,
         trees of at most max_depth doublings; L_min / L_max unused).
         path="fused" runs the persistent sampler (sps_hmc_run); path="plain"
         the lock-step forward-mode comparison baseline (sps_hmc_run_forward_mode,
-        HMC with the identity metric only)."""
+        HMC with the identity metric only).  mode="exact" samples on the exact
+        photometry (HMC, identity metric; prec selects the contraction)."""
         x0 = _f32(theta0_unb, None if isinstance(theta0_unb, torch.Tensor) else self.device)
         dev = x0.device
         mo = _f32(mag_obs, dev)
@@ -227,6 +228,7 @@ class Context:
         cfg.L_min, cfg.L_max = L_min, L_max
         cfg.target_accept, cfg.eps0, cfg.seed = target_accept, eps0, seed
         cfg.mode = MODES[mode]
+        cfg.prec = PRECS[prec]
         cfg.use_graph, cfg.autotune = int(use_graph), int(autotune)
         cfg.adapt_mass = {False: 0, True: 1, "diag": 1, "dense": 2, "none": 0}.get(adapt_mass, adapt_mass)
         cfg.sampler = {"hmc": 0, "nuts": 1}[sampler]

@@ -571,7 +571,7 @@ sps_status sps_set_galaxies(sps_ctx* ctx, const float* z, int64_t n_gal, int32_t
 static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gidx, int64_t n,
                             const float* mobs, const float* sigma, const uint32_t* mask, sps_prec prec,
                             float* mag_out, float* ll_out, float* grad_out, cudaStream_t s,
-                            bool want_z = false) {
+                            bool want_z = false, double* ll64_out = nullptr) {
     const Consts& c = ctx->c;
     const int NG = want_z ? SPS_NPARAM + 1 : SPS_NPARAM;
     // tcgen05 for BF16 operands (SIMT when disabled) and for 3xTF32; FP32 is SIMT
@@ -647,7 +647,8 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
         }
         CK(launch_exact_like(c, gv, th, gi, m, ctx->cJ.as<float>(), ctx->rowinfo.as<float>(), mo, sg,
                              mk, mag_out ? mag_out + r0 * c.n_band : nullptr,
-                             ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s, cJz, rowz));
+                             ll_out ? ll_out + r0 : nullptr, ctx->gbar.as<float>(), nf, s, cJz, rowz,
+                             ll64_out ? ll64_out + r0 : nullptr));
         if (grad_out) {
             if (tc) {
                 if (tf)
@@ -986,16 +987,97 @@ extern "C" sps_status sps_wait_probe(sps_ctx* ctx, int32_t ready, uint32_t spin_
     return SPS_OK;
 }
 
+// HMC on the exact photometry (Eq. photo_integral_exact): one gradient
+// evaluation of every chain per round through the exact path (the tensor-core
+// contractions for BF16 and 3xTF32), then one trajectory-asynchronous leapfrog
+// step of every chain (hmc_plain.cu: k_async_step), for as many rounds as the
+// longest chain's leapfrog steps.  Same sampler and draws as sps_hmc_run's
+// HMC with the identity metric.
+static sps_status hmc_exact(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
+                            const float* mag_obs, const float* sigma, const uint32_t* mask,
+                            float* samples_out, sps_hmc_stats* stats, cudaStream_t s) {
+    if (cfg->sampler != SPS_HMC) return fail(SPS_E_UNSUPPORTED, "the exact-path sampler runs HMC");
+    if (cfg->adapt_mass != 0) return fail(SPS_E_UNSUPPORTED, "the exact-path sampler uses the identity metric");
+    if (cfg->prec != SPS_FP32 && cfg->prec != SPS_BF16 && cfg->prec != SPS_TF32X3)
+        return fail(SPS_E_INVALID_ARG, "bad precision");
+    if (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096) return fail(SPS_E_SHAPE, "L range");
+    const int64_t G = ctx->n_gal;
+    const int C = cfg->chains_per_gal;
+    const int64_t NC = G * C;
+    const Consts& c = ctx->c;
+    const size_t GB = (size_t)G * c.n_band;
+    Stager st{ctx, s};
+    const float* x0 = st.in(theta0_unb, (size_t)NC * SPS_NPARAM);
+    const float* mo = st.in(mag_obs, GB);
+    const float* sg = st.in(sigma, GB);
+    const uint32_t* mk = st.in(mask, (size_t)G);
+    float* so = st.out(samples_out, (size_t)NC * cfg->n_samp * SPS_NPARAM);
+    float* acc = stats ? st.out(stats->accept_prob, (size_t)NC) : nullptr;
+    float* epo = stats ? st.out(stats->step_size, (size_t)NC) : nullptr;
+    int32_t* dv = stats ? st.out(stats->divergences, (size_t)NC) : nullptr;
+    int64_t* nev = stats ? st.out(stats->grad_evals, (size_t)NC) : nullptr;
+    int32_t* sto = stats ? st.out(stats->status, (size_t)NC) : nullptr;
+    if (sps_status r = st.check(); r != SPS_OK) return r;
+    HmcParams hp{C, cfg->n_warm, cfg->n_samp, cfg->L_min, cfg->L_max, cfg->target_accept, cfg->eps0,
+                 cfg->seed, 0, 1};
+    CK(ctx->pst.reserve(sizeof(PlainChain) * (size_t)NC));
+    CK(ctx->pth.reserve(sizeof(float) * SPS_NPARAM * (size_t)NC));
+    CK(ctx->pll.reserve(sizeof(double) * (size_t)NC));
+    CK(ctx->pgr.reserve(sizeof(float) * SPS_NPARAM * (size_t)NC));
+    CK(ctx->pgi.reserve(sizeof(int32_t) * (size_t)NC));
+    CK(ctx->rowz.reserve(sizeof(float) * (size_t)std::max<int64_t>(NC, 2)));   // FP32 log L (unused)
+    PlainChain* pst = ctx->pst.as<PlainChain>();
+    float* th = ctx->pth.as<float>();
+    double* ll = ctx->pll.as<double>();
+    float* gr = ctx->pgr.as<float>();
+    int32_t* gi = ctx->pgi.as<int32_t>();
+    float* llf = ctx->rowz.as<float>();
+    const sps_prec prec = (sps_prec)cfg->prec;
+    auto gradient = [&]() -> sps_status {
+        return run_exact(ctx, th, gi, NC, mo, sg, mk, prec, nullptr, llf, gr, s, false, ll);
+    };
+    CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
+    CK(plain_hmc_init(c, NC, C, x0, hp.eps0, pst, th, gi, s));
+    if (sps_status r = gradient(); r != SPS_OK) return r;
+    CK(plain_hmc_absorb(c, NC, pst, ll, gr, s));
+    CK(plain_hmc_start(c, hp, NC, pst, th, s));
+    int rounds = 0;
+    int* rbuf = ctx->nonfinite.as<int>() + 2;
+    CK(async_hmc_rounds(hp, NC, rbuf, s));
+    CK(cudaMemcpyAsync(&rounds, rbuf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < rounds; ++r) {
+        if (sps_status e = gradient(); e != SPS_OK) return e;
+        CK(async_hmc_step(c, hp, NC, pst, ll, gr, th, so, s));
+    }
+    CK(plain_hmc_stats(hp, NC, pst, acc, epo, dv, nev, sto, s));
+    int fl[2] = {0, 0};
+    CK(st.finish());
+    CK(cudaMemcpyAsync(fl, ctx->nonfinite.p, sizeof(fl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fl[1]) return fail(SPS_E_TIMEOUT, "a tensor-core pipeline wait timed out");
+    return SPS_OK;
+}
+
 extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const float* theta0_unb,
                                   const float* mag_obs, const float* sigma, const uint32_t* mask,
                                   float* samples_out, sps_hmc_stats* stats, void* stream) {
     if (!ctx || !cfg) return fail(SPS_E_INVALID_ARG, "null argument");
     if (ctx->n_gal <= 0) return fail(SPS_E_STATE, "no galaxy set");
-    if (cfg->mode != SPS_APPROX) return fail(SPS_E_UNSUPPORTED, "HMC runs on the approximate path");
-    if (!ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
+    if (cfg->mode != SPS_APPROX && cfg->mode != SPS_EXACT) return fail(SPS_E_INVALID_ARG, "bad mode");
+    if (cfg->mode == SPS_APPROX && !ctx->has_approx) return fail(SPS_E_STATE, "galaxy set built without approx tables");
     if (cfg->chains_per_gal < 1 || cfg->chains_per_gal > 64) return fail(SPS_E_SHAPE, "chains_per_gal in [1, 64]");
     if (cfg->n_warm < 0 || cfg->n_samp < 0 || cfg->n_warm + cfg->n_samp < 1)
         return fail(SPS_E_SHAPE, "iteration counts");
+    if (cfg->mode == SPS_EXACT) {
+        if (!(cfg->eps0 > 0) || !(cfg->target_accept > 0 && cfg->target_accept < 1))
+            return fail(SPS_E_INVALID_ARG, "eps0 / target_accept");
+        if (!theta0_unb || !mag_obs || !sigma || !mask) return fail(SPS_E_INVALID_ARG, "null input");
+        if ((int64_t)ctx->n_gal * cfg->chains_per_gal > ((int64_t)1 << 31)) return fail(SPS_E_SHAPE, "too many chains");
+        DeviceGuard dg(ctx->device);
+        CK(dg.err);
+        return hmc_exact(ctx, cfg, theta0_unb, mag_obs, sigma, mask, samples_out, stats, (cudaStream_t)stream);
+    }
     const bool nuts = cfg->sampler == SPS_NUTS;
     if (cfg->sampler != SPS_HMC && !nuts) return fail(SPS_E_INVALID_ARG, "sampler");
     if (!nuts && (cfg->L_min < 1 || cfg->L_max < cfg->L_min || cfg->L_max > 4096))

@@ -290,7 +290,8 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
                              const uint32_t* __restrict__ mask, float* __restrict__ mag_out,
                              float* __restrict__ ll_out, float* __restrict__ gbar,
                              float* __restrict__ rowinfo, int* __restrict__ nonfinite,
-                             const float* __restrict__ cJz, float* __restrict__ rowz) {
+                             const float* __restrict__ cJz, float* __restrict__ rowz,
+                             double* __restrict__ ll64_out) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const int B = c.n_band;
@@ -299,6 +300,7 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
         atomicOr(nonfinite, 1);
         if (rowz) rowz[row] = 0.0f;
         if (ll_out) ll_out[row] = __int_as_float(0x7fc00000);
+        if (ll64_out) ll64_out[row] = __longlong_as_double(0x7ff8000000000000ll);
         for (int b = 0; b < B; ++b) {
             if (mag_out) mag_out[row * B + b] = __int_as_float(0x7fc00000);
             if (gbar) gbar[row * B + b] = 0.0f;
@@ -340,6 +342,7 @@ __global__ void k_exact_like(const __grid_constant__ Consts c, const Galaxies g,
     }
     if (rowz) rowz[row] = gz;
     if (ll_out) ll_out[row] = (float)ll;
+    if (ll64_out) ll64_out[row] = ll;
     if (rowinfo) {
         rowinfo[row * 4 + 0] = g0;
         rowinfo[row * 4 + 1] = gAV;
@@ -605,11 +608,11 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
                               const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
                               const float* mag_obs, const float* sigma, const uint32_t* mask,
                               float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
-                              cudaStream_t s, const float* cJz, float* rowz) {
+                              cudaStream_t s, const float* cJz, float* rowz, double* ll64_out) {
     if (n <= 0) return cudaSuccess;
     k_exact_like<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, g, theta, gal_idx, n, cJ, mag_obs,
                                                              sigma, mask, mag_out, loglike_out, gbar,
-                                                             rowinfo, nonfinite, cJz, rowz);
+                                                             rowinfo, nonfinite, cJz, rowz, ll64_out);
     return cudaGetLastError();
 }
 

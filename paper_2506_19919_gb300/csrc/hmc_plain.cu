@@ -70,16 +70,12 @@ __global__ void k_plain_absorb(const __grid_constant__ Consts c, int64_t n, Plai
     st[i] = s;
 }
 
-// Start of iteration s.it for every chain: momentum, start state, half kick, drift.
-__global__ void k_plain_start(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
-                              PlainChain* __restrict__ st, float* __restrict__ theta) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    PlainChain s = st[i];
+// Start of iteration s.it of chain i: momentum, start state, half kick, drift.
+// Returns false (and leaves the chain inactive) once every iteration is done.
+__device__ __forceinline__ bool begin_iteration(const HmcParams& hp, int64_t i, PlainChain& s) {
     if (s.it >= hp.n_warm + hp.n_samp) {
         s.active = 0;
-        st[i] = s;
-        return;
+        return false;
     }
     const uint32_t k0 = (uint32_t)(hp.seed & 0xffffffffu), k1 = (uint32_t)(hp.seed >> 32);
     uint32_t w[16];
@@ -117,38 +113,24 @@ __global__ void k_plain_start(const __grid_constant__ Consts c, const HmcParams 
         s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
     }
     s.active = 1;
-    st[i] = s;
-    write_theta(c, s, theta + i * SPS_NPARAM);
+    return true;
 }
 
-// One leapfrog round after the gradient evaluation at every chain's x.
-__global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
-                             PlainChain* __restrict__ st, const double* __restrict__ ll,
-                             const float* __restrict__ gth, float* __restrict__ theta,
-                             float* __restrict__ samples) {
+__global__ void k_plain_start(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
+                              PlainChain* __restrict__ st, float* __restrict__ theta) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     PlainChain s = st[i];
-    s.nev += 1;                                   // every round evaluates every chain
-    if (!s.active) {
-        st[i] = s;
-        return;
-    }
-    absorb(c, s, ll[i], gth + i * SPS_NPARAM);
-#pragma unroll
-    for (int k = 0; k < SPS_NPARAM; ++k) s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
-    if (s.l + 1 < s.L) {
-#pragma unroll
-        for (int k = 0; k < SPS_NPARAM; ++k) {
-            s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
-            s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
-        }
-        s.l += 1;
-        st[i] = s;
-        write_theta(c, s, theta + i * SPS_NPARAM);
-        return;
-    }
-    // end of the trajectory: accept / reject, adaptation, sample
+    const bool on = begin_iteration(hp, i, s);
+    st[i] = s;
+    if (on) write_theta(c, s, theta + i * SPS_NPARAM);
+}
+
+// End of chain i's trajectory at s.x (after its last half kick): accept or
+// reject on the FP64 energy difference, step-size adaptation in the warm-up,
+// the sample in the sampling phase; the chain is then inactive.
+__device__ __forceinline__ void end_trajectory(const Consts& c, const HmcParams& hp, int64_t i, PlainChain& s,
+                                               float* __restrict__ samples) {
     float kin = 0.0f;
 #pragma unroll
     for (int k = 0; k < SPS_NPARAM; ++k) kin = fmaf(s.p[k], s.p[k], kin);
@@ -188,7 +170,86 @@ __global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams h
     }
     s.it = it + 1;
     s.active = 0;
+}
+
+// One leapfrog round after the gradient evaluation at every chain's x.
+__global__ void k_plain_step(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
+                             PlainChain* __restrict__ st, const double* __restrict__ ll,
+                             const float* __restrict__ gth, float* __restrict__ theta,
+                             float* __restrict__ samples) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s = st[i];
+    s.nev += 1;                                   // every round evaluates every chain
+    if (!s.active) {
+        st[i] = s;
+        return;
+    }
+    absorb(c, s, ll[i], gth + i * SPS_NPARAM);
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+    if (s.l + 1 < s.L) {
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) {
+            s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+            s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
+        }
+        s.l += 1;
+        st[i] = s;
+        write_theta(c, s, theta + i * SPS_NPARAM);
+        return;
+    }
+    end_trajectory(c, hp, i, s, samples);
     st[i] = s;
+}
+
+// Trajectory-asynchronous round of the exact-path sampler: after the
+// gradient evaluation at every chain's x, one leapfrog step of every active
+// chain; a chain whose trajectory ends starts its next iteration at once
+// (same draws and sampler as above), so every round's evaluations are used
+// until the chain has run all its iterations.
+__global__ void k_async_step(const __grid_constant__ Consts c, const HmcParams hp, int64_t n,
+                             PlainChain* __restrict__ st, const double* __restrict__ ll,
+                             const float* __restrict__ gth, float* __restrict__ theta,
+                             float* __restrict__ samples) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlainChain s = st[i];
+    if (!s.active) return;
+    s.nev += 1;
+    absorb(c, s, ll[i], gth + i * SPS_NPARAM);
+#pragma unroll
+    for (int k = 0; k < SPS_NPARAM; ++k) s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+    if (s.l + 1 < s.L) {
+#pragma unroll
+        for (int k = 0; k < SPS_NPARAM; ++k) {
+            s.p[k] = fmaf(0.5f * s.eps, s.g[k], s.p[k]);
+            s.x[k] = fmaf(s.eps, s.p[k], s.x[k]);
+        }
+        s.l += 1;
+        st[i] = s;
+        write_theta(c, s, theta + i * SPS_NPARAM);
+        return;
+    }
+    end_trajectory(c, hp, i, s, samples);
+    if (begin_iteration(hp, i, s)) write_theta(c, s, theta + i * SPS_NPARAM);
+    st[i] = s;
+}
+
+// Rounds the asynchronous sampler needs: the largest, over chains, of the
+// chain's leapfrog steps over all its iterations, sum_it L(it), from the same
+// Philox words that draw L.
+__global__ void k_traj_rounds(const HmcParams hp, int64_t n, int* __restrict__ max_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k0 = (uint32_t)(hp.seed & 0xffffffffu), k1 = (uint32_t)(hp.seed >> 32);
+    const uint64_t span = (uint64_t)(hp.L_max - hp.L_min + 1);
+    long long tot = 0;
+    for (int it = 0; it < hp.n_warm + hp.n_samp; ++it) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)it, 3u, (uint32_t)i, 0u), k0, k1);
+        tot += hp.L_min + (int)(((uint64_t)r.y * span) >> 32);
+    }
+    atomicMax(max_out, (int)min(tot, (long long)0x7fffffff));
 }
 
 __global__ void k_plain_stats(const HmcParams hp, int64_t n, const PlainChain* __restrict__ st, float* acc,
@@ -232,6 +293,21 @@ cudaError_t plain_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, Plai
                            const float* gth, float* theta, float* samples, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_plain_step<<<grid_for(n), 128, 0, s>>>(c, hp, n, st, ll, gth, theta, samples);
+    return cudaGetLastError();
+}
+
+cudaError_t async_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, const double* ll,
+                           const float* gth, float* theta, float* samples, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_async_step<<<grid_for(n), 128, 0, s>>>(c, hp, n, st, ll, gth, theta, samples);
+    return cudaGetLastError();
+}
+
+cudaError_t async_hmc_rounds(const HmcParams& hp, int64_t n, int* max_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(max_out, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_traj_rounds<<<grid_for(n), 128, 0, s>>>(hp, n, max_out);
     return cudaGetLastError();
 }
 

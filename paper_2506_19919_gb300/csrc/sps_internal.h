@@ -153,7 +153,8 @@ cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* t
                               float* mag_out, float* loglike_out, float* gbar, int* nonfinite,
                               cudaStream_t s,
                               const float* cJz = nullptr,   // with cJz: rowz[r] = the explicit
-                              float* rowz = nullptr);       // (fixed-weights) part of dlogL/dz
+                              float* rowz = nullptr,        // (fixed-weights) part of dlogL/dz
+                              double* ll64_out = nullptr);  // log L in FP64 (the samplers' accept)
 cudaError_t launch_exact_vgen(const Consts& c, const Grid& grid, const Galaxies& g,
                               const float* theta, const int32_t* gal_idx, int64_t n,
                               const float* gbar, float* V32, uint16_t* Vbf, cudaStream_t s,
@@ -233,6 +234,10 @@ cudaError_t plain_hmc_start(const Consts& c, const HmcParams& hp, int64_t n, Pla
                             cudaStream_t s);
 cudaError_t plain_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, const double* ll,
                            const float* gth, float* theta, float* samples, cudaStream_t s);
+// exact-path sampler: trajectory-asynchronous rounds (hmc_plain.cu)
+cudaError_t async_hmc_step(const Consts& c, const HmcParams& hp, int64_t n, PlainChain* st, const double* ll,
+                           const float* gth, float* theta, float* samples, cudaStream_t s);
+cudaError_t async_hmc_rounds(const HmcParams& hp, int64_t n, int* max_out, cudaStream_t s);
 cudaError_t plain_hmc_stats(const HmcParams& hp, int64_t n, const PlainChain* st, float* acc, float* eps_out,
                             int32_t* div_out, int64_t* nev_out, int32_t* status_out, cudaStream_t s);
 cudaError_t launch_leapfrog(const Consts& c, const Galaxies& g, const float* x0,

@@ -241,3 +241,18 @@ def test_dense_metric_learns_the_covariance():
     diag = H.run_hmc(_CorrGauss(), x0, np.zeros(C, int), seed=5, n_warm=300, n_samp=10, L_min=4,
                      L_max=12, adapt_mass=True, metric="diag")
     assert np.median(out["eps"]) > 3 * np.median(diag["eps"])
+
+
+def test_exact_target_is_the_oracle_exact_posterior():
+    """ExactTarget (band weights computed once per galaxy) gives the same log
+    posterior and gradient as the oracle's exact photometry evaluated afresh."""
+    from oracle import sps as O
+    wl = W.config(1, n_gal=3)
+    mobs = O.photometry(wl.theta_true, wl.z, wl.tables, "exact").numpy() + wl.noise
+    t = H.ExactTarget(wl.tables, wl.z, mobs, wl.sigma, wl.mask, W.PRIOR_LO, W.PRIOR_HI)
+    x = W.unbounded_of(W.prior_draw(np.random.default_rng(4), 3))
+    lp, g = t(x, np.arange(3))
+    lp2, g2 = O.logpost_and_grad_unbounded(x, wl.z, wl.tables, mobs, wl.sigma, wl.mask, W.PRIOR_LO,
+                                           W.PRIOR_HI, mode="exact")
+    np.testing.assert_allclose(lp, lp2.numpy(), rtol=1e-13)
+    np.testing.assert_allclose(g, g2.numpy(), rtol=1e-11, atol=1e-11 * np.abs(g2.numpy()).max())
