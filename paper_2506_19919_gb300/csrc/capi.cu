@@ -708,7 +708,10 @@ sps_status sps_photometry(sps_ctx* ctx, const float* theta, const int32_t* gal_i
     float* mo = st.out(mag_out, (size_t)n * ctx->c.n_band);
     if (sps_status r = st.check(); r != SPS_OK) return r;
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
-    if (mode == SPS_APPROX) {
+    if (mode == SPS_APPROX && ctx->c.n_met <= 12 && !ctx->c.mdf_age && !std::getenv("SPS_LIKE_ROWS")) {
+        // forward-only team evaluation, one row per warp
+        CK(launch_phot_team(ctx->c, ctx->gal(), th, gi, n, mo, ctx->nonfinite.as<int>(), s));
+    } else if (mode == SPS_APPROX) {
         CK(launch_approx_rows(ctx->c, ctx->gal(), th, 0, gi, n, nullptr, nullptr, nullptr, mo, nullptr,
                               nullptr, nullptr, ctx->nonfinite.as<int>(), s));
     } else {

@@ -104,7 +104,7 @@ __device__ __forceinline__ void tc_setup(Ctl* ctl, int warp, int epi_threads = 4
 template <int BN, int STAGES, bool TF>
 __device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtensorMap* tA,
                                            const CUtensorMap* tB, int m0, int n_tiles, int n_kb,
-                                           int* err, int kchunk) {
+                                           int* err, int kchunk, int nt0 = 0) {
     using R = Ring<BN, STAGES, TF>;
     int it = 0;
     const int n_items = n_tiles * ((n_kb + kchunk - 1) / kchunk);
@@ -120,10 +120,10 @@ __device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtens
             uint8_t* b = a + R::kA;
             tc::mbar_expect_tx(&ctl->full[s], R::kStage);
             tc::tma_load_2d(a, &tA[0], kb * R::kBK, m0, &ctl->full[s]);
-            tc::tma_load_2d(b, &tB[0], kb * R::kBK, nt * BN, &ctl->full[s]);
+            tc::tma_load_2d(b, &tB[0], kb * R::kBK, (nt0 + nt) * BN, &ctl->full[s]);
             if (TF) {
                 tc::tma_load_2d(b + R::kB, &tA[1], kb * R::kBK, m0, &ctl->full[s]);
-                tc::tma_load_2d(b + R::kB + R::kA, &tB[1], kb * R::kBK, nt * BN, &ctl->full[s]);
+                tc::tma_load_2d(b + R::kB + R::kA, &tB[1], kb * R::kBK, (nt0 + nt) * BN, &ctl->full[s]);
             }
             ctl->issued = it + 1;
         }
@@ -302,66 +302,89 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             for (int cc = 0; cc < ncol / 32; ++cc) {
                 const int nb0 = col0 + cc * 32;
                 if (nb0 >= c.n_lam) break;                 // warp-uniform
-                float S[32];
-                tc::tmem_ld32(ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
-                                  (uint32_t)(buf * kFwdBN + half * ncol + cc * 32), S);
-                // 32 columns x this warp's bands; the tabulated-curve form is a
-                // separate copy of the loop, run only by groups holding a
-                // tabulated band, so that the Gaussian / top-hat loop keeps
-                // its instruction footprint
+                const uint32_t taddr = ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
+                                       (uint32_t)(buf * kFwdBN + half * ncol + cc * 32);
+                // 32 columns x this warp's bands, in groups of CG columns: the
+                // band-independent terms of a column (S q / lambda and its
+                // products with E = 10^-0.4A, E base and E dterm, which give c
+                // and the A_V and delta factors) are formed once per group, then
+                // each band whose support some lane reaches in the group adds
+                // its weights over the group's columns (independent columns, so
+                // the band loop keeps its ILP).  Columns past the grid carry
+                // S = 0 (zero-filled table rows).  The tabulated-curve form is a
+                // separate copy, run only by groups holding a tabulated band, so
+                // that the Gaussian / top-hat loop keeps its instruction footprint.
                 auto columns = [&](auto tab_tag) {
                     constexpr bool kTab = decltype(tab_tag)::value;
+                    constexpr int CG = 8;                  // = the TMEM load width below
 #pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
-                        const bool ov = lo < nb0 + 32 && hi > nb0;
-                        if (!__any_sync(0xffffffffu, ov)) continue;
-                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, z0 = 0.f, z1 = 0.f;
+                    for (int h = 0; h < 32 / CG; ++h) {
+                        const int g0 = nb0 + h * CG;
+                        uint32_t act = 0;                          // warp-uniform
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int nn = nb0 + j;
-                            if (nn >= lo && nn < hi) {
-                                const float4 L4 = __ldg(grid.lamc + nn);
-                                const float pw = __expf(dl * L4.z);
-                                const float base = L4.y * pw + eb * L4.w;
-                                const float E = exp2f(cA * base);
-                                const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
-                                float w = L4.x;
-                                float wz = 0.0f;
-                                if (kTab && gs[k] < 0.0f) {
-                                    const int b = b0 + k;
-                                    const float lam = __ldg(grid.lam + nn);
-                                    const float ut = (lam - gc[k]) * -gs[k];
-                                    w *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], ut);
-                                    if (KZ)     // q T', T' = dT/du / step, 1/step = -gs/(1+z)
-                                        wz = L4.x * lam * tab_dT32(grid.band_T + c.tab_off[b], c.tab_n[b], ut) *
-                                             (-gs[k] * iopz);
-                                } else if (gs[k] != 0.0f) {
-                                    const float lam = __ldg(grid.lam + nn);
-                                    const float u = (lam - gc[k]) * gs[k];
-                                    w *= __expf(-0.5f * u * u);
-                                    if (KZ) wz = -w * lam * u * (gs[k] * iopz);   // q T', T' = -u T / s
-                                }
-                                const float Sw = S[j] * w;
-                                const float es = Sw * E;
-                                a0 += Sw;
-                                a1 += es;
-                                a2 = fmaf(es, base, a2);
-                                a3 = fmaf(es, dterm, a3);
-                                if (KZ) {
-                                    const float Sz = S[j] * wz;
-                                    z0 += Sz;
-                                    z1 = fmaf(Sz, E, z1);
+                        for (int k = 0; k < NB; ++k) {
+                            const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+                            if (__any_sync(0xffffffffu, lo < g0 + CG && hi > g0)) act |= 1u << k;
+                        }
+                        if (act == 0u) continue;
+                        float S[CG];
+                        tc::tmem_ld8(taddr + (uint32_t)(h * CG), S);
+                        float s0[CG], sE[CG], sEb[CG], sEd[CG], lm[CG];
+#pragma unroll
+                        for (int jj = 0; jj < CG; ++jj) {
+                            const int nn = min(g0 + jj, c.n_lam - 1);
+                            const float4 L4 = __ldg(grid.lamc + nn);
+                            lm[jj] = __ldg(grid.lam + nn);
+                            const float pw = __expf(dl * L4.z);
+                            const float base = L4.y * pw + eb * L4.w;
+                            const float E = exp2f(cA * base);
+                            const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
+                            s0[jj] = S[jj] * L4.x;
+                            sE[jj] = s0[jj] * E;
+                            sEb[jj] = sE[jj] * base;
+                            sEd[jj] = sE[jj] * dterm;
+                        }
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) {
+                            if (!((act >> k) & 1u)) continue;
+                            const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+                            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, z0 = 0.f, z1 = 0.f;
+#pragma unroll
+                            for (int jj = 0; jj < CG; ++jj) {
+                                const int nn = g0 + jj;
+                                if (nn >= lo && nn < hi) {
+                                    float w = 1.0f;
+                                    float wz = 0.0f;               // KZ: lambda T'
+                                    if (kTab && gs[k] < 0.0f) {
+                                        const int b = b0 + k;
+                                        const float ut = (lm[jj] - gc[k]) * -gs[k];
+                                        w = tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], ut);
+                                        if (KZ)     // T' = dT/du / step, 1/step = -gs/(1+z)
+                                            wz = lm[jj] * tab_dT32(grid.band_T + c.tab_off[b], c.tab_n[b], ut) *
+                                                 (-gs[k] * iopz);
+                                    } else if (gs[k] != 0.0f) {
+                                        const float u = (lm[jj] - gc[k]) * gs[k];
+                                        w = __expf(-0.5f * u * u);
+                                        if (KZ) wz = -w * lm[jj] * u * (gs[k] * iopz);   // T' = -u T / s
+                                    }
+                                    a0 = fmaf(s0[jj], w, a0);
+                                    a1 = fmaf(sE[jj], w, a1);
+                                    a2 = fmaf(sEb[jj], w, a2);
+                                    a3 = fmaf(sEd[jj], w, a3);
+                                    if (KZ) {
+                                        z0 = fmaf(s0[jj], wz, z0);
+                                        z1 = fmaf(sE[jj], wz, z1);
+                                    }
                                 }
                             }
-                        }
-                        acc[k][0] += a0;
-                        acc[k][1] += a1;
-                        acc[k][2] += a2;
-                        acc[k][3] += a3;
-                        if (KZ) {
-                            accz[k][0] += z0;
-                            accz[k][1] += z1;
+                            acc[k][0] += a0;
+                            acc[k][1] += a1;
+                            acc[k][2] += a2;
+                            acc[k][3] += a3;
+                            if (KZ) {
+                                accz[k][0] += z0;
+                                accz[k][1] += z1;
+                            }
                         }
                     }
                 };

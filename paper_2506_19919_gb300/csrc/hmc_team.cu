@@ -1238,7 +1238,114 @@ k_like_team(const __grid_constant__ Consts c, const Galaxies g, const float* __r
     }
 }
 
+// AB magnitudes of n independent rows (separable model), one row per warp
+// through the team layout without the adjoint: SFH, burst and MDF weights,
+// then per band one pass over the galaxy's c_SSP rows, S_b = sum_j q_j
+// sum_i w_i C_bij, and m_b = zp_b - 2.5 log10(1e9 10^lgM F_b S_b)
+// (Eq. photo_integral_approx).  Every warp of a block takes its next row
+// after one block barrier, as k_like_team.  Non-finite parameters or a
+// galaxy index out of range give NaN rows and raise *nonfinite.
+__global__ void __launch_bounds__(512, 1)
+k_phot_team(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
+            const int32_t* __restrict__ gal_idx, int64_t n, float* __restrict__ mag_out,
+            int* __restrict__ nonfinite) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ EdgeTables et;
+    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    TeamWork<1>& t = *reinterpret_cast<TeamWork<1>*>(smem + (size_t)warp * sizeof(TeamWork<1>));
+    const int lane = lane_id();
+    const int B = c.n_band, A = c.n_age, Zn = c.n_met, K = c.K;
+    for (int i = threadIdx.x; i <= c.n_age; i += blockDim.x) et.age[i] = c.log_age_edge[i];
+    for (int i = threadIdx.x; i <= c.n_met; i += blockDim.x) et.lgz[i] = c.lgz_edge[i];
+    const int64_t per_round = (int64_t)gridDim.x * warps;
+    const int64_t rounds = (n + per_round - 1) / per_round;
+    constexpr int kZ2 = kZnReg / 2;
+    for (int64_t r = 0; r < rounds; ++r) {
+        __syncthreads();
+        const int64_t row = (r * gridDim.x + blockIdx.x) * warps + warp;
+        if (row >= n) continue;
+        const int64_t gi = gal_idx ? (int64_t)gal_idx[row] : row;
+        const float xk = (lane < SPS_NPARAM) ? theta[row * SPS_NPARAM + lane] : 0.0f;
+        const bool ok = __all_sync(kFull, isfinite(xk)) && gi >= 0 && gi < g.n;
+        if (!ok) {
+            if (lane == 0) atomicOr(nonfinite, 1);
+            if (lane < B) mag_out[row * B + lane] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        for (int i = lane; i < A; i += 32) t.bins[i] = g.bins[(size_t)gi * A + i];
+        if (lane < SPS_NPARAM) t.th[0][lane] = xk;
+        __syncwarp();
+        const float lnT = g.lnT[gi], lT10 = g.lT10[gi];
+        age_met_parts<true>(c, age_view(t, 0, et), t.bins, lnT, lT10, t.th[0], false);
+        __syncwarp();
+        const double M = warp_sum_d(mass_partial(c, age_view(t, 0, et)));
+        age_weights(c, age_view(t, 0, et), t.th[0], M);
+        float2 qr[kZ2];
+#pragma unroll
+        for (int j = 0; j < kZ2; ++j)
+            qr[j] = make_float2((2 * j < Zn) ? t.q[0][2 * j] : 0.0f, (2 * j + 1 < Zn) ? t.q[0][2 * j + 1] : 0.0f);
+        float wl[4];
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+            const int i = lane + 32 * tt;
+            wl[tt] = (i < A) ? t.w[0][i] : 0.0f;
+        }
+        const double lgm = (double)t.th[0][0] + 9.0;
+        const float AV = t.th[0][9], dl = t.th[0][10], ff = t.th[0][11];
+        const float* Cg = g.cssp + (size_t)gi * B * K;
+#pragma unroll 1
+        for (int b = 0; b < B; ++b) {
+            const float* C = Cg + (size_t)b * K;
+            float2 U[kZ2];
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) U[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int tt = 0; tt < 4; ++tt) {
+                const int i = lane + 32 * tt;
+                float cs[kZnReg];
+#pragma unroll
+                for (int j = 0; j < kZnReg; ++j) cs[j] = 0.0f;
+                if (i < A) load_row(C + i * Zn, Zn, cs);
+                const float2 w2 = make_float2(wl[tt], wl[tt]);
+#pragma unroll
+                for (int j = 0; j < kZ2; ++j) U[j] = __ffma2_rn(w2, make_float2(cs[2 * j], cs[2 * j + 1]), U[j]);
+            }
+            float2 v = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) v = __ffma2_rn(qr[j], U[j], v);
+            const float S = warp_sum(v.x + v.y);
+            if (lane == 0) {
+                const size_t gb = (size_t)gi * B + b;
+                const float4 dc = g.dust_eff[gb];
+                const float F = dust_eval(dc.x, dc.y, dc.z, AV, dl, ff).F;
+                const double m = g.zp[gb] - 2.5 * (log10_flux(F * S) + lgm);
+                mag_out[row * B + b] = (float)m;
+                if (!isfinite(m)) atomicOr(nonfinite, 1);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_phot_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
+                             int64_t n, float* mag_out, int* nonfinite, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    constexpr int kWarps = 8;
+    const size_t smem = sizeof(TeamWork<1>) * kWarps;
+    cudaError_t e = cudaFuncSetAttribute(k_phot_team, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phot_team, 32 * kWarps, smem)) != cudaSuccess)
+        return e;
+    const int64_t need = (n + kWarps - 1) / kWarps;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * sms);
+    k_phot_team<<<blocks, 32 * kWarps, smem, s>>>(c, g, theta, gal_idx, n, mag_out, nonfinite);
+    return cudaGetLastError();
+}
 
 template <bool kNonsep>
 static cudaError_t like_launch(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,

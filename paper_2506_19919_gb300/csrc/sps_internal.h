@@ -217,6 +217,10 @@ struct HmcParams {
 cudaError_t launch_like_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
                              int64_t n, const float* mag_obs, const float* sigma, const uint32_t* mask,
                              float* ll_out, float* grad_out, int* nonfinite, cudaStream_t s);
+// approximate-path magnitudes of independent rows through the team layout,
+// forward only (separable model, n_met <= 12); see hmc_team.cu
+cudaError_t launch_phot_team(const Consts& c, const Galaxies& g, const float* theta, const int32_t* gal_idx,
+                             int64_t n, float* mag_out, int* nonfinite, cudaStream_t s);
 // rows: the age-dependent-MDF variant (one chain per warp, per-age q matrix); see hmc_team.cu
 size_t hmc_team_smem_per_warp(int cpw, bool rows);
 cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm);
