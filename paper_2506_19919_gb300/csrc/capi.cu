@@ -634,8 +634,8 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
             TcMaps tm;
             const bool ok = tf ? (make_tmap_f32(&tm.a[0], ctx->W.p, c.k_pad, m, c.k_pad, 128) &&
                                   make_tmap_f32(&tm.a[1], ctx->Wlo.p, c.k_pad, m, c.k_pad, 128) &&
-                                  make_tmap_f32(&tm.b[0], ctx->ssp_t_hi.p, c.k_pad, c.n_lam, c.k_pad, 256) &&
-                                  make_tmap_f32(&tm.b[1], ctx->ssp_t_lo.p, c.k_pad, c.n_lam, c.k_pad, 256))
+                                  make_tmap_f32(&tm.b[0], ctx->ssp_t_hi.p, c.k_pad, c.n_lam, c.k_pad, 128) &&
+                                  make_tmap_f32(&tm.b[1], ctx->ssp_t_lo.p, c.k_pad, c.n_lam, c.k_pad, 128))
                                : (make_tmap_bf16(&tm.a[0], ctx->W.p, c.k_pad, m, c.k_pad, 128) &&
                                   make_tmap_bf16(&tm.b[0], ctx->ssp_t_bf.p, c.k_pad, c.n_lam, c.k_pad, 256));
             if (!ok) return fail(SPS_E_CUDA, "tensor map encoding failed");

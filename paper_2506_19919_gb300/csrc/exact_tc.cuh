@@ -23,7 +23,14 @@ constexpr int kThreadsTC = 192;   // adjoint: TMA warp, MMA warp, 4 epilogue war
 constexpr int kFwdGroupBands = 8; // forward: bands per epilogue warp
 constexpr int kFwdMaxEpiWarps = 16;
 constexpr int kFwdBN = 256;
-constexpr int kFwdStages = 4;    // BF16 ring depth (TF32: 2; four tiles per stage)
+constexpr int kFwdStages = 4;    // BF16 ring depth
+// 3xTF32 forward: 128-column tiles, each with two TMEM accumulators (the
+// hi x hi product, and the hi x lo + lo x hi corrections, added in FP32 in the
+// epilogue), so that the large accumulator takes a third of the additions:
+// the tensor core's FP32 accumulation loses a fraction of an ulp per addition
+// in one direction, which over 3 x 168 additions left fluxes ~1.5e-5 low
+constexpr int kFwdBNtf = 128;
+constexpr int kFwdStagesTf = 3;  // four 16 KB tiles per stage
 constexpr int kAdjBN = 224;      // K = 1344 = 6 x 224: each 128-row block streams V six times
 constexpr int kAdjStages = 5;    // BF16 ring depth (TF32: 2)
 constexpr uint32_t kTmemCols = 512;
@@ -130,8 +137,10 @@ __device__ __forceinline__ void tc_produce(Ctl* ctl, uint8_t* ring, const CUtens
     }
 }
 
-// MMA issuer (one lane).
-template <int BN, int STAGES, bool TF>
+// MMA issuer (one lane).  SPLIT (3xTF32): per buffer two accumulators of
+// BN columns, the hi x hi product in the first, the two correction products
+// in the second.
+template <int BN, int STAGES, bool TF, bool SPLIT = false>
 __device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int n_kb, int* err,
                                        int kchunk) {
     using R = Ring<BN, STAGES, TF>;
@@ -146,7 +155,8 @@ __device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int
         const int kb0 = kc * kchunk, kb_end = min(kb0 + kchunk, n_kb);
         if (!wait_or_abort(&ctl->tempty[buf], (use & 1u) ^ 1u, ctl, err)) break;
         tc::tc_fence_after();
-        const uint32_t d = ctl->tmem_base + (uint32_t)(buf * BN);
+        const uint32_t d = ctl->tmem_base + (uint32_t)(buf * (SPLIT ? 2 * BN : BN));
+        const uint32_t dc = SPLIT ? d + (uint32_t)BN : d;        // corrections
         bool ok = true;
         for (int kb = kb0; kb < kb_end; ++kb, ++it) {
             const int s = it % STAGES;
@@ -164,9 +174,10 @@ __device__ __forceinline__ void tc_mma(Ctl* ctl, uint8_t* ring, int n_tiles, int
                 // four k-steps of 8 FP32 (32 bytes) per 128-byte row
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    tc::mma_tf32(d, da + 2 * k, dbl + 2 * k, idesc, ((kb - kb0) | k) != 0);   // hi lo
-                    tc::mma_tf32(d, dal + 2 * k, db + 2 * k, idesc, 1);              // lo hi
-                    tc::mma_tf32(d, da + 2 * k, db + 2 * k, idesc, 1);               // hi hi
+                    const bool acc = ((kb - kb0) | k) != 0;
+                    tc::mma_tf32(dc, da + 2 * k, dbl + 2 * k, idesc, acc);                 // hi lo
+                    tc::mma_tf32(dc, dal + 2 * k, db + 2 * k, idesc, 1);                   // lo hi
+                    tc::mma_tf32(d, da + 2 * k, db + 2 * k, idesc, SPLIT ? acc : true);   // hi hi
                 }
             } else {
                 // four k-steps of 16 BF16 (32 bytes) per 128-byte row
@@ -236,25 +247,27 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
     constexpr int NB = kFwdGroupBands;
     extern __shared__ unsigned char smem_raw[];
     Ctl* ctl;
-    constexpr int ST = TF ? 2 : kFwdStages;
-    using R = Ring<kFwdBN, ST, TF>;
-    uint8_t* ring = carve<kFwdBN, ST, TF>(smem_raw, ctl);
+    constexpr int BN = TF ? kFwdBNtf : kFwdBN;
+    constexpr int ST = TF ? kFwdStagesTf : kFwdStages;
+    constexpr int ACC = TF ? 2 * BN : BN;          // TMEM columns per buffer
+    using R = Ring<BN, ST, TF>;
+    uint8_t* ring = carve<BN, ST, TF>(smem_raw, ctl);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTM;
-    const int n_tiles = (c.n_lam + kFwdBN - 1) / kFwdBN;
+    const int n_tiles = (c.n_lam + BN - 1) / BN;
     const int n_kb = (c.k_pad + R::kBK - 1) / R::kBK;
     const int epi_threads = (int)blockDim.x - 64;
     tc_setup<ST>(ctl, warp, epi_threads);
     if (warp == 0) {
-        if (lane == 0) tc_produce<kFwdBN, ST, TF>(ctl, ring, tm.a, tm.b, m0, n_tiles, n_kb, err, n_kb);
+        if (lane == 0) tc_produce<BN, ST, TF>(ctl, ring, tm.a, tm.b, m0, n_tiles, n_kb, err, n_kb);
     } else if (warp == 1) {
-        if (lane == 0) tc_mma<kFwdBN, ST, TF>(ctl, ring, n_tiles, n_kb, err, n_kb);
+        if (lane == 0) tc_mma<BN, ST, TF, TF>(ctl, ring, n_tiles, n_kb, err, n_kb);
     } else {
         const int e = warp - 2;
         const int q = warp & 3;                    // TMEM lane quarter this warp may access (warp id mod 4)
         const int half = (e >> 2) % n_halves;      // column half (one group only)
         const int b0 = ((e >> 2) / n_halves) * NB; // first band of this warp's group
-        const int ncol = kFwdBN / n_halves;
+        const int ncol = BN / n_halves;
         const int rl = 32 * q + lane;
         const int64_t pos = (int64_t)m0 + rl;
         const bool live = pos < n;
@@ -298,12 +311,12 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             const uint32_t use = (uint32_t)(nt >> 1);
             if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
             tc::tc_fence_after();
-            const int col0 = nt * kFwdBN + half * ncol;
+            const int col0 = nt * BN + half * ncol;
             for (int cc = 0; cc < ncol / 32; ++cc) {
                 const int nb0 = col0 + cc * 32;
                 if (nb0 >= c.n_lam) break;                 // warp-uniform
                 const uint32_t taddr = ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
-                                       (uint32_t)(buf * kFwdBN + half * ncol + cc * 32);
+                                       (uint32_t)(buf * ACC + half * ncol + cc * 32);
                 // 32 columns x this warp's bands, in groups of CG columns: the
                 // band-independent terms of a column (S q / lambda and its
                 // products with E = 10^-0.4A, E base and E dterm, which give c
@@ -329,6 +342,12 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                         if (act == 0u) continue;
                         float S[CG];
                         tc::tmem_ld8(taddr + (uint32_t)(h * CG), S);
+                        if (TF) {                          // + the corrections, FP32 round to nearest
+                            float Sc[CG];
+                            tc::tmem_ld8(taddr + (uint32_t)(BN + h * CG), Sc);
+#pragma unroll
+                            for (int jj = 0; jj < CG; ++jj) S[jj] += Sc[jj];
+                        }
                         float s0[CG], sE[CG], sEb[CG], sEd[CG], lm[CG];
 #pragma unroll
                         for (int jj = 0; jj < CG; ++jj) {
