@@ -41,6 +41,12 @@ sys.path.insert(0, ROOT)
 import sps_workloads as W  # noqa: E402
 
 ESS_TARGET = 100.0
+# Dual-averaging target acceptance of the HMC legs.  With the workload's
+# fixed trajectory lengths L ~ U(8, 64), a lower target lengthens each
+# trajectory; measured on the full workload at 500 + 500 iterations,
+# posteriors/min at fixed ESS: 0.6 -> 3,599, 0.65 -> 4,264, 0.7 -> 4,634-4,655,
+# 0.72 -> 4,689, 0.75 -> 4,627, 0.8 (the library default) -> 4,286, 0.9 -> 3,179.
+TARGET_ACCEPT = 0.7
 METRIC = "posteriors/min at fixed ESS"
 UNIT = "posteriors/min"
 
@@ -174,7 +180,7 @@ def _hmc_workload(rank: int, n_gal: int | None = None, iters=None):
 def _config(tables, G, C, n_warm, n_samp, L, sampler, mdf_age, ws):
     """The workload description of the bench line (both arms)."""
     return {"workload": W.CONFIG_NAMES[3], "galaxies": G, "chains_per_gal": C,
-            "n_warm": n_warm, "n_samp": n_samp, "L": list(L),
+            "n_warm": n_warm, "n_samp": n_samp, "L": list(L), "target_accept": TARGET_ACCEPT,
             "ssp_grid": [tables.n_age, tables.n_met, tables.n_lam],
             "bands": tables.n_band, "photometry": "approx", "sampler": sampler,
             "mdf": "age-dependent" if mdf_age else "separable",
@@ -217,6 +223,7 @@ def run_ours(args):
     cfg.chains_per_gal, cfg.n_warm, cfg.n_samp = C, n_warm, n_samp
     cfg.L_min, cfg.L_max = wl.extra["L_min"], wl.extra["L_max"]
     cfg.seed = 2506199190 + rank
+    cfg.target_accept = TARGET_ACCEPT
     cfg.use_graph, cfg.autotune = 1, 1
     cfg.sampler = 1 if args.sampler == "nuts" else 0
     import ctypes as Ct
@@ -326,7 +333,7 @@ def _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, full):
     G, C = wl.n_gal, wl.chains
     n_it = wl.extra["n_warm"] + wl.extra["n_samp"]
     kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"],
-              seed=2506199190, path="plain")
+              seed=2506199190, path="plain", target_accept=TARGET_ACCEPT)
     res = {"path": "sps_hmc_run_forward_mode: chains in lock step, L_max rounds per iteration, "
                    "unfused forward-mode gradient of every chain every round"}
     if full:
@@ -369,7 +376,7 @@ def _hmc_exact(ctx, wl, x0, mobs, hmc_s_per_step):
     G, C = wl.n_gal, wl.chains
     nw = ns = 10
     kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"], seed=2506199190,
-              mode="exact", prec="bf16", samples=False)
+              mode="exact", prec="bf16", samples=False, target_accept=TARGET_ACCEPT)
     ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=1, n_samp=0, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -441,7 +448,7 @@ def _models(wl, dev):
         mo = (mt + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)).contiguous()
         x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
         kw = dict(chains_per_gal=wl.chains, seed=2506199190, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"],
-                  samples=False)
+                  samples=False, target_accept=TARGET_ACCEPT)
         ctx.hmc_run(x0, mo, wl.sigma, wl.mask, n_warm=2, n_samp=2, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -666,7 +673,7 @@ def _cpu_baseline(wl, mobs, post_frac, budget_s=20.0):
     iters = 0
     while True:
         OH.run_hmc(tgt, x0, np.repeat(np.arange(n), wl.chains), seed=1, n_warm=1, n_samp=0,
-                   L_min=wl.extra["L_min"], L_max=wl.extra["L_max"])
+                   L_min=wl.extra["L_min"], L_max=wl.extra["L_max"], target_accept=TARGET_ACCEPT)
         iters += 1
         if time.perf_counter() - t0 > budget_s or iters >= 50:
             break

@@ -330,9 +330,23 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                 auto columns = [&](auto tab_tag) {
                     constexpr bool kTab = decltype(tab_tag)::value;
                     constexpr int CG = 8;                  // = the TMEM load width below
+                    // group h + 1's TMEM words are loaded while group h is computed
+                    uint32_t rn[CG], rc[CG];
+                    tc::tmem_ld8_issue(taddr, rn);
+                    if (TF) tc::tmem_ld8_issue(taddr + (uint32_t)BN, rc);
 #pragma unroll
                     for (int h = 0; h < 32 / CG; ++h) {
                         const int g0 = nb0 + h * CG;
+                        tc::tmem_ld8_wait(rn);
+                        if (TF) tc::tmem_ld8_wait(rc);
+                        float S[CG];
+#pragma unroll
+                        for (int jj = 0; jj < CG; ++jj)     // + the corrections, FP32 round to nearest
+                            S[jj] = TF ? __uint_as_float(rn[jj]) + __uint_as_float(rc[jj]) : __uint_as_float(rn[jj]);
+                        if (h + 1 < 32 / CG) {
+                            tc::tmem_ld8_issue(taddr + (uint32_t)((h + 1) * CG), rn);
+                            if (TF) tc::tmem_ld8_issue(taddr + (uint32_t)(BN + (h + 1) * CG), rc);
+                        }
                         uint32_t act = 0;                          // warp-uniform
 #pragma unroll
                         for (int k = 0; k < NB; ++k) {
@@ -340,14 +354,6 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                             if (__any_sync(0xffffffffu, lo < g0 + CG && hi > g0)) act |= 1u << k;
                         }
                         if (act == 0u) continue;
-                        float S[CG];
-                        tc::tmem_ld8(taddr + (uint32_t)(h * CG), S);
-                        if (TF) {                          // + the corrections, FP32 round to nearest
-                            float Sc[CG];
-                            tc::tmem_ld8(taddr + (uint32_t)(BN + h * CG), Sc);
-#pragma unroll
-                            for (int jj = 0; jj < CG; ++jj) S[jj] += Sc[jj];
-                        }
                         float s0[CG], sE[CG], sEb[CG], sEd[CG], lm[CG];
 #pragma unroll
                         for (int jj = 0; jj < CG; ++jj) {
