@@ -51,11 +51,13 @@ METRIC = "posteriors/min at fixed ESS"
 UNIT = "posteriors/min"
 
 # DRAM traffic of one k_hmc_team launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of the five full-size launches in one ncu capture,
-# profiles/k_hmc_team_hmc4096gal_x4_launches.md), valid only while the
-# kernel's sources hash to the recorded value; otherwise reported as null.
+# dram__bytes_write.sum, mean of five launches of a reduced case with the same
+# 4,096-galaxy working set at 50 + 50 iterations, scaled by gradient
+# evaluations to 500 + 500; profiles/k_hmc_team_hmc4096gal_x4_launches.md),
+# valid only while the kernel's sources hash to the recorded value; otherwise
+# reported as null.
 KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_eval.cuh", "sps_internal.h", "philox.cuh")
-TRAFFIC = {"sha": "3867ec2e562fc6b4", "bytes": 200.460e9 + 10.543e9}
+TRAFFIC = {"sha": "9852f7a3036a38a4", "bytes": 186.50e9 + 10.147e9}
 
 
 def _kernel_sha():
