@@ -1165,7 +1165,7 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
     const int cpw0 = cands[0].first;
     auto blocks_for = [&](int cpw, int warps, int& blocks) -> cudaError_t {
         int per_sm = 0;
-        cudaError_t e = hmc_team_occupancy(cpw, rows, warps, &per_sm);
+        cudaError_t e = hmc_team_occupancy(cpw, rows, nuts, warps, &per_sm);
         if (e != cudaSuccess) return e;
         blocks = std::max(1, per_sm) * sms;
         return cudaSuccess;

@@ -376,28 +376,30 @@ __device__ __forceinline__ void team_eval(const Consts& c, TeamWork<CPW>& t, con
     __syncwarp();
     // qbar: sum the lanes' partials, one chain per round (two half sums);
     // with kNonsep the MDF gradient is already formed and qbar is zero
+    if constexpr (kNonsep) {
 #pragma unroll
-    for (int ch = 0; ch < CPW; ++ch) {
-        if constexpr (kNonsep) {
+        for (int ch = 0; ch < CPW; ++ch)
             if (lane < Zn) t.qb[ch][lane] = 0.0f;
-            __syncwarp();
-            continue;
-        }
+        __syncwarp();
+    } else {
 #pragma unroll
-        for (int j = 0; j < kZ2; ++j) {
-            t.u.red[lane][2 * j] = qbr[ch][j].x;
-            t.u.red[lane][2 * j + 1] = qbr[ch][j].y;
-        }
-        __syncwarp();
-        const int j = lane & 15, h = lane >> 4;
-        float s = 0.0f;
-        if (j < kZnReg) {
+        for (int ch = 0; ch < CPW; ++ch) {
+#pragma unroll
+            for (int j = 0; j < kZ2; ++j) {
+                t.u.red[lane][2 * j] = qbr[ch][j].x;
+                t.u.red[lane][2 * j + 1] = qbr[ch][j].y;
+            }
+            __syncwarp();
+            const int j = lane & 15, h = lane >> 4;
+            float s = 0.0f;
+            if (j < kZnReg) {
 #pragma unroll 8
-            for (int r = 0; r < 16; ++r) s += t.u.red[16 * h + r][j];
+                for (int r = 0; r < 16; ++r) s += t.u.red[16 * h + r][j];
+            }
+            s += __shfl_down_sync(kFull, s, 16);
+            if (lane < Zn) t.qb[ch][lane] = s;
+            __syncwarp();
         }
-        s += __shfl_down_sync(kFull, s, 16);
-        if (lane < Zn) t.qb[ch][lane] = s;
-        __syncwarp();
     }
     // ---- through the SFH, burst and MDF weights; then to unbounded space
 #pragma unroll 1
@@ -995,7 +997,7 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
                                           const uint32_t* __restrict__ mask, const int32_t* __restrict__ gal_order,
                                           ChainMetric* __restrict__ metric, int* nch_out, int* nb_out) {
     const int lane = lane_id();
-    const int B = c.n_band, K = c.K;
+    const int B = c.n_band;
     const uint32_t all = (B >= 32) ? 0xffffffffu : ((1u << B) - 1u);
     const int C = hp.chains_per_gal;
     const int groups = (C + CPW - 1) / CPW;
@@ -1063,39 +1065,39 @@ __device__ __noinline__ int64_t team_init(const Consts& c, const Galaxies& g, co
 }
 
 // One leapfrog step of every live chain after the team's evaluation.
-template <int CPW>
+template <int CPW, bool kNuts>
 __device__ __forceinline__ void team_step(const Consts& c, TeamWork<CPW>& t, const HmcParams& hp, int nch,
                                           float* __restrict__ samples) {
-    const int lane = lane_id();
-    const int n_it = hp.n_warm + hp.n_samp;
-    if (hp.nuts) {
+    if constexpr (kNuts) {
 #pragma unroll 1
         for (int ch = 0; ch < CPW; ++ch)
             if (!t.done[ch]) nuts_leaf<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
-        return;
-    }
+    } else {
+        const int lane = lane_id();
+        const int n_it = hp.n_warm + hp.n_samp;
 #pragma unroll 1
-    for (int ch = 0; ch < CPW; ++ch) {
-        if (t.done[ch]) continue;
-        if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
-        __syncwarp();
-        const int l = t.l[ch] + 1;
-        if (l == t.L[ch]) {
-            end_traj<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
-            if (t.it[ch] >= n_it) {
-                if (lane == 0) t.done[ch] = 1;
-                __syncwarp();
-            } else {
-                start_traj<CPW>(t, ch, hp);
-            }
-        } else {
+        for (int ch = 0; ch < CPW; ++ch) {
+            if (t.done[ch]) continue;
             if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
             __syncwarp();
-            metric_apply(t, ch, hp.adapt_mass == 2);
-            if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
-            __syncwarp();
-            if (lane == 0) t.l[ch] = l;
-            __syncwarp();
+            const int l = t.l[ch] + 1;
+            if (l == t.L[ch]) {
+                end_traj<CPW>(c, t, ch, hp, (ch < nch) ? samples : nullptr);
+                if (t.it[ch] >= n_it) {
+                    if (lane == 0) t.done[ch] = 1;
+                    __syncwarp();
+                } else {
+                    start_traj<CPW>(t, ch, hp);
+                }
+            } else {
+                if (lane < SPS_NPARAM) t.p[ch][lane] = fmaf(0.5f * t.eps[ch], t.g[ch][lane], t.p[ch][lane]);
+                __syncwarp();
+                metric_apply(t, ch, hp.adapt_mass == 2);
+                if (lane < SPS_NPARAM) t.x[ch][lane] = fmaf(t.eps[ch], t.v[ch][lane], t.x[ch][lane]);
+                __syncwarp();
+                if (lane == 0) t.l[ch] = l;
+                __syncwarp();
+            }
         }
     }
 }
@@ -1112,7 +1114,7 @@ __host__ __device__ constexpr size_t team_stride() {
 // (galaxy, chain group) items; the warps of a block advance one evaluation per
 // pass together (one block barrier per pass), so that they run the same code
 // at the same time and share the instruction cache.
-template <int CPW, bool kNonsep>
+template <int CPW, bool kNonsep, bool kNuts>
 __global__ void __launch_bounds__(512, 1)
 k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams hp,
            const float* __restrict__ theta0, const float* __restrict__ mag_obs,
@@ -1157,13 +1159,13 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
 #pragma unroll 1
             for (int ch = 0; ch < CPW; ++ch)
                 if (!t.done[ch]) {
-                    if (hp.nuts)
+                    if constexpr (kNuts)
                         nuts_start<CPW>(t, ch, hp);
                     else
                         start_traj<CPW>(t, ch, hp);
                 }
         } else {
-            team_step<CPW>(c, t, hp, nch, samples);
+            team_step<CPW, kNuts>(c, t, hp, nch, samples);
         }
         ++pass;
         bool any = false;
@@ -1383,7 +1385,7 @@ size_t hmc_team_smem_per_warp(int cpw, bool rows) {
     return cpw >= 4 ? sizeof(TeamWork<4>) : cpw == 2 ? sizeof(TeamWork<2>) : sizeof(TeamWork<1>);
 }
 
-template <int CPW, bool kNonsep>
+template <int CPW, bool kNonsep, bool kNuts>
 static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcParams& hp,
                                const float* theta0, const float* mag_obs, const float* sigma,
                                const uint32_t* mask, const int32_t* gal_order, float* samples,
@@ -1391,29 +1393,55 @@ static cudaError_t team_launch(const Consts& c, const Galaxies& g, const HmcPara
                                int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                                cudaStream_t s) {
     const size_t smem = team_stride<CPW, kNonsep>() * warps;
-    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kNonsep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = k_hmc_team<CPW, kNonsep, kNuts>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_hmc_team<CPW, kNonsep><<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order,
-                                                            samples, acc, eps_out, div, nevals, status, queue,
-                                                            metric);
+    kern<<<blocks, warps * 32, smem, s>>>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                                          div, nevals, status, queue, metric);
     return cudaGetLastError();
 }
 
-template <int CPW, bool kNonsep>
+template <int CPW, bool kNonsep, bool kNuts>
 static cudaError_t team_occupancy(int warps, int* blocks_per_sm) {
     const size_t smem = team_stride<CPW, kNonsep>() * warps;
-    cudaError_t e = cudaFuncSetAttribute(k_hmc_team<CPW, kNonsep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = k_hmc_team<CPW, kNonsep, kNuts>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hmc_team<CPW, kNonsep>, warps * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, warps * 32, smem);
 }
 
-cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm) {
-    if (rows) return team_occupancy<1, true>(warps, blocks_per_sm);
-    if (cpw >= 4) return team_occupancy<4, false>(warps, blocks_per_sm);
-    if (cpw == 2) return team_occupancy<2, false>(warps, blocks_per_sm);
-    return team_occupancy<1, false>(warps, blocks_per_sm);
+// The sampler is a template parameter (HMC or NUTS code only in each kernel);
+// chains per warp: 1, 2 or 4; the age-dependent MDF takes one chain per warp.
+template <bool kNuts>
+static cudaError_t occupancy_of(int cpw, bool rows, int warps, int* blocks_per_sm) {
+    if (rows) return team_occupancy<1, true, kNuts>(warps, blocks_per_sm);
+    if (cpw >= 4) return team_occupancy<4, false, kNuts>(warps, blocks_per_sm);
+    if (cpw == 2) return team_occupancy<2, false, kNuts>(warps, blocks_per_sm);
+    return team_occupancy<1, false, kNuts>(warps, blocks_per_sm);
+}
+
+cudaError_t hmc_team_occupancy(int cpw, bool rows, bool nuts, int warps, int* blocks_per_sm) {
+    return nuts ? occupancy_of<true>(cpw, rows, warps, blocks_per_sm)
+                : occupancy_of<false>(cpw, rows, warps, blocks_per_sm);
+}
+
+template <bool kNuts>
+static cudaError_t launch_of(int cpw, bool rows, const Consts& c, const Galaxies& g, const HmcParams& hp,
+                             const float* theta0, const float* mag_obs, const float* sigma, const uint32_t* mask,
+                             const int32_t* gal_order, float* samples, float* acc, float* eps_out, int32_t* div,
+                             int64_t* nevals, int32_t* status, int* queue, ChainMetric* metric, int blocks,
+                             int warps, cudaStream_t s) {
+    if (rows)
+        return team_launch<1, true, kNuts>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                                           eps_out, div, nevals, status, queue, metric, blocks, warps, s);
+    if (cpw >= 4)
+        return team_launch<4, false, kNuts>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                                            eps_out, div, nevals, status, queue, metric, blocks, warps, s);
+    if (cpw == 2)
+        return team_launch<2, false, kNuts>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
+                                            eps_out, div, nevals, status, queue, metric, blocks, warps, s);
+    return team_launch<1, false, kNuts>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                                        div, nevals, status, queue, metric, blocks, warps, s);
 }
 
 cudaError_t launch_hmc_team(int cpw, bool rows, const Consts& c, const Galaxies& g, const HmcParams& hp,
@@ -1422,17 +1450,11 @@ cudaError_t launch_hmc_team(int cpw, bool rows, const Consts& c, const Galaxies&
                             float* acc, float* eps_out, int32_t* div, int64_t* nevals,
                             int32_t* status, int* queue, ChainMetric* metric, int blocks, int warps,
                             cudaStream_t s) {
-    if (rows)
-        return team_launch<1, true>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
-                                    div, nevals, status, queue, metric, blocks, warps, s);
-    if (cpw >= 4)
-        return team_launch<4, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                                     eps_out, div, nevals, status, queue, metric, blocks, warps, s);
-    if (cpw == 2)
-        return team_launch<2, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc,
-                                     eps_out, div, nevals, status, queue, metric, blocks, warps, s);
-    return team_launch<1, false>(c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
-                                 div, nevals, status, queue, metric, blocks, warps, s);
+    if (hp.nuts)
+        return launch_of<true>(cpw, rows, c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                               div, nevals, status, queue, metric, blocks, warps, s);
+    return launch_of<false>(cpw, rows, c, g, hp, theta0, mag_obs, sigma, mask, gal_order, samples, acc, eps_out,
+                            div, nevals, status, queue, metric, blocks, warps, s);
 }
 
 }  // namespace sps

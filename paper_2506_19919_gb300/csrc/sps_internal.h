@@ -223,7 +223,7 @@ cudaError_t launch_phot_team(const Consts& c, const Galaxies& g, const float* th
                              int64_t n, float* mag_out, int* nonfinite, cudaStream_t s);
 // rows: the age-dependent-MDF variant (one chain per warp, per-age q matrix); see hmc_team.cu
 size_t hmc_team_smem_per_warp(int cpw, bool rows);
-cudaError_t hmc_team_occupancy(int cpw, bool rows, int warps, int* blocks_per_sm);
+cudaError_t hmc_team_occupancy(int cpw, bool rows, bool nuts, int warps, int* blocks_per_sm);
 cudaError_t launch_hmc_team(int cpw, bool rows, const Consts& c, const Galaxies& g, const HmcParams& hp,
                             const float* theta0, const float* mag_obs, const float* sigma,
                             const uint32_t* mask, const int32_t* gal_order, float* samples,
