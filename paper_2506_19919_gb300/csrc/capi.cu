@@ -594,7 +594,9 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
         CK(ctx->V.reserve((size_t)rows * c.lam_pad * 4));
         CK(ctx->Wbar.reserve((size_t)rows * c.k_pad * 4));
         if (tf) CK(ctx->Vlo.reserve((size_t)rows * c.lam_pad * 4));
+        CK(ctx->keep.reserve((size_t)rows * (size_t)keep_stride(c) * 4));
     }
+    float* keep = grad_out ? ctx->keep.as<float>() : nullptr;
     if (want_z) {
         CK(ctx->cJz.reserve((size_t)rows * c.n_band * 2 * 4));
         CK(ctx->rowz.reserve((size_t)rows * 4));
@@ -629,7 +631,7 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
         }
         if (tc) CK(launch_zsort(gv, gi, m, perm, pos_of, zcounts, s));
         CK(launch_exact_weights(c, grid, gv, th, gi, m, bf16, ctx->W.as<float>(), ctx->W.as<uint16_t>(), s,
-                                pos_of, tf ? ctx->Wlo.as<float>() : nullptr));
+                                pos_of, tf ? ctx->Wlo.as<float>() : nullptr, keep));
         if (tc) {
             TcMaps tm;
             const bool ok = tf ? (make_tmap_f32(&tm.a[0], ctx->W.p, c.k_pad, m, c.k_pad, 128) &&
@@ -673,7 +675,7 @@ static sps_status run_exact(sps_ctx* ctx, const float* theta, const int32_t* gid
                 CK(launch_exact_adj(c, grid, m, bf16, ctx->V.as<float>(), ctx->Wbar.as<float>(), s));
             }
             CK(launch_exact_grad(c, gv, th, gi, m, ctx->rowinfo.as<float>(), ctx->Wbar.as<float>(),
-                                 grad_out + r0 * NG, s, rowz));
+                                 grad_out + r0 * NG, s, rowz, keep));
         }
     }
     return SPS_OK;

@@ -87,6 +87,7 @@ struct sps_ctx {
     DevBuf hmcn;                      // NUTS tree state per chain
     DevBuf zperm;                     // redshift order of the rows of a tensor-core chunk
     DevBuf Wlo, Vlo;                  // low TF32 halves of W and v (3xTF32 exact path)
+    DevBuf keep;                      // exact path: weight arrays per row, kept for the gradient
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -133,7 +134,7 @@ struct sps_ctx {
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &gdtdz, &gdzp, &gddust, &gdcssp, &cJz, &rowz, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,
-                         &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo, &tabT, &tabT64};
+                         &pgi, &hmcn, &zperm, &ssp_hi, &ssp_lo, &ssp_t_hi, &ssp_t_lo, &Wlo, &Vlo, &keep, &tabT, &tabT64};
         for (DevBuf* b : all) b->release();
         for (auto& b : stage) b.release();
     }

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
           const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
           int bf16, float* __restrict__ W32, uint16_t* __restrict__ Wbf,
-          const int32_t* __restrict__ pos_of, float* __restrict__ W32lo) {
+          const int32_t* __restrict__ pos_of, float* __restrict__ W32lo, float* __restrict__ keep) {
     __shared__ RowScratch scratch[kWarpsApprox];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     RowScratch& s = scratch[warp];
@@ -48,7 +48,26 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
         load_params(c, theta + row * SPS_NPARAM, false, p);
         if (gi < 0 || gi >= g.n) p.finite = false;
         if (p.finite) {
-            age_met_weights(c, s, g.bins + (size_t)gi * c.n_age, g.lnT[gi], g.lT10[gi], p, false);
+            // with keep (a gradient follows): the derivative integrals too, and the
+            // arrays the adjoint needs are kept for it (m and w are the same
+            // either way: the derivatives are separate accumulators)
+            const double M = age_met_weights(c, s, g.bins + (size_t)gi * c.n_age, g.lnT[gi], g.lT10[gi], p,
+                                             keep != nullptr);
+            if (keep) {
+                const int A = c.n_age;
+                float* kr = keep + row * keep_stride(c);
+                if (lane == 0) *reinterpret_cast<double*>(kr) = M;
+                float* ka = kr + 2;
+                for (int i = lane; i < A; i += 32) {
+                    ka[i] = s.m[i];
+                    ka[A + i] = s.dm[0][i];
+                    ka[2 * A + i] = s.dm[1][i];
+                    ka[3 * A + i] = s.dm[2][i];
+                    ka[4 * A + i] = s.pi[i];
+                    ka[5 * A + i] = s.w[i];
+                }
+                if (lane < c.n_met) ka[6 * A + lane] = s.q[lane];
+            }
         } else {
             for (int i = lane; i < c.n_age; i += 32) s.w[i] = __int_as_float(0x7fc00000);
             if (lane < c.n_met) s.q[lane] = 1.0f;
@@ -453,7 +472,8 @@ k_exact_adj(const __grid_constant__ Consts c, const Grid grid, int64_t n,
 __global__ void __launch_bounds__(32 * kWarpsApprox)
 k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __restrict__ theta,
              const int32_t* __restrict__ gal_idx, int64_t n, const float* __restrict__ rowinfo,
-             const float* __restrict__ Wbar, float* __restrict__ grad_out, const float* __restrict__ rowz) {
+             const float* __restrict__ Wbar, float* __restrict__ grad_out, const float* __restrict__ rowz,
+             const float* __restrict__ keep) {
     __shared__ RowScratch scratch[kWarpsApprox];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     RowScratch& s = scratch[warp];
@@ -469,7 +489,23 @@ k_exact_grad(const __grid_constant__ Consts c, const Galaxies g, const float* __
             if (lane < NG) grad_out[row * NG + lane] = __int_as_float(0x7fc00000);
             continue;
         }
-        const double M = age_met_weights(c, s, g.bins + (size_t)gi * A, g.lnT[gi], g.lT10[gi], p, true);
+        double M;
+        if (keep) {                                // the weights kernel's arrays of this row
+            const float* kr = keep + row * keep_stride(c);
+            M = *reinterpret_cast<const double*>(kr);
+            const float* ka = kr + 2;
+            for (int i = lane; i < A; i += 32) {
+                s.m[i] = ka[i];
+                s.dm[0][i] = ka[A + i];
+                s.dm[1][i] = ka[2 * A + i];
+                s.dm[2][i] = ka[3 * A + i];
+                s.pi[i] = ka[4 * A + i];
+                s.w[i] = ka[5 * A + i];
+            }
+            if (lane < Zn) s.q[lane] = ka[6 * A + lane];
+        } else {
+            M = age_met_weights(c, s, g.bins + (size_t)gi * A, g.lnT[gi], g.lT10[gi], p, true);
+        }
         for (int k = lane; k < K; k += 32) s.u.kbuf[k] = Wbar[row * c.k_pad + k];
         __syncwarp();
         float gr[SPS_NPARAM];
@@ -519,10 +555,11 @@ int blocks_rows(int64_t rows, int per_block) {
 cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxies& g,
                                  const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
                                  float* W32, uint16_t* Wbf, cudaStream_t s, const int32_t* pos_of,
-                                 float* W32lo) {
+                                 float* W32lo, float* keep) {
     if (n <= 0) return cudaSuccess;
     k_weights<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, grid, g, theta, gal_idx,
-                                                                         n, bf16, W32, Wbf, pos_of, W32lo);
+                                                                         n, bf16, W32, Wbf, pos_of, W32lo,
+                                                                         keep);
     return cudaGetLastError();
 }
 
@@ -642,10 +679,11 @@ cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int b
 
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
-                              const float* Wbar, float* grad_out, cudaStream_t s, const float* rowz) {
+                              const float* Wbar, float* grad_out, cudaStream_t s, const float* rowz,
+                              const float* keep) {
     if (n <= 0) return cudaSuccess;
     k_exact_grad<<<blocks_rows(n, kWarpsApprox), 32 * kWarpsApprox, 0, s>>>(c, g, theta, gal_idx, n,
-                                                                            rowinfo, Wbar, grad_out, rowz);
+                                                                            rowinfo, Wbar, grad_out, rowz, keep);
     return cudaGetLastError();
 }
 

@@ -140,7 +140,9 @@ cudaError_t launch_exact_weights(const Consts& c, const Grid& grid, const Galaxi
                                  const float* theta, const int32_t* gal_idx, int64_t n,
                                  int bf16, float* W32, uint16_t* Wbf, cudaStream_t s,
                                  const int32_t* pos_of = nullptr,    // W row of each row (or itself)
-                                 float* W32lo = nullptr);            // with W32lo: W32 = TF32 hi, W32lo = lo
+                                 float* W32lo = nullptr,             // with W32lo: W32 = TF32 hi, W32lo = lo
+                                 float* keep = nullptr);             // with keep: the row's weight arrays
+                                                                     // (keep_stride floats per row)
 cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& g,
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
                              const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s,
@@ -164,7 +166,13 @@ cudaError_t launch_exact_adj(const Consts& c, const Grid& grid, int64_t n, int b
 cudaError_t launch_exact_grad(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* rowinfo,
                               const float* Wbar, float* grad_out, cudaStream_t s,
-                              const float* rowz = nullptr);   // with rowz: 13 columns, z last
+                              const float* rowz = nullptr,    // with rowz: 13 columns, z last
+                              const float* keep = nullptr);   // weight arrays kept by the weights kernel
+// Floats per row of the kept weight arrays: M (FP64, two floats), then
+// m, dm/dtau, dm/dalpha, dm/dbeta, pi, w over the age bins and q over the
+// metallicity bins; a multiple of 4 floats, so that every row's M is 8-byte
+// aligned.
+__host__ __device__ inline int64_t keep_stride(const Consts& c) { return (2 + 6 * (int64_t)c.n_age + c.n_met + 3) / 4 * 4; }
 
 // Tensor-core (tcgen05) contractions; the tensor maps describe the operands:
 // a[0], b[0] the A (rows) and B (table) operands, and for 3xTF32 (tf) a[1],
