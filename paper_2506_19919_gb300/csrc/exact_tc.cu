@@ -125,7 +125,8 @@ k_adj_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
 }  // namespace
 
 size_t tc_fwd_smem(bool tf) {
-    return (tf ? Ring<kFwdBNtf, kFwdStagesTf, true>::kBytes : Ring<kFwdBN, kFwdStages, false>::kBytes) + 256 + 1024;
+    return (tf ? Ring<kFwdBNtf, kFwdStagesTf, true>::kBytes : Ring<kFwdBN, kFwdStages, false>::kBytes) + 256 +
+           kFwdConstBytes + 1024;
 }
 size_t tc_adj_smem(bool tf) {
     return (tf ? Ring<kAdjBN, 2, true>::kBytes : Ring<kAdjBN, kAdjStages, false>::kBytes) + sizeof(Ctl) + 1024;

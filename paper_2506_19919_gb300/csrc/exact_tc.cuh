@@ -34,6 +34,10 @@ constexpr int kFwdStagesTf = 3;  // four 16 KB tiles per stage
 constexpr int kAdjBN = 224;      // K = 1344 = 6 x 224: each 128-row block streams V six times
 constexpr int kAdjStages = 5;    // BF16 ring depth (TF32: 2)
 constexpr uint32_t kTmemCols = 512;
+// Forward epilogue: per warp, the wavelength constants (lamc, lam) of the
+// 32-column chunk being processed, staged in shared memory after the control
+// block (the next chunk's are loaded into registers meanwhile).
+constexpr int kFwdConstBytes = kFwdMaxEpiWarps * 32 * (16 + 4);
 
 // Ring of STAGES stages; a stage holds an A tile (kTM rows) and a B tile (BN
 // rows) of one k-block, twice (hi and lo parts) for 3xTF32.
@@ -306,15 +310,40 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
         bool has_tab = false;                      // a tabulated band in this warp's group
 #pragma unroll
         for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < B && c.band_kind[b0 + k] == 2);
+        // this warp's staging of the chunk constants (lane j: column nb0 + j,
+        // clamped to the grid), and the registers holding the next chunk's
+        float4* cst4 = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(ctl) + 256) + 32 * e;
+        float* cstl = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ctl) + 256 + kFwdMaxEpiWarps * 32 * 16) +
+                      32 * e;
+        float4 pL4;
+        float pl;
+        {
+            const int nn = min(half * ncol + lane, c.n_lam - 1);
+            pL4 = __ldg(grid.lamc + nn);
+            pl = __ldg(grid.lam + nn);
+        }
         for (int nt = 0; nt < n_tiles; ++nt) {
             const int buf = nt & 1;
             const uint32_t use = (uint32_t)(nt >> 1);
             if (!warp_wait(&ctl->tfull[buf], use & 1u, ctl, err)) break;
             tc::tc_fence_after();
             const int col0 = nt * BN + half * ncol;
+            const int col_end = min(col0 + ncol, c.n_lam);
             for (int cc = 0; cc < ncol / 32; ++cc) {
                 const int nb0 = col0 + cc * 32;
                 if (nb0 >= c.n_lam) break;                 // warp-uniform
+                // publish this chunk's constants, then load the next chunk's
+                // (the next one processed: in this tile, else the next tile's first)
+                __syncwarp();
+                cst4[lane] = pL4;
+                cstl[lane] = pl;
+                __syncwarp();
+                {
+                    const int nx = (nb0 + 32 < col_end) ? nb0 + 32 : (nt + 1) * BN + half * ncol;
+                    const int nn = min(nx + lane, c.n_lam - 1);
+                    pL4 = __ldg(grid.lamc + nn);
+                    pl = __ldg(grid.lam + nn);
+                }
                 const uint32_t taddr = ctl->tmem_base + ((uint32_t)(32 * q) << 16) +
                                        (uint32_t)(buf * ACC + half * ncol + cc * 32);
                 // 32 columns x this warp's bands, in groups of CG columns: the
@@ -357,9 +386,8 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                         float s0[CG], sE[CG], sEb[CG], sEd[CG], lm[CG];
 #pragma unroll
                         for (int jj = 0; jj < CG; ++jj) {
-                            const int nn = min(g0 + jj, c.n_lam - 1);
-                            const float4 L4 = __ldg(grid.lamc + nn);
-                            lm[jj] = __ldg(grid.lam + nn);
+                            const float4 L4 = cst4[h * CG + jj];
+                            lm[jj] = cstl[h * CG + jj];
                             const float pw = __expf(dl * L4.z);
                             const float base = L4.y * pw + eb * L4.w;
                             const float E = exp2f(cA * base);
