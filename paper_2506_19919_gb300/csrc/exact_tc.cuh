@@ -401,6 +401,34 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                         for (int k = 0; k < NB; ++k) {
                             if (!((act >> k) & 1u)) continue;
                             const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+                            if constexpr (!KZ && !kTab) {
+                                // Gaussian / top-hat band weights of column pairs, packed
+                                // FP32x2; a column outside the support adds S x 0
+                                float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;
+                                const float2 ngc = make_float2(-gc[k], -gc[k]), gs2 = make_float2(gs[k], gs[k]);
+                                const float2 m05 = make_float2(-0.5f, -0.5f);
+                                const bool gauss = gs[k] != 0.0f;
+#pragma unroll
+                                for (int jj = 0; jj < CG; jj += 2) {
+                                    const int nn = g0 + jj;
+                                    const bool i0 = nn >= lo && nn < hi, i1 = nn + 1 >= lo && nn + 1 < hi;
+                                    float2 w = make_float2(i0 ? 1.0f : 0.0f, i1 ? 1.0f : 0.0f);
+                                    if (gauss) {
+                                        const float2 u = __fmul2_rn(__fadd2_rn(make_float2(lm[jj], lm[jj + 1]), ngc), gs2);
+                                        const float2 t = __fmul2_rn(__fmul2_rn(m05, u), u);
+                                        w = make_float2(i0 ? __expf(t.x) : 0.0f, i1 ? __expf(t.y) : 0.0f);
+                                    }
+                                    p0 = __ffma2_rn(make_float2(s0[jj], s0[jj + 1]), w, p0);
+                                    p1 = __ffma2_rn(make_float2(sE[jj], sE[jj + 1]), w, p1);
+                                    p2 = __ffma2_rn(make_float2(sEb[jj], sEb[jj + 1]), w, p2);
+                                    p3 = __ffma2_rn(make_float2(sEd[jj], sEd[jj + 1]), w, p3);
+                                }
+                                acc[k][0] += p0.x + p0.y;
+                                acc[k][1] += p1.x + p1.y;
+                                acc[k][2] += p2.x + p2.y;
+                                acc[k][3] += p3.x + p3.y;
+                                continue;
+                            }
                             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, z0 = 0.f, z1 = 0.f;
 #pragma unroll
                             for (int jj = 0; jj < CG; ++jj) {
