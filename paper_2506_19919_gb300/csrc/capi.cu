@@ -474,6 +474,9 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         if (e != cudaSuccess) return e;
         return cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
     };
+    // per-column copy of the row scales (the adjoint epilogue's factor)
+    std::vector<float> cscale((size_t)c.k_pad, 0.0f);
+    for (int k = 0; k < c.K; ++k) cscale[(size_t)k] = rscale[(size_t)(k / c.n_met)];
     // 3xTF32 halves of the FP32 tables
     std::vector<float> s_hi(s32.size()), s_lo(s32.size()), st_hi(st32.size()), st_lo(st32.size());
     for (size_t i = 0; i < s32.size(); ++i) tf32_split_host(s32[i], s_hi[i], s_lo[i]);
@@ -489,6 +492,7 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         (e = upload(ctx->ssp_bf, sbf.data(), sbf.size() * 2)) != cudaSuccess ||
         (e = upload(ctx->ssp_t_bf, stbf.data(), stbf.size() * 2)) != cudaSuccess ||
         (e = upload(ctx->row_scale, rscale.data(), rscale.size() * 4)) != cudaSuccess ||
+        (e = upload(ctx->col_scale, cscale.data(), cscale.size() * 4)) != cudaSuccess ||
         (e = upload(ctx->age_edges, edges.data(), edges.size() * 8)) != cudaSuccess ||
         (e = upload(ctx->bp0, t->band_p0, sizeof(double) * B)) != cudaSuccess ||
         (e = upload(ctx->bp1, t->band_p1, sizeof(double) * B)) != cudaSuccess ||

@@ -76,22 +76,40 @@ k_weights(const __grid_constant__ Consts c, const Grid grid, const Galaxies g,
         const int64_t wr = pos_of ? (int64_t)pos_of[row] : row;
         const bool nonsep = c.mdf_age != 0 && p.finite;
         if (nonsep) mdf_rows_fill(c, c.lgz_edge, p.th[7], p.th[8], s.u.kbuf);
-        for (int k = lane; k < c.k_pad; k += 32) {
-            float v = 0.0f;
-            int i = 0;
-            if (k < c.K) {
-                i = k / c.n_met;
-                v = s.w[i] * (nonsep ? s.u.kbuf[k] : s.q[k % c.n_met]);
+        // W_k = w_i q_j, k = i Zn + j: a lane writes the pair (k, k + 1) for
+        // k = 2 lane + 64 t (k_pad is even), with (i, j) of k kept incrementally
+        const int Zn = c.n_met;
+        int k = 2 * lane;
+        int i = k / Zn, j = k - i * Zn;
+        const int di = 64 / Zn, dj = 64 - di * Zn;
+        for (; k < c.k_pad; k += 64) {
+            int i1 = i, j1 = j + 1;
+            if (j1 == Zn) {
+                j1 = 0;
+                ++i1;
             }
+            float v0 = 0.0f, v1 = 0.0f;
+            if (k < c.K) v0 = s.w[i] * (nonsep ? s.u.kbuf[k] : s.q[j]);
+            if (k + 1 < c.K) v1 = s.w[i1] * (nonsep ? s.u.kbuf[k + 1] : s.q[j1]);
+            const int64_t o = wr * c.k_pad + k;
             if (bf16) {
-                Wbf[wr * c.k_pad + k] = f_to_bf16(k < c.K ? v * grid.row_scale[i] : 0.0f);
+                const float b0 = k < c.K ? v0 * grid.row_scale[i] : 0.0f;
+                const float b1 = k + 1 < c.K ? v1 * grid.row_scale[i1] : 0.0f;
+                *reinterpret_cast<uint32_t*>(Wbf + o) = (uint32_t)f_to_bf16(b0) | ((uint32_t)f_to_bf16(b1) << 16);
             } else if (W32lo) {                        // 3xTF32 operand halves
-                float hi, lo;
-                tf32_split(v, hi, lo);
-                W32[wr * c.k_pad + k] = hi;
-                W32lo[wr * c.k_pad + k] = lo;
+                float h0, l0, h1, l1;
+                tf32_split(v0, h0, l0);
+                tf32_split(v1, h1, l1);
+                *reinterpret_cast<float2*>(W32 + o) = make_float2(h0, h1);
+                *reinterpret_cast<float2*>(W32lo + o) = make_float2(l0, l1);
             } else {
-                W32[wr * c.k_pad + k] = v;
+                *reinterpret_cast<float2*>(W32 + o) = make_float2(v0, v1);
+            }
+            i += di;
+            j += dj;
+            if (j >= Zn) {
+                j -= Zn;
+                ++i;
             }
         }
         __syncwarp();

@@ -93,9 +93,13 @@ k_adj_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                     for (int j = 0; j < 32; j += 4) {
                         const int k = k0 + j;
                         float v[4];
+                        float cs[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+                        if (!TF) {
+                            const float4 c4 = __ldg(reinterpret_cast<const float4*>(grid.col_scale + k));
+                            cs[0] = c4.x; cs[1] = c4.y; cs[2] = c4.z; cs[3] = c4.w;
+                        }
 #pragma unroll
-                        for (int t = 0; t < 4; ++t)
-                            v[t] = (TF || k + t >= c.K) ? S[j + t] : S[j + t] * __ldg(grid.row_scale + (k + t) / c.n_met);
+                        for (int t = 0; t < 4; ++t) v[t] = TF ? S[j + t] : S[j + t] * cs[t];
                         if (k + 3 < c.K) {
                             float4* o = reinterpret_cast<float4*>(orow + k);
                             if (kc == 0) {

@@ -307,6 +307,15 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
             if (KZ) accz[k][0] = accz[k][1] = 0.0f;
         }
+        // warp-wide hull of each band's support (lanes without the band excluded):
+        // a group is visited for a band if the hull reaches it
+        int hlo[NB], hhi[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
+            hlo[k] = (int)__reduce_min_sync(0xffffffffu, (unsigned)(lo < hi ? lo : 0xffff));
+            hhi[k] = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lo < hi ? hi : 0));
+        }
         bool has_tab = false;                      // a tabulated band in this warp's group
 #pragma unroll
         for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < B && c.band_kind[b0 + k] == 2);
@@ -379,8 +388,7 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                         uint32_t act = 0;                          // warp-uniform
 #pragma unroll
                         for (int k = 0; k < NB; ++k) {
-                            const int lo = (int)(sxy[k] & 0xffffu), hi = (int)(sxy[k] >> 16);
-                            if (__any_sync(0xffffffffu, lo < g0 + CG && hi > g0)) act |= 1u << k;
+                            if (hlo[k] < g0 + CG && hhi[k] > g0) act |= 1u << k;
                         }
                         if (act == 0u) continue;
                         float s0[CG], sE[CG], sEb[CG], sEd[CG], lm[CG];

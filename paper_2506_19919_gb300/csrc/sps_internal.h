@@ -68,6 +68,7 @@ struct Grid {
     const uint16_t* ssp_bf;  // [k_pad][lam_pad] SSP table, BF16 bits, row-scaled by 2^-e_i
     const uint16_t* ssp_t_bf;// [lam_pad][k_pad] transposed BF16 row-scaled
     const float* row_scale;  // [A] 2^e_i
+    const float* col_scale;  // [k_pad] 2^e_i of column k = i Zn + j, 0 past K
     const float* band_T;     // tabulated transmission samples, all TABLE bands (FP32)
     const double* band_T64;  // the same in FP64 (per-galaxy set-up kernels)
 };
