@@ -400,7 +400,7 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
              const float* __restrict__ theta, const int32_t* __restrict__ gal_idx, int64_t n,
              const float* __restrict__ gbar, float* __restrict__ V, uint16_t* __restrict__ Vbf,
              float* __restrict__ Vlo) {
-    extern __shared__ float ssum[];                // [lam_pad]
+    extern __shared__ __align__(16) float ssum[];  // [lam_pad]
     __shared__ float gb[kMaxBands];
     __shared__ int2 sp[kMaxBands];
     __shared__ float2 gg[kMaxBands];
@@ -436,6 +436,35 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
     }
     const float* t = theta + row * SPS_NPARAM;
     const float AV = t[9], dl = t[10], ff = t[11];
+    if (Vbf) {
+        // BF16 v in column pairs: F = F_floor + (1 - F_floor) 2^{cA (k0 e^{delta lnr} + E_b D)}
+        // in packed FP32x2 (the terms of dust_eval), one 32-bit store per pair
+        const float eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
+        const float cA = -0.4f * kLog2_10f * AV * (1.0f / 4.05f);
+        const float2 dl2 = make_float2(dl, dl), eb2 = make_float2(eb, eb), cA2 = make_float2(cA, cA);
+        const float2 ff2 = make_float2(ff, ff), omf2 = make_float2(1.0f - ff, 1.0f - ff);
+        uint32_t* vrow = reinterpret_cast<uint32_t*>(Vbf + row * c.lam_pad);
+        const float2* s2 = reinterpret_cast<const float2*>(ssum);
+        for (int p = threadIdx.x; 2 * p < c.lam_pad; p += blockDim.x) {
+            const float2 sum = s2[p];
+            uint32_t out = 0u;
+            if (sum.x != 0.0f || sum.y != 0.0f) {
+                const int nn = 2 * p;
+                const float4 La = grid.lamc[nn];
+                const float4 Lb = (nn + 1 < c.n_lam) ? grid.lamc[nn + 1] : La;
+                const float2 pa = __fmul2_rn(dl2, make_float2(La.z, Lb.z));
+                const float2 pw = make_float2(__expf(pa.x), __expf(pa.y));
+                const float2 base = __ffma2_rn(make_float2(La.y, Lb.y), pw, __fmul2_rn(eb2, make_float2(La.w, Lb.w)));
+                const float2 ea = __fmul2_rn(cA2, base);
+                const float2 E = make_float2(exp2f(ea.x), exp2f(ea.y));
+                const float2 F = __ffma2_rn(omf2, E, ff2);
+                const float2 v = __fmul2_rn(F, sum);
+                out = (uint32_t)f_to_bf16(v.x) | ((uint32_t)f_to_bf16(v.y) << 16);
+            }
+            vrow[p] = out;
+        }
+        return;
+    }
     for (int nn = threadIdx.x; nn < c.lam_pad; nn += blockDim.x) {
         const float sum = ssum[nn];
         float v = 0.0f;
