@@ -500,6 +500,7 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
         (e = upload(ctx->tabT64, tab64.data(), sizeof(double) * tab64.size())) != cudaSuccess ||
         (e = ctx->lam32.reserve(sizeof(float) * L)) != cudaSuccess ||
         (e = ctx->lamc.reserve(sizeof(float4) * L)) != cudaSuccess ||
+        (e = ctx->lamq.reserve(sizeof(float2) * L)) != cudaSuccess ||
         (e = ctx->nonfinite.reserve(64)) != cudaSuccess || (e = ctx->queue.reserve(64)) != cudaSuccess ||
         (e = ctx->err.reserve(64)) != cudaSuccess) {
         delete ctx;
@@ -507,7 +508,7 @@ sps_status sps_create(sps_ctx** out, const sps_tables* t, const sps_config* cfg_
                                                 : cuda_fail(e, "table upload");
     }
     if ((e = launch_lambda_consts(ctx->lam64.as<double>(), L, ctx->lamc.as<float4>(),
-                                  ctx->lam32.as<float>(), 0)) != cudaSuccess ||
+                                  ctx->lam32.as<float>(), ctx->lamq.as<float2>(), 0)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         delete ctx;
         return cuda_fail(e, "lambda constants");

@@ -69,7 +69,7 @@ struct sps_ctx {
     double gl_x[sps::kMaxGL], gl_w[sps::kMaxGL];
     std::vector<double> band_p0, band_p1;
     // tables
-    DevBuf lam64, lam32, lamc, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, col_scale, age_edges, bp0, bp1;
+    DevBuf lam64, lam32, lamc, lamq, ssp, ssp_t, ssp_bf, ssp_t_bf, row_scale, col_scale, age_edges, bp0, bp1;
     DevBuf ssp_hi, ssp_lo, ssp_t_hi, ssp_t_lo;   // 3xTF32 halves of the FP32 tables
     DevBuf tabT, tabT64;                         // tabulated transmission samples
     // galaxies
@@ -99,6 +99,7 @@ struct sps_ctx {
         Grid g;
         g.lam = lam32.as<float>();
         g.lamc = lamc.as<float4>();
+        g.lamq = lamq.as<float2>();
         g.lam64 = lam64.as<double>();
         g.ssp = ssp.as<float>();
         g.ssp_t = ssp_t.as<float>();
@@ -131,7 +132,7 @@ struct sps_ctx {
     ~sps_ctx() {
         sps::DeviceGuard dg(device);
         if (graph) cudaGraphExecDestroy(graph);
-        DevBuf* all[] = {&lam64, &lam32, &lamc, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale, &col_scale,
+        DevBuf* all[] = {&lam64, &lam32, &lamc, &lamq, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale, &col_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &gdtdz, &gdzp, &gddust, &gdcssp, &cJz, &rowz, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
                          &rowinfo, &tcerr, &plainT, &plainC, &hmcm, &pst, &pth, &pll, &pgr,

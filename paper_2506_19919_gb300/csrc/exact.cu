@@ -423,12 +423,13 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
         const int lo = sp[b].x, hi = min(sp[b].y, c.n_lam);
         const float2 gp = gg[b];
         for (int nn = lo + threadIdx.x; nn < hi; nn += blockDim.x) {
-            float wb = __ldg(&grid.lamc[nn].x);
+            const float2 lq = __ldg(grid.lamq + nn);      // (lambda, q / lambda)
+            float wb = lq.y;
             if (kind == 1) {
-                const float u = (__ldg(grid.lam + nn) - gp.x) * gp.y;
+                const float u = (lq.x - gp.x) * gp.y;
                 wb *= __expf(-0.5f * u * u);
             } else if (kind == 2) {
-                wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (__ldg(grid.lam + nn) - gp.x) * -gp.y);
+                wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (lq.x - gp.x) * -gp.y);
             }
             ssum[nn] = fmaf(gbb, wb, ssum[nn]);
         }

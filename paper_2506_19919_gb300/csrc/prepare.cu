@@ -68,7 +68,7 @@ __device__ T block_sum(T v, T* sh) {
 
 // Per-wavelength constants: (q_n / lambda_n, k0, ln(lambda/lambda_V), Drude).
 __global__ void k_lambda_consts(const double* __restrict__ lam, int L, float4* __restrict__ out,
-                                float* __restrict__ lam32) {
+                                float* __restrict__ lam32, float2* __restrict__ lamq) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= L) return;
     double l = lam[n];
@@ -79,6 +79,7 @@ __global__ void k_lambda_consts(const double* __restrict__ lam, int L, float4* _
     out[n] = make_float4((float)(q / l), (float)calzetti_k0(lum), (float)log(l / 5500.0),
                          (float)drude_shape(lum));
     lam32[n] = (float)l;
+    lamq[n] = make_float2((float)l, (float)(q / l));
 }
 
 // One block per galaxy.
@@ -294,9 +295,9 @@ k_cssp(const __grid_constant__ Consts c, const Grid grid, const Galaxies gal,
 
 }  // namespace
 
-cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32,
+cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32, float2* lamq,
                                  cudaStream_t s) {
-    k_lambda_consts<<<(L + 255) / 256, 256, 0, s>>>(lam, L, out, lam32);
+    k_lambda_consts<<<(L + 255) / 256, 256, 0, s>>>(lam, L, out, lam32, lamq);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct Galaxies {
 struct Grid {
     const float* lam;        // [L] Angstrom
     const float4* lamc;      // [L] (q_n / lambda_n, k0, ln(lambda/lambda_V), Drude shape)
+    const float2* lamq;      // [L] (lambda, q_n / lambda_n) in FP32
     const double* lam64;     // [L] Angstrom, FP64
     const float* ssp_t;      // [lam_pad][k_pad] SSP table transposed, FP32 (zero padded)
     const float* ssp;        // [k_pad][lam_pad] SSP table, FP32 (zero padded)
@@ -148,7 +149,7 @@ cudaError_t launch_exact_fwd(const Consts& c, const Grid& grid, const Galaxies& 
                              const float* theta, const int32_t* gal_idx, int64_t n, int bf16,
                              const float* W32, const uint16_t* Wbf, float* cJ, cudaStream_t s,
                              float* cJz = nullptr);   // with cJz: [r][b][2] sum_n wb' S (1, E)
-cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32,
+cudaError_t launch_lambda_consts(const double* lam, int L, float4* out, float* lam32, float2* lamq,
                                  cudaStream_t s);
 cudaError_t launch_exact_like(const Consts& c, const Galaxies& g, const float* theta,
                               const int32_t* gal_idx, int64_t n, const float* cJ, float* rowinfo,
