@@ -293,7 +293,7 @@ def run_ours(args):
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived)",
                      "algorithmic": "4 * n_obs_bands * K FLOP per gradient evaluation"},
         "clocks": clocks,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * max(1, int(ctx.info().get("hmc_launches", 1))),
         "wall_s": wall,
     }
     if rank == 0 and not args.skip_extra:

@@ -387,6 +387,9 @@ typedef struct {
     int32_t device;
     int32_t sfh_gl_order;
     int32_t max_panels;
+    int32_t hmc_launches;   /* sampler-kernel launches of the last approximate-path
+                               sps_hmc_run: 1, or 2 when its last wave of two-chain
+                               teams ran as one-chain teams (0 before any run) */
 } sps_info;
 sps_status sps_get_info(const sps_ctx* ctx, sps_info* out);
 

@@ -56,7 +56,7 @@ class sps_info(C.Structure):
     _fields_ = [("n_age", C.c_int32), ("n_met", C.c_int32), ("n_lam", C.c_int32),
                 ("n_band", C.c_int32), ("k_pad", C.c_int32), ("n_gal", C.c_int64),
                 ("has_approx", C.c_int32), ("device", C.c_int32), ("sfh_gl_order", C.c_int32),
-                ("max_panels", C.c_int32)]
+                ("max_panels", C.c_int32), ("hmc_launches", C.c_int32)]
 
 
 _P = C.c_void_p

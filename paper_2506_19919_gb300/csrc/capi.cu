@@ -953,6 +953,7 @@ sps_status sps_get_info(const sps_ctx* ctx, sps_info* out) {
     out->device = ctx->device;
     out->sfh_gl_order = ctx->c.gl_order;
     out->max_panels = kMaxPanels;
+    out->hmc_launches = ctx->hmc_launches;
     return SPS_OK;
 }
 
@@ -1230,12 +1231,39 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         CK(blocks_for(cpw, warps, blocks));
     }
 
+    // When the last wave of two-chain teams would fill under 3/4 of the
+    // resident warps, its chains run as one-chain teams in a second launch
+    // (HMC, separable model, an even chain count): the same chains and draws,
+    // spread over more warps. SPS_HMC_TAIL=0 keeps one launch.
+    int64_t main_end = -1;      // two-chain items of the first launch (< 0: all)
+    int blocks1 = 0;
+    {
+        const int64_t slots = (int64_t)blocks * warps;
+        const int64_t items = G * (int64_t)((C + cpw - 1) / cpw);
+        const char* tv = std::getenv("SPS_HMC_TAIL");
+        if (!nuts && !rows && cpw == 2 && C % 2 == 0 && !(tv && tv[0] == '0') && items > slots &&
+            items % slots != 0 && 4 * (items % slots) < 3 * slots) {
+            main_end = items / slots * slots;
+            CK(blocks_for(1, warps, blocks1));
+        }
+    }
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        return launch_hmc_team(cpw, rows, c, ctx->gal(), hp, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
-                               ctx->queue.as<int>(), cmet, blocks, warps, s);
+        HmcParams h1 = hp;
+        h1.item_end = main_end;
+        e = launch_hmc_team(cpw, rows, c, ctx->gal(), h1, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+                            ctx->queue.as<int>(), cmet, blocks, warps, s);
+        if (e != cudaSuccess || main_end < 0) return e;
+        e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        HmcParams h2 = hp;
+        h2.item0 = 2 * main_end;      // one-chain items: two per two-chain item
+        h2.item_end = G * (int64_t)C;
+        return launch_hmc_team(1, rows, c, ctx->gal(), h2, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+                               ctx->queue.as<int>(), cmet, blocks1, warps, s);
     };
+    ctx->hmc_launches = main_end < 0 ? 1 : 2;
     if (cfg->use_graph) {
         char kb[512];
         std::snprintf(kb, sizeof(kb), "%p%p%p%p%p%p%p%p%p%p%p%lld%d%d%d%d%d%d%d%llu%g%g", (const void*)x0,
@@ -1246,7 +1274,8 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
         char kc[64];
         std::snprintf(kc, sizeof(kc), "%p%p%d", (void*)cmet, (void*)hp.nuts, hp.max_depth);
         std::string gk = std::string(kb) + ":" + std::to_string(blocks) + ":" + std::to_string(cpw) + kc + ":" +
-                         std::to_string(hp.sync_every);
+                         std::to_string(hp.sync_every) + ":" + std::to_string(main_end) + ":" +
+                         std::to_string(blocks1);
         if (!ctx->graph || gk != ctx->graph_key) {
             if (ctx->graph) {
                 cudaGraphExecDestroy(ctx->graph);

@@ -88,6 +88,7 @@ struct sps_ctx {
     DevBuf zperm;                     // redshift order of the rows of a tensor-core chunk
     DevBuf Wlo, Vlo;                  // low TF32 halves of W and v (3xTF32 exact path)
     DevBuf keep;                      // exact path: weight arrays per row, kept for the gradient
+    int hmc_launches = 0;             // team-kernel launches of the last approximate-path HMC run
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache

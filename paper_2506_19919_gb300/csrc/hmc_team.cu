@@ -1144,10 +1144,12 @@ k_hmc_team(const __grid_constant__ Consts c, const Galaxies g, const HmcParams h
             int q = 0;
             if (lane == 0) q = atomicAdd(queue, 1);
             q = __shfl_sync(kFull, q, 0);
-            if ((int64_t)q >= g.n * groups) {
+            const int64_t qe = (int64_t)q + hp.item0;
+            if (qe >= (hp.item_end >= 0 ? hp.item_end : g.n * groups)) {
                 drained = true;
             } else {
-                gi = team_init<CPW>(c, g, hp, t, q, theta0, mag_obs, sigma, mask, gal_order, metric, &nch, &nb);
+                gi = team_init<CPW>(c, g, hp, t, (int)qe, theta0, mag_obs, sigma, mask, gal_order, metric, &nch,
+                                    &nb);
                 have = true;
                 pass = 0;
             }

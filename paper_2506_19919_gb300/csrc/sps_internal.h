@@ -221,6 +221,9 @@ struct HmcParams {
     int sync_every;         // passes between the block barriers of the team kernel (>= 1)
     int max_depth;          // NUTS tree depth limit (1..kNutsMaxDepth)
     NutsChain* nuts;        // per-chain NUTS state; null runs HMC
+    // team kernel: the launch takes work items [item0, item_end) of its own
+    // grouping (item_end < 0: all of them)
+    int64_t item0 = 0, item_end = -1;
 };
 // log L + gradient of independent rows through the team evaluation (n_met <= 12);
 // see hmc_team.cu
