@@ -50,14 +50,15 @@ TARGET_ACCEPT = 0.7
 METRIC = "posteriors/min at fixed ESS"
 UNIT = "posteriors/min"
 
-# DRAM traffic of one k_hmc_team launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of five launches of a reduced case with the same
-# 4,096-galaxy working set at 50 + 50 iterations, scaled by gradient
-# evaluations to 500 + 500; profiles/k_hmc_team_hmc4096gal_x4_launches.md),
+# DRAM traffic of one bench step's k_hmc_team launches on this workload (the
+# whole waves of two-chain teams and the last wave's one-chain teams;
+# dram__bytes_read.sum + dram__bytes_write.sum, mean of five steps of a reduced
+# case with the same 4,096-galaxy working set at 50 + 50 iterations, scaled by
+# gradient evaluations to 500 + 500; profiles/k_hmc_team_hmc4096gal_x4_launches.md),
 # valid only while the kernel's sources hash to the recorded value; otherwise
 # reported as null.
 KERNEL_SOURCES = ("hmc_team.cu", "sps_device.cuh", "sps_eval.cuh", "sps_internal.h", "philox.cuh")
-TRAFFIC = {"sha": "9852f7a3036a38a4", "bytes": 186.50e9 + 10.147e9}
+TRAFFIC = {"sha": "3c9f052df06e2568", "bytes": 217.10e9 + 11.23e9}
 
 
 def _kernel_sha():
