@@ -305,6 +305,7 @@ def run_ours(args):
         out["survey"] = _survey(dev)
     if rank == 0 and not args.skip_plain:
         out["plain_hmc"] = _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, args.plain_full)
+        out["plain_hmc"]["own_ess_full_runs"] = _own_ess_runs(dev)
     if rank == 0 and not args.skip_nuts:
         out["nuts"] = _nuts(ctx, wl, x0, mobs, value, float(nev.sum()) / (ms_local / 1e3))
     if rank == 0 and not args.skip_exact_hmc:
@@ -366,6 +367,45 @@ def _plain_hmc(ctx, wl, x0, mobs, post, value, ms_step, full):
                     "own_posteriors_per_min": own / (s_run / 60.0),
                     "own_frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean())})
     return res
+
+
+def _own_ess_runs(dev, n_gal=512):
+    """Both samplers run in full (500 + 500 iterations) on 512 galaxies of
+    the bench recipe, 4 chains each, each scored by the ESS of its own draws:
+    the fused-vs-baseline comparison measured end to end, without scaling
+    iterations or borrowing the other run's ESS."""
+    import torch
+
+    import paper_2506_19919_gb300 as pkg
+    wl = _hmc_workload(0, n_gal)
+    G, C = wl.n_gal, wl.chains
+    ctx = pkg.Context(wl.tables, device=dev.index)
+    ctx.set_galaxies(wl.z, build_approx=True)
+    mt = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev), mode="approx")
+    mobs = (mt + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)).contiguous()
+    x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
+    kw = dict(chains_per_gal=C, L_min=wl.extra["L_min"], L_max=wl.extra["L_max"], seed=2506199190,
+              target_accept=TARGET_ACCEPT)
+    n_warm, n_samp = wl.extra["n_warm"], wl.extra["n_samp"]
+    out = {"galaxies": G, "chains_per_gal": C, "n_warm": n_warm, "n_samp": n_samp}
+    for path in ("fused", "plain"):
+        ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=2, n_samp=2, samples=False, path=path, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = ctx.hmc_run(x0, mobs, wl.sigma, wl.mask, n_warm=n_warm, n_samp=n_samp, path=path, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        ess, rhat = pkg.diagnostics(o["samples"], G, C)
+        ess_g = ess.min(1)
+        post = float(np.minimum(1.0, ess_g / ESS_TARGET).sum())
+        out[path] = {"s": s, "median_ess": float(np.median(ess_g)), "posteriors_per_min": post / (s / 60.0),
+                     "frac_rhat_lt_1p2": float((rhat.max(1) < 1.2).mean())}
+    out["fused_vs_plain_posteriors_per_min"] = (out["fused"]["posteriors_per_min"] /
+                                                max(out["plain"]["posteriors_per_min"], 1e-30))
+    ctx.close()
+    return out
 
 
 def _hmc_exact(ctx, wl, x0, mobs, hmc_s_per_step):
