@@ -1245,23 +1245,37 @@ extern "C" sps_status sps_hmc_run(sps_ctx* ctx, const sps_hmc_config* cfg, const
             items % slots != 0 && 4 * (items % slots) < 3 * slots) {
             main_end = items / slots * slots;
             CK(blocks_for(1, warps, blocks1));
+            if (!ctx->side) {
+                CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming));
+            }
         }
     }
+    // The tail launch goes on a side stream forked after the queue resets, so
+    // its blocks take SMs as the main launch's blocks retire; the join makes
+    // the call's stream wait for both.  The two launches pull from separate
+    // queue counters and touch disjoint chains.
     auto enqueue = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
+        cudaError_t e = cudaMemsetAsync(ctx->queue.p, 0, 2 * sizeof(int), s);
         if (e != cudaSuccess) return e;
         HmcParams h1 = hp;
         h1.item_end = main_end;
+        if (main_end >= 0) {
+            if ((e = cudaEventRecord(ctx->fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess) return e;
+        }
         e = launch_hmc_team(cpw, rows, c, ctx->gal(), h1, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
                             ctx->queue.as<int>(), cmet, blocks, warps, s);
         if (e != cudaSuccess || main_end < 0) return e;
-        e = cudaMemsetAsync(ctx->queue.p, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
         HmcParams h2 = hp;
         h2.item0 = 2 * main_end;      // one-chain items: two per two-chain item
         h2.item_end = G * (int64_t)C;
-        return launch_hmc_team(1, rows, c, ctx->gal(), h2, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
-                               ctx->queue.as<int>(), cmet, blocks1, warps, s);
+        e = launch_hmc_team(1, rows, c, ctx->gal(), h2, x0, mo, sg, mk, ord, so, acc, epo, dv, nev, sto,
+                            ctx->queue.as<int>() + 1, cmet, blocks1, warps, ctx->side);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ctx->join, ctx->side)) != cudaSuccess) return e;
+        return cudaStreamWaitEvent(s, ctx->join, 0);
     };
     ctx->hmc_launches = main_end < 0 ? 1 : 2;
     if (cfg->use_graph) {

@@ -89,6 +89,8 @@ struct sps_ctx {
     DevBuf Wlo, Vlo;                  // low TF32 halves of W and v (3xTF32 exact path)
     DevBuf keep;                      // exact path: weight arrays per row, kept for the gradient
     int hmc_launches = 0;             // team-kernel launches of the last approximate-path HMC run
+    cudaStream_t side = nullptr;      // HMC: the one-chain tail launch runs beside the main one
+    cudaEvent_t fork = nullptr, join = nullptr;
     bool use_tc = true;   // tcgen05 contraction for BF16 operands
     DevBuf stage[12];
     // HMC graph cache
@@ -133,6 +135,9 @@ struct sps_ctx {
     ~sps_ctx() {
         sps::DeviceGuard dg(device);
         if (graph) cudaGraphExecDestroy(graph);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
         DevBuf* all[] = {&lam64, &lam32, &lamc, &lamq, &ssp, &ssp_t, &ssp_bf, &ssp_t_bf, &row_scale, &col_scale,
                          &age_edges, &bp0, &bp1, &gz, &glnT, &glT10, &gbins, &gzp, &gsup, &ggauss,
                          &gcssp, &gdust, &gdtdz, &gdzp, &gddust, &gdcssp, &cJz, &rowz, &nonfinite, &queue, &err, &W, &V, &Wbar, &cJ, &gbar,
