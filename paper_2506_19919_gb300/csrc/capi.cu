@@ -1044,8 +1044,9 @@ static sps_status hmc_exact(sps_ctx* ctx, const sps_hmc_config* cfg, const float
     int32_t* gi = ctx->pgi.as<int32_t>();
     float* llf = ctx->rowz.as<float>();
     const sps_prec prec = (sps_prec)cfg->prec;
+    cudaStream_t gs = s;                  // the stream the gradient is enqueued on
     auto gradient = [&]() -> sps_status {
-        return run_exact(ctx, th, gi, NC, mo, sg, mk, prec, nullptr, llf, gr, s, false, ll);
+        return run_exact(ctx, th, gi, NC, mo, sg, mk, prec, nullptr, llf, gr, gs, false, ll);
     };
     CK(cudaMemsetAsync(ctx->nonfinite.p, 0, 2 * sizeof(int), s));
     CK(plain_hmc_init(c, NC, C, x0, hp.eps0, pst, th, gi, s));
@@ -1057,9 +1058,47 @@ static sps_status hmc_exact(sps_ctx* ctx, const sps_hmc_config* cfg, const float
     CK(async_hmc_rounds(hp, NC, rbuf, s));
     CK(cudaMemcpyAsync(&rounds, rbuf, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int r = 0; r < rounds; ++r) {
-        if (sps_status e = gradient(); e != SPS_OK) return e;
-        CK(async_hmc_step(c, hp, NC, pst, ll, gr, th, so, s));
+    // A round (the exact log L + gradient of every chain, then one leapfrog
+    // step each) is the same sequence of launches every time: captured once
+    // as a CUDA graph (on a private stream; the buffers it uses were reserved
+    // by the first gradient above) and replayed, so the host encodes tensor
+    // maps and issues launches once per call instead of once per round.
+    // SPS_EXACT_GRAPH=0 enqueues every round directly.
+    const char* gv = std::getenv("SPS_EXACT_GRAPH");
+    if (rounds > 1 && !(gv && gv[0] == '0')) {
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr0 = nullptr;
+        cudaGraphExec_t gx = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        sps_status rs = SPS_OK;
+        if (e == cudaSuccess) {
+            gs = cs;
+            rs = gradient();
+            if (rs == SPS_OK) e = async_hmc_step(c, hp, NC, pst, ll, gr, th, so, cs);
+            gs = s;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &gr0);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess && rs == SPS_OK) e = cudaGraphInstantiate(&gx, gr0, 0);
+        if (gr0) cudaGraphDestroy(gr0);
+        cudaStreamDestroy(cs);
+        if (rs != SPS_OK) {
+            if (gx) cudaGraphExecDestroy(gx);
+            return rs;
+        }
+        if (e != cudaSuccess) {
+            if (gx) cudaGraphExecDestroy(gx);
+            return cuda_fail(e, "exact round capture");
+        }
+        for (int r = 0; r < rounds && e == cudaSuccess; ++r) e = cudaGraphLaunch(gx, s);
+        cudaGraphExecDestroy(gx);
+        if (e != cudaSuccess) return cuda_fail(e, "exact round launch");
+    } else {
+        for (int r = 0; r < rounds; ++r) {
+            if (sps_status e = gradient(); e != SPS_OK) return e;
+            CK(async_hmc_step(c, hp, NC, pst, ll, gr, th, so, s));
+        }
     }
     CK(plain_hmc_stats(hp, NC, pst, acc, epo, dv, nev, sto, s));
     int fl[2] = {0, 0};
