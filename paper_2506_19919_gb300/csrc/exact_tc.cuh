@@ -270,13 +270,18 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
         const int e = warp - 2;
         const int q = warp & 3;                    // TMEM lane quarter this warp may access (warp id mod 4)
         const int half = (e >> 2) % n_halves;      // column half (one group only)
-        const int b0 = ((e >> 2) / n_halves) * NB; // first band of this warp's group
+        const int B = c.n_band;
+        // the bands split evenly over the groups (12 bands: 6 + 6, not 8 + 4);
+        // this warp's bands are [b0, b_end)
+        const int n_groups = (B + NB - 1) / NB;
+        const int bpg = (B + n_groups - 1) / n_groups;
+        const int b0 = ((e >> 2) / n_halves) * bpg;
+        const int b_end = min(b0 + bpg, B);
         const int ncol = BN / n_halves;
         const int rl = 32 * q + lane;
         const int64_t pos = (int64_t)m0 + rl;
         const bool live = pos < n;
         const int64_t row = live ? (perm ? (int64_t)perm[pos] : pos) : 0;
-        const int B = c.n_band;
         int64_t gi = live ? (gal_idx ? (int64_t)gal_idx[row] : row) : 0;
         const bool valid = live && gi >= 0 && gi < g.n;
         if (!valid) gi = 0;
@@ -297,13 +302,13 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             const int b = b0 + k;
             int2 sp = make_int2(0, 0);
             float2 ga = make_float2(0.f, 0.f);
-            if (b < B && valid) {
+            if (b < b_end && valid) {
                 sp = g.support[gi * B + b];
                 ga = g.gauss[gi * B + b];
             }
             sxy[k] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
             gc[k] = ga.x;
-            gs[k] = (b < B && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 top-hat, > 0 Gaussian, < 0 table
+            gs[k] = (b < b_end && c.band_kind[b] != 0) ? ga.y : 0.0f;   // 0 top-hat, > 0 Gaussian, < 0 table
             acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
             if (KZ) accz[k][0] = accz[k][1] = 0.0f;
         }
@@ -318,7 +323,7 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
         }
         bool has_tab = false;                      // a tabulated band in this warp's group
 #pragma unroll
-        for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < B && c.band_kind[b0 + k] == 2);
+        for (int k = 0; k < NB; ++k) has_tab = has_tab || (b0 + k < b_end && c.band_kind[b0 + k] == 2);
         // this warp's staging of the chunk constants (lane j: column nb0 + j,
         // clamped to the grid), and the registers holding the next chunk's
         float4* cst4 = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(ctl) + 256) + 32 * e;
@@ -490,7 +495,7 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
         if (valid && !ctl->abort) {
 #pragma unroll
             for (int k = 0; k < NB; ++k)
-                if (b0 + k < B) {
+                if (b0 + k < b_end) {
                     float* o = cJ + (row * B + b0 + k) * 4;
                     atomicAdd(o + 0, acc[k][0]);
                     atomicAdd(o + 1, acc[k][1]);
