@@ -14,7 +14,10 @@ import sps_workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_split_last_wave_matches_one_launch():
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_split_last_wave_matches_one_launch(use_graph):
+    """With and without graph capture (the bench's path: the side-stream fork
+    and join captured into the graph)."""
     import paper_2506_19919_gb300 as pkg
     wl = W.config(3, n_gal=1300)
     dev = torch.device("cuda", 0)
@@ -23,7 +26,7 @@ def test_split_last_wave_matches_one_launch():
     mt = ctx.photometry(torch.as_tensor(wl.theta_true, dtype=torch.float32, device=dev), mode="approx")
     mo = (mt + torch.as_tensor(wl.noise, dtype=torch.float32, device=dev)).contiguous()
     x0 = torch.as_tensor(wl.extra["theta0_unb"], dtype=torch.float32, device=dev)
-    kw = dict(chains_per_gal=4, n_warm=4, n_samp=4, L_min=4, L_max=12, autotune=False, use_graph=False)
+    kw = dict(chains_per_gal=4, n_warm=4, n_samp=4, L_min=4, L_max=12, autotune=False, use_graph=use_graph)
     runs = {}
     for tail in ("1", "0"):
         os.environ["SPS_HMC_TAIL"] = tail
