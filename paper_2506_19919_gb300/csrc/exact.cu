@@ -422,12 +422,13 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
         const int kind = c.band_kind[b];
         const int lo = sp[b].x, hi = min(sp[b].y, c.n_lam);
         const float2 gp = gg[b];
+        const float gsv = gp.y * 0.84932180028801904f;   // e^{-u^2 / 2} = 2^{-(u sqrt(log2(e) / 2))^2}
         for (int nn = lo + threadIdx.x; nn < hi; nn += blockDim.x) {
             const float2 lq = __ldg(grid.lamq + nn);      // (lambda, q / lambda)
             float wb = lq.y;
             if (kind == 1) {
-                const float u = (lq.x - gp.x) * gp.y;
-                wb *= __expf(-0.5f * u * u);
+                const float u = (lq.x - gp.x) * gsv;
+                wb *= exp2f(-(u * u));
             } else if (kind == 2) {
                 wb *= tab_T32(grid.band_T + c.tab_off[b], c.tab_n[b], (lq.x - gp.x) * -gp.y);
             }

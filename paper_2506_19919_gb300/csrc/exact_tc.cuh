@@ -418,8 +418,9 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                                 // Gaussian / top-hat band weights of column pairs, packed
                                 // FP32x2; a column outside the support adds S x 0
                                 float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;
-                                const float2 ngc = make_float2(-gc[k], -gc[k]), gs2 = make_float2(gs[k], gs[k]);
-                                const float2 m05 = make_float2(-0.5f, -0.5f);
+                                // e^{-u^2 / 2} = 2^{-v^2}, v = u sqrt(log2(e) / 2)
+                                const float gsv = gs[k] * 0.84932180028801904f;
+                                const float2 ngc = make_float2(-gc[k], -gc[k]), gs2 = make_float2(gsv, gsv);
                                 const bool gauss = gs[k] != 0.0f;
 #pragma unroll
                                 for (int jj = 0; jj < CG; jj += 2) {
@@ -428,8 +429,8 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                                     float2 w = make_float2(i0 ? 1.0f : 0.0f, i1 ? 1.0f : 0.0f);
                                     if (gauss) {
                                         const float2 u = __fmul2_rn(__fadd2_rn(make_float2(lm[jj], lm[jj + 1]), ngc), gs2);
-                                        const float2 t = __fmul2_rn(__fmul2_rn(m05, u), u);
-                                        w = make_float2(i0 ? __expf(t.x) : 0.0f, i1 ? __expf(t.y) : 0.0f);
+                                        const float2 t = __fmul2_rn(u, u);
+                                        w = make_float2(i0 ? exp2f(-t.x) : 0.0f, i1 ? exp2f(-t.y) : 0.0f);
                                     }
                                     p0 = __ffma2_rn(make_float2(s0[jj], s0[jj + 1]), w, p0);
                                     p1 = __ffma2_rn(make_float2(sE[jj], sE[jj + 1]), w, p1);
