@@ -443,7 +443,8 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
         // in packed FP32x2 (the terms of dust_eval), one 32-bit store per pair
         const float eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
         const float cA = -0.4f * kLog2_10f * AV * (1.0f / 4.05f);
-        const float2 dl2 = make_float2(dl, dl), eb2 = make_float2(eb, eb), cA2 = make_float2(cA, cA);
+        const float dlg = dl * 1.4426950408889634f;     // delta log2(e)
+        const float2 dl2 = make_float2(dlg, dlg), eb2 = make_float2(eb, eb), cA2 = make_float2(cA, cA);
         const float2 ff2 = make_float2(ff, ff), omf2 = make_float2(1.0f - ff, 1.0f - ff);
         uint32_t* vrow = reinterpret_cast<uint32_t*>(Vbf + row * c.lam_pad);
         const float2* s2 = reinterpret_cast<const float2*>(ssum);
@@ -455,7 +456,7 @@ k_exact_vgen(const __grid_constant__ Consts c, const Grid grid, const Galaxies g
                 const float4 La = grid.lamc[nn];
                 const float4 Lb = (nn + 1 < c.n_lam) ? grid.lamc[nn + 1] : La;
                 const float2 pa = __fmul2_rn(dl2, make_float2(La.z, Lb.z));
-                const float2 pw = make_float2(__expf(pa.x), __expf(pa.y));
+                const float2 pw = make_float2(exp2f(pa.x), exp2f(pa.y));
                 const float2 base = __ffma2_rn(make_float2(La.y, Lb.y), pw, __fmul2_rn(eb2, make_float2(La.w, Lb.w)));
                 const float2 ea = __fmul2_rn(cA2, base);
                 const float2 E = make_float2(exp2f(ea.x), exp2f(ea.y));

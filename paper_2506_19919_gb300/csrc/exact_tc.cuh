@@ -292,6 +292,8 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
             dl = t[10];
             eb = fmaxf(0.85f - 1.9f * dl, 0.0f);
         }
+        const float dl2 = dl * 1.4426950408889634f;     // delta log2(e)
+        const float nd19 = eb > 0.0f ? -1.9f : 0.0f;    // d E_b / d delta
         uint32_t sxy[NB];                          // support [lo, hi): lo | hi << 16
         float gc[NB], gs[NB];
         float acc[NB][4];
@@ -401,10 +403,10 @@ k_fwd_tc(const __grid_constant__ TcMaps tm, const __grid_constant__ Consts c, co
                         for (int jj = 0; jj < CG; ++jj) {
                             const float4 L4 = cst4[h * CG + jj];
                             lm[jj] = cstl[h * CG + jj];
-                            const float pw = __expf(dl * L4.z);
-                            const float base = L4.y * pw + eb * L4.w;
+                            const float ypw = L4.y * exp2f(dl2 * L4.z);      // k0 (l / l_V)^delta
+                            const float base = fmaf(eb, L4.w, ypw);
                             const float E = exp2f(cA * base);
-                            const float dterm = L4.y * pw * L4.z - (eb > 0.0f ? 1.9f * L4.w : 0.0f);
+                            const float dterm = fmaf(ypw, L4.z, nd19 * L4.w);
                             s0[jj] = S[jj] * L4.x;
                             sE[jj] = s0[jj] * E;
                             sEb[jj] = sE[jj] * base;
